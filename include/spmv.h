@@ -1,0 +1,207 @@
+/*
+ * spmv.h -- C ABI of the row-partitioned FP64 SpMV operation DAG.
+ *
+ * The operation is the distributed sparse matrix-vector product of
+ * Pearson, Javeed and Devine, "Machine Learning for CUDA+MPI Design Rules",
+ * Sec. III-A and Fig. 3: contiguous, even row blocks of A, x and y are owned
+ * by P ranks; rank p computes y_p = A_L x_L + A_R x_R, where A_L holds the
+ * columns of its own block, A_R the rest, and x_R is assembled from the x
+ * entries other ranks pack and send.  Here the P ranks are virtual ranks
+ * sharing one GPU, and the exchange is a device-to-device copy.
+ *
+ * The four operations of Fig. 3c, with their dependencies (the DAG G_P):
+ *   PACK   -> COPY       sendbuf[k] = x[send_idx[k]]  (Pack vertex)
+ *   COPY   -> REMOTE     recvbuf <- sendbuf           (PostSends/PostRecvs/Wait*)
+ *   LOCAL  -> REMOTE     y_p = A_L,p x_L              (y_L vertex)
+ *                        y_p += A_R,p x_R             (y_R vertex)
+ * A schedule is a topological order of the operations plus a map of each
+ * operation to a stream (Sec. III-B, Eq. 1); synchronisation is inserted as
+ * Table III prescribes.
+ *
+ * Conventions for every entry point:
+ *   - Returns an spmv_status; never throws.  On failure a message is stored
+ *     per thread and returned by spmv_last_error().
+ *   - Device pointers (suffix _dev) are caller-owned, on the current device,
+ *     and must stay valid until the work issued on the given stream ends.
+ *     Host pointers (suffix _host) are read or written before return, unless
+ *     stated otherwise.
+ *   - Work is asynchronous on the given stream(s); no hidden synchronisation
+ *     except in spmv_part_create, spmv_part_destroy, spmv_part_export_plan,
+ *     spmv_part_query(SPMV_Q_ERROR) and the _host entry points.
+ *   - Indices: column indices are int32 and n < 2^31; the number of nonzeros
+ *     must also be below 2^31.
+ *   - All FP values and accumulations are IEEE binary64.
+ */
+#ifndef SPMV_H
+#define SPMV_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_EINVAL = -1,    /* bad argument (size, pointer, selector, CSR) */
+    SPMV_ENOMEM = -2,    /* a device or host allocation failed */
+    SPMV_ECUDA = -3,     /* a CUDA runtime call failed */
+    SPMV_ESCHED = -4,    /* schedule rejected: not a topological order, or a
+                            stream id out of range; nothing was launched */
+    SPMV_EBOUNDS = -5,   /* a size exceeds a fixed limit of the library */
+    SPMV_ETIMEOUT = -6   /* a bounded device wait gave up (see SPMV_Q_ERROR) */
+} spmv_status;
+
+/* Operation kinds; op id = part * 4 + kind (coarse granularity: part 0). */
+enum { SPMV_OP_PACK = 0, SPMV_OP_LOCAL = 1, SPMV_OP_COPY = 2, SPMV_OP_REMOTE = 3 };
+
+/* Granularity of the operations (Sec. III-A: one Pack vertex for all
+ * peers versus one per peer). */
+enum { SPMV_COARSE = 0, SPMV_PER_PARTITION = 1 };
+
+typedef struct spmv_part spmv_part;   /* opaque; owns all plan memory */
+
+/*
+ * Build the partition plan (Sec. III-A, Fig. 3b) of the n x n CSR matrix
+ * (row_ptr[n+1] int64, col_idx[nnz] int32, vals[nnz] double, all HOST
+ * memory, read during the call) over P row-block ranks with
+ * r_p = floor(p n / P), and upload it to the current device.
+ *   A_L,p : entries of rows r_p..r_{p+1} with column in the same range,
+ *           columns rebased to the block (x_L = x + r_p);
+ *   H_p   : the sorted distinct columns outside the range (x_R's entries);
+ *   A_R,p : the other entries, columns renumbered to positions in H_p;
+ *   send buffer: destination-major, then source rank, then ascending column,
+ *           so destination p's part is x[H_p] and the exchange is one copy.
+ * granularity selects SPMV_COARSE (4 ops, each over every rank) or
+ * SPMV_PER_PARTITION (4P ops).  Columns within a row may come in any order
+ * and may repeat; each entry is kept and summed in the order given.
+ * Errors: SPMV_EINVAL for n < 0, P < 1, a decreasing row_ptr, a column out
+ * of [0, n), or NULL pointers with n > 0; SPMV_EBOUNDS for n or nnz >=
+ * 2^31; SPMV_ENOMEM / SPMV_ECUDA.  *out is NULL on failure.
+ */
+int spmv_part_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                     const double* vals, int P, int granularity, spmv_part** out);
+
+/* Synchronises the device, releases every graph, event and buffer. NULL ok. */
+int spmv_part_destroy(spmv_part* part);
+
+/* Scalar queries; `part_idx` selects a rank where the quantity is per rank
+ * (ignored otherwise). */
+enum {
+    SPMV_Q_N = 0, SPMV_Q_P = 1, SPMV_Q_GRANULARITY = 2,
+    SPMV_Q_NNZ = 3, SPMV_Q_NNZ_LOCAL = 4, SPMV_Q_NNZ_REMOTE = 5,
+    SPMV_Q_N_SEND = 6,            /* total send-buffer entries */
+    SPMV_Q_N_HALO = 7,            /* |H_p| of rank part_idx */
+    SPMV_Q_N_REMOTE_ROWS = 8,     /* rows with at least one remote entry */
+    SPMV_Q_N_OPS = 9,             /* operations of the DAG */
+    SPMV_Q_N_EDGES = 10,          /* dependency edges of the DAG */
+    SPMV_Q_ALG_BYTES = 11,        /* algorithmic bytes of one SpMV (DESIGN) */
+    SPMV_Q_ALG_BYTES_LOCAL = 12,  /* algorithmic bytes of the LOCAL op */
+    SPMV_Q_DEVICE_BYTES = 13,     /* device memory the plan holds */
+    SPMV_Q_LAST_RECORDS = 14,     /* events recorded for DAG edges by the last issue */
+    SPMV_Q_LAST_WAITS = 15,       /* stream waits issued for DAG edges by the last issue */
+    SPMV_Q_ERROR = 16,            /* device error word (0 = none); synchronises */
+    SPMV_Q_LOCAL_VARIANT = 17,
+    SPMV_Q_N_LOCAL_TILES = 18,
+    SPMV_Q_LAST_LAUNCHES = 19     /* kernels launched by the last issue */
+};
+int spmv_part_query(const spmv_part* part, int what, int part_idx, int64_t* out);
+
+/* Plan arrays for bit-exact comparisons, copied back from the DEVICE copy
+ * the kernels use, in canonical per-rank form. */
+enum {
+    SPMV_X_BOUNDS = 0,     /* int64[P+1]   row bounds r_p */
+    SPMV_X_L_PTR = 1,      /* int64[rows_p+1] local row pointer from 0 (rank) */
+    SPMV_X_L_COL = 2,      /* int32 rebased local columns (rank) */
+    SPMV_X_L_VAL = 3,      /* double local values (rank) */
+    SPMV_X_R_PTR = 4,      /* int64[rows_p+1] remote row pointer from 0 (rank) */
+    SPMV_X_R_COL = 5,      /* int32 positions in H_p (rank) */
+    SPMV_X_R_VAL = 6,      /* double remote values (rank) */
+    SPMV_X_HALO = 7,       /* int32 H_p (rank) */
+    SPMV_X_SEND_IDX = 8,   /* int32[n_send] x index of each send slot */
+    SPMV_X_HALO_OFF = 9,   /* int64[P+1] start of destination p's part */
+    SPMV_X_SEG_OFF = 10,   /* int64[P*P+1] start of segment (dst p, src q) at p*P+q */
+    SPMV_X_SENDBUF = 11,   /* double[n_send] current send buffer */
+    SPMV_X_RECVBUF = 12    /* double[n_send] current receive buffer */
+};
+/* Element count of array `what` (for rank part_idx where per rank), or < 0. */
+int64_t spmv_part_export_len(const spmv_part* part, int what, int part_idx);
+/* Copy array `what` to host_dst (capacity cap elements); synchronises. */
+int spmv_part_export_plan(const spmv_part* part, int what, int part_idx,
+                          void* host_dst, int64_t cap);
+
+/* DAG of the plan's operations as (src op, dst op) int32 pairs. */
+int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
+                  int64_t* n_pairs_out);
+
+/* Kernel variant of the LOCAL and REMOTE products. */
+enum {
+    SPMV_VARIANT_TILE = 0,     /* thread-per-row over bulk-copied smem tiles */
+    SPMV_VARIANT_VECTOR = 1,   /* `param` lanes per row (2..32), 128-bit loads */
+    SPMV_VARIANT_MERGE = 2     /* merge-path split with deterministic carries */
+};
+int spmv_part_set_variant(spmv_part* part, int variant, int param);
+
+/*
+ * The four operations (Fig. 3c).  `part_idx` = -1 runs the op for every
+ * rank in one launch (coarse); 0 <= part_idx < P runs rank part_idx's op.
+ *   spmv_pack:      sendbuf slots owned by source rank part_idx <- x
+ *   spmv_local:     y rows of rank part_idx <- A_L x_L (overwrites)
+ *   spmv_halo_copy: destination part_idx's slice of recvbuf <- sendbuf
+ *   spmv_remote:    y rows of rank part_idx with remote entries += A_R x_R
+ * x_dev / y_dev: n doubles on the device (caller-owned).
+ */
+int spmv_pack(spmv_part* part, int part_idx, const double* x_dev, cudaStream_t s);
+int spmv_local(spmv_part* part, int part_idx, const double* x_dev, double* y_dev,
+               cudaStream_t s);
+int spmv_halo_copy(spmv_part* part, int part_idx, cudaStream_t s);
+int spmv_remote(spmv_part* part, int part_idx, double* y_dev, cudaStream_t s);
+
+/*
+ * Run one implementation (Sec. III-B): op_order[n_ops] is a permutation of
+ * the op ids, stream_of_op[op id] in [0, n_streams) binds each op to
+ * streams[..].  Before anything is launched the order is checked to be
+ * topological for the DAG and every stream id to be in range (else
+ * SPMV_ESCHED).  Issue follows Table III: an op waits (cudaStreamWaitEvent)
+ * on an event recorded right after each predecessor bound to another
+ * stream, and nothing for a predecessor on its own stream.  The artificial
+ * start and end vertices are a fork from streams[0] to every other used
+ * stream and a join of all of them back into streams[0], so back-to-back
+ * runs never overlap.
+ * flags: SPMV_RUN_EAGER issues the ops now, in order.
+ *        SPMV_RUN_CAPTURE captures the same issue into a CUDA graph started
+ *          on streams[0], instantiates it and returns its handle in
+ *          *graph_handle_inout (nothing runs).  x_dev and y_dev are baked in.
+ *        SPMV_RUN_REPLAY launches graph *graph_handle_inout on streams[0];
+ *          x_dev / y_dev must equal the captured ones (else SPMV_EINVAL).
+ * A graph keeps only dependencies, so two orders that differ only in the
+ * relative order of ops on different streams give the same graph.
+ */
+enum { SPMV_RUN_EAGER = 0, SPMV_RUN_CAPTURE = 1, SPMV_RUN_REPLAY = 2 };
+int spmv_schedule_run(spmv_part* part, const int32_t* op_order,
+                      const int32_t* stream_of_op, int n_ops,
+                      cudaStream_t* streams, int n_streams,
+                      const double* x_dev, double* y_dev,
+                      int flags, int64_t* graph_handle_inout);
+
+/* Release one captured graph (handle from SPMV_RUN_CAPTURE). */
+int spmv_graph_destroy(spmv_part* part, int64_t graph_handle);
+
+/*
+ * End-to-end product through host buffers: copies x_host (n doubles,
+ * should be pinned) into a plan-owned device vector, replays graph
+ * `graph_handle` (captured with spmv_part_io_buffers' vectors) on stream s,
+ * and copies y back into y_host; returns after the stream finished.
+ */
+int spmv_part_io_buffers(spmv_part* part, double** x_dev_out, double** y_dev_out);
+int spmv_apply_host(spmv_part* part, int64_t graph_handle, const double* x_host,
+                    double* y_host, cudaStream_t s);
+
+/* Thread-local message describing the last failure of this thread. */
+const char* spmv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMV_H */
