@@ -198,6 +198,30 @@ int spmv_part_io_buffers(spmv_part* part, double** x_dev_out, double** y_dev_out
 int spmv_apply_host(spmv_part* part, int64_t graph_handle, const double* x_host,
                     double* y_host, cudaStream_t s);
 
+/*
+ * Plain CSR product y = A x on caller-owned DEVICE arrays with the
+ * merge-path kernel (equal work per CTA whatever the row lengths; rows cut
+ * between threads or CTAs are finished in a fixed order, so y is
+ * deterministic).  row_ptr_dev: int32[n+1] with row_ptr[0] = 0 and
+ * row_ptr[n] = nnz, non-decreasing; col_idx_dev: int32[nnz] in [0, n);
+ * vals_dev: double[nnz]; x_dev, y_dev: double[n]; every array 16-byte
+ * aligned.  The arrays are read only inside their bounds.  Scratch: 48 bytes
+ * per 2048 merge items (rows + entries), taken with cudaMallocAsync on s and
+ * released with cudaFreeAsync on s.  Preconditions on the CSR contents are
+ * the caller's: they are not checked on the device.
+ * Errors: SPMV_EINVAL (sizes, NULL or misaligned pointers), SPMV_EBOUNDS
+ * (n + nnz >= 2^31 - 2048), SPMV_ENOMEM, SPMV_ECUDA.  A bounded device
+ * wait that gives up is reported by spmv_csr_error.
+ */
+int spmv_csr_merge(int64_t n, int64_t nnz, const int32_t* row_ptr_dev,
+                   const int32_t* col_idx_dev, const double* vals_dev,
+                   const double* x_dev, double* y_dev, cudaStream_t s);
+
+/* Device error word of the plan-free entry points on the current device
+ * (0 = none; SPMV_ETIMEOUT's magnitude after a bounded wait gave up); reads
+ * and clears it, synchronising the device. */
+int spmv_csr_error(int64_t* out);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* spmv_last_error(void);
 

@@ -1,0 +1,697 @@
+// C ABI of the partitioned SpMV library (include/spmv.h): plan life cycle,
+// the four operations of Fig. 3c, and the schedule runner of Sec. III-B with
+// Table III synchronisation, eager or captured as a CUDA graph.
+#include "part.h"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+using spmvk::fail;
+using spmvk::check_cuda;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail_status(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define API_TRY try {
+#define API_CATCH                                                                         \
+    }                                                                                     \
+    catch (const spmvk::Fail& f) {                                                        \
+        return fail_status(f.code, f.msg);                                                \
+    }                                                                                     \
+    catch (const std::bad_alloc&) {                                                       \
+        return fail_status(SPMV_ENOMEM, "host allocation failed");                        \
+    }                                                                                     \
+    catch (...) {                                                                         \
+        return fail_status(SPMV_EINVAL, "unexpected exception");                          \
+    }
+
+void need(bool ok, int code, const char* msg) {
+    if (!ok) fail(code, "%s", msg);
+}
+
+void check_part(const spmv_part* pt) { need(pt != nullptr, SPMV_EINVAL, "part is NULL"); }
+
+void check_rank(const spmv_part* pt, int part_idx) {
+    if (part_idx < -1 || part_idx >= pt->P) fail(SPMV_EINVAL, "part index %d not in [-1, %d)", part_idx, pt->P);
+}
+
+// The operations' DAG (Fig. 3c): pack -> copy -> remote, local -> remote;
+// per rank, pack of q -> copy of p whenever q sends to p.
+void build_dag(spmv_part* pt) {
+    const int P = pt->P;
+    pt->edges.clear();
+    if (pt->gran == SPMV_COARSE) {
+        pt->n_ops = 4;
+        pt->edges = {{SPMV_OP_PACK, SPMV_OP_COPY}, {SPMV_OP_COPY, SPMV_OP_REMOTE},
+                     {SPMV_OP_LOCAL, SPMV_OP_REMOTE}};
+    } else {
+        pt->n_ops = 4 * P;
+        for (int p = 0; p < P; ++p) {
+            for (int q = 0; q < P; ++q) {
+                if (q == p) continue;
+                if (pt->seg_off[(size_t)p * P + q + 1] > pt->seg_off[(size_t)p * P + q])
+                    pt->edges.push_back({4 * q + SPMV_OP_PACK, 4 * p + SPMV_OP_COPY});
+            }
+            pt->edges.push_back({4 * p + SPMV_OP_COPY, 4 * p + SPMV_OP_REMOTE});
+            pt->edges.push_back({4 * p + SPMV_OP_LOCAL, 4 * p + SPMV_OP_REMOTE});
+        }
+    }
+    pt->preds.assign(pt->n_ops, {});
+    for (auto& e : pt->edges) pt->preds[e.second].push_back(e.first);
+}
+
+spmvk::CsrArgs local_args(spmv_part* pt, const double* x, double* y) {
+    spmvk::CsrArgs a{};
+    a.ptr = pt->l_ptr;
+    a.col = pt->l_col;
+    a.val = pt->l_val;
+    a.rowmap = nullptr;
+    a.x = x;
+    a.y = y;
+    a.accumulate = 0;
+    a.n_rows = (int)pt->n;
+    a.nnz_total = (int)pt->nnz_l;
+    a.guarded = 0;
+    a.err = pt->err;
+    return a;
+}
+
+spmvk::CsrArgs remote_args(spmv_part* pt, double* y) {
+    spmvk::CsrArgs a{};
+    a.ptr = pt->rr_ptr;
+    a.col = pt->r_col;
+    a.val = pt->r_val;
+    a.rowmap = pt->rr_row;
+    a.x = pt->recvbuf;
+    a.y = y;
+    a.accumulate = 1;
+    a.n_rows = (int)pt->n_rr;
+    a.nnz_total = (int)pt->nnz_r;
+    a.guarded = 0;
+    a.err = pt->err;
+    return a;
+}
+
+// Each op returns the number of kernels it launched.
+int op_pack(spmv_part* pt, int q, const double* x, cudaStream_t s) {
+    if (q < 0) {
+        check_cuda(spmvk::launch_gather(x, pt->send_idx, nullptr, pt->sendbuf, pt->n_send, pt->num_sms, s),
+                   "pack");
+        return pt->n_send > 0;
+    }
+    const int64_t c = pt->pack_off[q + 1] - pt->pack_off[q];
+    check_cuda(spmvk::launch_gather(x, pt->send_idx, pt->pack_pos + pt->pack_off[q], pt->sendbuf, c,
+                                    pt->num_sms, s),
+               "pack");
+    return c > 0;
+}
+
+int op_copy(spmv_part* pt, int p, cudaStream_t s) {
+    const int64_t a = p < 0 ? 0 : pt->halo_off[p];
+    const int64_t b = p < 0 ? pt->n_send : pt->halo_off[p + 1];
+    check_cuda(spmvk::launch_copy(pt->sendbuf + a, pt->recvbuf + a, b - a, pt->num_sms, s), "halo copy");
+    return b > a;
+}
+
+int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, cudaStream_t s) {
+    const std::vector<int64_t>& off = remote ? pt->rtile_off : pt->ltile_off;
+    const int tb = (int)(p < 0 ? 0 : off[p]);
+    const int te = (int)(p < 0 ? off[pt->P] : off[p + 1]);
+    if (pt->variant == SPMV_VARIANT_MERGE) {
+        const std::vector<int64_t>& mo = remote ? pt->rmtile_off : pt->lmtile_off;
+        const int mb = (int)(p < 0 ? 0 : mo[p]);
+        const int me = (int)(p < 0 ? mo[pt->P] : mo[p + 1]);
+        check_cuda(spmvk::launch_merge(a, remote ? pt->rmtiles : pt->lmtiles, mb, me,
+                                       remote ? pt->rcarry : pt->lcarry, pt->num_sms, s),
+                   "merge product");
+        return me > mb ? 2 : 0;
+    }
+    const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
+    if (pt->variant == SPMV_VARIANT_VECTOR) {
+        check_cuda(spmvk::launch_vector(a, tiles, tb, te, pt->vparam, pt->num_sms, s), "vector product");
+    } else {
+        check_cuda(spmvk::launch_tile(a, tiles, tb, te, pt->geom, pt->num_sms, s), "tile product");
+    }
+    return te > tb;
+}
+
+int op_local(spmv_part* pt, int p, const double* x, double* y, cudaStream_t s) {
+    return launch_product(pt, local_args(pt, x, y), false, p, s);
+}
+
+int op_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
+    return launch_product(pt, remote_args(pt, y), true, p, s);
+}
+
+int run_op(spmv_part* pt, int op, const double* x, double* y, cudaStream_t s) {
+    const int kind = op % 4;
+    const int p = pt->gran == SPMV_COARSE ? -1 : op / 4;
+    switch (kind) {
+        case SPMV_OP_PACK: return op_pack(pt, p, x, s);
+        case SPMV_OP_LOCAL: return op_local(pt, p, x, y, s);
+        case SPMV_OP_COPY: return op_copy(pt, p, s);
+        default: return op_remote(pt, p, y, s);
+    }
+}
+
+void validate_schedule(const spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops,
+                       int n_streams) {
+    if (!order || !stream_of) fail(SPMV_EINVAL, "op_order or stream_of_op is NULL");
+    if (n_ops != pt->n_ops) fail(SPMV_ESCHED, "%d ops given, the DAG has %d", n_ops, pt->n_ops);
+    if (n_streams < 1) fail(SPMV_EINVAL, "n_streams = %d", n_streams);
+    std::vector<int> pos(n_ops, -1);
+    for (int i = 0; i < n_ops; ++i) {
+        const int v = order[i];
+        if (v < 0 || v >= n_ops) fail(SPMV_ESCHED, "op id %d out of range", v);
+        if (pos[v] >= 0) fail(SPMV_ESCHED, "op %d appears twice", v);
+        pos[v] = i;
+    }
+    for (int v = 0; v < n_ops; ++v)
+        if (stream_of[v] < 0 || stream_of[v] >= n_streams)
+            fail(SPMV_ESCHED, "op %d bound to stream %d of %d", v, stream_of[v], n_streams);
+    for (auto& e : pt->edges)
+        if (pos[e.first] > pos[e.second])
+            fail(SPMV_ESCHED, "order is not topological: op %d must precede op %d", e.first, e.second);
+}
+
+void ensure_events(spmv_part* pt, int n_streams) {
+    if (pt->op_ev.empty()) {
+        pt->op_ev.assign(pt->n_ops, nullptr);
+        for (auto& e : pt->op_ev) check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        check_cuda(cudaEventCreateWithFlags(&pt->fork_ev, cudaEventDisableTiming), "event");
+    }
+    while ((int)pt->join_ev.size() < n_streams) {
+        cudaEvent_t e;
+        check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        pt->join_ev.push_back(e);
+    }
+}
+
+// Issue one implementation (order + stream map) with Table III events.
+void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops, cudaStream_t* streams,
+           int n_streams, const double* x, double* y) {
+    cudaStream_t origin = streams[0];
+    std::vector<char> used(n_streams, 0);
+    for (int v = 0; v < n_ops; ++v) used[stream_of[v]] = 1;
+    // start vertex: fork every other used stream from the origin
+    check_cuda(cudaEventRecord(pt->fork_ev, origin), "fork record");
+    for (int s = 1; s < n_streams; ++s)
+        if (used[s]) check_cuda(cudaStreamWaitEvent(streams[s], pt->fork_ev, 0), "fork wait");
+    // which ops feed a successor bound to another stream
+    std::vector<char> cross(n_ops, 0);
+    for (auto& e : pt->edges)
+        if (stream_of[e.first] != stream_of[e.second]) cross[e.first] = 1;
+    int64_t records = 0, waits = 0, launches = 0;
+    for (int i = 0; i < n_ops; ++i) {
+        const int v = order[i];
+        cudaStream_t sv = streams[stream_of[v]];
+        for (int u : pt->preds[v]) {
+            if (stream_of[u] != stream_of[v]) {   // Table III: BoundGPU_i -> BoundGPU_j
+                check_cuda(cudaStreamWaitEvent(sv, pt->op_ev[u], 0), "stream wait");
+                ++waits;
+            }                                     // same stream: nothing
+        }
+        launches += run_op(pt, v, x, y, sv);
+        if (cross[v]) {
+            check_cuda(cudaEventRecord(pt->op_ev[v], sv), "event record");
+            ++records;
+        }
+    }
+    // end vertex: join every other used stream back into the origin
+    for (int s = 1; s < n_streams; ++s) {
+        if (!used[s]) continue;
+        check_cuda(cudaEventRecord(pt->join_ev[s], streams[s]), "join record");
+        check_cuda(cudaStreamWaitEvent(origin, pt->join_ev[s], 0), "join wait");
+    }
+    pt->last_records = records;
+    pt->last_waits = waits;
+    pt->last_launches = launches;
+}
+
+int64_t alg_bytes_local(const spmv_part* pt) {
+    // 12 B per entry, 4 B per row pointer (+1), 8 B x read, 8 B y written
+    return 12 * pt->nnz_l + 4 * (pt->n + 1) + 8 * pt->n + 8 * pt->n;
+}
+
+int64_t alg_bytes_total(const spmv_part* pt) {
+    // local product, the remote product (entries, compressed row pointers
+    // and row ids, y read-modify-write of its rows), the pack (indices read,
+    // slots written; its x reads are counted in the local product's x),
+    // the exchange (read + write) and the remote product's halo reads
+    int64_t b = alg_bytes_local(pt);
+    b += 12 * pt->nnz_r + 4 * (pt->n_rr + 1) + 4 * pt->n_rr + 16 * pt->n_rr;
+    b += 4 * pt->n_send + 8 * pt->n_send;   // pack: index read, slot write
+    b += 16 * pt->n_send;                   // exchange: read + write
+    b += 8 * pt->n_send;                    // remote: halo read
+    return b;
+}
+
+template <class T>
+std::vector<T> d2h(const T* d, int64_t count) {
+    std::vector<T> h((size_t)std::max<int64_t>(count, 0));
+    if (count > 0) check_cuda(cudaMemcpy(h.data(), d, (size_t)count * sizeof(T), cudaMemcpyDeviceToHost), "export");
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spmv_part_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* vals, int P,
+                     int granularity, spmv_part** out) {
+    if (!out) return fail_status(SPMV_EINVAL, "out is NULL");
+    *out = nullptr;
+    spmv_part* pt = nullptr;
+    API_TRY
+    if (granularity != SPMV_COARSE && granularity != SPMV_PER_PARTITION)
+        fail(SPMV_EINVAL, "granularity %d", granularity);
+    pt = new spmv_part();
+    pt->P = P;
+    pt->gran = granularity;
+    check_cuda(cudaGetDevice(&pt->device), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&pt->num_sms, cudaDevAttrMultiProcessorCount, pt->device), "SM count");
+    spmvk::build_plan(pt, n, row_ptr, col_idx, vals);
+    spmvk::build_tiles(pt, spmvk::default_tile_geom());
+    build_dag(pt);
+    *out = pt;
+    pt = nullptr;
+    return SPMV_OK;
+    }
+    catch (const spmvk::Fail& f) {
+        if (pt) { spmvk::free_plan(pt); delete pt; }
+        return fail_status(f.code, f.msg);
+    }
+    catch (const std::bad_alloc&) {
+        if (pt) { spmvk::free_plan(pt); delete pt; }
+        return fail_status(SPMV_ENOMEM, "host allocation failed");
+    }
+    catch (...) {
+        if (pt) { spmvk::free_plan(pt); delete pt; }
+        return fail_status(SPMV_EINVAL, "unexpected exception");
+    }
+}
+
+int spmv_part_destroy(spmv_part* pt) {
+    if (!pt) return SPMV_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    spmvk::free_plan(pt);
+    delete pt;
+    if (e != cudaSuccess) return fail_status(SPMV_ECUDA, cudaGetErrorString(e));
+    return SPMV_OK;
+}
+
+int spmv_part_query(const spmv_part* pt, int what, int part_idx, int64_t* out) {
+    API_TRY
+    check_part(pt);
+    need(out != nullptr, SPMV_EINVAL, "out is NULL");
+    switch (what) {
+        case SPMV_Q_N: *out = pt->n; break;
+        case SPMV_Q_P: *out = pt->P; break;
+        case SPMV_Q_GRANULARITY: *out = pt->gran; break;
+        case SPMV_Q_NNZ: *out = pt->nnz; break;
+        case SPMV_Q_NNZ_LOCAL: *out = pt->nnz_l; break;
+        case SPMV_Q_NNZ_REMOTE: *out = pt->nnz_r; break;
+        case SPMV_Q_N_SEND: *out = pt->n_send; break;
+        case SPMV_Q_N_HALO:
+            if (part_idx < 0 || part_idx >= pt->P) fail(SPMV_EINVAL, "rank %d", part_idx);
+            *out = pt->halo_off[part_idx + 1] - pt->halo_off[part_idx];
+            break;
+        case SPMV_Q_N_REMOTE_ROWS: *out = pt->n_rr; break;
+        case SPMV_Q_N_OPS: *out = pt->n_ops; break;
+        case SPMV_Q_N_EDGES: *out = (int64_t)pt->edges.size(); break;
+        case SPMV_Q_ALG_BYTES: *out = alg_bytes_total(pt); break;
+        case SPMV_Q_ALG_BYTES_LOCAL: *out = alg_bytes_local(pt); break;
+        case SPMV_Q_DEVICE_BYTES: *out = (int64_t)pt->device_bytes; break;
+        case SPMV_Q_LAST_RECORDS: *out = pt->last_records; break;
+        case SPMV_Q_LAST_WAITS: *out = pt->last_waits; break;
+        case SPMV_Q_ERROR: {
+            int h = 0;
+            check_cuda(cudaDeviceSynchronize(), "synchronize");
+            check_cuda(cudaMemcpy(&h, pt->err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+            *out = h;
+            break;
+        }
+        case SPMV_Q_LOCAL_VARIANT: *out = pt->variant; break;
+        case SPMV_Q_N_LOCAL_TILES: *out = pt->ltile_off.empty() ? 0 : pt->ltile_off[pt->P]; break;
+        case SPMV_Q_LAST_LAUNCHES: *out = pt->last_launches; break;
+        default: fail(SPMV_EINVAL, "unknown query %d", what);
+    }
+    API_CATCH
+    return SPMV_OK;
+}
+
+int64_t spmv_part_export_len(const spmv_part* pt, int what, int p) {
+    if (!pt) return -1;
+    const bool rank_ok = p >= 0 && p < pt->P;
+    const int64_t rows = rank_ok ? pt->bounds[p + 1] - pt->bounds[p] : 0;
+    switch (what) {
+        case SPMV_X_BOUNDS: return pt->P + 1;
+        case SPMV_X_SEND_IDX: return pt->n_send;
+        case SPMV_X_HALO_OFF: return pt->P + 1;
+        case SPMV_X_SEG_OFF: return (int64_t)pt->P * pt->P + 1;
+        case SPMV_X_SENDBUF: return pt->n_send;
+        case SPMV_X_RECVBUF: return pt->n_send;
+        default: break;
+    }
+    if (!rank_ok) return -1;
+    switch (what) {
+        case SPMV_X_L_PTR: return rows + 1;
+        case SPMV_X_R_PTR: return rows + 1;
+        case SPMV_X_HALO: return pt->halo_off[p + 1] - pt->halo_off[p];
+        case SPMV_X_L_COL:
+        case SPMV_X_L_VAL: {
+            int32_t a = 0, b = 0;
+            if (cudaMemcpy(&a, pt->l_ptr + pt->bounds[p], 4, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            if (cudaMemcpy(&b, pt->l_ptr + pt->bounds[p + 1], 4, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            return (int64_t)b - a;
+        }
+        case SPMV_X_R_COL:
+        case SPMV_X_R_VAL: {
+            int32_t a = 0, b = 0;
+            if (cudaMemcpy(&a, pt->rr_ptr + pt->rr_off[p], 4, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            if (cudaMemcpy(&b, pt->rr_ptr + pt->rr_off[p + 1], 4, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            return (int64_t)b - a;
+        }
+        default: return -1;
+    }
+}
+
+int spmv_part_export_plan(const spmv_part* pt, int what, int p, void* dst, int64_t cap) {
+    API_TRY
+    check_part(pt);
+    const int64_t len = spmv_part_export_len(pt, what, p);
+    if (len < 0) fail(SPMV_EINVAL, "bad selector %d / rank %d", what, p);
+    if (len > cap) fail(SPMV_EINVAL, "capacity %lld < %lld", (long long)cap, (long long)len);
+    if (len > 0 && !dst) fail(SPMV_EINVAL, "host_dst is NULL");
+    if (len == 0) return SPMV_OK;
+    check_cuda(cudaDeviceSynchronize(), "synchronize");
+    int64_t* d64 = static_cast<int64_t*>(dst);
+    int32_t* d32 = static_cast<int32_t*>(dst);
+    double* df = static_cast<double*>(dst);
+    switch (what) {
+        case SPMV_X_BOUNDS: std::copy(pt->bounds.begin(), pt->bounds.end(), d64); break;
+        case SPMV_X_HALO_OFF: std::copy(pt->halo_off.begin(), pt->halo_off.end(), d64); break;
+        case SPMV_X_SEG_OFF: std::copy(pt->seg_off.begin(), pt->seg_off.end(), d64); break;
+        case SPMV_X_SEND_IDX: {
+            auto h = d2h(pt->send_idx, len);
+            std::copy(h.begin(), h.end(), d32);
+            break;
+        }
+        case SPMV_X_SENDBUF: {
+            auto h = d2h(pt->sendbuf, len);
+            std::copy(h.begin(), h.end(), df);
+            break;
+        }
+        case SPMV_X_RECVBUF: {
+            auto h = d2h(pt->recvbuf, len);
+            std::copy(h.begin(), h.end(), df);
+            break;
+        }
+        case SPMV_X_HALO: {
+            auto h = d2h(pt->send_idx + pt->halo_off[p], len);
+            std::copy(h.begin(), h.end(), d32);
+            break;
+        }
+        case SPMV_X_L_PTR:
+        case SPMV_X_L_COL:
+        case SPMV_X_L_VAL: {
+            const int64_t rows = pt->bounds[p + 1] - pt->bounds[p];
+            auto ptr = d2h(pt->l_ptr + pt->bounds[p], rows + 1);
+            if (what == SPMV_X_L_PTR) {
+                for (int64_t i = 0; i <= rows; ++i) d64[i] = (int64_t)ptr[(size_t)i] - ptr[0];
+            } else if (what == SPMV_X_L_COL) {
+                auto h = d2h(pt->l_col + ptr[0], len);
+                std::copy(h.begin(), h.end(), d32);
+            } else {
+                auto h = d2h(pt->l_val + ptr[0], len);
+                std::copy(h.begin(), h.end(), df);
+            }
+            break;
+        }
+        case SPMV_X_R_PTR: {
+            const int64_t rows = pt->bounds[p + 1] - pt->bounds[p];
+            const int64_t a = pt->rr_off[p], b = pt->rr_off[p + 1];
+            auto rrow = d2h(pt->rr_row + a, b - a);
+            auto rptr = d2h(pt->rr_ptr + a, b - a + 1);
+            std::vector<int64_t> cnt((size_t)rows + 1, 0);
+            for (int64_t i = 0; i < b - a; ++i)
+                cnt[(size_t)(rrow[(size_t)i] - pt->bounds[p]) + 1] = (int64_t)rptr[(size_t)i + 1] - rptr[(size_t)i];
+            d64[0] = 0;
+            for (int64_t i = 1; i <= rows; ++i) d64[i] = d64[i - 1] + cnt[(size_t)i];
+            break;
+        }
+        case SPMV_X_R_COL:
+        case SPMV_X_R_VAL: {
+            int32_t k0 = 0;
+            check_cuda(cudaMemcpy(&k0, pt->rr_ptr + pt->rr_off[p], 4, cudaMemcpyDeviceToHost), "export");
+            if (what == SPMV_X_R_COL) {
+                auto h = d2h(pt->r_col + k0, len);
+                for (int64_t i = 0; i < len; ++i) d32[i] = h[(size_t)i] - (int32_t)pt->halo_off[p];
+            } else {
+                auto h = d2h(pt->r_val + k0, len);
+                std::copy(h.begin(), h.end(), df);
+            }
+            break;
+        }
+        default: fail(SPMV_EINVAL, "bad selector %d", what);
+    }
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_part_dag(const spmv_part* pt, int32_t* edges, int64_t cap_pairs, int64_t* n_pairs) {
+    API_TRY
+    check_part(pt);
+    need(n_pairs != nullptr, SPMV_EINVAL, "n_pairs_out is NULL");
+    *n_pairs = (int64_t)pt->edges.size();
+    if (edges) {
+        if (cap_pairs < (int64_t)pt->edges.size()) fail(SPMV_EINVAL, "capacity too small");
+        for (size_t i = 0; i < pt->edges.size(); ++i) {
+            edges[2 * i] = pt->edges[i].first;
+            edges[2 * i + 1] = pt->edges[i].second;
+        }
+    }
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_part_set_variant(spmv_part* pt, int variant, int param) {
+    API_TRY
+    check_part(pt);
+    if (!pt->graphs.empty()) fail(SPMV_EINVAL, "destroy the captured graphs before changing the variant");
+    if (variant == SPMV_VARIANT_TILE) {
+        static const spmvk::TileGeom geoms[] = {
+            {128, 3456, 4}, {128, 3456, 2}, {256, 4096, 3}, {256, 6912, 2}, {128, 2048, 6}};
+        const int ng = (int)(sizeof geoms / sizeof geoms[0]);
+        if (param < 0 || param >= ng) fail(SPMV_EINVAL, "tile geometry %d not in [0, %d)", param, ng);
+        const spmvk::TileGeom g = geoms[param];
+        if (!spmvk::tile_geom_supported(g)) fail(SPMV_EINVAL, "tile geometry not compiled");
+        check_cuda(cudaDeviceSynchronize(), "synchronize");
+        if (g.threads != pt->geom.threads || g.nnz_cap != pt->geom.nnz_cap || g.stages != pt->geom.stages)
+            spmvk::build_tiles(pt, g);
+    } else if (variant == SPMV_VARIANT_VECTOR) {
+        if (param != 2 && param != 4 && param != 8 && param != 16 && param != 32)
+            fail(SPMV_EINVAL, "vector width %d not in {2,4,8,16,32}", param);
+    } else if (variant == SPMV_VARIANT_MERGE) {
+        check_cuda(cudaDeviceSynchronize(), "synchronize");
+        if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
+    } else {
+        fail(SPMV_EINVAL, "unknown variant %d", variant);
+    }
+    pt->variant = variant;
+    pt->vparam = param;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_pack(spmv_part* pt, int p, const double* x, cudaStream_t s) {
+    API_TRY
+    check_part(pt);
+    check_rank(pt, p);
+    need(x != nullptr || pt->n == 0, SPMV_EINVAL, "x_dev is NULL");
+    pt->last_launches = op_pack(pt, p, x, s);
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_local(spmv_part* pt, int p, const double* x, double* y, cudaStream_t s) {
+    API_TRY
+    check_part(pt);
+    check_rank(pt, p);
+    need((x != nullptr && y != nullptr) || pt->n == 0, SPMV_EINVAL, "x_dev or y_dev is NULL");
+    pt->last_launches = op_local(pt, p, x, y, s);
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_halo_copy(spmv_part* pt, int p, cudaStream_t s) {
+    API_TRY
+    check_part(pt);
+    check_rank(pt, p);
+    pt->last_launches = op_copy(pt, p, s);
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
+    API_TRY
+    check_part(pt);
+    check_rank(pt, p);
+    need(y != nullptr || pt->n == 0, SPMV_EINVAL, "y_dev is NULL");
+    pt->last_launches = op_remote(pt, p, y, s);
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops,
+                      cudaStream_t* streams, int n_streams, const double* x, double* y, int flags,
+                      int64_t* handle) {
+    API_TRY
+    check_part(pt);
+    need(streams != nullptr, SPMV_EINVAL, "streams is NULL");
+    if (flags == SPMV_RUN_REPLAY) {
+        need(handle != nullptr, SPMV_EINVAL, "graph handle is NULL");
+        auto it = pt->graphs.find(*handle);
+        if (it == pt->graphs.end()) fail(SPMV_EINVAL, "unknown graph handle %lld", (long long)*handle);
+        if (it->second.x != x || it->second.y != y) fail(SPMV_EINVAL, "x_dev / y_dev differ from the captured ones");
+        check_cuda(cudaGraphLaunch(it->second.exec, streams[0]), "cudaGraphLaunch");
+        return SPMV_OK;
+    }
+    if (flags != SPMV_RUN_EAGER && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "unknown flags %d", flags);
+    validate_schedule(pt, order, stream_of, n_ops, n_streams);
+    need((x != nullptr && y != nullptr) || pt->n == 0, SPMV_EINVAL, "x_dev or y_dev is NULL");
+    ensure_events(pt, n_streams);
+    if (flags == SPMV_RUN_EAGER) {
+        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y);
+        return SPMV_OK;
+    }
+    need(handle != nullptr, SPMV_EINVAL, "graph handle is NULL");
+    check_cuda(cudaStreamBeginCapture(streams[0], cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y);
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(streams[0], &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw;
+    }
+    cudaGraph_t g = nullptr;
+    check_cuda(cudaStreamEndCapture(streams[0], &g), "end capture");
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    check_cuda(e, "cudaGraphInstantiate");
+    const int64_t id = pt->next_graph++;
+    pt->graphs[id] = spmvk::GraphRec{exec, x, y};
+    *handle = id;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_graph_destroy(spmv_part* pt, int64_t handle) {
+    API_TRY
+    check_part(pt);
+    auto it = pt->graphs.find(handle);
+    if (it == pt->graphs.end()) fail(SPMV_EINVAL, "unknown graph handle %lld", (long long)handle);
+    check_cuda(cudaDeviceSynchronize(), "synchronize");
+    cudaGraphExecDestroy(it->second.exec);
+    pt->graphs.erase(it);
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_part_io_buffers(spmv_part* pt, double** x_out, double** y_out) {
+    API_TRY
+    check_part(pt);
+    need(x_out && y_out, SPMV_EINVAL, "output pointer is NULL");
+    if (!pt->io_x) {
+        pt->io_x = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
+        pt->io_y = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
+    }
+    *x_out = pt->io_x;
+    *y_out = pt->io_y;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_apply_host(spmv_part* pt, int64_t handle, const double* x_host, double* y_host, cudaStream_t s) {
+    API_TRY
+    check_part(pt);
+    need(pt->n == 0 || (x_host && y_host), SPMV_EINVAL, "host buffer is NULL");
+    auto it = pt->graphs.find(handle);
+    if (it == pt->graphs.end()) fail(SPMV_EINVAL, "unknown graph handle %lld", (long long)handle);
+    if (!pt->io_x || it->second.x != pt->io_x || it->second.y != pt->io_y)
+        fail(SPMV_EINVAL, "graph was not captured on the plan's io buffers");
+    const size_t bytes = (size_t)pt->n * sizeof(double);
+    if (bytes) check_cuda(cudaMemcpyAsync(pt->io_x, x_host, bytes, cudaMemcpyHostToDevice, s), "copy x in");
+    check_cuda(cudaGraphLaunch(it->second.exec, s), "cudaGraphLaunch");
+    if (bytes) check_cuda(cudaMemcpyAsync(y_host, pt->io_y, bytes, cudaMemcpyDeviceToHost, s), "copy y out");
+    check_cuda(cudaStreamSynchronize(s), "synchronize");
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_csr_merge(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                   const double* x, double* y, cudaStream_t s) {
+    API_TRY
+    if (n < 0 || nnz < 0) fail(SPMV_EINVAL, "n = %lld, nnz = %lld", (long long)n, (long long)nnz);
+    const int items = spmvk::merge_items_per_tile();
+    if (n + nnz >= (int64_t(1) << 31) - items) fail(SPMV_EBOUNDS, "n + nnz too large for int32 merge paths");
+    if (n == 0) return SPMV_OK;
+    if (!row_ptr || !x || !y || (nnz > 0 && (!col_idx || !vals))) fail(SPMV_EINVAL, "NULL device pointer");
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(row_ptr) | reinterpret_cast<uintptr_t>(col_idx) |
+                          reinterpret_cast<uintptr_t>(vals) | reinterpret_cast<uintptr_t>(x) |
+                          reinterpret_cast<uintptr_t>(y);
+    if (mis & 15) fail(SPMV_EINVAL, "device arrays must be 16-byte aligned");
+    int dev = 0, sms = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int n_tiles = (int)((n + nnz + items - 1) / items);
+    void* scratch = nullptr;
+    const size_t tile_bytes = (size_t)n_tiles * sizeof(spmvk::MergeTile);
+    check_cuda(cudaMallocAsync(&scratch, tile_bytes + (size_t)n_tiles * sizeof(spmvk::Carry), s), "cudaMallocAsync");
+    spmvk::MergeTile* tiles = static_cast<spmvk::MergeTile*>(scratch);
+    spmvk::Carry* carries = reinterpret_cast<spmvk::Carry*>(static_cast<char*>(scratch) + tile_bytes);
+    spmvk::CsrArgs a{};
+    a.ptr = row_ptr;
+    a.col = col_idx;
+    a.val = vals;
+    a.rowmap = nullptr;
+    a.x = x;
+    a.y = y;
+    a.accumulate = 0;
+    a.n_rows = (int)n;
+    a.nnz_total = (int)nnz;
+    a.guarded = 1;
+    a.err = nullptr;
+    cudaError_t e = spmvk::launch_merge_partition(row_ptr, 0, (int)n, 0, tiles, n_tiles, s);
+    if (e == cudaSuccess) e = spmvk::launch_merge(a, tiles, 0, n_tiles, carries, sms, s);
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    check_cuda(e, "merge product");
+    check_cuda(ef, "cudaFreeAsync");
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_csr_error(int64_t* out) {
+    API_TRY
+    need(out != nullptr, SPMV_EINVAL, "out is NULL");
+    check_cuda(cudaDeviceSynchronize(), "synchronize");
+    int h = 0;
+    check_cuda(spmvk::read_clear_csr_error(&h), "error word");
+    *out = h;
+    API_CATCH
+    return SPMV_OK;
+}
+
+const char* spmv_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

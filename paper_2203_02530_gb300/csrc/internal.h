@@ -1,0 +1,82 @@
+// Internal declarations shared by the host runtime and the kernels of the
+// partitioned SpMV library.  Not part of the C ABI (include/spmv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+namespace spmvk {
+
+// Tile of rows processed by one CTA iteration: rows [r0, r1) of a CSR whose
+// entries [k0, k1) are staged in shared memory.  xoff is added to every
+// column index before x is read.  flags: TILE_LONG marks a single row longer
+// than the stage capacity, summed by the whole CTA straight from global
+// memory.
+struct Tile {
+    int32_t r0, r1, k0, k1;
+    int32_t xoff, flags, pad0, pad1;
+};
+static_assert(sizeof(Tile) == 32, "tile descriptor is two int4");
+enum { TILE_LONG = 1 };
+
+// Geometry of the thread-per-row tile kernel.
+struct TileGeom {
+    int threads;   // rows per tile (one thread per row)
+    int nnz_cap;   // entries per tile stage
+    int stages;    // shared-memory ring depth
+};
+
+// Merge-path tile: merge items [d0, d1) of the (row ends, entries) merge of
+// one rank's CSR; (r0, k0) is the path coordinate at d0, (r1, k1) at d1.
+struct MergeTile {
+    int32_t r0, r1, k0, k1;
+    int32_t xoff, pad0, pad1, pad2;
+};
+static_assert(sizeof(MergeTile) == 32, "merge tile descriptor is two int4");
+
+// Carry of a row cut by a merge tile boundary.
+struct Carry {
+    int32_t row;   // row index (in the CSR's row space), -1 when none
+    int32_t pad;
+    double val;
+};
+
+// Operands of one CSR product launch.
+struct CsrArgs {
+    const int32_t* ptr;     // row pointer of the CSR (row space indices)
+    const int32_t* col;
+    const double* val;
+    const int32_t* rowmap;  // nullptr: output row = row; else y[rowmap[row]]
+    const double* x;
+    double* y;
+    int accumulate;         // 0: y = A x ; 1: y += A x
+    int n_rows;             // rows of the CSR row space
+    int nnz_total;          // entries of the CSR (bounds the guarded reads)
+    int guarded;            // 1: arrays are not padded past their ends
+    int* err;               // device error word
+};
+
+// Launchers (kernels.cu).  All return cudaGetLastError() after the launch.
+cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* pos,
+                          double* dst, int64_t count, int num_sms, cudaStream_t s);
+cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_sms,
+                        cudaStream_t s);
+cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin,
+                        int tile_end, const TileGeom& g, int num_sms, cudaStream_t s);
+cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
+                          int lanes, int num_sms, cudaStream_t s);
+cudaError_t launch_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begin,
+                         int tile_end, Carry* carries, int num_sms, cudaStream_t s);
+cudaError_t launch_merge_partition(const int32_t* ptr, int row_begin, int row_end, int32_t xoff,
+                                   MergeTile* tiles, int n_tiles, cudaStream_t s);
+int merge_items_per_tile();
+cudaError_t read_clear_csr_error(int* out);
+int tile_ctas_per_sm(const TileGeom& g);
+bool tile_geom_supported(const TileGeom& g);
+TileGeom default_tile_geom();
+
+}  // namespace spmvk

@@ -1,0 +1,410 @@
+// Kernels of the row-partitioned FP64 SpMV (Sec. III-A, Fig. 3 of Pearson,
+// Javeed and Devine): the Pack gather, the halo exchange copy, and the CSR
+// products y_L = A_L x_L and y += A_R x_R.
+//
+// Design for sm_103a: FP64 FMA issues at 2 lanes/clk/SM on this part, so a
+// CSR product with HBM at full speed is nearly FP64-bound.  Every product
+// kernel therefore spends exactly one DFMA per stored entry on the main path
+// (one thread walks a row), and gets coalescing from bulk copies
+// (cp.async.bulk, the TMA engine) of whole tiles into a shared-memory ring
+// instead of from lanes cooperating on a row, which would cost FP64 adds in
+// shuffle reductions.  Every row is summed by one thread in storage order,
+// so results do not depend on the grid, the stream or the schedule.
+#include "internal.h"
+
+#include <cuda_runtime.h>
+
+namespace spmvk {
+
+// ------------------------------------------------------------------------
+// PTX helpers: mbarrier, bulk copy, global timer
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of an mbarrier, giving up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+// Bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0),
+// completion reported to an mbarrier as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s per wait
+constexpr uint64_t kDrainLimitNs = 100000000ull;   // 0.1 s per drain wait
+constexpr int kErrTimeout = 6;                     // -SPMV_ETIMEOUT
+
+__device__ __forceinline__ void store_row(const CsrArgs& a, int row, double sum) {
+    if (a.rowmap) {
+        const int o = __ldg(a.rowmap + row);
+        a.y[o] = a.accumulate ? a.y[o] + sum : sum;
+    } else {
+        a.y[row] = a.accumulate ? a.y[row] + sum : sum;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Pack: dst[k] = x[idx[k]] for every slot k (pos == nullptr) or for the
+// slots listed in pos[0..count).
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gather_kernel(const double* __restrict__ x,
+                                                     const int32_t* __restrict__ idx,
+                                                     const int32_t* __restrict__ pos,
+                                                     double* __restrict__ dst, int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const int64_t k = pos ? (int64_t)__ldg(pos + i) : i;
+        dst[k] = __ldg(x + __ldg(idx + k));
+    }
+}
+
+cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* pos,
+                          double* dst, int64_t count, int num_sms, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    const int64_t cap = (int64_t)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    gather_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, idx, pos, dst, count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Halo exchange: dst[0..count) = src[0..count)
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ src,
+                                                   double* __restrict__ dst, int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    if (vec) {
+        const int64_t pairs = count >> 1;
+        const double2* s2 = reinterpret_cast<const double2*>(src);
+        double2* d2 = reinterpret_cast<double2*>(dst);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += stride)
+            d2[i] = __ldg(s2 + i);
+        if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) dst[count - 1] = src[count - 1];
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+            dst[i] = __ldg(src + i);
+    }
+}
+
+cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_sms,
+                        cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count / 2 + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    const int64_t cap = (int64_t)num_sms * 4;
+    if (blocks > cap) blocks = cap;
+    copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Thread-per-row CSR product over bulk-copied tiles.
+//
+// Persistent CTAs walk tiles tile_begin + blockIdx.x + j * gridDim.x.  One
+// elected thread copies each tile's values, columns and row pointers into a
+// ring of ST shared-memory stages with cp.async.bulk (start addresses rounded
+// down to 16 bytes, sizes rounded up; the device arrays are padded so the
+// rounded reads stay in bounds).  Thread i of the CTA sums row r0 + i of the
+// tile in storage order with one DFMA per entry.
+// ------------------------------------------------------------------------
+template <int NT, int CAP>
+struct TileLayout {
+    static constexpr int VAL_N = CAP + 2;    // doubles: k0 rounded down to even, k1 up
+    static constexpr int COL_N = CAP + 8;    // ints: rounded to multiples of 4
+    static constexpr int PTR_N = NT + 8;     // ints: rows r0..r1 inclusive, rounded
+    static constexpr int VAL_OFF = 0;
+    static constexpr int COL_OFF = VAL_N * 8;
+    static constexpr int PTR_OFF = COL_OFF + COL_N * 4;
+    static constexpr int BYTES = PTR_OFF + PTR_N * 4;
+    static_assert(CAP % 4 == 0 && NT % 4 == 0, "16-byte aligned stage parts");
+    static_assert(BYTES % 16 == 0, "stage size keeps 16-byte alignment");
+};
+
+template <int NT, int CAP, int ST>
+__global__ void __launch_bounds__(NT) csr_tile_kernel(CsrArgs a, const Tile* __restrict__ tiles,
+                                                      int tile_begin, int tile_end) {
+    using L = TileLayout<NT, CAP>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[ST];
+    __shared__ double red[NT];
+
+    const int tid = threadIdx.x;
+    const int first = tile_begin + (int)blockIdx.x;
+    const int stride = (int)gridDim.x;
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // Producer: thread 0 issues the copies of the j-th tile of this CTA.
+    auto issue = [&](int j) {
+        const int t = first + j * stride;
+        if (t >= tile_end) return;
+        const int s = j % ST;
+        const Tile d = tiles[t];
+        const uint32_t bar = smem_u32(&bars[s]);
+        if (d.flags & TILE_LONG) {
+            mbar_arrive_expect_tx(bar, 0);
+            return;
+        }
+        const int va = d.k0 & ~1, vb = (d.k1 + 1) & ~1;
+        const int ca = d.k0 & ~3, cb = (d.k1 + 3) & ~3;
+        const int pa = d.r0 & ~3, pb = (d.r1 + 4) & ~3;
+        const uint32_t vbytes = (uint32_t)(vb - va) * 8u;
+        const uint32_t cbytes = (uint32_t)(cb - ca) * 4u;
+        const uint32_t pbytes = (uint32_t)(pb - pa) * 4u;
+        unsigned char* st = smem + (size_t)s * L::BYTES;
+        mbar_arrive_expect_tx(bar, vbytes + cbytes + pbytes);
+        if (vbytes) bulk_g2s(smem_u32(st + L::VAL_OFF), a.val + va, vbytes, bar);
+        if (cbytes) bulk_g2s(smem_u32(st + L::COL_OFF), a.col + ca, cbytes, bar);
+        bulk_g2s(smem_u32(st + L::PTR_OFF), a.ptr + pa, pbytes, bar);
+    };
+
+    if (tid == 0) {
+        for (int j = 0; j < ST - 1; ++j) issue(j);
+    }
+
+    int j = 0;
+    bool aborted = false;
+    for (;; ++j) {
+        const int t = first + j * stride;
+        if (t >= tile_end) break;
+        if (tid == 0) {
+            // stage (j-1) % ST was released by the barrier that ended j-1
+            fence_proxy_async_smem();
+            issue(j + ST - 1);
+        }
+        const int s = j % ST;
+        const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / ST) & 1), kWaitLimitNs);
+        // every thread leaves together if any wait gave up
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        const Tile d = tiles[t];
+        {
+            if (d.flags & TILE_LONG) {
+                // one row longer than a stage: the CTA sums it from global
+                // memory with a fixed-order tree, so the result is still
+                // independent of the launch.
+                const double* xb = a.x + d.xoff;
+                double part = 0.0;
+                for (int k = d.k0 + tid; k < d.k1; k += NT)
+                    part = fma(__ldg(a.val + k), __ldg(xb + __ldg(a.col + k)), part);
+                red[tid] = part;
+                __syncthreads();
+                for (int w = NT / 2; w > 0; w >>= 1) {
+                    if (tid < w) red[tid] += red[tid + w];
+                    __syncthreads();
+                }
+                if (tid == 0) store_row(a, d.r0, red[0]);
+            } else {
+                const int row = d.r0 + tid;
+                if (row < d.r1) {
+                    const unsigned char* st = smem + (size_t)s * L::BYTES;
+                    const double* vs = reinterpret_cast<const double*>(st + L::VAL_OFF);
+                    const int32_t* cs = reinterpret_cast<const int32_t*>(st + L::COL_OFF);
+                    const int32_t* ps = reinterpret_cast<const int32_t*>(st + L::PTR_OFF);
+                    const int va = d.k0 & ~1, ca = d.k0 & ~3, pa = d.r0 & ~3;
+                    const int kb = ps[row - pa] - va;
+                    const int ke = ps[row + 1 - pa] - va;
+                    const int dc = va - ca;   // column slot of value slot 0
+                    const double* xb = a.x + d.xoff;
+                    double sum = 0.0;
+#pragma unroll 4
+                    for (int k = kb; k < ke; ++k) sum = fma(vs[k], __ldg(xb + cs[k + dc]), sum);
+                    store_row(a, row, sum);
+                }
+            }
+        }
+        __syncthreads();   // stage s is free again
+    }
+    if (aborted && tid == 0) {
+        atomicExch(a.err, kErrTimeout);
+        // let the copies still in flight land before the CTA leaves
+        for (int jj = j + 1; jj < j + ST; ++jj) {
+            if (first + jj * stride >= tile_end) break;
+            mbar_wait_bounded(smem_u32(&bars[jj % ST]), (uint32_t)((jj / ST) & 1), kDrainLimitNs);
+        }
+    }
+}
+
+template <int NT, int CAP, int ST>
+static cudaError_t run_tile(const CsrArgs& a, const Tile* tiles, int tb, int te, int num_sms,
+                            cudaStream_t s) {
+    using L = TileLayout<NT, CAP>;
+    const size_t smem = (size_t)ST * L::BYTES;
+    static unsigned long long configured = 0;   // one bit per device ordinal
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev >= 64 || !(configured >> dev & 1ull)) {
+        cudaError_t e = cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ull << dev;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST>,
+                                                                  NT, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int n_tiles = te - tb;
+    int grid = num_sms * occ;
+    if (grid > n_tiles) grid = n_tiles;
+    csr_tile_kernel<NT, CAP, ST><<<grid, NT, smem, s>>>(a, tiles, tb, te);
+    return cudaGetLastError();
+}
+
+template <int NT, int CAP, int ST>
+static int ctas_per_sm_of() {
+    using L = TileLayout<NT, CAP>;
+    const size_t smem = (size_t)ST * L::BYTES;
+    cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST>, NT, smem) !=
+        cudaSuccess)
+        return 0;
+    return occ;
+}
+
+// The geometries compiled into the library (threads, entries per stage,
+// stages).  The plan builds its tiles for one of them.
+#define SPMV_TILE_GEOMS(X) \
+    X(128, 3456, 4)        \
+    X(128, 3456, 2)        \
+    X(256, 4096, 3)        \
+    X(256, 6912, 2)        \
+    X(128, 2048, 6)
+
+TileGeom default_tile_geom() { return TileGeom{128, 3456, 4}; }
+
+bool tile_geom_supported(const TileGeom& g) {
+#define X(nt, cap, st) \
+    if (g.threads == nt && g.nnz_cap == cap && g.stages == st) return true;
+    SPMV_TILE_GEOMS(X)
+#undef X
+    return false;
+}
+
+int tile_ctas_per_sm(const TileGeom& g) {
+#define X(nt, cap, st) \
+    if (g.threads == nt && g.nnz_cap == cap && g.stages == st) return ctas_per_sm_of<nt, cap, st>();
+    SPMV_TILE_GEOMS(X)
+#undef X
+    return 0;
+}
+
+cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
+                        const TileGeom& g, int num_sms, cudaStream_t s) {
+    if (tile_end <= tile_begin) return cudaSuccess;
+#define X(nt, cap, st) \
+    if (g.threads == nt && g.nnz_cap == cap && g.stages == st) \
+        return run_tile<nt, cap, st>(a, tiles, tile_begin, tile_end, num_sms, s);
+    SPMV_TILE_GEOMS(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------------
+// Vector-per-row CSR: V lanes share a row; each lane reads 4 consecutive
+// entries per step with 128-bit loads (two double2 values, one int4 of
+// columns) from a 4-aligned start, masks entries outside the row, and the
+// V partial sums meet in a fixed xor-butterfly.  Rows come from the same
+// tile table (rows r0..r1 with their x offset).
+// ------------------------------------------------------------------------
+template <int V>
+__global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* __restrict__ tiles,
+                                                         int tile_begin, int tile_end) {
+    constexpr int GROUPS = 256 / V;
+    const int lane = threadIdx.x % V;
+    const int group = threadIdx.x / V;
+    for (int t = tile_begin + (int)blockIdx.x; t < tile_end; t += (int)gridDim.x) {
+        const Tile d = tiles[t];
+        const double* xb = a.x + d.xoff;
+        for (int rbase = d.r0; rbase < d.r1; rbase += GROUPS) {
+            const int row = rbase + group;
+            double sum = 0.0;
+            if (row < d.r1) {
+                const int kb = __ldg(a.ptr + row), ke = __ldg(a.ptr + row + 1);
+                for (int k4 = (kb & ~3) + 4 * lane; k4 < ke; k4 += 4 * V) {
+                    const int4 c = __ldg(reinterpret_cast<const int4*>(a.col + k4));
+                    const double2 v0 = __ldg(reinterpret_cast<const double2*>(a.val + k4));
+                    const double2 v1 = __ldg(reinterpret_cast<const double2*>(a.val + k4 + 2));
+                    if (k4 + 0 >= kb && k4 + 0 < ke) sum = fma(v0.x, __ldg(xb + c.x), sum);
+                    if (k4 + 1 >= kb && k4 + 1 < ke) sum = fma(v0.y, __ldg(xb + c.y), sum);
+                    if (k4 + 2 >= kb && k4 + 2 < ke) sum = fma(v1.x, __ldg(xb + c.z), sum);
+                    if (k4 + 3 >= kb && k4 + 3 < ke) sum = fma(v1.y, __ldg(xb + c.w), sum);
+                }
+            }
+#pragma unroll
+            for (int off = V / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off, V);
+            if (row < d.r1 && lane == 0) store_row(a, row, sum);
+        }
+    }
+}
+
+cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
+                          int lanes, int num_sms, cudaStream_t s) {
+    if (tile_end <= tile_begin) return cudaSuccess;
+    int grid = num_sms * 8;
+    if (grid > tile_end - tile_begin) grid = tile_end - tile_begin;
+    switch (lanes) {
+        case 2: csr_vector_kernel<2><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 4: csr_vector_kernel<4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 8: csr_vector_kernel<8><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 16: csr_vector_kernel<16><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 32: csr_vector_kernel<32><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spmvk

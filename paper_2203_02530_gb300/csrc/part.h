@@ -1,0 +1,119 @@
+// Plan object behind the opaque spmv_part handle (include/spmv.h).
+#pragma once
+
+#include "internal.h"
+#include "../../include/spmv.h"
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace spmvk {
+
+// Raised inside the library, turned into a status at the ABI.
+struct Fail {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const char* fmt, ...);
+void check_cuda(cudaError_t e, const char* what);
+
+// Device allocation owned by a plan.  Every array is padded by kPad bytes
+// (zero-filled) so that the 16-byte-rounded bulk copies and 128-bit vector
+// loads near the end of an array stay inside the allocation.
+constexpr size_t kPad = 256;
+
+struct DevArray {
+    void* p = nullptr;
+    size_t bytes = 0;   // payload bytes (without padding)
+};
+
+struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    const double* x = nullptr;
+    double* y = nullptr;
+};
+
+}  // namespace spmvk
+
+struct spmv_part {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0;
+    int P = 1;
+    int gran = SPMV_COARSE;
+    std::vector<int64_t> bounds;      // P+1 row bounds r_p
+
+    // sizes
+    int64_t nnz = 0, nnz_l = 0, nnz_r = 0, n_send = 0, n_rr = 0;
+    std::vector<int64_t> halo_off;    // P+1 destination offsets in the send buffer
+    std::vector<int64_t> seg_off;     // P*P+1 segment (dst p, src q) offsets
+    std::vector<int64_t> rr_off;      // P+1 offsets into the remote-row list per rank
+    std::vector<int64_t> pack_off;    // P+1 offsets into pack_pos per source rank
+
+    // device arrays
+    // A_L of every rank as one CSR over the n global rows with columns
+    // rebased to the owning block (x_L = x + r_p).
+    int32_t* l_ptr = nullptr;         // n+1
+    int32_t* l_col = nullptr;
+    double* l_val = nullptr;
+    // A_R compressed to the rows that have remote entries
+    int32_t* rr_row = nullptr;        // n_rr global row ids
+    int32_t* rr_ptr = nullptr;        // n_rr+1
+    int32_t* r_col = nullptr;         // positions in the receive buffer
+    double* r_val = nullptr;
+    int32_t* send_idx = nullptr;      // n_send global x indices
+    int32_t* pack_pos = nullptr;      // n_send send slots grouped by source rank
+    double* sendbuf = nullptr;
+    double* recvbuf = nullptr;
+    int* err = nullptr;               // device error word
+    double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
+    double* io_y = nullptr;
+
+    // tiles (thread-per-row and vector kernels)
+    spmvk::TileGeom geom{};
+    spmvk::Tile* ltiles = nullptr;
+    spmvk::Tile* rtiles = nullptr;
+    std::vector<int64_t> ltile_off;   // P+1
+    std::vector<int64_t> rtile_off;   // P+1
+    // merge-path tiles (built on first use of the merge variant)
+    spmvk::MergeTile* lmtiles = nullptr;
+    spmvk::MergeTile* rmtiles = nullptr;
+    spmvk::Carry* lcarry = nullptr;
+    spmvk::Carry* rcarry = nullptr;
+    std::vector<int64_t> lmtile_off;  // P+1
+    std::vector<int64_t> rmtile_off;  // P+1
+
+    int variant = SPMV_VARIANT_TILE;
+    int vparam = 0;
+
+    // DAG of the operations
+    int n_ops = 0;
+    std::vector<std::pair<int, int>> edges;
+    std::vector<std::vector<int>> preds;
+
+    // schedule runtime
+    std::vector<cudaEvent_t> op_ev;   // one per op
+    std::vector<cudaEvent_t> join_ev; // one per stream slot (grown on demand)
+    cudaEvent_t fork_ev = nullptr;
+    std::map<int64_t, spmvk::GraphRec> graphs;
+    int64_t next_graph = 1;
+    int64_t last_records = 0, last_waits = 0, last_launches = 0;
+
+    std::vector<spmvk::DevArray> allocs;   // everything to free
+    size_t device_bytes = 0;
+};
+
+namespace spmvk {
+void build_plan(spmv_part* pt, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                const double* vals);
+void build_tiles(spmv_part* pt, const TileGeom& g);
+void build_merge_tiles(spmv_part* pt);
+void* dev_alloc(spmv_part* pt, size_t bytes);
+void free_plan(spmv_part* pt);
+}  // namespace spmvk

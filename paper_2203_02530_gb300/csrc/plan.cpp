@@ -1,0 +1,307 @@
+// Partition plan of the row-partitioned SpMV (Sec. III-A, Fig. 3b of
+// Pearson, Javeed and Devine), built on the host once and kept in HBM:
+//   - P contiguous, even row blocks r_p = floor(p n / P);
+//   - A_L: the entries of block p whose column lies in the block, columns
+//     rebased so that x_L = x + r_p ("A_L x_L can be computed directly");
+//   - H_p: the distinct remote columns of block p, ascending ("A is static,
+//     so the entries that make up x_R are fixed");
+//   - A_R: the remaining entries, columns renumbered to positions in the
+//     receive buffer (the column-compressed off-diagonal block), stored only
+//     for rows that have remote entries;
+//   - send buffer slots destination-major, then source rank, then ascending
+//     column, so destination p's part is x[H_p] and the exchange is one copy.
+#include "part.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace spmvk {
+
+void fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    throw Fail{code, std::string(buf)};
+}
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    cudaGetLastError();   // clear a non-sticky error
+    if (e == cudaErrorMemoryAllocation) fail(SPMV_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    fail(SPMV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* dev_alloc(spmv_part* pt, size_t bytes) {
+    void* p = nullptr;
+    const size_t total = bytes + kPad;
+    check_cuda(cudaMalloc(&p, total), "cudaMalloc");
+    pt->allocs.push_back(DevArray{p, bytes});
+    pt->device_bytes += total;
+    cudaError_t e = cudaMemset(p, 0, total);
+    check_cuda(e, "cudaMemset");
+    return p;
+}
+
+template <class T>
+static T* upload(spmv_part* pt, const std::vector<T>& h) {
+    T* d = static_cast<T*>(dev_alloc(pt, h.size() * sizeof(T)));
+    if (!h.empty())
+        check_cuda(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice),
+                   "upload");
+    return d;
+}
+
+static void free_one(spmv_part* pt, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < pt->allocs.size(); ++i) {
+        if (pt->allocs[i].p == p) {
+            cudaFree(p);
+            pt->device_bytes -= pt->allocs[i].bytes + kPad;
+            pt->allocs.erase(pt->allocs.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+void free_plan(spmv_part* pt) {
+    for (auto& g : pt->graphs)
+        if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    pt->graphs.clear();
+    for (cudaEvent_t e : pt->op_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : pt->join_ev)
+        if (e) cudaEventDestroy(e);
+    if (pt->fork_ev) cudaEventDestroy(pt->fork_ev);
+    pt->op_ev.clear();
+    pt->join_ev.clear();
+    pt->fork_ev = nullptr;
+    for (auto& a : pt->allocs) cudaFree(a.p);
+    pt->allocs.clear();
+    pt->device_bytes = 0;
+}
+
+void build_plan(spmv_part* pt, int64_t n, const int64_t* rp, const int32_t* ci,
+                const double* va) {
+    const int P = pt->P;
+    if (n < 0) fail(SPMV_EINVAL, "n = %lld < 0", (long long)n);
+    if (n >= (int64_t(1) << 31)) fail(SPMV_EBOUNDS, "n = %lld needs 64-bit columns", (long long)n);
+    if (P < 1) fail(SPMV_EINVAL, "P = %d < 1", P);
+    if (P > 1024) fail(SPMV_EBOUNDS, "P = %d above the limit 1024", P);
+    if (!rp) fail(SPMV_EINVAL, "row_ptr is NULL");
+    const int64_t base = rp[0];
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) fail(SPMV_EINVAL, "row_ptr decreases at row %lld", (long long)i);
+    const int64_t nnz = rp[n] - base;
+    if (nnz >= (int64_t(1) << 31) - 64) fail(SPMV_EBOUNDS, "nnz = %lld too large", (long long)nnz);
+    if (nnz > 0 && (!ci || !va)) fail(SPMV_EINVAL, "col_idx or vals is NULL");
+    for (int64_t k = base; k < rp[n]; ++k)
+        if (ci[k] < 0 || ci[k] >= n)
+            fail(SPMV_EINVAL, "column %d out of range at entry %lld", ci[k], (long long)(k - base));
+
+    pt->n = n;
+    pt->nnz = nnz;
+    pt->bounds.resize(P + 1);
+    for (int p = 0; p <= P; ++p) pt->bounds[p] = (int64_t)p * n / P;
+    const std::vector<int64_t>& B = pt->bounds;
+
+    // ---- split rows into A_L (global row order) and A_R (compressed rows)
+    std::vector<int32_t> l_ptr(n + 1, 0), l_col;
+    std::vector<double> l_val;
+    std::vector<int32_t> rr_row, rr_ptr(1, 0), r_col;
+    std::vector<double> r_val;
+    int64_t n_local = 0;
+    l_col.reserve((size_t)nnz);
+    l_val.reserve((size_t)nnz);
+    pt->rr_off.assign(P + 1, 0);
+    pt->halo_off.assign(P + 1, 0);
+    std::vector<int32_t> send_idx;
+    std::vector<int32_t> stamp(n > 0 ? (size_t)n : 1, -1), pos(n > 0 ? (size_t)n : 1, 0);
+    std::vector<int32_t> distinct;
+    for (int p = 0; p < P; ++p) {
+        const int64_t rb = B[p], re = B[p + 1];
+        pt->rr_off[p] = (int64_t)rr_row.size();
+        const size_t r_first = r_col.size();
+        for (int64_t i = rb; i < re; ++i) {
+            int32_t nr = 0;
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t c = ci[k];
+                if (c >= rb && c < re) {
+                    l_col.push_back((int32_t)(c - rb));
+                    l_val.push_back(va[k]);
+                    ++n_local;
+                } else {
+                    r_col.push_back(c);   // global column for now
+                    r_val.push_back(va[k]);
+                    if (stamp[(size_t)c] != p) {
+                        stamp[(size_t)c] = p;
+                        distinct.push_back(c);
+                    }
+                    ++nr;
+                }
+            }
+            l_ptr[(size_t)i + 1] = (int32_t)n_local;
+            if (nr) {
+                rr_row.push_back((int32_t)i);
+                rr_ptr.push_back((int32_t)r_col.size());
+            }
+        }
+        // H_p: the distinct remote columns, ascending; a column's slot in
+        // the receive buffer is halo_off[p] + its rank in H_p
+        pt->halo_off[p] = (int64_t)send_idx.size();
+        std::sort(distinct.begin(), distinct.end());
+        for (int32_t c : distinct) {
+            pos[(size_t)c] = (int32_t)send_idx.size();
+            send_idx.push_back(c);
+        }
+        distinct.clear();
+        for (size_t k = r_first; k < r_col.size(); ++k) r_col[k] = pos[(size_t)r_col[k]];
+    }
+    pt->rr_off[P] = (int64_t)rr_row.size();
+    pt->halo_off[P] = (int64_t)send_idx.size();
+    pt->nnz_l = n_local;
+    pt->nnz_r = (int64_t)r_col.size();
+    pt->n_send = (int64_t)send_idx.size();
+    pt->n_rr = (int64_t)rr_row.size();
+
+    // ---- segments (dst p, src q): H_p is ascending and q's columns are a
+    // contiguous range, so each segment is a contiguous slice of p's part
+    pt->seg_off.assign((size_t)P * P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        const int32_t* h0 = send_idx.data() + pt->halo_off[p];
+        const int32_t* h1 = send_idx.data() + pt->halo_off[p + 1];
+        for (int q = 0; q < P; ++q) {
+            const int32_t* at = std::lower_bound(h0, h1, (int32_t)B[q]);
+            pt->seg_off[(size_t)p * P + q] = pt->halo_off[p] + (at - h0);
+        }
+    }
+    pt->seg_off[(size_t)P * P] = pt->n_send;
+
+    // ---- send slots grouped by source rank (per-rank Pack ops)
+    std::vector<int32_t> pack_pos;
+    pack_pos.reserve((size_t)pt->n_send);
+    pt->pack_off.assign(P + 1, 0);
+    for (int q = 0; q < P; ++q) {
+        pt->pack_off[q] = (int64_t)pack_pos.size();
+        for (int p = 0; p < P; ++p) {
+            const int64_t s0 = pt->seg_off[(size_t)p * P + q];
+            const int64_t s1 = pt->seg_off[(size_t)p * P + q + 1];
+            for (int64_t k = s0; k < s1; ++k) pack_pos.push_back((int32_t)k);
+        }
+    }
+    pt->pack_off[P] = (int64_t)pack_pos.size();
+
+    // ---- upload
+    pt->l_ptr = upload(pt, l_ptr);
+    pt->l_col = upload(pt, l_col);
+    pt->l_val = upload(pt, l_val);
+    pt->rr_row = upload(pt, rr_row);
+    pt->rr_ptr = upload(pt, rr_ptr);
+    pt->r_col = upload(pt, r_col);
+    pt->r_val = upload(pt, r_val);
+    pt->send_idx = upload(pt, send_idx);
+    pt->pack_pos = upload(pt, pack_pos);
+    pt->sendbuf = static_cast<double*>(dev_alloc(pt, (size_t)pt->n_send * sizeof(double)));
+    pt->recvbuf = static_cast<double*>(dev_alloc(pt, (size_t)pt->n_send * sizeof(double)));
+    pt->err = static_cast<int*>(dev_alloc(pt, sizeof(int)));
+}
+
+// Greedy row tiles of one CSR row range: consecutive rows while the tile
+// holds at most g.threads rows and g.nnz_cap entries; a row longer than the
+// capacity gets a tile of its own marked TILE_LONG.
+static void tile_range(const std::vector<int32_t>& ptr, int64_t rb, int64_t re, int32_t xoff,
+                       const TileGeom& g, std::vector<Tile>& out) {
+    int64_t r = rb;
+    while (r < re) {
+        const int64_t len = (int64_t)ptr[(size_t)r + 1] - ptr[(size_t)r];
+        if (len > g.nnz_cap) {
+            out.push_back(Tile{(int32_t)r, (int32_t)(r + 1), ptr[(size_t)r], ptr[(size_t)r + 1], xoff,
+                               TILE_LONG, 0, 0});
+            ++r;
+            continue;
+        }
+        const int64_t start = r;
+        int64_t cnt = 0;
+        while (r < re && r - start < g.threads) {
+            const int64_t l = (int64_t)ptr[(size_t)r + 1] - ptr[(size_t)r];
+            if (l > g.nnz_cap || cnt + l > g.nnz_cap) break;
+            cnt += l;
+            ++r;
+        }
+        out.push_back(Tile{(int32_t)start, (int32_t)r, ptr[(size_t)start], ptr[(size_t)r], xoff, 0, 0, 0});
+    }
+}
+
+template <class T>
+static std::vector<T> download(const T* d, size_t count) {
+    std::vector<T> h(count);
+    if (count) check_cuda(cudaMemcpy(h.data(), d, count * sizeof(T), cudaMemcpyDeviceToHost), "download");
+    return h;
+}
+
+void build_tiles(spmv_part* pt, const TileGeom& g) {
+    const int P = pt->P;
+    const std::vector<int32_t> l_ptr = download(pt->l_ptr, (size_t)pt->n + 1);
+    const std::vector<int32_t> rr_ptr = download(pt->rr_ptr, (size_t)pt->n_rr + 1);
+    std::vector<Tile> lt, rt;
+    pt->ltile_off.assign(P + 1, 0);
+    pt->rtile_off.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        pt->ltile_off[p] = (int64_t)lt.size();
+        tile_range(l_ptr, pt->bounds[p], pt->bounds[p + 1], (int32_t)pt->bounds[p], g, lt);
+        pt->rtile_off[p] = (int64_t)rt.size();
+        tile_range(rr_ptr, pt->rr_off[p], pt->rr_off[p + 1], 0, g, rt);
+    }
+    pt->ltile_off[P] = (int64_t)lt.size();
+    pt->rtile_off[P] = (int64_t)rt.size();
+    free_one(pt, pt->ltiles);
+    free_one(pt, pt->rtiles);
+    pt->ltiles = upload(pt, lt);
+    pt->rtiles = upload(pt, rt);
+    pt->geom = g;
+}
+
+// Merge-path tiles of every rank, local and remote, plus one carry slot
+// per tile.  Coordinates come from a device-side path search on the row
+// pointers the kernels use.
+void build_merge_tiles(spmv_part* pt) {
+    const int P = pt->P;
+    const int items = merge_items_per_tile();
+    std::vector<int32_t> l_ptr_b(P + 1), rr_ptr_b(P + 1);
+    for (int p = 0; p <= P; ++p) {
+        check_cuda(cudaMemcpy(&l_ptr_b[p], pt->l_ptr + pt->bounds[p], 4, cudaMemcpyDeviceToHost), "merge plan");
+        check_cuda(cudaMemcpy(&rr_ptr_b[p], pt->rr_ptr + pt->rr_off[p], 4, cudaMemcpyDeviceToHost), "merge plan");
+    }
+    pt->lmtile_off.assign(P + 1, 0);
+    pt->rmtile_off.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        const int64_t li = (pt->bounds[p + 1] - pt->bounds[p]) + (int64_t)(l_ptr_b[p + 1] - l_ptr_b[p]);
+        const int64_t ri = (pt->rr_off[p + 1] - pt->rr_off[p]) + (int64_t)(rr_ptr_b[p + 1] - rr_ptr_b[p]);
+        pt->lmtile_off[p + 1] = pt->lmtile_off[p] + (li + items - 1) / items;
+        pt->rmtile_off[p + 1] = pt->rmtile_off[p] + (ri + items - 1) / items;
+    }
+    free_one(pt, pt->lmtiles);
+    free_one(pt, pt->rmtiles);
+    free_one(pt, pt->lcarry);
+    free_one(pt, pt->rcarry);
+    pt->lmtiles = static_cast<MergeTile*>(dev_alloc(pt, (size_t)pt->lmtile_off[P] * sizeof(MergeTile)));
+    pt->rmtiles = static_cast<MergeTile*>(dev_alloc(pt, (size_t)pt->rmtile_off[P] * sizeof(MergeTile)));
+    pt->lcarry = static_cast<Carry*>(dev_alloc(pt, (size_t)pt->lmtile_off[P] * sizeof(Carry)));
+    pt->rcarry = static_cast<Carry*>(dev_alloc(pt, (size_t)pt->rmtile_off[P] * sizeof(Carry)));
+    for (int p = 0; p < P; ++p) {
+        check_cuda(launch_merge_partition(pt->l_ptr, (int)pt->bounds[p], (int)pt->bounds[p + 1],
+                                          (int32_t)pt->bounds[p], pt->lmtiles + pt->lmtile_off[p],
+                                          (int)(pt->lmtile_off[p + 1] - pt->lmtile_off[p]), 0),
+                   "merge partition");
+        check_cuda(launch_merge_partition(pt->rr_ptr, (int)pt->rr_off[p], (int)pt->rr_off[p + 1], 0,
+                                          pt->rmtiles + pt->rmtile_off[p],
+                                          (int)(pt->rmtile_off[p + 1] - pt->rmtile_off[p]), 0),
+                   "merge partition");
+    }
+    check_cuda(cudaDeviceSynchronize(), "merge partition");
+}
+
+}  // namespace spmvk

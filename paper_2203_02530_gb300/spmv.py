@@ -1,0 +1,254 @@
+"""Python binding of the C ABI in ``include/spmv.h`` (ctypes).
+
+Functions carry the C names and only marshal arguments: device pointers are
+ints or objects with ``data_ptr()`` (PyTorch tensors), streams are ints or
+objects with ``cuda_stream`` (``torch.cuda.Stream``).  Every step of the
+product runs in ``libspmv.so``; there is no fallback: importing this module
+fails if the library is not built.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspmv.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "spmv.h")
+
+# status codes and selectors (include/spmv.h)
+OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
+COARSE, PER_PARTITION = 0, 1
+RUN_EAGER, RUN_CAPTURE, RUN_REPLAY = 0, 1, 2
+VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE = 0, 1, 2
+(Q_N, Q_P, Q_GRANULARITY, Q_NNZ, Q_NNZ_LOCAL, Q_NNZ_REMOTE, Q_N_SEND, Q_N_HALO,
+ Q_N_REMOTE_ROWS, Q_N_OPS, Q_N_EDGES, Q_ALG_BYTES, Q_ALG_BYTES_LOCAL,
+ Q_DEVICE_BYTES, Q_LAST_RECORDS, Q_LAST_WAITS, Q_ERROR, Q_LOCAL_VARIANT,
+ Q_N_LOCAL_TILES, Q_LAST_LAUNCHES) = range(20)
+(X_BOUNDS, X_L_PTR, X_L_COL, X_L_VAL, X_R_PTR, X_R_COL, X_R_VAL, X_HALO,
+ X_SEND_IDX, X_HALO_OFF, X_SEG_OFF, X_SENDBUF, X_RECVBUF) = range(13)
+_X_DTYPE = {X_BOUNDS: np.int64, X_L_PTR: np.int64, X_L_COL: np.int32,
+            X_L_VAL: np.float64, X_R_PTR: np.int64, X_R_COL: np.int32,
+            X_R_VAL: np.float64, X_HALO: np.int32, X_SEND_IDX: np.int32,
+            X_HALO_OFF: np.int64, X_SEG_OFF: np.int64, X_SENDBUF: np.float64,
+            X_RECVBUF: np.float64}
+
+
+class SpmvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("spmv error %d: %s" % (code, msg))
+        self.code = code
+
+
+def declared_functions():
+    """Names of the functions include/spmv.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spmv_\w+)\s*\(", text)))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libspmv.so is not built (run __graft_entry__.build() "
+                          "or python -m paper_2203_02530_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "spmv_part_create": [i64, vp, vp, vp, i32, i32, ctypes.POINTER(vp)],
+        "spmv_part_destroy": [vp],
+        "spmv_part_query": [vp, i32, i32, P64],
+        "spmv_part_export_len": [vp, i32, i32],
+        "spmv_part_export_plan": [vp, i32, i32, vp, i64],
+        "spmv_part_dag": [vp, vp, i64, P64],
+        "spmv_part_set_variant": [vp, i32, i32],
+        "spmv_pack": [vp, i32, vp, vp],
+        "spmv_local": [vp, i32, vp, vp, vp],
+        "spmv_halo_copy": [vp, i32, vp],
+        "spmv_remote": [vp, i32, vp, vp],
+        "spmv_schedule_run": [vp, vp, vp, i32, vp, i32, vp, vp, i32, P64],
+        "spmv_graph_destroy": [vp, i64],
+        "spmv_part_io_buffers": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
+        "spmv_apply_host": [vp, i64, vp, vp, vp],
+        "spmv_csr_merge": [i64, i64, vp, vp, vp, vp, vp, vp],
+        "spmv_csr_error": [P64],
+        "spmv_last_error": [],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L.spmv_part_export_len.restype = i64
+    L.spmv_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(a))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def spmv_last_error():
+    return lib.spmv_last_error().decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise SpmvError(rc, spmv_last_error())
+
+
+def spmv_part_create(n, row_ptr, col_idx, vals, P, granularity=COARSE):
+    """Build a plan from HOST CSR arrays; returns the opaque handle."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(vals, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(lib.spmv_part_create(int(n), _ptr(rp), _ptr(ci), _ptr(va), int(P),
+                                int(granularity), ctypes.byref(h)))
+    return h
+
+
+def spmv_part_destroy(h):
+    _check(lib.spmv_part_destroy(h))
+
+
+def spmv_part_query(h, what, part_idx=-1):
+    out = ctypes.c_int64()
+    _check(lib.spmv_part_query(h, int(what), int(part_idx), ctypes.byref(out)))
+    return out.value
+
+
+def spmv_part_export_len(h, what, part_idx=-1):
+    return int(lib.spmv_part_export_len(h, int(what), int(part_idx)))
+
+
+def spmv_part_export_plan(h, what, part_idx=-1):
+    n = spmv_part_export_len(h, what, part_idx)
+    if n < 0:
+        raise SpmvError(EINVAL, "bad export selector")
+    out = np.empty(n, dtype=_X_DTYPE[what])
+    _check(lib.spmv_part_export_plan(h, int(what), int(part_idx), _ptr(out), n))
+    return out
+
+
+def spmv_part_dag(h):
+    n = ctypes.c_int64()
+    _check(lib.spmv_part_dag(h, None, 0, ctypes.byref(n)))
+    buf = np.empty(2 * n.value, dtype=np.int32)
+    _check(lib.spmv_part_dag(h, _ptr(buf), n.value, ctypes.byref(n)))
+    return [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(n.value)]
+
+
+def spmv_part_set_variant(h, variant, param=0):
+    _check(lib.spmv_part_set_variant(h, int(variant), int(param)))
+
+
+def spmv_pack(h, part_idx, x_dev, stream):
+    _check(lib.spmv_pack(h, int(part_idx), _ptr(x_dev), _stream(stream)))
+
+
+def spmv_local(h, part_idx, x_dev, y_dev, stream):
+    _check(lib.spmv_local(h, int(part_idx), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_halo_copy(h, part_idx, stream):
+    _check(lib.spmv_halo_copy(h, int(part_idx), _stream(stream)))
+
+
+def spmv_remote(h, part_idx, y_dev, stream):
+    _check(lib.spmv_remote(h, int(part_idx), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_schedule_run(h, op_order, stream_of_op, streams, x_dev, y_dev,
+                      flags=RUN_EAGER, graph_handle=0):
+    """Run, capture or replay one implementation; returns the graph handle."""
+    order = np.ascontiguousarray(op_order, dtype=np.int32)
+    smap = np.ascontiguousarray(stream_of_op, dtype=np.int32)
+    sarr = (ctypes.c_void_p * len(streams))(*[_stream(s).value for s in streams])
+    g = ctypes.c_int64(int(graph_handle))
+    _check(lib.spmv_schedule_run(h, _ptr(order), _ptr(smap), len(order), sarr,
+                                 len(streams), _ptr(x_dev), _ptr(y_dev), int(flags),
+                                 ctypes.byref(g)))
+    return g.value
+
+
+def spmv_graph_destroy(h, graph_handle):
+    _check(lib.spmv_graph_destroy(h, int(graph_handle)))
+
+
+def spmv_part_io_buffers(h):
+    x = ctypes.c_void_p()
+    y = ctypes.c_void_p()
+    _check(lib.spmv_part_io_buffers(h, ctypes.byref(x), ctypes.byref(y)))
+    return x.value, y.value
+
+
+def spmv_apply_host(h, graph_handle, x_host, y_host, stream):
+    _check(lib.spmv_apply_host(h, int(graph_handle), _ptr(x_host), _ptr(y_host),
+                               _stream(stream)))
+
+
+def spmv_csr_merge(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_dev, stream):
+    _check(lib.spmv_csr_merge(int(n), int(nnz), _ptr(row_ptr_dev), _ptr(col_idx_dev),
+                              _ptr(vals_dev), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_csr_error():
+    out = ctypes.c_int64()
+    _check(lib.spmv_csr_error(ctypes.byref(out)))
+    return out.value
+
+
+class Part:
+    """Owns one plan handle; methods forward to the functions above."""
+
+    def __init__(self, n, row_ptr, col_idx, vals, P, granularity=COARSE):
+        self.h = spmv_part_create(n, row_ptr, col_idx, vals, P, granularity)
+        self.n, self.P, self.granularity = int(n), int(P), granularity
+
+    def close(self):
+        if self.h is not None:
+            spmv_part_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def query(self, what, part_idx=-1):
+        return spmv_part_query(self.h, what, part_idx)
+
+    def export(self, what, part_idx=-1):
+        return spmv_part_export_plan(self.h, what, part_idx)
+
+    def dag(self):
+        return spmv_part_dag(self.h)
+
+    @property
+    def n_ops(self):
+        return self.query(Q_N_OPS)
+
+    def set_variant(self, variant, param=0):
+        spmv_part_set_variant(self.h, variant, param)
+
+    def run(self, order, stream_of_op, streams, x, y, flags=RUN_EAGER, graph=0):
+        return spmv_schedule_run(self.h, order, stream_of_op, streams, x, y, flags, graph)

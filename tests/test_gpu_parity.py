@@ -1,0 +1,419 @@
+"""GPU parity: every kernel, operation and schedule of the library against
+the CPU oracle, through the C ABI.
+
+Plan arrays, pack and exchange buffers are compared bit for bit; y within
+the FP64 dot-product bound 1e-12 * sum_j |a_ij x_j| (exactly for integer
+data); every valid schedule must give a bit-identical y."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import schedules as OS
+from paper_2203_02530_gb300 import workloads as W
+from tests.gpu_util import assert_fp64_close, dev, reference, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _dense_row_matrix():
+    # one row holding 20000 entries among short rows: longer than a tile
+    # stage and spread over many merge tiles
+    n = 20000
+    rng = np.random.default_rng(21)
+    lens = rng.integers(0, 6, size=n)
+    lens[777] = n
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    cols = []
+    for i in range(n):
+        c = np.arange(n) if lens[i] == n else np.sort(rng.choice(n, size=lens[i], replace=False))
+        cols.append(c)
+    ci = np.concatenate(cols).astype(np.int32)
+    va = rng.uniform(-1, 1, size=ci.size)
+    return n, rp, ci, va
+
+
+def _empty_rows():
+    n = 1000
+    rp = np.zeros(n + 1, dtype=np.int64)
+    return n, rp, np.zeros(0, np.int32), np.zeros(0)
+
+
+CASES = {
+    "lap64": (lambda: W.laplacian_5pt(64), 2),
+    "st27_20": (lambda: W.stencil_27pt(20, seed=1), 4),
+    "st27_ragged": (lambda: W.stencil_27pt(0, seed=3, dims=(7, 13, 29)), 3),
+    "powerlaw": (lambda: W.powerlaw(40000, seed=3), 8),
+    "rand_dup": (lambda: W.random_csr(300, density=0.05, seed=4, duplicates=True,
+                                      shuffle_cols=True), 3),
+    "dense_row": (_dense_row_matrix, 4),
+    "empty_rows": (_empty_rows, 2),
+    "tiny_P_gt_n": (lambda: W.random_csr(5, density=0.6, seed=5), 8),
+    "one": (lambda: W.random_csr(1, density=1.0, seed=6, empty_rows=False), 1),
+    "band": (lambda: W.band(15000, 150000, 3750, seed=7), 4),
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        gen, P = CASES[name]
+        n, rp, ci, va = gen()
+        x = W.uniform_x(n, seed=99)
+        _cache[name] = (n, rp, ci, va, P, x)
+    return _cache[name]
+
+
+VARIANTS = [("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)] + [("merge", 0)]
+
+
+def make_part(n, rp, ci, va, P, gran=0):
+    from paper_2203_02530_gb300 import spmv
+    return spmv.Part(n, rp, ci, va, P, gran)
+
+
+def set_variant(part, v):
+    from paper_2203_02530_gb300 import spmv
+    kind, param = v
+    part.set_variant({"tile": spmv.VARIANT_TILE, "vector": spmv.VARIANT_VECTOR,
+                      "merge": spmv.VARIANT_MERGE}[kind], param)
+
+
+def run_default(part, x_d, y_d, stream):
+    """pack, local, copy, remote on one stream (the default schedule)."""
+    from paper_2203_02530_gb300 import spmv
+    spmv.spmv_pack(part.h, -1, x_d, stream)
+    spmv.spmv_local(part.h, -1, x_d, y_d, stream)
+    spmv.spmv_halo_copy(part.h, -1, stream)
+    spmv.spmv_remote(part.h, -1, y_d, stream)
+
+
+# ------------------------------------------------------------------ plan
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_plan_arrays_bit_exact(name):
+    from paper_2203_02530_gb300 import spmv
+    torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    ref = oracle.OraclePlan(n, rp, ci, va, P)
+    with make_part(n, rp, ci, va, P) as part:
+        pairs = [(spmv.X_BOUNDS, oracle.BOUNDS), (spmv.X_SEND_IDX, oracle.SEND_IDX),
+                 (spmv.X_HALO_OFF, oracle.HALO_OFF), (spmv.X_SEG_OFF, oracle.SEG_OFF)]
+        for a, b in pairs:
+            assert np.array_equal(part.export(a), ref.export(b)), a
+        per = [(spmv.X_L_PTR, oracle.L_PTR), (spmv.X_L_COL, oracle.L_COL),
+               (spmv.X_L_VAL, oracle.L_VAL), (spmv.X_R_PTR, oracle.R_PTR),
+               (spmv.X_R_COL, oracle.R_COL), (spmv.X_R_VAL, oracle.R_VAL),
+               (spmv.X_HALO, oracle.HALO)]
+        for p in range(P):
+            for a, b in per:
+                assert np.array_equal(part.export(a, p), ref.export(b, p)), (a, p)
+        assert part.query(spmv.Q_NNZ) == rp[-1] - rp[0]
+        assert part.query(spmv.Q_NNZ_LOCAL) + part.query(spmv.Q_NNZ_REMOTE) == rp[-1] - rp[0]
+
+
+# ------------------------------------------------------------------ pack / copy
+@pytest.mark.parametrize("name", ["lap64", "st27_ragged", "powerlaw", "rand_dup", "tiny_P_gt_n"])
+def test_pack_and_copy_bit_exact(name):
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    ref = oracle.OraclePlan(n, rp, ci, va, P)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    with make_part(n, rp, ci, va, P) as part:
+        # coarse
+        spmv.spmv_pack(part.h, -1, x_d, s)
+        spmv.spmv_halo_copy(part.h, -1, s)
+        s.synchronize()
+        ref.pack(-1, x)
+        ref.copy(-1)
+        assert np.array_equal(part.export(spmv.X_SENDBUF), ref.export(oracle.SENDBUF))
+        assert np.array_equal(part.export(spmv.X_RECVBUF), ref.export(oracle.RECVBUF))
+        # per rank, in an interleaved order, on a fresh vector
+        x2 = W.uniform_x(n, seed=5)
+        x2_d = dev(x2)
+        ref.clear_buffers()
+        for q in reversed(range(P)):
+            spmv.spmv_pack(part.h, q, x2_d, s)
+            ref.pack(q, x2)
+        for p in range(P):
+            spmv.spmv_halo_copy(part.h, p, s)
+            ref.copy(p)
+        s.synchronize()
+        assert np.array_equal(part.export(spmv.X_SENDBUF), ref.export(oracle.SENDBUF))
+        assert np.array_equal(part.export(spmv.X_RECVBUF), ref.export(oracle.RECVBUF))
+
+
+# ------------------------------------------------------------------ products
+@pytest.mark.parametrize("variant", VARIANTS, ids=lambda v: "%s%d" % v)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_product_parity_every_variant(name, variant):
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    y_d = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P) as part:
+        set_variant(part, variant)
+        run_default(part, x_d, y_d, s)
+        s.synchronize()
+        y1 = y_d.cpu().numpy()[:n].copy()
+        assert_fp64_close(y1, want, scale, "%s %s" % (name, variant))
+        run_default(part, x_d, y_d, s)
+        s.synchronize()
+        assert np.array_equal(y_d.cpu().numpy()[:n], y1), "not deterministic"
+        assert part.query(spmv.Q_ERROR) == 0
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=lambda v: "%s%d" % v)
+def test_integer_data_is_exact(variant):
+    torch = torch_cuda()
+    n, rp, ci, va = W.random_csr(2500, density=0.004, seed=8, integer=True, duplicates=True)
+    x = W.uniform_x(n, seed=9, integer=True)
+    want = oracle.csr_spmv(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, 5) as part:
+        set_variant(part, variant)
+        run_default(part, x_d, y_d, s)
+        s.synchronize()
+        assert np.array_equal(y_d.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------------ schedules
+def _sync_expect(dag_edges, smap):
+    rec, waits, _ = OS.sync_counts(dag_edges, smap)
+    return rec, waits
+
+
+@pytest.mark.parametrize("name", ["lap64", "st27_20", "powerlaw"])
+def test_every_coarse_schedule_gives_identical_y(name):
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P) as part:
+        edges = part.dag()
+        assert sorted(edges) == sorted(OS.coarse_dag()[1])
+        scheds = list(E.enumerate_schedules(E.Dag(4, edges), 2))
+        assert len(scheds) == 24
+        first = None
+        for order, smap in scheds:
+            y_d.fill_(float("nan"))
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
+            assert (part.query(spmv.Q_LAST_RECORDS), part.query(spmv.Q_LAST_WAITS)) == \
+                _sync_expect(edges, smap)
+            g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+            torch.cuda.synchronize()
+            ye = y_d.cpu().numpy().copy()
+            y_d.fill_(float("nan"))
+            torch.cuda.synchronize()
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            torch.cuda.synchronize()
+            yg = y_d.cpu().numpy()
+            assert np.array_equal(ye, yg)
+            if first is None:
+                first = ye
+                assert_fp64_close(ye, want, scale, name)
+            assert np.array_equal(ye, first), (order, smap)
+            spmv.spmv_graph_destroy(part.h, g)
+
+
+def _random_schedule(dag, n_streams, rng):
+    done, used, order, smap = 0, 0, [], [0] * dag.n_ops
+    while len(order) < dag.n_ops:
+        ready = dag.ready(done)
+        v = ready[rng.randrange(len(ready))]
+        s = rng.randrange(min(used + 1, n_streams))
+        order.append(v)
+        smap[v] = s
+        used = max(used, s + 1)
+        done |= 1 << v
+    return order, smap
+
+
+@pytest.mark.parametrize("name,variant", [("st27_ragged", ("tile", 0)), ("powerlaw", ("merge", 0)),
+                                          ("powerlaw", ("tile", 2)), ("band", ("vector", 4))])
+def test_per_partition_schedules_give_identical_y(name, variant):
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    ref = oracle.OraclePlan(n, rp, ci, va, P)
+    seg = ref.export(oracle.SEG_OFF)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P, spmv.PER_PARTITION) as part:
+        set_variant(part, variant)
+        edges = part.dag()
+        _, oedges = OS.per_partition_dag(P, lambda q, p: seg[p * P + q + 1] > seg[p * P + q])
+        assert sorted(edges) == sorted(oedges)
+        dag = E.Dag(4 * P, edges)
+        rng = random.Random(1)
+        first = None
+        for it in range(24):
+            order, smap = _random_schedule(dag, 4, rng)
+            y_d.fill_(float("nan"))
+            if it % 2:
+                g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+                part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            else:
+                part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
+                assert (part.query(spmv.Q_LAST_RECORDS), part.query(spmv.Q_LAST_WAITS)) == \
+                    _sync_expect(edges, smap)
+            torch.cuda.synchronize()
+            y = y_d.cpu().numpy().copy()
+            if it % 2:
+                spmv.spmv_graph_destroy(part.h, g)
+            if first is None:
+                first = y
+                assert_fp64_close(y, want, scale, name)
+            assert np.array_equal(y, first), (order, smap)
+
+
+def test_invalid_schedules_are_rejected_before_launch():
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case("lap64")
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    x_d = dev(x)
+    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P) as part:
+        bad = [([2, 0, 1, 3], [0, 0, 0, 0]),    # copy before pack
+               ([0, 2, 3, 1], [0, 0, 0, 0]),    # remote before local
+               ([0, 1, 2, 3], [0, 2, 0, 0]),    # stream out of range
+               ([0, 1, 2, 2], [0, 0, 0, 0]),    # op repeated
+               ([0, 1, 2], [0, 0, 0])]          # op missing
+        for order, smap in bad:
+            with pytest.raises(spmv.SpmvError) as e:
+                part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
+            assert e.value.code == spmv.ESCHED
+        torch.cuda.synchronize()
+        assert np.isnan(y_d.cpu().numpy()).all(), "something ran"
+        with pytest.raises(spmv.SpmvError) as e:
+            spmv.spmv_pack(part.h, P, x_d, streams[0])
+        assert e.value.code == spmv.EINVAL
+
+
+# ------------------------------------------------------------------ standalone merge
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_standalone_merge_product(name):
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    if rp[0] != 0:
+        pytest.skip("needs row_ptr[0] == 0")
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    # exact-size tensors: the kernel must stay inside each array
+    rp_d = dev(rp.astype(np.int32))
+    ci_d = dev(ci) if ci.size else torch.empty(0, dtype=torch.int32, device="cuda")
+    va_d = dev(va) if va.size else torch.empty(0, dtype=torch.float64, device="cuda")
+    x_d = dev(x) if n else torch.empty(0, dtype=torch.float64, device="cuda")
+    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    spmv.spmv_csr_merge(n, int(rp[-1]), rp_d, ci_d, va_d, x_d, y_d, s)
+    s.synchronize()
+    assert_fp64_close(y_d.cpu().numpy(), want, scale, name)
+    y1 = y_d.cpu().numpy().copy()
+    spmv.spmv_csr_merge(n, int(rp[-1]), rp_d, ci_d, va_d, x_d, y_d, s)
+    s.synchronize()
+    assert np.array_equal(y_d.cpu().numpy(), y1)
+    assert spmv.spmv_csr_error() == 0
+
+
+def test_standalone_merge_rejects_misaligned():
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case("lap64")
+    rp_d = dev(rp.astype(np.int32))
+    big = torch.zeros(ci.size + 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_csr_merge(n, int(rp[-1]), rp_d, big[1:], dev(va), dev(x),
+                            torch.empty(n, dtype=torch.float64, device="cuda"), None)
+    assert e.value.code == spmv.EINVAL
+
+
+# ------------------------------------------------------------------ host buffers
+def test_apply_host_buffers():
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case("st27_20")
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    with make_part(n, rp, ci, va, P) as part:
+        xi, yi = spmv.spmv_part_io_buffers(part.h)
+        g = part.run([0, 1, 2, 3], [0, 0, 0, 0], [s], xi, yi, spmv.RUN_CAPTURE)
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty(n, dtype=torch.float64).pin_memory()
+        spmv.spmv_apply_host(part.h, g, xh, yh, s)
+        assert_fp64_close(yh.numpy(), want, scale, "host path")
+        with pytest.raises(spmv.SpmvError):
+            g2 = part.run([0, 1, 2, 3], [0, 0, 0, 0], [s], dev(x), yi, spmv.RUN_CAPTURE)
+            spmv.spmv_apply_host(part.h, g2, xh, yh, s)
+
+
+# ------------------------------------------------------------------ full sizes
+def test_full_size_27pt_150_all_schedules():
+    """The 3-D 27-point stencil on 150^3 (n = 3 375 000, 89 915 392 entries),
+    P = 4, 2 streams, all 24 schedules captured as graphs: bit-identical y,
+    checked in full against the oracle."""
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    n, rp, ci, va = W.stencil_27pt(150, seed=1)
+    assert n == 3375000 and rp[-1] == 448 ** 3
+    x = W.uniform_x(n, seed=2)
+    want, scale = reference(n, rp, ci, va, x)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, 4) as part:
+        del ci, va
+        assert [part.query(spmv.Q_N_HALO, p) for p in range(4)] == [22650, 45150, 45150, 22650]
+        first = None
+        for order, smap in E.enumerate_schedules(E.Dag(4, part.dag()), 2):
+            g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+            y_d.fill_(float("nan"))
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            torch.cuda.synchronize()
+            y = y_d.cpu().numpy()
+            spmv.spmv_graph_destroy(part.h, g)
+            if first is None:
+                first = y.copy()
+                assert_fp64_close(first, want, scale, "27pt 150^3")
+            else:
+                assert np.array_equal(y, first)
+        assert part.query(spmv.Q_ERROR) == 0
+
+
+def test_full_size_powerlaw_4M_per_partition():
+    """Random power-law matrix, n = 4M, P = 8 per-rank DAG: merge-path and
+    thread-per-row products against the oracle in full."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va = W.powerlaw(4_000_000, seed=3)
+    x = W.uniform_x(n, seed=4)
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, 8, spmv.PER_PARTITION) as part:
+        for variant in (("merge", 0), ("tile", 2)):
+            set_variant(part, variant)
+            y_d.fill_(float("nan"))
+            order = [4 * p + k for k in (0, 1, 2, 3) for p in range(8)]
+            part.run(order, [0] * 32, [s], x_d, y_d, spmv.RUN_EAGER)
+            s.synchronize()
+            assert_fp64_close(y_d.cpu().numpy(), want, scale, "powerlaw %s" % (variant,))
