@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the row-partitioned FP64 SpMV hot path on one GB300.
+
+Workload: 3-D 27-point stencil on 150^3 (n = 3 375 000, 89 915 392 entries,
+values U[-1,1] with diagonal 27, seeds 1 and 2), P = 4 virtual ranks, 2
+streams.  Every valid schedule of the pack / local / copy / remote DAG is
+enumerated (24) and captured as a CUDA graph; each is measured with the
+paper's protocol (samples repeated for 0.01 s, Sec. III-C.3) and the fastest
+is the one timed.  A step is one replay of that graph: one whole SpMV.
+
+Output: one JSON line (rank 0).  ``value`` is effective GB/s = algorithmic
+bytes per SpMV x steps / time, summed over ranks (each rank runs its own
+replica: weak scaling, no data-path collective).  ``--impl reference`` times
+the CPU oracle on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV effective GB/s (% HBM peak), batched/served vs plain; p50/p99 latency"
+WORKLOAD = "27-point stencil 150^3 (n=3375000, nnz=89915392), P=4 row blocks, 2 streams, best of 24 schedules"
+FALLBACK_HBM = 6800.0
+
+
+# ---------------------------------------------------------------- ranks
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(dist, value, device=None):
+    """Largest value over ranks (barrier included)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None, period_ms=100):
+        self.uuid = uuid
+        self.period_ms = period_ms
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", str(self.period_ms)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [c.strip() for c in line.split(",")]
+                if len(f) < 9:
+                    continue
+                if self.uuid and self.uuid not in f[0] and f[0] not in self.uuid:
+                    continue
+                rows.append(f)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3])] or [0.0])}
+
+
+def clocks_rejected(c):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(c.get("reasons", [])):
+        return True
+    if c.get("sm_mhz") and c.get("sm_max_mhz") and c["sm_mhz"] < 0.6 * c["sm_max_mhz"] \
+            and "sw_power_cap" not in c.get("reasons", []):
+        return True
+    return False
+
+
+# ---------------------------------------------------------------- peaks
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "merge.cu"):
+        with open(os.path.join(ROOT, "paper_2203_02530_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_full_launch")
+
+
+# ---------------------------------------------------------------- workload
+def workload(seed_a=1, seed_x=2, g=150):
+    from paper_2203_02530_gb300 import workloads as W
+    n, rp, ci, va = W.stencil_27pt(g, seed=seed_a)
+    x = W.uniform_x(n, seed=seed_x)
+    return n, rp, ci, va, x
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(n, rp, ci, va, x, P, seconds):
+    """Time the oracle's partitioned SpMV (single thread) for about
+    `seconds`; returns (GB/s, reps, seconds, alg_bytes)."""
+    import oracle
+    pl = oracle.OraclePlan(n, rp, ci, va, P)
+    nnz = int(rp[-1] - rp[0])
+    nnz_r = sum(len(pl.export(oracle.R_COL, p)) for p in range(P))
+    nsend = len(pl.export(oracle.SEND_IDX))
+    rr = 0
+    for p in range(P):
+        r = pl.export(oracle.R_PTR, p)
+        rr += int((r[1:] > r[:-1]).sum())
+    alg = cpu_alg_bytes(n, nnz - nnz_r, nnz_r, rr, nsend)
+    pl.spmv(x)   # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        pl.spmv(x)
+        reps += 1
+        t = time.perf_counter() - t0
+        if t >= seconds:
+            break
+    pl.close()
+    return alg * reps / t / 1e9, reps, t, alg
+
+
+def cpu_alg_bytes(n, nnz_l, nnz_r, n_rr, n_send):
+    # the same counting as the library: local entries, row pointers, x, y;
+    # remote entries, its compressed rows and y update; pack, exchange, halo
+    b = 12 * nnz_l + 4 * (n + 1) + 8 * n + 8 * n
+    b += 12 * nnz_r + 4 * (n_rr + 1) + 4 * n_rr + 16 * n_rr
+    b += 12 * n_send + 16 * n_send + 8 * n_send
+    return b
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2203_02530_gb300 import autotune, benchmark, spmv
+    from paper_2203_02530_gb300 import schedules as E
+
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    n, rp, ci, va, x = workload()
+    P, S = 4, 2
+    part = spmv.Part(n, rp, ci, va, P, spmv.COARSE)
+    x_d = torch.from_numpy(x).to(dev)
+    y_d = torch.empty(n, dtype=torch.float64, device=dev)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
+    sig = autotune.signature(n, rp, P, props.name)
+    variant, vparam, tune_times = autotune.tune(part, x_d, y_d, streams[0], sig=sig,
+                                                use_cache=not args.retune)
+
+    # every schedule, captured once, measured with the paper's protocol
+    dag = E.Dag(part.n_ops, part.dag())
+    sched = []
+    for order, smap in E.enumerate_schedules(dag, S):
+        g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+        sample = lambda g=g, o=order, m=smap: part.run(o, m, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+        t = min(benchmark.measurements(sample, streams[0], 3))
+        sched.append((t, order, smap, g))
+    sched.sort(key=lambda r: r[0])
+    t_best, order, smap, g = sched[0]
+    spread = sched[-1][0] / sched[0][0]
+    for r in sched[1:]:
+        spmv.spmv_graph_destroy(part.h, r[3])
+    step = lambda: part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+    part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
+    launches_per_step = part.query(spmv.Q_LAST_LAUNCHES)
+    alg = part.query(spmv.Q_ALG_BYTES)
+    alg_local = part.query(spmv.Q_ALG_BYTES_LOCAL)
+    nnz_l = part.query(spmv.Q_NNZ_LOCAL)
+
+    def timed_region():
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_region")
+        e0.record(streams[0])
+        for _ in range(args.steps):
+            step()
+        e1.record(streams[0])
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if dist:
+            dist.barrier()
+        return e0.elapsed_time(e1) * 1e-3, clocks
+
+    elapsed, clocks = timed_region()
+    remeasured = False
+    if clocks_rejected(clocks):
+        elapsed, clocks = timed_region()
+        remeasured = True
+    elapsed = max_over_ranks(dist, elapsed, dev)
+    value = world * alg * args.steps / elapsed / 1e9
+
+    # the dominant kernel (LOCAL product), timed alone on the stream the
+    # schedule launches it on, with CUDA events
+    s_local = streams[smap[spmv.OP_LOCAL]]
+    t_local = benchmark.time_loop(lambda: spmv.spmv_local(part.h, -1, x_d, y_d, s_local),
+                                  s_local, max(50, min(args.steps, 1000)))
+    peak, peak_kind = hbm_peak()
+    achieved = alg_local / t_local / 1e9
+    kname = {spmv.VARIANT_TILE: "csr_tile_kernel", spmv.VARIANT_VECTOR: "csr_vector_kernel",
+             spmv.VARIANT_MERGE: "merge_kernel"}[variant]
+    traffic = profiled_traffic("%s/%d" % (kname, vparam))
+
+    # paper protocol: per-measurement latency percentiles of the best schedule
+    meas = benchmark.measurements(step, streams[0], args.measurements)
+
+    # end to end through the C ABI with host buffers
+    xi, yi = spmv.spmv_part_io_buffers(part.h)
+    ge = part.run(order, smap, streams, xi, yi, spmv.RUN_CAPTURE)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        spmv.spmv_apply_host(part.h, ge, xh, yh, streams[0])
+    k_e2e = max(10, min(args.steps, 200))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        spmv.spmv_apply_host(part.h, ge, xh, yh, streams[0])
+    t_e2e = max_over_ranks(dist, (time.perf_counter() - t0) / k_e2e, dev)
+    err = part.query(spmv.Q_ERROR)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, reps, secs, _ = oracle_rate(n, rp, ci, va, x, P, args.cpu_seconds)
+        cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "%d full partitioned SpMVs of the same matrix (P=4) in %.1f s, "
+                         "single-threaded C oracle on the host cores (nproc=%d)" % (
+                             reps, secs, os.cpu_count() or 0)}
+    part.close()
+    if rank != 0:
+        return None
+    sm_mhz = clocks.get("sm_mhz") or 0.0
+    fp64_peak = 2.0 * props.multi_processor_count * (sm_mhz or 2070.0) * 1e6   # DFMA/s
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed / args.steps * 1e3, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": int(rp[-1]), "P": P, "streams": S,
+                   "schedules": len(sched), "best_order": order, "best_streams": smap,
+                   "variant": [variant, vparam], "l2": "inputs larger than L2 (A is 1.08 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "alg_bytes_per_step": alg},
+        "percent_hbm": round(100.0 * value / world / peak, 2),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_local, "launch_us": round(t_local * 1e6, 2)},
+        "fp64": {"dfma_per_s": round(nnz_l / t_local / 1e9, 1), "unit": "G DFMA/s",
+                 "peak": round(fp64_peak / 1e9, 1), "frac": round(nnz_l / t_local / fp64_peak, 4),
+                 "note": "2 DFMA/clk/SM at the sampled SM clock"},
+        "latency_us": {"p50": round(benchmark.percentile(meas, 50) * 1e6, 2),
+                       "p99": round(benchmark.percentile(meas, 99) * 1e6, 2),
+                       "measurements": len(meas), "protocol": "0.01 s of samples each"},
+        "schedule_spread": round(spread, 4),
+        "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                "ms_per_step": round(t_e2e * 1e3, 4)},
+        "cpu_baseline": cpu,
+        "clocks": clocks, "remeasured": remeasured,
+        "gpu_launches": launches_per_step * args.steps,
+        "device_error_word": err,
+        "autotune_us": {"%d,%d" % k: round(v * 1e6, 1) for k, v in tune_times.items()},
+    }
+    return line
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    """The CPU oracle, as it stands, on the host cores; rank 0 only."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    # calibrate: size a 150 x 150 x Z slab of the same stencil so that
+    # warmup + steps samples end within the time budget
+    from paper_2203_02530_gb300 import workloads as W
+    budget = args.reference_budget
+    n8, rp8, ci8, va8 = W.stencil_27pt(0, seed=1, dims=(8, 150, 150))
+    rate, _, _, _ = oracle_rate(n8, rp8, ci8, va8, W.uniform_x(n8, seed=2), 4, 1.0)
+    per_step = budget / float(args.steps + args.warmup)
+    bytes_per_plane = 12 * 27 * 150 * 150
+    z = int(max(4, min(150, per_step * rate * 1e9 / bytes_per_plane)))
+    n, rp, ci, va = W.stencil_27pt(0, seed=1, dims=(z, 150, 150))
+    x = W.uniform_x(n, seed=2)
+    sample = ("27-point stencil %dx150x150 (n=%d, the full workload when z=150), P=4"
+              % (z, n))
+    P = 4
+    pl = oracle.OraclePlan(n, rp, ci, va, P)
+    nnz = int(rp[-1])
+    nnz_r = sum(len(pl.export(oracle.R_COL, p)) for p in range(P))
+    nsend = len(pl.export(oracle.SEND_IDX))
+    rr = sum(int((np.diff(pl.export(oracle.R_PTR, p)) > 0).sum()) for p in range(P))
+    alg = cpu_alg_bytes(n, nnz - nnz_r, nnz_r, rr, nsend)
+    for _ in range(args.warmup):
+        pl.spmv(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pl.spmv(x)
+    t = time.perf_counter() - t0
+    value = alg * args.steps / t / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "kind": "oracle", "cores": 1,
+                         "sample": sample + ", single-threaded C oracle (nproc=%d)" % (os.cpu_count() or 0)},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--measurements", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--reference-budget", type=float, default=90.0,
+                    help="seconds of oracle work the reference arm aims for")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        line = run_ours(args, world, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,76 @@
+"""Kernel-variant autotuner for the CSR products.
+
+Candidates are the variants compiled into the library: thread-per-row tile
+geometries, vector-per-row widths and the merge-path kernel.  Each is timed
+on the plan's LOCAL operation with CUDA events; the fastest wins.  Results
+are cached in a JSON file keyed by a matrix signature (size, entries, row
+length statistics, ranks) and the device name, so a plan of the same shape
+skips the search.
+"""
+import json
+import os
+
+import numpy as np
+
+from . import spmv
+from .benchmark import time_loop
+
+CACHE = os.environ.get("SPMV_TUNE_CACHE",
+                       os.path.join(os.path.expanduser("~"), ".cache", "spmv_gb300_tune.json"))
+
+CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
+              + [(spmv.VARIANT_VECTOR, w) for w in (2, 4, 8)]
+              + [(spmv.VARIANT_MERGE, 0)])
+
+
+def signature(n, row_ptr, P, device_name):
+    lens = np.diff(np.asarray(row_ptr))
+    if lens.size == 0:
+        stats = (0, 0, 0)
+    else:
+        stats = (int(lens.max()), round(float(lens.mean()), 1), round(float(lens.std()), 1))
+    return "n=%d nnz=%d max=%d mean=%.1f std=%.1f P=%d dev=%s" % (
+        n, int(row_ptr[-1] - row_ptr[0]), stats[0], stats[1], stats[2], P, device_name)
+
+
+def _load_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_cache(path, data):
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
+         cache_path=CACHE, use_cache=True):
+    """Pick the fastest variant for part's LOCAL product and apply it.
+    Returns (variant, param, {candidate: seconds})."""
+    cache = _load_cache(cache_path) if (use_cache and sig) else {}
+    if sig and sig in cache:
+        v, p = cache[sig]["best"]
+        part.set_variant(v, p)
+        return v, p, {tuple(int(c) for c in k.split(",")): t
+                      for k, t in cache[sig]["times"].items()}
+    times = {}
+    for v, p in candidates:
+        part.set_variant(v, p)
+        times[(v, p)] = time_loop(lambda: spmv.spmv_local(part.h, -1, x_dev, y_dev, stream),
+                                  stream, reps)
+    best = min(times, key=times.get)
+    part.set_variant(*best)
+    if sig and use_cache:
+        cache[sig] = {"best": list(best),
+                      "times": {"%d,%d" % k: t for k, t in times.items()}}
+        _save_cache(cache_path, cache)
+    return best[0], best[1], times

@@ -488,14 +488,15 @@ int spmv_part_set_variant(spmv_part* pt, int variant, int param) {
     if (!pt->graphs.empty()) fail(SPMV_EINVAL, "destroy the captured graphs before changing the variant");
     if (variant == SPMV_VARIANT_TILE) {
         static const spmvk::TileGeom geoms[] = {
-            {128, 3456, 4}, {128, 3456, 2}, {256, 4096, 3}, {256, 6912, 2}, {128, 2048, 6}};
+            {128, 3456, 2, 16}, {128, 3456, 2, 32}, {256, 6912, 2, 16}, {128, 3456, 4, 16}, {128, 2048, 3, 16}};
         const int ng = (int)(sizeof geoms / sizeof geoms[0]);
         if (param < 0 || param >= ng) fail(SPMV_EINVAL, "tile geometry %d not in [0, %d)", param, ng);
         const spmvk::TileGeom g = geoms[param];
         if (!spmvk::tile_geom_supported(g)) fail(SPMV_EINVAL, "tile geometry not compiled");
         check_cuda(cudaDeviceSynchronize(), "synchronize");
-        if (g.threads != pt->geom.threads || g.nnz_cap != pt->geom.nnz_cap || g.stages != pt->geom.stages)
+        if (g.threads != pt->geom.threads || g.nnz_cap != pt->geom.nnz_cap)
             spmvk::build_tiles(pt, g);
+        pt->geom = g;
     } else if (variant == SPMV_VARIANT_VECTOR) {
         if (param != 2 && param != 4 && param != 8 && param != 16 && param != 32)
             fail(SPMV_EINVAL, "vector width %d not in {2,4,8,16,32}", param);

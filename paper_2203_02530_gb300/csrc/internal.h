@@ -28,6 +28,7 @@ struct TileGeom {
     int threads;   // rows per tile (one thread per row)
     int nnz_cap;   // entries per tile stage
     int stages;    // shared-memory ring depth
+    int chunk;     // x gathers issued together per thread
 };
 
 // Merge-path tile: merge items [d0, d1) of the (row ends, entries) merge of

@@ -68,6 +68,31 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// Bulk copy with an L2 eviction policy (evict-first for data read once).
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Read-only load of x kept in L2 (x is gathered many times per product).
+__device__ __forceinline__ double ldg_keep(const double* p, uint64_t policy) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(policy));
+    return v;
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -164,10 +189,12 @@ struct TileLayout {
     static_assert(BYTES % 16 == 0, "stage size keeps 16-byte alignment");
 };
 
-template <int NT, int CAP, int ST>
-__global__ void __launch_bounds__(NT) csr_tile_kernel(CsrArgs a, const Tile* __restrict__ tiles,
+template <int NT, int CAP, int ST, int CH>
+__global__ void __launch_bounds__(NT, 1) csr_tile_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                       int tile_begin, int tile_end) {
     using L = TileLayout<NT, CAP>;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[ST];
     __shared__ double red[NT];
@@ -201,9 +228,9 @@ __global__ void __launch_bounds__(NT) csr_tile_kernel(CsrArgs a, const Tile* __r
         const uint32_t pbytes = (uint32_t)(pb - pa) * 4u;
         unsigned char* st = smem + (size_t)s * L::BYTES;
         mbar_arrive_expect_tx(bar, vbytes + cbytes + pbytes);
-        if (vbytes) bulk_g2s(smem_u32(st + L::VAL_OFF), a.val + va, vbytes, bar);
-        if (cbytes) bulk_g2s(smem_u32(st + L::COL_OFF), a.col + ca, cbytes, bar);
-        bulk_g2s(smem_u32(st + L::PTR_OFF), a.ptr + pa, pbytes, bar);
+        if (vbytes) bulk_g2s_hint(smem_u32(st + L::VAL_OFF), a.val + va, vbytes, bar, pol_stream);
+        if (cbytes) bulk_g2s_hint(smem_u32(st + L::COL_OFF), a.col + ca, cbytes, bar, pol_stream);
+        bulk_g2s_hint(smem_u32(st + L::PTR_OFF), a.ptr + pa, pbytes, bar, pol_stream);
     };
 
     if (tid == 0) {
@@ -257,8 +284,28 @@ __global__ void __launch_bounds__(NT) csr_tile_kernel(CsrArgs a, const Tile* __r
                     const int dc = va - ca;   // column slot of value slot 0
                     const double* xb = a.x + d.xoff;
                     double sum = 0.0;
-#pragma unroll 4
-                    for (int k = kb; k < ke; ++k) sum = fma(vs[k], __ldg(xb + cs[k + dc]), sum);
+                    // CH gathers of x in flight before their FMAs; the
+                    // FMAs still run in storage order
+                    for (int k = kb; k < ke; k += CH) {
+                        // slots past the row gather x[xoff] (a valid
+                        // address) so that every load is unconditional;
+                        // only the FMAs are masked
+                        // (branch-free, so the gathers can all be in
+                        // flight; a masked slot's FMA result is discarded)
+                        double xv[CH], vv[CH];
+#pragma unroll
+                        for (int u = 0; u < CH; ++u) {
+                            const bool m = k + u < ke;
+                            const int c = m ? cs[k + u + dc] : 0;
+                            vv[u] = m ? vs[k + u] : 0.0;
+                            xv[u] = ldg_keep(xb + c, pol_keep);
+                        }
+#pragma unroll
+                        for (int u = 0; u < CH; ++u) {
+                            const double t = fma(vv[u], xv[u], sum);
+                            sum = (k + u < ke) ? t : sum;
+                        }
+                    }
                     store_row(a, row, sum);
                 }
             }
@@ -275,7 +322,7 @@ __global__ void __launch_bounds__(NT) csr_tile_kernel(CsrArgs a, const Tile* __r
     }
 }
 
-template <int NT, int CAP, int ST>
+template <int NT, int CAP, int ST, int CH>
 static cudaError_t run_tile(const CsrArgs& a, const Tile* tiles, int tb, int te, int num_sms,
                             cudaStream_t s) {
     using L = TileLayout<NT, CAP>;
@@ -285,31 +332,31 @@ static cudaError_t run_tile(const CsrArgs& a, const Tile* tiles, int tb, int te,
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
     if (dev >= 64 || !(configured >> dev & 1ull)) {
-        cudaError_t e = cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST>,
+        cudaError_t e = cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) configured |= 1ull << dev;
     }
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH>,
                                                                   NT, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int n_tiles = te - tb;
     int grid = num_sms * occ;
     if (grid > n_tiles) grid = n_tiles;
-    csr_tile_kernel<NT, CAP, ST><<<grid, NT, smem, s>>>(a, tiles, tb, te);
+    csr_tile_kernel<NT, CAP, ST, CH><<<grid, NT, smem, s>>>(a, tiles, tb, te);
     return cudaGetLastError();
 }
 
-template <int NT, int CAP, int ST>
+template <int NT, int CAP, int ST, int CH>
 static int ctas_per_sm_of() {
     using L = TileLayout<NT, CAP>;
     const size_t smem = (size_t)ST * L::BYTES;
-    cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST>, NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH>, NT, smem) !=
         cudaSuccess)
         return 0;
     return occ;
@@ -318,25 +365,26 @@ static int ctas_per_sm_of() {
 // The geometries compiled into the library (threads, entries per stage,
 // stages).  The plan builds its tiles for one of them.
 #define SPMV_TILE_GEOMS(X) \
-    X(128, 3456, 4)        \
-    X(128, 3456, 2)        \
-    X(256, 4096, 3)        \
-    X(256, 6912, 2)        \
-    X(128, 2048, 6)
+    X(128, 3456, 2, 16)    \
+    X(128, 3456, 2, 32)    \
+    X(256, 6912, 2, 16)    \
+    X(128, 3456, 4, 16)    \
+    X(128, 2048, 3, 16)
 
-TileGeom default_tile_geom() { return TileGeom{128, 3456, 4}; }
+TileGeom default_tile_geom() { return TileGeom{128, 3456, 2, 16}; }
 
 bool tile_geom_supported(const TileGeom& g) {
-#define X(nt, cap, st) \
-    if (g.threads == nt && g.nnz_cap == cap && g.stages == st) return true;
+#define X(nt, cap, st, ch) \
+    if (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch) return true;
     SPMV_TILE_GEOMS(X)
 #undef X
     return false;
 }
 
 int tile_ctas_per_sm(const TileGeom& g) {
-#define X(nt, cap, st) \
-    if (g.threads == nt && g.nnz_cap == cap && g.stages == st) return ctas_per_sm_of<nt, cap, st>();
+#define X(nt, cap, st, ch) \
+    if (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch) \
+        return ctas_per_sm_of<nt, cap, st, ch>();
     SPMV_TILE_GEOMS(X)
 #undef X
     return 0;
@@ -345,9 +393,9 @@ int tile_ctas_per_sm(const TileGeom& g) {
 cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
                         const TileGeom& g, int num_sms, cudaStream_t s) {
     if (tile_end <= tile_begin) return cudaSuccess;
-#define X(nt, cap, st) \
-    if (g.threads == nt && g.nnz_cap == cap && g.stages == st) \
-        return run_tile<nt, cap, st>(a, tiles, tile_begin, tile_end, num_sms, s);
+#define X(nt, cap, st, ch) \
+    if (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch) \
+        return run_tile<nt, cap, st, ch>(a, tiles, tile_begin, tile_end, num_sms, s);
     SPMV_TILE_GEOMS(X)
 #undef X
     return cudaErrorInvalidValue;
@@ -364,6 +412,7 @@ template <int V>
 __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                          int tile_begin, int tile_end) {
     constexpr int GROUPS = 256 / V;
+    const uint64_t pol_keep = policy_evict_last();
     const int lane = threadIdx.x % V;
     const int group = threadIdx.x / V;
     for (int t = tile_begin + (int)blockIdx.x; t < tile_end; t += (int)gridDim.x) {
@@ -378,10 +427,19 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* 
                     const int4 c = __ldg(reinterpret_cast<const int4*>(a.col + k4));
                     const double2 v0 = __ldg(reinterpret_cast<const double2*>(a.val + k4));
                     const double2 v1 = __ldg(reinterpret_cast<const double2*>(a.val + k4 + 2));
-                    if (k4 + 0 >= kb && k4 + 0 < ke) sum = fma(v0.x, __ldg(xb + c.x), sum);
-                    if (k4 + 1 >= kb && k4 + 1 < ke) sum = fma(v0.y, __ldg(xb + c.y), sum);
-                    if (k4 + 2 >= kb && k4 + 2 < ke) sum = fma(v1.x, __ldg(xb + c.z), sum);
-                    if (k4 + 3 >= kb && k4 + 3 < ke) sum = fma(v1.y, __ldg(xb + c.w), sum);
+                    const bool m0 = k4 + 0 >= kb && k4 + 0 < ke, m1 = k4 + 1 >= kb && k4 + 1 < ke;
+                    const bool m2 = k4 + 2 >= kb && k4 + 2 < ke, m3 = k4 + 3 >= kb && k4 + 3 < ke;
+                    // masked slots read x[xoff]: entries of a neighbouring
+                    // row may index another rank's block
+                    const double x0 = ldg_keep(xb + (m0 ? c.x : 0), pol_keep);
+                    const double x1 = ldg_keep(xb + (m1 ? c.y : 0), pol_keep);
+                    const double x2 = ldg_keep(xb + (m2 ? c.z : 0), pol_keep);
+                    const double x3 = ldg_keep(xb + (m3 ? c.w : 0), pol_keep);
+                    double t;
+                    t = fma(v0.x, x0, sum); sum = m0 ? t : sum;
+                    t = fma(v0.y, x1, sum); sum = m1 ? t : sum;
+                    t = fma(v1.x, x2, sum); sum = m2 ? t : sum;
+                    t = fma(v1.y, x3, sum); sum = m3 ? t : sum;
                 }
             }
 #pragma unroll
