@@ -217,6 +217,34 @@ int spmv_csr_merge(int64_t n, int64_t nnz, const int32_t* row_ptr_dev,
                    const int32_t* col_idx_dev, const double* vals_dev,
                    const double* x_dev, double* y_dev, cudaStream_t s);
 
+/*
+ * spmv_csr_merge without any allocation: the same product, kernels and
+ * result as spmv_csr_merge, with its scratch (tile coordinates and row
+ * carries) in a fixed array compiled into the library instead of memory
+ * taken at call time.  The paper has no counterpart; this entry point is for
+ * callers that must not allocate device memory during a call: code that
+ * runs inside a host application owning every device allocation through its
+ * own fixed pool, latency-bound loops where an allocation may synchronise
+ * or grow a pool at an unpredictable moment, and work recorded into a CUDA
+ * graph whose owner does not accept memory-allocation nodes.
+ *   Limit: n + nnz <= 134 217 728 (65 536 tiles of 2048 merge items); larger
+ *   inputs fail with SPMV_EBOUNDS before anything is launched.  The array
+ *   takes 3 MiB on every GPU that loads the library, until the process exits.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call on a device uses the same array.  Each call rewrites
+ *   the part it reads before reading it, so leftovers of an earlier call are
+ *   never used, but calls whose work overlaps on the GPU (other streams, or
+ *   other host threads) race on the array and must be serialised by the
+ *   caller.
+ * Arguments, alignment, preconditions and other errors as spmv_csr_merge.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+int spmv_csr_merge_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr_dev,
+                           const int32_t* col_idx_dev, const double* vals_dev,
+                           const double* x_dev, double* y_dev, cudaStream_t s);
+
 /* Device error word of the plan-free entry points on the current device
  * (0 = none; SPMV_ETIMEOUT's magnitude after a bounded wait gave up); reads
  * and clears it, synchronising the device. */

@@ -682,6 +682,40 @@ int spmv_csr_merge(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t
     return SPMV_OK;
 }
 
+int spmv_csr_merge_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                           const double* vals, const double* x, double* y, cudaStream_t s) {
+    API_TRY
+    if (n < 0 || nnz < 0) fail(SPMV_EINVAL, "n = %lld, nnz = %lld", (long long)n, (long long)nnz);
+    const int64_t cap = spmvk::noalloc_max_items();
+    if (n + nnz > cap)
+        fail(SPMV_EBOUNDS, "n + nnz = %lld exceeds the fixed scratch of the no-allocation path (at most %lld)",
+             (long long)(n + nnz), (long long)cap);
+    if (n == 0) return SPMV_OK;
+    if (!row_ptr || !x || !y || (nnz > 0 && (!col_idx || !vals))) fail(SPMV_EINVAL, "NULL device pointer");
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(row_ptr) | reinterpret_cast<uintptr_t>(col_idx) |
+                          reinterpret_cast<uintptr_t>(vals) | reinterpret_cast<uintptr_t>(x) |
+                          reinterpret_cast<uintptr_t>(y);
+    if (mis & 15) fail(SPMV_EINVAL, "device arrays must be 16-byte aligned");
+    int dev = 0, sms = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    spmvk::CsrArgs a{};
+    a.ptr = row_ptr;
+    a.col = col_idx;
+    a.val = vals;
+    a.rowmap = nullptr;
+    a.x = x;
+    a.y = y;
+    a.accumulate = 0;
+    a.n_rows = (int)n;
+    a.nnz_total = (int)nnz;
+    a.guarded = 1;
+    a.err = nullptr;
+    check_cuda(spmvk::launch_merge_noalloc(a, sms, s), "no-allocation merge product");
+    API_CATCH
+    return SPMV_OK;
+}
+
 int spmv_csr_error(int64_t* out) {
     API_TRY
     need(out != nullptr, SPMV_EINVAL, "out is NULL");

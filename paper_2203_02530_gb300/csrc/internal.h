@@ -76,6 +76,8 @@ cudaError_t launch_merge_partition(const int32_t* ptr, int row_begin, int row_en
                                    MergeTile* tiles, int n_tiles, cudaStream_t s);
 int merge_items_per_tile();
 cudaError_t read_clear_csr_error(int* out);
+int64_t noalloc_max_items();
+cudaError_t launch_merge_noalloc(const CsrArgs& a, int num_sms, cudaStream_t s);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);
 TileGeom default_tile_geom();

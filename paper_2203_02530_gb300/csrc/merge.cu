@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 namespace spmvk {
 
 namespace {
@@ -367,6 +369,52 @@ cudaError_t read_clear_csr_error(int* out) {
     if (e != cudaSuccess) return e;
     const int zero = 0;
     return cudaMemcpyToSymbol(g_csr_err, &zero, sizeof(int));
+}
+
+// ------------------------------------------------------------------------
+// Fixed scratch for the no-allocation entry point.  Every GPU that loads the
+// library holds this array until the process exits.  Its name is only a
+// host-side stand-in in host code: the device address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+// ------------------------------------------------------------------------
+constexpr int kNoAllocMaxTiles = 65536;
+constexpr size_t kNoAllocTileBytes = (size_t)kNoAllocMaxTiles * sizeof(MergeTile);
+constexpr size_t kNoAllocBytes = kNoAllocTileBytes + (size_t)kNoAllocMaxTiles * sizeof(Carry);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+int64_t noalloc_max_items() { return (int64_t)kNoAllocMaxTiles * MERGE_ITEMS; }
+
+cudaError_t launch_merge_noalloc(const CsrArgs& a, int num_sms, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            g_noalloc_addr[dev] = base;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    const int64_t items = (int64_t)a.n_rows + a.nnz_total;
+    if (items > noalloc_max_items()) return cudaErrorInvalidValue;
+    const int n_tiles = (int)((items + MERGE_ITEMS - 1) / MERGE_ITEMS);
+    MergeTile* tiles = static_cast<MergeTile*>(base);
+    Carry* carries = reinterpret_cast<Carry*>(static_cast<unsigned char*>(base) + kNoAllocTileBytes);
+    // tiles [0, n_tiles) and their carries are rewritten before they are
+    // read, so nothing left by an earlier call is ever used
+    e = launch_merge_partition(a.ptr, 0, a.n_rows, 0, tiles, n_tiles, s);
+    if (e != cudaSuccess) return e;
+    return launch_merge(a, tiles, 0, n_tiles, carries, num_sms, s);
 }
 
 }  // namespace spmvk

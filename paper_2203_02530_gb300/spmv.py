@@ -72,6 +72,7 @@ def _load():
         "spmv_part_io_buffers": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
         "spmv_apply_host": [vp, i64, vp, vp, vp],
         "spmv_csr_merge": [i64, i64, vp, vp, vp, vp, vp, vp],
+        "spmv_csr_merge_noalloc": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_error": [P64],
         "spmv_last_error": [],
     }
@@ -208,6 +209,13 @@ def spmv_apply_host(h, graph_handle, x_host, y_host, stream):
 def spmv_csr_merge(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_dev, stream):
     _check(lib.spmv_csr_merge(int(n), int(nnz), _ptr(row_ptr_dev), _ptr(col_idx_dev),
                               _ptr(vals_dev), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_csr_merge_noalloc(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_dev, stream):
+    """spmv_csr_merge with its scratch in the library's fixed device array
+    (no allocation during the call; see include/spmv.h for the limit)."""
+    _check(lib.spmv_csr_merge_noalloc(int(n), int(nnz), _ptr(row_ptr_dev), _ptr(col_idx_dev),
+                                      _ptr(vals_dev), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
 
 
 def spmv_csr_error():
