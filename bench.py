@@ -210,39 +210,66 @@ def cpu_alg_bytes(n, nnz_l, nnz_r, n_rr, n_send):
 
 
 # ---------------------------------------------------------------- our arm
+WORKLOADS = {
+    # name: (description, generator, P, streams, granularity, search)
+    "stencil27": (WORKLOAD, lambda: workload(), 4, 2, 0, "exhaustive"),
+    "laplacian": ("5-point Laplacian 64x64 (n=4096, nnz=20224), P=2, 1 stream, the default "
+                  "schedule (pack, local, copy, remote); L2-resident: replay latency",
+                  lambda: laplacian(), 2, 1, 0, "fixed"),
+    "powerlaw": ("random power-law n=4M (Zipf(2) row lengths, cap 4096; 80% of columns within "
+                 "+-n/8), P=8 per-rank DAG (32 ops), 4 streams, MCTS-sampled schedules",
+                 lambda: powerlaw(), 8, 4, 1, "mcts"),
+}
+
+
+def laplacian():
+    from paper_2203_02530_gb300 import workloads as W
+    n, rp, ci, va = W.laplacian_5pt(64)
+    return n, rp, ci, va, W.uniform_x(n, seed=0)
+
+
+def powerlaw():
+    from paper_2203_02530_gb300 import workloads as W
+    n, rp, ci, va = W.powerlaw(4_000_000, seed=3)
+    return n, rp, ci, va, W.uniform_x(n, seed=4)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
     torch.cuda.set_device(local)
     dist = dist_init(world, "nccl")
-    from paper_2203_02530_gb300 import autotune, benchmark, spmv
-    from paper_2203_02530_gb300 import schedules as E
+    from paper_2203_02530_gb300 import autotune, benchmark, search, spmv
 
+    desc, gen, P, S, gran, mode = WORKLOADS[args.workload]
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
-    n, rp, ci, va, x = workload()
-    P, S = 4, 2
-    part = spmv.Part(n, rp, ci, va, P, spmv.COARSE)
+    n, rp, ci, va, x = gen()
+    part = spmv.Part(n, rp, ci, va, P, gran)
     x_d = torch.from_numpy(x).to(dev)
     y_d = torch.empty(n, dtype=torch.float64, device=dev)
     streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
     sig = autotune.signature(n, rp, P, props.name)
-    variant, vparam, tune_times = autotune.tune(part, x_d, y_d, streams[0], sig=sig,
-                                                use_cache=not args.retune)
+    tuned = autotune.tune(part, x_d, y_d, streams[0], sig=sig, use_cache=not args.retune)
+    variant, vparam = tuned["local"]
+    tune_times = tuned["times"]
 
-    # every schedule, captured once, measured with the paper's protocol
-    dag = E.Dag(part.n_ops, part.dag())
-    sched = []
-    for order, smap in E.enumerate_schedules(dag, S):
-        g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
-        sample = lambda g=g, o=order, m=smap: part.run(o, m, streams, x_d, y_d, spmv.RUN_REPLAY, g)
-        t = min(benchmark.measurements(sample, streams[0], 3))
-        sched.append((t, order, smap, g))
-    sched.sort(key=lambda r: r[0])
-    t_best, order, smap, g = sched[0]
-    spread = sched[-1][0] / sched[0][0]
-    for r in sched[1:]:
-        spmv.spmv_graph_destroy(part.h, r[3])
+    # the design space: every schedule (coarse DAG), MCTS samples (per-rank
+    # DAG) or the single default order
+    rec = search.Recorder(args.records, meta={"workload": args.workload}) if args.records else None
+    evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec, measurements=3
+                                      if mode == "exhaustive" else 1)
+    if mode == "exhaustive":
+        sched = search.exhaustive(part, streams, evaluate)
+    elif mode == "mcts":
+        sched, _ = search.mcts(part, streams, evaluate, args.mcts_iters, seed=0)
+    else:
+        order = list(range(part.n_ops))
+        sched = [(order, [0] * part.n_ops, evaluate(order, [0] * part.n_ops))]
+    sched.sort(key=lambda r: r[2])
+    order, smap, t_best = sched[0]
+    spread = sched[-1][2] / sched[0][2]
+    g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
     step = lambda: part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
     part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
     launches_per_step = part.query(spmv.Q_LAST_LAUNCHES)
@@ -281,15 +308,15 @@ def run_ours(args, world, rank, local):
     elapsed = max_over_ranks(dist, elapsed, dev)
     value = world * alg * args.steps / elapsed / 1e9
 
-    # the dominant kernel (LOCAL product), timed alone on the stream the
-    # schedule launches it on, with CUDA events
+    # the dominant kernel (LOCAL product, coarse launch), timed alone on the
+    # stream the schedule launches it on, with CUDA events
     s_local = streams[smap[spmv.OP_LOCAL]]
     t_local = benchmark.time_loop(lambda: spmv.spmv_local(part.h, -1, x_d, y_d, s_local),
                                   s_local, max(50, min(args.steps, 1000)))
     peak, peak_kind = hbm_peak()
     achieved = alg_local / t_local / 1e9
     kname = {spmv.VARIANT_TILE: "csr_tile_kernel", spmv.VARIANT_VECTOR: "csr_vector_kernel",
-             spmv.VARIANT_MERGE: "merge_kernel"}[variant]
+             spmv.VARIANT_MERGE: "merge_kernel", spmv.VARIANT_PAIRS: "csr_pair_kernel"}[variant]
     traffic = profiled_traffic("%s/%d" % (kname, vparam))
 
     # paper protocol: per-measurement latency percentiles of the best schedule
@@ -313,9 +340,9 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, reps, secs, _ = oracle_rate(n, rp, ci, va, x, P, args.cpu_seconds)
         cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "%d full partitioned SpMVs of the same matrix (P=4) in %.1f s, "
+               "sample": "%d full partitioned SpMVs of the same matrix (P=%d) in %.1f s, "
                          "single-threaded C oracle on the host cores (nproc=%d)" % (
-                             reps, secs, os.cpu_count() or 0)}
+                             reps, P, secs, os.cpu_count() or 0)}
     part.close()
     if rank != 0:
         return None
@@ -327,9 +354,13 @@ def run_ours(args, world, rank, local):
         "ms_per_step": round(elapsed / args.steps * 1e3, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "nnz": int(rp[-1]), "P": P, "streams": S,
-                   "schedules": len(sched), "best_order": order, "best_streams": smap,
-                   "variant": [variant, vparam], "l2": "inputs larger than L2 (A is 1.08 GB)",
+        "config": {"workload": desc, "n": n, "nnz": int(rp[-1]), "P": P, "streams": S,
+                   "granularity": "coarse" if gran == 0 else "per-rank",
+                   "search": mode, "schedules_measured": len(sched),
+                   "best_order": order, "best_streams": smap,
+                   "variant": {"local": list(tuned["local"]), "remote": list(tuned["remote"])},
+                   "l2": "inputs larger than L2" if 12 * int(rp[-1]) > 129e6
+                         else "L2-resident (replay latency)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "alg_bytes_per_step": alg},
         "percent_hbm": round(100.0 * value / world / peak, 2),
@@ -351,7 +382,8 @@ def run_ours(args, world, rank, local):
         "clocks": clocks, "remeasured": remeasured,
         "gpu_launches": launches_per_step * args.steps,
         "device_error_word": err,
-        "autotune_us": {"%d,%d" % k: round(v * 1e6, 1) for k, v in tune_times.items()},
+        "autotune_us": {"%s %d,%d" % ("local" if k[0] == spmv.OP_LOCAL else "remote", k[1], k[2]):
+                        round(v * 1e6, 1) for k, v in tune_times.items()},
     }
     return line
 
@@ -415,6 +447,11 @@ def main(argv=None):
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--reference-budget", type=float, default=90.0,
                     help="seconds of oracle work the reference arm aims for")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="stencil27",
+                    help="stencil27 (default): 27-point 150^3; laplacian: 5-point 64x64; "
+                         "powerlaw: n=4M with MCTS over the per-rank DAG")
+    ap.add_argument("--mcts-iters", type=int, default=2000)
+    ap.add_argument("--records", default=None, help="JSONL log of every measured schedule")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

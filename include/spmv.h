@@ -104,7 +104,9 @@ enum {
     SPMV_Q_ERROR = 16,            /* device error word (0 = none); synchronises */
     SPMV_Q_LOCAL_VARIANT = 17,
     SPMV_Q_N_LOCAL_TILES = 18,
-    SPMV_Q_LAST_LAUNCHES = 19     /* kernels launched by the last issue */
+    SPMV_Q_LAST_LAUNCHES = 19,    /* kernels launched by the last issue */
+    SPMV_Q_REMOTE_VARIANT = 20    /* 100 * variant + param of the REMOTE product
+                                     (SPMV_Q_LOCAL_VARIANT: of the LOCAL one) */
 };
 int spmv_part_query(const spmv_part* part, int what, int part_idx, int64_t* out);
 
@@ -135,13 +137,27 @@ int spmv_part_export_plan(const spmv_part* part, int what, int part_idx,
 int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
                   int64_t* n_pairs_out);
 
-/* Kernel variant of the LOCAL and REMOTE products. */
+/* Kernel variant of the LOCAL and REMOTE products (every variant gives the
+ * same y within the FP64 bound; each is deterministic on its own).
+ *   TILE   param = geometry 0..4: rows staged in shared memory by bulk
+ *          copies, 1 or 2 threads per row (the geometry fixes which)
+ *   VECTOR param = lanes per row (2..32), 4 entries per lane per step with
+ *          128-bit loads
+ *   PAIRS  param = lanes per row (1, 2, 4, 8), one aligned pair of entries per
+ *          lane per step, FMA count = the warp's longest share
+ *   MERGE  merge-path split with deterministic carries (param ignored)
+ * Fails with SPMV_EINVAL while captured graphs exist (they hold the old
+ * kernels' tables). */
 enum {
-    SPMV_VARIANT_TILE = 0,     /* thread-per-row over bulk-copied smem tiles */
-    SPMV_VARIANT_VECTOR = 1,   /* `param` lanes per row (2..32), 128-bit loads */
-    SPMV_VARIANT_MERGE = 2     /* merge-path split with deterministic carries */
+    SPMV_VARIANT_TILE = 0,
+    SPMV_VARIANT_VECTOR = 1,
+    SPMV_VARIANT_MERGE = 2,
+    SPMV_VARIANT_PAIRS = 3
 };
+/* Sets the variant of both products. */
 int spmv_part_set_variant(spmv_part* part, int variant, int param);
+/* Sets the variant of one product: op_kind SPMV_OP_LOCAL or SPMV_OP_REMOTE. */
+int spmv_part_set_op_variant(spmv_part* part, int op_kind, int variant, int param);
 
 /*
  * The four operations (Fig. 3c).  `part_idx` = -1 runs the op for every
@@ -249,6 +265,40 @@ int spmv_csr_merge_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr_dev,
  * (0 = none; SPMV_ETIMEOUT's magnitude after a bounded wait gave up); reads
  * and clears it, synchronising the device. */
 int spmv_csr_error(int64_t* out);
+
+/*
+ * Batched products: many independent CSR matrices (no partitioning) kept
+ * resident in HBM and multiplied in ONE persistent launch.  Work items are
+ * blocks of up to 256 rows of one matrix, claimed by CTAs through an atomic
+ * ticket; each row is summed by `lanes` lanes (set per matrix, e.g. by an
+ * autotuner) in a fixed order, so y is the same, bit for bit, as with
+ * spmv_batch_run_separate, which launches the same row code once per
+ * matrix.  Not part of the paper's method: a way of running many of its
+ * SpMVs at once.
+ * spmv_batch_create: `count` matrices given as HOST CSR arrays (n[m],
+ *   row_ptr[m][n[m]+1] int64, col_idx[m] int32 in [0, n[m]), vals[m]),
+ *   copied to the current device.  Errors as spmv_part_create.
+ * x_dev / y_dev: the concatenation of every matrix's x / y; matrix m's part
+ *   starts at spmv_batch_query(SPMV_BQ_OFFSET, m).
+ */
+typedef struct spmv_batch spmv_batch;
+enum {
+    SPMV_BQ_COUNT = 0, SPMV_BQ_TOTAL_ROWS = 1, SPMV_BQ_TOTAL_NNZ = 2, SPMV_BQ_ITEMS = 3,
+    SPMV_BQ_ALG_BYTES = 4,   /* 12 B/entry + 4 B/row pointer + 16 B/row (x read, y written) */
+    SPMV_BQ_OFFSET = 5, SPMV_BQ_N = 6, SPMV_BQ_NNZ = 7, SPMV_BQ_LANES = 8   /* of matrix m */
+};
+int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr,
+                      const int32_t* const* col_idx, const double* const* vals,
+                      spmv_batch** out);
+int spmv_batch_destroy(spmv_batch* batch);
+/* Lanes per row (1, 2, 4, 8, 16, 32) of matrix m, or of every matrix (m = -1). */
+int spmv_batch_set_lanes(spmv_batch* batch, int m, int lanes);
+int spmv_batch_query(const spmv_batch* batch, int what, int m, int64_t* out);
+/* Every product in one persistent launch on stream s. */
+int spmv_batch_run(spmv_batch* batch, const double* x_dev, double* y_dev, cudaStream_t s);
+/* The same products as one launch per matrix (only matrix m if m >= 0). */
+int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, double* y_dev,
+                            cudaStream_t s);
 
 /* Thread-local message describing the last failure of this thread. */
 const char* spmv_last_error(void);

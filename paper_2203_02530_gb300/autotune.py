@@ -20,6 +20,7 @@ CACHE = os.environ.get("SPMV_TUNE_CACHE",
 
 CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
               + [(spmv.VARIANT_VECTOR, w) for w in (2, 4, 8)]
+              + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8)]
               + [(spmv.VARIANT_MERGE, 0)])
 
 
@@ -54,23 +55,32 @@ def _save_cache(path, data):
 
 def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
          cache_path=CACHE, use_cache=True):
-    """Pick the fastest variant for part's LOCAL product and apply it.
-    Returns (variant, param, {candidate: seconds})."""
+    """Pick the fastest variant for each of part's products (LOCAL, then
+    REMOTE) and apply them.  Returns {"local": (variant, param),
+    "remote": (variant, param), "times": {(op, variant, param): seconds}}."""
     cache = _load_cache(cache_path) if (use_cache and sig) else {}
-    if sig and sig in cache:
-        v, p = cache[sig]["best"]
-        part.set_variant(v, p)
-        return v, p, {tuple(int(c) for c in k.split(",")): t
-                      for k, t in cache[sig]["times"].items()}
+    if sig and sig in cache and "local" in cache[sig]:
+        e = cache[sig]
+        part.set_op_variant(spmv.OP_LOCAL, *e["local"])
+        part.set_op_variant(spmv.OP_REMOTE, *e["remote"])
+        return {"local": tuple(e["local"]), "remote": tuple(e["remote"]),
+                "times": {tuple(int(c) for c in k.split(",")): t for k, t in e["times"].items()}}
     times = {}
-    for v, p in candidates:
-        part.set_variant(v, p)
-        times[(v, p)] = time_loop(lambda: spmv.spmv_local(part.h, -1, x_dev, y_dev, stream),
-                                  stream, reps)
-    best = min(times, key=times.get)
-    part.set_variant(*best)
+    ops = [(spmv.OP_LOCAL, lambda: spmv.spmv_local(part.h, -1, x_dev, y_dev, stream)),
+           (spmv.OP_REMOTE, lambda: spmv.spmv_remote(part.h, -1, y_dev, stream))]
+    best = {}
+    for op, run in ops:
+        for trial in range(2):   # two interleaved passes; keep the faster
+            for v, p in candidates:
+                part.set_op_variant(op, v, p)
+                t = time_loop(run, stream, reps)
+                times[(op, v, p)] = min(t, times.get((op, v, p), t))
+        b = min(((v, p) for v, p in candidates), key=lambda vp: times[(op,) + vp])
+        part.set_op_variant(op, *b)
+        best[op] = b
+    out = {"local": best[spmv.OP_LOCAL], "remote": best[spmv.OP_REMOTE], "times": times}
     if sig and use_cache:
-        cache[sig] = {"best": list(best),
-                      "times": {"%d,%d" % k: t for k, t in times.items()}}
+        cache[sig] = {"local": list(out["local"]), "remote": list(out["remote"]),
+                      "times": {"%d,%d,%d" % k: t for k, t in times.items()}}
         _save_cache(cache_path, cache)
-    return best[0], best[1], times
+    return out

@@ -19,6 +19,12 @@ int fail_status(int code, const std::string& msg) {
     return code;
 }
 
+}  // namespace
+
+void spmvk::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
 #define API_TRY try {
 #define API_CATCH                                                                         \
     }                                                                                     \
@@ -124,7 +130,9 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
     const std::vector<int64_t>& off = remote ? pt->rtile_off : pt->ltile_off;
     const int tb = (int)(p < 0 ? 0 : off[p]);
     const int te = (int)(p < 0 ? off[pt->P] : off[p + 1]);
-    if (pt->variant == SPMV_VARIANT_MERGE) {
+    const int var = pt->variant[remote ? 1 : 0];
+    const int param = pt->vparam[remote ? 1 : 0];
+    if (var == SPMV_VARIANT_MERGE) {
         const std::vector<int64_t>& mo = remote ? pt->rmtile_off : pt->lmtile_off;
         const int mb = (int)(p < 0 ? 0 : mo[p]);
         const int me = (int)(p < 0 ? mo[pt->P] : mo[p + 1]);
@@ -134,8 +142,16 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         return me > mb ? 2 : 0;
     }
     const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
-    if (pt->variant == SPMV_VARIANT_VECTOR) {
-        check_cuda(spmvk::launch_vector(a, tiles, tb, te, pt->vparam, pt->num_sms, s), "vector product");
+    if (var == SPMV_VARIANT_VECTOR || var == SPMV_VARIANT_PAIRS) {
+        const std::vector<int64_t>& bo = remote ? pt->rblock_off : pt->lblock_off;
+        const int bb = (int)(p < 0 ? 0 : bo[p]);
+        const int be = (int)(p < 0 ? bo[pt->P] : bo[p + 1]);
+        const spmvk::Tile* blocks = remote ? pt->rblocks : pt->lblocks;
+        if (var == SPMV_VARIANT_VECTOR)
+            check_cuda(spmvk::launch_vector(a, blocks, bb, be, param, pt->num_sms, s), "vector product");
+        else
+            check_cuda(spmvk::launch_pairs(a, blocks, bb, be, param, pt->num_sms, s), "pair product");
+        return be > bb;
     } else {
         check_cuda(spmvk::launch_tile(a, tiles, tb, te, pt->geom, pt->num_sms, s), "tile product");
     }
@@ -338,7 +354,8 @@ int spmv_part_query(const spmv_part* pt, int what, int part_idx, int64_t* out) {
             *out = h;
             break;
         }
-        case SPMV_Q_LOCAL_VARIANT: *out = pt->variant; break;
+        case SPMV_Q_LOCAL_VARIANT: *out = pt->variant[0] * 100 + pt->vparam[0]; break;
+        case SPMV_Q_REMOTE_VARIANT: *out = pt->variant[1] * 100 + pt->vparam[1]; break;
         case SPMV_Q_N_LOCAL_TILES: *out = pt->ltile_off.empty() ? 0 : pt->ltile_off[pt->P]; break;
         case SPMV_Q_LAST_LAUNCHES: *out = pt->last_launches; break;
         default: fail(SPMV_EINVAL, "unknown query %d", what);
@@ -482,32 +499,56 @@ int spmv_part_dag(const spmv_part* pt, int32_t* edges, int64_t cap_pairs, int64_
     return SPMV_OK;
 }
 
-int spmv_part_set_variant(spmv_part* pt, int variant, int param) {
-    API_TRY
-    check_part(pt);
+// Validates (variant, param) and prepares the tables it needs.
+static void prepare_variant(spmv_part* pt, int variant, int param) {
     if (!pt->graphs.empty()) fail(SPMV_EINVAL, "destroy the captured graphs before changing the variant");
     if (variant == SPMV_VARIANT_TILE) {
-        static const spmvk::TileGeom geoms[] = {
-            {128, 3456, 2, 16}, {128, 3456, 2, 32}, {256, 6912, 2, 16}, {128, 3456, 4, 16}, {128, 2048, 3, 16}};
+        static const spmvk::TileGeom geoms[] = {{256, 3456, 2, 16, 2},
+                                                {512, 6912, 2, 16, 2},
+                                                {256, 3456, 3, 16, 2},
+                                                {128, 3456, 2, 32, 1},
+                                                {256, 2048, 3, 8, 2}};
         const int ng = (int)(sizeof geoms / sizeof geoms[0]);
         if (param < 0 || param >= ng) fail(SPMV_EINVAL, "tile geometry %d not in [0, %d)", param, ng);
         const spmvk::TileGeom g = geoms[param];
         if (!spmvk::tile_geom_supported(g)) fail(SPMV_EINVAL, "tile geometry not compiled");
         check_cuda(cudaDeviceSynchronize(), "synchronize");
-        if (g.threads != pt->geom.threads || g.nnz_cap != pt->geom.nnz_cap)
+        if (g.rows() != pt->geom.rows() || g.nnz_cap != pt->geom.nnz_cap)
             spmvk::build_tiles(pt, g);
         pt->geom = g;
     } else if (variant == SPMV_VARIANT_VECTOR) {
         if (param != 2 && param != 4 && param != 8 && param != 16 && param != 32)
             fail(SPMV_EINVAL, "vector width %d not in {2,4,8,16,32}", param);
+    } else if (variant == SPMV_VARIANT_PAIRS) {
+        if (param != 1 && param != 2 && param != 4 && param != 8)
+            fail(SPMV_EINVAL, "lanes per row %d not in {1,2,4,8}", param);
     } else if (variant == SPMV_VARIANT_MERGE) {
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
     } else {
         fail(SPMV_EINVAL, "unknown variant %d", variant);
     }
-    pt->variant = variant;
-    pt->vparam = param;
+}
+
+int spmv_part_set_variant(spmv_part* pt, int variant, int param) {
+    API_TRY
+    check_part(pt);
+    prepare_variant(pt, variant, param);
+    pt->variant[0] = pt->variant[1] = variant;
+    pt->vparam[0] = pt->vparam[1] = param;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_part_set_op_variant(spmv_part* pt, int op_kind, int variant, int param) {
+    API_TRY
+    check_part(pt);
+    if (op_kind != SPMV_OP_LOCAL && op_kind != SPMV_OP_REMOTE)
+        fail(SPMV_EINVAL, "op kind %d has no product variant", op_kind);
+    prepare_variant(pt, variant, param);
+    const int i = op_kind == SPMV_OP_REMOTE ? 1 : 0;
+    pt->variant[i] = variant;
+    pt->vparam[i] = param;
     API_CATCH
     return SPMV_OK;
 }

@@ -25,10 +25,12 @@ enum { TILE_LONG = 1 };
 
 // Geometry of the thread-per-row tile kernel.
 struct TileGeom {
-    int threads;   // rows per tile (one thread per row)
+    int threads;   // threads per CTA
     int nnz_cap;   // entries per tile stage
     int stages;    // shared-memory ring depth
     int chunk;     // x gathers issued together per thread
+    int lanes;     // threads per row; a tile holds threads / lanes rows
+    int rows() const { return threads / lanes; }
 };
 
 // Merge-path tile: merge items [d0, d1) of the (row ends, entries) merge of
@@ -70,6 +72,8 @@ cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin,
                         int tile_end, const TileGeom& g, int num_sms, cudaStream_t s);
 cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
                           int lanes, int num_sms, cudaStream_t s);
+cudaError_t launch_pairs(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
+                         int lanes, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begin,
                          int tile_end, Carry* carries, int num_sms, cudaStream_t s);
 cudaError_t launch_merge_partition(const int32_t* ptr, int row_begin, int row_end, int32_t xoff,

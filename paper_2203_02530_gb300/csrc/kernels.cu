@@ -176,23 +176,24 @@ cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_s
 // rounded reads stay in bounds).  Thread i of the CTA sums row r0 + i of the
 // tile in storage order with one DFMA per entry.
 // ------------------------------------------------------------------------
-template <int NT, int CAP>
+template <int ROWS, int CAP>
 struct TileLayout {
     static constexpr int VAL_N = CAP + 2;    // doubles: k0 rounded down to even, k1 up
     static constexpr int COL_N = CAP + 8;    // ints: rounded to multiples of 4
-    static constexpr int PTR_N = NT + 8;     // ints: rows r0..r1 inclusive, rounded
+    static constexpr int PTR_N = ROWS + 8;   // ints: rows r0..r1 inclusive, rounded
     static constexpr int VAL_OFF = 0;
     static constexpr int COL_OFF = VAL_N * 8;
     static constexpr int PTR_OFF = COL_OFF + COL_N * 4;
     static constexpr int BYTES = PTR_OFF + PTR_N * 4;
-    static_assert(CAP % 4 == 0 && NT % 4 == 0, "16-byte aligned stage parts");
+    static_assert(CAP % 4 == 0 && ROWS % 4 == 0, "16-byte aligned stage parts");
     static_assert(BYTES % 16 == 0, "stage size keeps 16-byte alignment");
 };
 
-template <int NT, int CAP, int ST, int CH>
+template <int NT, int CAP, int ST, int CH, int LANES>
 __global__ void __launch_bounds__(NT, 1) csr_tile_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                       int tile_begin, int tile_end) {
-    using L = TileLayout<NT, CAP>;
+    static_assert(LANES == 1 || LANES == 2 || LANES == 4, "lanes per row");
+    using L = TileLayout<NT / LANES, CAP>;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     extern __shared__ __align__(128) unsigned char smem[];
@@ -272,42 +273,52 @@ __global__ void __launch_bounds__(NT, 1) csr_tile_kernel(CsrArgs a, const Tile* 
                 }
                 if (tid == 0) store_row(a, d.r0, red[0]);
             } else {
-                const int row = d.r0 + tid;
+                // LANES threads share a row: thread h takes entries
+                // kb + h, kb + h + LANES, ...; the FMA loop runs as many
+                // times as the warp's longest share, and the LANES partial
+                // sums meet in a fixed xor-butterfly
+                const int row = d.r0 + tid / LANES;
+                const int h = tid % LANES;
+                const unsigned char* st = smem + (size_t)s * L::BYTES;
+                const double* vs = reinterpret_cast<const double*>(st + L::VAL_OFF);
+                const int32_t* cs = reinterpret_cast<const int32_t*>(st + L::COL_OFF);
+                const int32_t* ps = reinterpret_cast<const int32_t*>(st + L::PTR_OFF);
+                const int va = d.k0 & ~1, ca = d.k0 & ~3, pa = d.r0 & ~3;
+                const int dc = va - ca;   // column slot of value slot 0
+                int kb = 0, cnt = 0;
                 if (row < d.r1) {
-                    const unsigned char* st = smem + (size_t)s * L::BYTES;
-                    const double* vs = reinterpret_cast<const double*>(st + L::VAL_OFF);
-                    const int32_t* cs = reinterpret_cast<const int32_t*>(st + L::COL_OFF);
-                    const int32_t* ps = reinterpret_cast<const int32_t*>(st + L::PTR_OFF);
-                    const int va = d.k0 & ~1, ca = d.k0 & ~3, pa = d.r0 & ~3;
-                    const int kb = ps[row - pa] - va;
+                    kb = ps[row - pa] - va + h;
                     const int ke = ps[row + 1 - pa] - va;
-                    const int dc = va - ca;   // column slot of value slot 0
-                    const double* xb = a.x + d.xoff;
-                    double sum = 0.0;
-                    // CH gathers of x in flight before their FMAs; the
-                    // FMAs still run in storage order
-                    for (int k = kb; k < ke; k += CH) {
-                        // slots past the row gather x[xoff] (a valid
-                        // address) so that every load is unconditional;
-                        // only the FMAs are masked
-                        // (branch-free, so the gathers can all be in
-                        // flight; a masked slot's FMA result is discarded)
-                        double xv[CH], vv[CH];
-#pragma unroll
-                        for (int u = 0; u < CH; ++u) {
-                            const bool m = k + u < ke;
-                            const int c = m ? cs[k + u + dc] : 0;
-                            vv[u] = m ? vs[k + u] : 0.0;
-                            xv[u] = ldg_keep(xb + c, pol_keep);
-                        }
-#pragma unroll
-                        for (int u = 0; u < CH; ++u) {
-                            const double t = fma(vv[u], xv[u], sum);
-                            sum = (k + u < ke) ? t : sum;
-                        }
-                    }
-                    store_row(a, row, sum);
+                    cnt = ke > kb ? (ke - kb + LANES - 1) / LANES : 0;
                 }
+                const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+                const double* xb = a.x + d.xoff;
+                double sum = 0.0;
+                for (int base = 0; base < wmax; base += CH) {
+                    // CH gathers in flight before their FMAs; slots past
+                    // the share read x[xoff] (a valid address) so every
+                    // load is unconditional, and their FMA results are
+                    // discarded; FMAs still run in storage order
+                    double xv[CH], vv[CH];
+#pragma unroll
+                    for (int u = 0; u < CH; ++u) {
+                        const bool m = base + u < cnt;
+                        const int k = kb + LANES * (base + u);
+                        const int c = m ? cs[k + dc] : 0;
+                        vv[u] = m ? vs[k] : 0.0;
+                        xv[u] = ldg_keep(xb + c, pol_keep);
+                    }
+#pragma unroll
+                    for (int u = 0; u < CH; ++u) {
+                        if (base + u >= wmax) break;   // warp-uniform
+                        const double t = fma(vv[u], xv[u], sum);
+                        sum = (base + u < cnt) ? t : sum;
+                    }
+                }
+#pragma unroll
+                for (int off = LANES / 2; off > 0; off >>= 1)
+                    sum += __shfl_xor_sync(0xffffffffu, sum, off, LANES);
+                if (row < d.r1 && h == 0) store_row(a, row, sum);
             }
         }
         __syncthreads();   // stage s is free again
@@ -322,41 +333,41 @@ __global__ void __launch_bounds__(NT, 1) csr_tile_kernel(CsrArgs a, const Tile* 
     }
 }
 
-template <int NT, int CAP, int ST, int CH>
+template <int NT, int CAP, int ST, int CH, int LANES>
 static cudaError_t run_tile(const CsrArgs& a, const Tile* tiles, int tb, int te, int num_sms,
                             cudaStream_t s) {
-    using L = TileLayout<NT, CAP>;
+    using L = TileLayout<NT / LANES, CAP>;
     const size_t smem = (size_t)ST * L::BYTES;
     static unsigned long long configured = 0;   // one bit per device ordinal
     int dev = 0;
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
     if (dev >= 64 || !(configured >> dev & 1ull)) {
-        cudaError_t e = cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH>,
+        cudaError_t e = cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH, LANES>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) configured |= 1ull << dev;
     }
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH, LANES>,
                                                                   NT, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int n_tiles = te - tb;
     int grid = num_sms * occ;
     if (grid > n_tiles) grid = n_tiles;
-    csr_tile_kernel<NT, CAP, ST, CH><<<grid, NT, smem, s>>>(a, tiles, tb, te);
+    csr_tile_kernel<NT, CAP, ST, CH, LANES><<<grid, NT, smem, s>>>(a, tiles, tb, te);
     return cudaGetLastError();
 }
 
-template <int NT, int CAP, int ST, int CH>
+template <int NT, int CAP, int ST, int CH, int LANES>
 static int ctas_per_sm_of() {
-    using L = TileLayout<NT, CAP>;
+    using L = TileLayout<NT / LANES, CAP>;
     const size_t smem = (size_t)ST * L::BYTES;
-    cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH, LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH>, NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH, LANES>, NT, smem) !=
         cudaSuccess)
         return 0;
     return occ;
@@ -364,27 +375,30 @@ static int ctas_per_sm_of() {
 
 // The geometries compiled into the library (threads, entries per stage,
 // stages).  The plan builds its tiles for one of them.
-#define SPMV_TILE_GEOMS(X) \
-    X(128, 3456, 2, 16)    \
-    X(128, 3456, 2, 32)    \
-    X(256, 6912, 2, 16)    \
-    X(128, 3456, 4, 16)    \
-    X(128, 2048, 3, 16)
+// (threads, entries per stage, stages, gathers per chunk, threads per row)
+#define SPMV_TILE_GEOMS(X)      \
+    X(256, 3456, 2, 16, 2)      \
+    X(512, 6912, 2, 16, 2)      \
+    X(256, 3456, 3, 16, 2)      \
+    X(128, 3456, 2, 32, 1)      \
+    X(256, 2048, 3, 8, 2)
 
-TileGeom default_tile_geom() { return TileGeom{128, 3456, 2, 16}; }
+TileGeom default_tile_geom() { return TileGeom{256, 3456, 2, 16, 2}; }
+
+#define GEOM_IS(nt, cap, st, ch, ln) \
+    (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch && g.lanes == ln)
 
 bool tile_geom_supported(const TileGeom& g) {
-#define X(nt, cap, st, ch) \
-    if (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch) return true;
+#define X(nt, cap, st, ch, ln) \
+    if (GEOM_IS(nt, cap, st, ch, ln)) return true;
     SPMV_TILE_GEOMS(X)
 #undef X
     return false;
 }
 
 int tile_ctas_per_sm(const TileGeom& g) {
-#define X(nt, cap, st, ch) \
-    if (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch) \
-        return ctas_per_sm_of<nt, cap, st, ch>();
+#define X(nt, cap, st, ch, ln) \
+    if (GEOM_IS(nt, cap, st, ch, ln)) return ctas_per_sm_of<nt, cap, st, ch, ln>();
     SPMV_TILE_GEOMS(X)
 #undef X
     return 0;
@@ -393,9 +407,9 @@ int tile_ctas_per_sm(const TileGeom& g) {
 cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
                         const TileGeom& g, int num_sms, cudaStream_t s) {
     if (tile_end <= tile_begin) return cudaSuccess;
-#define X(nt, cap, st, ch) \
-    if (g.threads == nt && g.nnz_cap == cap && g.stages == st && g.chunk == ch) \
-        return run_tile<nt, cap, st, ch>(a, tiles, tile_begin, tile_end, num_sms, s);
+#define X(nt, cap, st, ch, ln) \
+    if (GEOM_IS(nt, cap, st, ch, ln)) \
+        return run_tile<nt, cap, st, ch, ln>(a, tiles, tile_begin, tile_end, num_sms, s);
     SPMV_TILE_GEOMS(X)
 #undef X
     return cudaErrorInvalidValue;
@@ -447,6 +461,85 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* 
             if (row < d.r1 && lane == 0) store_row(a, row, sum);
         }
     }
+}
+
+// ------------------------------------------------------------------------
+// Pair-per-lane CSR: V lanes share a row; the row's entries are covered by
+// aligned pairs [k, k+1) (k even) and lane h takes pairs h, h+V, h+2V, ...
+// Each pair is one 16-byte load of values and one 8-byte load of columns.
+// FP64 cost on this part is per warp instruction whatever the active mask,
+// so the FMA loop runs exactly as many pairs as the warp's longest share
+// (warp-uniform), U pairs of gathers are in flight per lane, and the V
+// partial sums meet in a fixed xor-butterfly.  For a 27-entry row and V = 2
+// this is 14 FMA instructions + 1 add per 16 rows.
+// ------------------------------------------------------------------------
+template <int V, int U>
+__global__ void __launch_bounds__(256, 4) csr_pair_kernel(CsrArgs a, const Tile* __restrict__ tiles,
+                                                       int tile_begin, int tile_end) {
+    constexpr int GROUPS = 256 / V;
+    const uint64_t pol_keep = policy_evict_last();
+    const int lane = threadIdx.x % V;
+    const int group = threadIdx.x / V;
+    for (int t = tile_begin + (int)blockIdx.x; t < tile_end; t += (int)gridDim.x) {
+        const Tile d = tiles[t];
+        const double* xb = a.x + d.xoff;
+        for (int rbase = d.r0; rbase < d.r1; rbase += GROUPS) {
+            const int row = rbase + group;
+            int kb = 0, ke = 0, k2 = 0, cnt = 0;
+            if (row < d.r1) {
+                kb = __ldg(a.ptr + row);
+                ke = __ldg(a.ptr + row + 1);
+                k2 = kb & ~1;
+                const int npairs = (ke - k2 + 1) >> 1;
+                cnt = npairs > lane ? (npairs - lane + V - 1) / V : 0;
+            }
+            const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+            double sum = 0.0;
+            for (int j0 = 0; j0 < wmax; j0 += U) {
+                double2 vv[U];
+                double x0[U], x1[U];
+                bool m0[U], m1[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u;
+                    const bool act = j < cnt;
+                    const int k = act ? k2 + 2 * (lane + V * j) : k2;   // k2 is a valid even index
+                    vv[u] = __ldg(reinterpret_cast<const double2*>(a.val + k));
+                    const int2 c = __ldg(reinterpret_cast<const int2*>(a.col + k));
+                    m0[u] = act && k >= kb;
+                    m1[u] = act && k + 1 < ke;
+                    x0[u] = ldg_keep(xb + (m0[u] ? c.x : 0), pol_keep);
+                    x1[u] = ldg_keep(xb + (m1[u] ? c.y : 0), pol_keep);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (j0 + u >= wmax) break;   // warp-uniform
+                    double t0 = fma(vv[u].x, x0[u], sum);
+                    sum = m0[u] ? t0 : sum;
+                    t0 = fma(vv[u].y, x1[u], sum);
+                    sum = m1[u] ? t0 : sum;
+                }
+            }
+#pragma unroll
+            for (int off = V / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off, V);
+            if (row < d.r1 && lane == 0) store_row(a, row, sum);
+        }
+    }
+}
+
+cudaError_t launch_pairs(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end, int lanes,
+                         int num_sms, cudaStream_t s) {
+    if (tile_end <= tile_begin) return cudaSuccess;
+    int grid = num_sms * 8;
+    if (grid > tile_end - tile_begin) grid = tile_end - tile_begin;
+    switch (lanes) {
+        case 1: csr_pair_kernel<1, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 2: csr_pair_kernel<2, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 4: csr_pair_kernel<4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 8: csr_pair_kernel<8, 2><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,

@@ -23,7 +23,7 @@ namespace {
 constexpr int MERGE_NT = 256;                       // threads per CTA
 constexpr int MERGE_IPT = 8;                        // items per thread
 constexpr int MERGE_ITEMS = MERGE_NT * MERGE_IPT;   // items per tile
-constexpr int MERGE_ST = 3;                         // stages
+constexpr int MERGE_ST = 2;                         // stages
 
 struct MergeLayout {
     static constexpr int VAL_N = MERGE_ITEMS + 2;
@@ -111,7 +111,7 @@ __device__ __forceinline__ int path_search(int d, int a_len, int b_len, F A) {
 // the last 16-byte boundary inside each array and the few entries past it
 // are read from global memory.
 template <bool GUARD>
-__global__ void __launch_bounds__(MERGE_NT) merge_kernel(CsrArgs a, const MergeTile* __restrict__ tiles,
+__global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const MergeTile* __restrict__ tiles,
                                                          int tile_begin, int tile_end,
                                                          Carry* __restrict__ carries) {
     using L = MergeLayout;
@@ -119,6 +119,9 @@ __global__ void __launch_bounds__(MERGE_NT) merge_kernel(CsrArgs a, const MergeT
     __shared__ __align__(8) uint64_t bars[MERGE_ST];
     __shared__ int c_row[MERGE_NT];
     __shared__ double c_val[MERGE_NT];
+    __shared__ int w_key[MERGE_NT / 32];
+    __shared__ double w_val[MERGE_NT / 32];
+    __shared__ int w_start[MERGE_NT / 32];
 
     const int tid = threadIdx.x;
     const int first = tile_begin + (int)blockIdx.x;
@@ -205,6 +208,11 @@ __global__ void __launch_bounds__(MERGE_NT) merge_kernel(CsrArgs a, const MergeT
         const int d1 = d0 + MERGE_IPT < items ? d0 + MERGE_IPT : items;
         int i = path_search(d0, a_len, b_len, row_end_rel);
         int k = d0 - i;   // entries consumed, relative to k0
+        // the thread's range ends at (i_end, k_end); its entries are
+        // k .. k_end-1 (at most MERGE_IPT), gathered up front so the
+        // loads are in flight together
+        const int i_end = path_search(d1, a_len, b_len, row_end_rel);
+        const int k_end = d1 - i_end;
         // does this thread start inside a row whose earlier entries belong to
         // a previous thread or tile?
         bool open_head = (k + d.k0) > ptr_at(d.r0 + i);
@@ -213,58 +221,86 @@ __global__ void __launch_bounds__(MERGE_NT) merge_kernel(CsrArgs a, const MergeT
         double head_val = 0.0;
         double sum = 0.0;
         const double* xb = a.x + d.xoff;
-        for (int it = d0; it < d1; ++it) {
-            // the next item is an entry of row i unless row i ends here; once
-            // every row end of the tile is consumed only entries of row r1
-            // remain, and once every entry is consumed only row ends remain
-            if (k < b_len && (i >= a_len || k < row_end_rel(i))) {
-                const int kg = k + d.k0;
-                sum = fma(val_at(kg), __ldg(xb + col_at(kg)), sum);
-                ++k;
-                partial = true;
+        double vv[MERGE_IPT], xv[MERGE_IPT];
+#pragma unroll
+        for (int u = 0; u < MERGE_IPT; ++u) {
+            const bool m = k + u < k_end;
+            const int kg = k + u + d.k0;
+            vv[u] = m ? val_at(kg) : 0.0;
+            xv[u] = __ldg(xb + (m ? col_at(kg) : 0));
+        }
+        // walk the merge path: row end i comes before entry j when
+        // row_end(i) <= j; rows i < i_end end inside this range
+        auto close_row = [&]() {
+            if (open_head) {
+                head_row = i;
+                head_val = sum;
+                open_head = false;
             } else {
-                if (open_head) {
-                    head_row = i;
-                    head_val = sum;
-                    open_head = false;
-                } else {
-                    put(a, d.r0 + i, sum);
-                }
-                sum = 0.0;
-                partial = false;
-                ++i;
+                put(a, d.r0 + i, sum);
+            }
+            sum = 0.0;
+            partial = false;
+            ++i;
+        };
+#pragma unroll
+        for (int u = 0; u < MERGE_IPT; ++u) {
+            if (k + u < k_end) {
+                while (i < i_end && row_end_rel(i) <= k + u) close_row();
+                sum = fma(vv[u], xv[u], sum);
+                partial = true;
             }
         }
-        c_row[tid] = partial ? i : -1;
-        c_val[tid] = sum;
+        while (i < i_end) close_row();
+        k = k_end;
+        // Rows cut between threads: S[t] = the partial sums of the run of
+        // threads ending at t that carry t's open row, combined by a
+        // segmented scan in a fixed tree order (shuffles within a warp, then
+        // the earlier warps of the run), so the result is deterministic.
+        const int key = partial ? i : -1;   // row still open after t's items
+        c_row[tid] = key;
         __syncthreads();
-        // a row this thread finished after others started it: add their
-        // partial sums in thread order, then this thread's part
-        if (head_row >= 0) {
-            int t0 = tid;
-            while (t0 > 0 && c_row[t0 - 1] == head_row) --t0;
-            double tot = 0.0;
-            if (t0 < tid) {
-                tot = c_val[t0];
-                for (int u = t0 + 1; u < tid; ++u) tot += c_val[u];
-                tot += head_val;
-            } else {
-                tot = head_val;
+        const int lane = tid & 31, warp = tid >> 5;
+        double v = key >= 0 ? sum : 0.0;
+        int f = (key < 0 || tid == 0 || c_row[tid - 1] != key) ? 1 : 0;   // run starts here
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double vu = __shfl_up_sync(0xffffffffu, v, off);
+            const int fu = __shfl_up_sync(0xffffffffu, f, off);
+            if (lane >= off) {
+                if (!f) v = vu + v;
+                f |= fu;
             }
+        }
+        if (lane == 31) {
+            w_key[warp] = key;
+            w_val[warp] = v;
+            w_start[warp] = f;
+        }
+        __syncthreads();
+        if (!f) {   // the run began in an earlier warp
+            double cin = 0.0;
+            for (int w = warp - 1; w >= 0 && w_key[w] == key; --w) {
+                cin = w_val[w] + cin;
+                if (w_start[w]) break;
+            }
+            v = cin + v;
+        }
+        c_val[tid] = v;
+        __syncthreads();
+        // a row this thread finished after earlier threads started it
+        if (head_row >= 0) {
+            const double tot = (tid > 0 && c_row[tid - 1] == head_row) ? c_val[tid - 1] + head_val
+                                                                       : head_val;
             put(a, d.r0 + head_row, tot);
         }
-        // the tile's carry: the row still open after the last item
-        if (tid == 0) {
-            const int last = (items + MERGE_IPT - 1) / MERGE_IPT - 1;
+        // the tile's carry: the row still open after the tile's last item
+        const int last = (items + MERGE_IPT - 1) / MERGE_IPT - 1;
+        if (tid == (last >= 0 ? last : 0)) {
             Carry c{-1, 0, 0.0};
             if (last >= 0 && c_row[last] >= 0) {
-                const int r = c_row[last];
-                int t0 = last;
-                while (t0 > 0 && c_row[t0 - 1] == r) --t0;
-                double tot = c_val[t0];
-                for (int u = t0 + 1; u <= last; ++u) tot += c_val[u];
-                c.row = d.r0 + r;
-                c.val = tot;
+                c.row = d.r0 + c_row[last];
+                c.val = c_val[last];
             }
             carries[t] = c;
         }

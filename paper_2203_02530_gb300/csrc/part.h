@@ -22,6 +22,7 @@ struct Fail {
 };
 [[noreturn]] void fail(int code, const char* fmt, ...);
 void check_cuda(cudaError_t e, const char* what);
+void set_last_error(const std::string& msg);   // message of spmv_last_error()
 
 // Device allocation owned by a plan.  Every array is padded by kPad bytes
 // (zero-filled) so that the 16-byte-rounded bulk copies and 128-bit vector
@@ -81,6 +82,12 @@ struct spmv_part {
     spmvk::Tile* rtiles = nullptr;
     std::vector<int64_t> ltile_off;   // P+1
     std::vector<int64_t> rtile_off;   // P+1
+    // fixed 256-row blocks (vector and pair kernels): independent of the
+    // tile geometry so their passes of 256 / lanes rows are always full
+    spmvk::Tile* lblocks = nullptr;
+    spmvk::Tile* rblocks = nullptr;
+    std::vector<int64_t> lblock_off;  // P+1
+    std::vector<int64_t> rblock_off;  // P+1
     // merge-path tiles (built on first use of the merge variant)
     spmvk::MergeTile* lmtiles = nullptr;
     spmvk::MergeTile* rmtiles = nullptr;
@@ -89,8 +96,9 @@ struct spmv_part {
     std::vector<int64_t> lmtile_off;  // P+1
     std::vector<int64_t> rmtile_off;  // P+1
 
-    int variant = SPMV_VARIANT_TILE;
-    int vparam = 0;
+    // product variant of the LOCAL [0] and REMOTE [1] operations
+    int variant[2] = {SPMV_VARIANT_TILE, SPMV_VARIANT_TILE};
+    int vparam[2] = {0, 0};
 
     // DAG of the operations
     int n_ops = 0;

@@ -19,6 +19,8 @@
 
 namespace spmvk {
 
+constexpr int64_t kBlockRows = 256;
+
 void fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -210,7 +212,7 @@ void build_plan(spmv_part* pt, int64_t n, const int64_t* rp, const int32_t* ci,
 }
 
 // Greedy row tiles of one CSR row range: consecutive rows while the tile
-// holds at most g.threads rows and g.nnz_cap entries; a row longer than the
+// holds at most g.rows() rows and g.nnz_cap entries; a row longer than the
 // capacity gets a tile of its own marked TILE_LONG.
 static void tile_range(const std::vector<int32_t>& ptr, int64_t rb, int64_t re, int32_t xoff,
                        const TileGeom& g, std::vector<Tile>& out) {
@@ -225,7 +227,7 @@ static void tile_range(const std::vector<int32_t>& ptr, int64_t rb, int64_t re, 
         }
         const int64_t start = r;
         int64_t cnt = 0;
-        while (r < re && r - start < g.threads) {
+        while (r < re && r - start < g.rows()) {
             const int64_t l = (int64_t)ptr[(size_t)r + 1] - ptr[(size_t)r];
             if (l > g.nnz_cap || cnt + l > g.nnz_cap) break;
             cnt += l;
@@ -262,6 +264,28 @@ void build_tiles(spmv_part* pt, const TileGeom& g) {
     pt->ltiles = upload(pt, lt);
     pt->rtiles = upload(pt, rt);
     pt->geom = g;
+    if (!pt->lblocks) {
+        std::vector<Tile> lb, rb;
+        pt->lblock_off.assign(P + 1, 0);
+        pt->rblock_off.assign(P + 1, 0);
+        auto blocks = [](const std::vector<int32_t>& ptr, int64_t r0, int64_t r1, int32_t xoff,
+                         std::vector<Tile>& out) {
+            for (int64_t r = r0; r < r1; r += kBlockRows) {
+                const int64_t e = std::min(r1, r + kBlockRows);
+                out.push_back(Tile{(int32_t)r, (int32_t)e, ptr[(size_t)r], ptr[(size_t)e], xoff, 0, 0, 0});
+            }
+        };
+        for (int p = 0; p < P; ++p) {
+            pt->lblock_off[p] = (int64_t)lb.size();
+            blocks(l_ptr, pt->bounds[p], pt->bounds[p + 1], (int32_t)pt->bounds[p], lb);
+            pt->rblock_off[p] = (int64_t)rb.size();
+            blocks(rr_ptr, pt->rr_off[p], pt->rr_off[p + 1], 0, rb);
+        }
+        pt->lblock_off[P] = (int64_t)lb.size();
+        pt->rblock_off[P] = (int64_t)rb.size();
+        pt->lblocks = upload(pt, lb);
+        pt->rblocks = upload(pt, rb);
+    }
 }
 
 // Merge-path tiles of every rank, local and remote, plus one carry slot

@@ -21,11 +21,11 @@ OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
 COARSE, PER_PARTITION = 0, 1
 RUN_EAGER, RUN_CAPTURE, RUN_REPLAY = 0, 1, 2
-VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE = 0, 1, 2
+VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS = 0, 1, 2, 3
 (Q_N, Q_P, Q_GRANULARITY, Q_NNZ, Q_NNZ_LOCAL, Q_NNZ_REMOTE, Q_N_SEND, Q_N_HALO,
  Q_N_REMOTE_ROWS, Q_N_OPS, Q_N_EDGES, Q_ALG_BYTES, Q_ALG_BYTES_LOCAL,
  Q_DEVICE_BYTES, Q_LAST_RECORDS, Q_LAST_WAITS, Q_ERROR, Q_LOCAL_VARIANT,
- Q_N_LOCAL_TILES, Q_LAST_LAUNCHES) = range(20)
+ Q_N_LOCAL_TILES, Q_LAST_LAUNCHES, Q_REMOTE_VARIANT) = range(21)
 (X_BOUNDS, X_L_PTR, X_L_COL, X_L_VAL, X_R_PTR, X_R_COL, X_R_VAL, X_HALO,
  X_SEND_IDX, X_HALO_OFF, X_SEG_OFF, X_SENDBUF, X_RECVBUF) = range(13)
 _X_DTYPE = {X_BOUNDS: np.int64, X_L_PTR: np.int64, X_L_COL: np.int32,
@@ -63,6 +63,7 @@ def _load():
         "spmv_part_export_plan": [vp, i32, i32, vp, i64],
         "spmv_part_dag": [vp, vp, i64, P64],
         "spmv_part_set_variant": [vp, i32, i32],
+        "spmv_part_set_op_variant": [vp, i32, i32, i32],
         "spmv_pack": [vp, i32, vp, vp],
         "spmv_local": [vp, i32, vp, vp, vp],
         "spmv_halo_copy": [vp, i32, vp],
@@ -161,6 +162,10 @@ def spmv_part_set_variant(h, variant, param=0):
     _check(lib.spmv_part_set_variant(h, int(variant), int(param)))
 
 
+def spmv_part_set_op_variant(h, op_kind, variant, param=0):
+    _check(lib.spmv_part_set_op_variant(h, int(op_kind), int(variant), int(param)))
+
+
 def spmv_pack(h, part_idx, x_dev, stream):
     _check(lib.spmv_pack(h, int(part_idx), _ptr(x_dev), _stream(stream)))
 
@@ -257,6 +262,9 @@ class Part:
 
     def set_variant(self, variant, param=0):
         spmv_part_set_variant(self.h, variant, param)
+
+    def set_op_variant(self, op_kind, variant, param=0):
+        spmv_part_set_op_variant(self.h, op_kind, variant, param)
 
     def run(self, order, stream_of_op, streams, x, y, flags=RUN_EAGER, graph=0):
         return spmv_schedule_run(self.h, order, stream_of_op, streams, x, y, flags, graph)

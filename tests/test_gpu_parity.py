@@ -66,7 +66,8 @@ def case(name):
     return _cache[name]
 
 
-VARIANTS = [("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)] + [("merge", 0)]
+VARIANTS = ([("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)]
+            + [("pairs", v) for v in (1, 2, 4, 8)] + [("merge", 0)])
 
 
 def make_part(n, rp, ci, va, P, gran=0):
@@ -78,7 +79,7 @@ def set_variant(part, v):
     from paper_2203_02530_gb300 import spmv
     kind, param = v
     part.set_variant({"tile": spmv.VARIANT_TILE, "vector": spmv.VARIANT_VECTOR,
-                      "merge": spmv.VARIANT_MERGE}[kind], param)
+                      "merge": spmv.VARIANT_MERGE, "pairs": spmv.VARIANT_PAIRS}[kind], param)
 
 
 def run_default(part, x_d, y_d, stream):
@@ -183,6 +184,31 @@ def test_integer_data_is_exact(variant):
         run_default(part, x_d, y_d, s)
         s.synchronize()
         assert np.array_equal(y_d.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("name", ["st27_ragged", "powerlaw", "dense_row"])
+def test_local_and_remote_variants_chosen_separately(name):
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P) as part:
+        for lv, rv in [((spmv.VARIANT_PAIRS, 2), (spmv.VARIANT_MERGE, 0)),
+                       ((spmv.VARIANT_MERGE, 0), (spmv.VARIANT_VECTOR, 8)),
+                       ((spmv.VARIANT_TILE, 4), (spmv.VARIANT_PAIRS, 4))]:
+            part.set_op_variant(spmv.OP_LOCAL, *lv)
+            part.set_op_variant(spmv.OP_REMOTE, *rv)
+            assert part.query(spmv.Q_LOCAL_VARIANT) == 100 * lv[0] + lv[1]
+            assert part.query(spmv.Q_REMOTE_VARIANT) == 100 * rv[0] + rv[1]
+            y_d.fill_(float("nan"))
+            run_default(part, x_d, y_d, s)
+            s.synchronize()
+            assert_fp64_close(y_d.cpu().numpy(), want, scale, "%s %s %s" % (name, lv, rv))
+        with pytest.raises(spmv.SpmvError):
+            part.set_op_variant(spmv.OP_PACK, spmv.VARIANT_TILE, 0)
 
 
 # ------------------------------------------------------------------ schedules
