@@ -219,7 +219,16 @@ WORKLOADS = {
     "powerlaw": ("random power-law n=4M (Zipf(2) row lengths, cap 4096; 80% of columns within "
                  "+-n/8), P=8 per-rank DAG (32 ops), 4 streams, MCTS-sampled schedules",
                  lambda: powerlaw(), 8, 4, 1, "mcts"),
+    "band": ("the paper's band matrix: 150000 x 150000, 1.5M entries uniform in |i-j| <= 37500, "
+             "P=4, 2 streams, all 24 schedules; L2-resident (replay latency)",
+             lambda: band(), 4, 2, 0, "exhaustive"),
 }
+
+
+def band():
+    from paper_2203_02530_gb300 import workloads as W
+    n, rp, ci, va = W.band(150_000, 1_500_000, 37_500, seed=7)
+    return n, rp, ci, va, W.uniform_x(n, seed=8)
 
 
 def laplacian():
@@ -257,16 +266,27 @@ def run_ours(args, world, rank, local):
     # the design space: every schedule (coarse DAG), MCTS samples (per-rank
     # DAG) or the single default order
     rec = search.Recorder(args.records, meta={"workload": args.workload}) if args.records else None
+    if args.records:
+        with open(args.records + ".dag.json", "w") as f:
+            json.dump({"n_ops": part.n_ops, "edges": part.dag(), "P": P, "streams": S}, f)
+    search_cmp = None
     evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec, measurements=3
                                       if mode == "exhaustive" else 1)
     if mode == "exhaustive":
         sched = search.exhaustive(part, streams, evaluate)
     elif mode == "mcts":
         sched, _ = search.mcts(part, streams, evaluate, args.mcts_iters, seed=0)
+        if args.random_baseline:
+            rand = search.random_sampling(part, streams, evaluate, args.random_baseline, seed=1)
+            rt = [r[2] for r in rand]
+            mt = [r[2] for r in sched[:args.random_baseline]]
+            search_cmp = {"samples": len(rand),
+                          "random": {"best_us": round(min(rt) * 1e6, 2), "worst_us": round(max(rt) * 1e6, 2)},
+                          "mcts": {"best_us": round(min(mt) * 1e6, 2), "worst_us": round(max(mt) * 1e6, 2)}}
     else:
         order = list(range(part.n_ops))
         sched = [(order, [0] * part.n_ops, evaluate(order, [0] * part.n_ops))]
-    sched.sort(key=lambda r: r[2])
+    sched = sorted(sched, key=lambda r: r[2])
     order, smap, t_best = sched[0]
     spread = sched[-1][2] / sched[0][2]
     g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
@@ -316,7 +336,8 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = hbm_peak()
     achieved = alg_local / t_local / 1e9
     kname = {spmv.VARIANT_TILE: "csr_tile_kernel", spmv.VARIANT_VECTOR: "csr_vector_kernel",
-             spmv.VARIANT_MERGE: "merge_kernel", spmv.VARIANT_PAIRS: "csr_pair_kernel"}[variant]
+             spmv.VARIANT_MERGE: "merge_kernel", spmv.VARIANT_PAIRS: "csr_pair_kernel",
+             spmv.VARIANT_WARP: "csr_warp_kernel"}[variant]
     traffic = profiled_traffic("%s/%d" % (kname, vparam))
 
     # paper protocol: per-measurement latency percentiles of the best schedule
@@ -375,6 +396,7 @@ def run_ours(args, world, rank, local):
                        "p99": round(benchmark.percentile(meas, 99) * 1e6, 2),
                        "measurements": len(meas), "protocol": "0.01 s of samples each"},
         "schedule_spread": round(spread, 4),
+        "search_vs_random": search_cmp,
         "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "ms_per_step": round(t_e2e * 1e3, 4)},
@@ -386,6 +408,216 @@ def run_ours(args, world, rank, local):
                         round(v * 1e6, 1) for k, v in tune_times.items()},
     }
     return line
+
+
+# ---------------------------------------------------------------- batched
+def run_batched(args, world, rank, local):
+    """256 independent SpMVs (n log-uniform in [1e3, 1e6]; 5-point, 7-point
+    and Zipf-row matrices) in one persistent launch, against the same
+    products as 256 launches (eager and captured in a CUDA graph)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    from paper_2203_02530_gb300 import autotune, benchmark, spmv
+    from paper_2203_02530_gb300 import workloads as W
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    mix = W.batch_mix(256, seed=5)
+    mats = [m for _, m in mix]
+    b = spmv.Batch(mats)
+    offs = b.offsets()
+    total = offs[-1]
+    x = W.uniform_x(total, seed=6)
+    x_d = torch.from_numpy(x).to(dev)
+    y_b = torch.empty(total, dtype=torch.float64, device=dev)
+    y_s = torch.empty(total, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    mrl = [(int(m[1][-1]) / m[0]) if m[0] else 0.0 for m in mats]
+    lanes = autotune.tune_batch(b, x_d, y_b, s, mean_row_lengths=mrl)
+    alg = b.query(spmv.BQ_ALG_BYTES)
+    batched = lambda: spmv.spmv_batch_run(b.h, x_d, y_b, s)
+    separate = lambda: spmv.spmv_batch_run_separate(b.h, -1, x_d, y_s, s)
+    batched()
+    separate()
+    s.synchronize()
+    identical = bool(torch.equal(y_b, y_s))
+    # the 256 launches captured once as a graph (the fairest plain form)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        separate()
+    for _ in range(args.warmup):
+        batched()
+    s.synchronize()
+    sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+    sampler.start()
+    torch.cuda.nvtx.range_push("timed_region")
+    t_b = benchmark.time_loop(batched, s, args.steps, warmup=0)
+    torch.cuda.nvtx.range_pop()
+    clocks = sampler.stop()
+    t_b = max_over_ranks(dist, t_b, dev)
+    t_sep = benchmark.time_loop(separate, s, max(3, args.steps // 10), warmup=args.warmup)
+    def replay():
+        with torch.cuda.stream(s):
+            g.replay()
+    t_graph = benchmark.time_loop(replay, s, max(3, args.steps // 4), warmup=args.warmup)
+    meas = benchmark.measurements(batched, s, args.measurements)
+    # end to end: x from pinned host memory, the product, y back to the host
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(total, dtype=torch.float64).pin_memory()
+
+    def e2e():
+        with torch.cuda.stream(s):
+            x_d.copy_(xh, non_blocking=True)
+        batched()
+        with torch.cuda.stream(s):
+            yh.copy_(y_b, non_blocking=True)
+        s.synchronize()
+    e2e()
+    k_e2e = max(5, min(args.steps, 50))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e()
+    t_e2e = (time.perf_counter() - t0) / k_e2e
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < args.cpu_seconds or reps == 0:
+            for m, (n, rp, ci, va) in enumerate(mats):
+                oracle.csr_spmv(n, rp, ci, va, x[offs[m]:offs[m] + n])
+            reps += 1
+        secs = time.perf_counter() - t0
+        cpu = {"value": round(alg * reps / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "%d passes over all 256 matrices (plain CSR products), single-threaded C "
+                         "oracle, %.1f s (nproc=%d)" % (reps, secs, os.cpu_count() or 0)}
+    b.close()
+    if rank != 0:
+        return None
+    peak, peak_kind = hbm_peak()
+    value = world * alg / t_b / 1e9
+    nnz = int(sum(int(m[1][-1]) for m in mats))
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_b * 1e3, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "batched: 256 independent SpMVs, n log-uniform in [1e3, 1e6], "
+                               "5-point / 7-point / Zipf-row (mean ~10) matrices, one persistent launch",
+                   "matrices": len(mats), "total_rows": total, "nnz": nnz,
+                   "lanes_histogram": {str(v): lanes.count(v) for v in sorted(set(lanes))},
+                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg},
+        "percent_hbm": round(100.0 * value / world / peak, 2),
+        "separate_launches": {"eager_gbs": round(alg / t_sep / 1e9, 2),
+                              "graph_gbs": round(alg / t_graph / 1e9, 2),
+                              "eager_ms": round(t_sep * 1e3, 4), "graph_ms": round(t_graph * 1e3, 4),
+                              "bit_identical_to_batched": identical},
+        "speedup_vs_separate_graph": round(t_graph / t_b, 3),
+        "speedup_vs_separate_eager": round(t_sep / t_b, 3),
+        "roofline": {"bound": "hbm", "kernel": "batch_persistent_kernel",
+                     "achieved": round(alg / t_b / 1e9, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(alg / t_b / 1e9 / peak, 4), "traffic": None, "peak_kind": peak_kind},
+        "latency_us": {"p50": round(benchmark.percentile(meas, 50) * 1e6, 2),
+                       "p99": round(benchmark.percentile(meas, 99) * 1e6, 2),
+                       "measurements": len(meas), "protocol": "0.01 s of samples each"},
+        "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
+                "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
+                "ms_per_step": round(t_e2e * 1e3, 4)},
+        "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
+    }
+
+
+# ---------------------------------------------------------------- serving
+def run_serving(args, world, rank, local):
+    """Poisson arrivals of SpMV requests over 64 resident matrices, each a
+    block of 1..8 right-hand sides with device-drawn inputs, served with
+    continuous batching against one plain launch per request."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import workloads as W
+    mix = W.serve_mix(64, seed=6)
+    mats = [m for _, m in mix]
+    b = spmv.Batch(mats)
+    sv = spmv.Server(b, n_streams=args.serve_streams, budget_bytes=40 << 30)
+    rate = args.serve_rate
+    arr = W.poisson_arrivals(rate, args.serve_seconds, seed=7)
+    rng = np.random.default_rng(8)
+    count = arr.size
+    mat = rng.integers(0, len(mats), size=count).astype(np.int32)
+    wid = rng.integers(1, 9, size=count).astype(np.int32)
+    sd = rng.integers(0, 2**63, size=count, dtype=np.uint64)
+    nn = np.array([m[0] for m in mats], dtype=np.int64)
+    zz = np.array([int(m[1][-1]) for m in mats], dtype=np.int64)
+    # algorithmic bytes of a request alone: its matrix once, X and Y
+    req_bytes = 12 * zz[mat] + 4 * (nn[mat] + 1) + 16 * nn[mat] * wid
+    warm = min(2000, count)
+    sv.run(mat[:warm], wid[:warm], sd[:warm], np.zeros(warm), spmv.SERVE_BATCHED, want_hash=False)
+    out = {}
+    for name, mode in (("served", spmv.SERVE_BATCHED), ("plain", spmv.SERVE_PLAIN)):
+        lat, hs, st = sv.run(mat, wid, sd, arr, mode, want_hash=True)
+        el = st["elapsed_ns"] * 1e-9
+        out[name] = {"p50_us": round(float(np.percentile(lat, 50)) * 1e6, 2),
+                     "p99_us": round(float(np.percentile(lat, 99)) * 1e6, 2),
+                     "throughput_req_s": round(count / el, 1), "gbs": round(req_bytes.sum() / el / 1e9, 2),
+                     "blocks": st["blocks"], "max_inflight": st["max_inflight"],
+                     "admitted_while_busy": st["admitted_while_busy"],
+                     "peak_pool_mb": round(st["peak_pool_bytes"] / 1e6, 1), "hash": hs}
+    same = bool(np.array_equal(out["served"].pop("hash"), out["plain"].pop("hash")))
+    # saturation: every request present at t = 0 (the most either form can do)
+    nsat = min(count, args.serve_saturation)
+    sat = {}
+    for name, mode in (("served", spmv.SERVE_BATCHED), ("plain", spmv.SERVE_PLAIN)):
+        lat, _, st = sv.run(mat[:nsat], wid[:nsat], sd[:nsat], np.zeros(nsat), mode, want_hash=False)
+        el = st["elapsed_ns"] * 1e-9
+        sat[name] = {"throughput_req_s": round(nsat / el, 1),
+                     "gbs": round(req_bytes[:nsat].sum() / el / 1e9, 2), "blocks": st["blocks"]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        t0, done = time.perf_counter(), 0
+        byts = 0
+        while time.perf_counter() - t0 < args.cpu_seconds and done < count:
+            m, k = int(mat[done]), int(wid[done])
+            n, rp, ci, va = mats[m]
+            X = W.request_x(int(sd[done]), n, k)
+            for j in range(k):
+                oracle.csr_spmv(n, rp, ci, va, X[:, j])
+            byts += int(req_bytes[done])
+            done += 1
+        secs = time.perf_counter() - t0
+        cpu = {"value": round(byts / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "%d requests (each column a plain CSR product), single-threaded C oracle, "
+                         "%.1f s (nproc=%d)" % (done, secs, os.cpu_count() or 0)}
+    sv.close()
+    total = int(sum(zz) * 12 + sum(nn) * 4)
+    b.close()
+    peak, peak_kind = hbm_peak()
+    value = sat["served"]["gbs"]
+    return {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": nsat, "warmup": warm, "ms_per_step": round(1e3 / sat["served"]["throughput_req_s"], 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals (%g req/s for %g s, %d requests) over 64 resident "
+                               "matrices (7-point stencils and power-law rows, %.2f GB), width 1..8, "
+                               "budget 40 GB, %d stream slots" % (rate, args.serve_seconds, count,
+                                                                   total / 1e9, args.serve_streams),
+                   "value": "saturation throughput of the served form (all requests present at t=0)"},
+        "open_loop": out, "saturation": sat,
+        "served_vs_plain_saturation": round(sat["served"]["gbs"] / sat["plain"]["gbs"], 3),
+        "results_identical_served_vs_plain": same,
+        "latency_us": {"p50": out["served"]["p50_us"], "p99": out["served"]["p99_us"],
+                       "protocol": "arrival to observed completion, open loop"},
+        "roofline": {"bound": "hbm", "kernel": "spmm_kernel", "achieved": value, "peak": peak,
+                     "unit": "GB/s", "frac": round(value / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind, "note": "per-request algorithmic bytes at saturation"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
+                "note": "inputs are drawn on the device from each request's seed; the host reads "
+                        "one 8-byte hash per request"},
+        "cpu_baseline": cpu, "gpu_launches": 3 * sat["served"]["blocks"],
+    }
 
 
 # ---------------------------------------------------------------- reference arm
@@ -447,11 +679,18 @@ def main(argv=None):
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--reference-budget", type=float, default=90.0,
                     help="seconds of oracle work the reference arm aims for")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="stencil27",
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serving"],
+                    default="stencil27",
                     help="stencil27 (default): 27-point 150^3; laplacian: 5-point 64x64; "
                          "powerlaw: n=4M with MCTS over the per-rank DAG")
     ap.add_argument("--mcts-iters", type=int, default=2000)
+    ap.add_argument("--random-baseline", type=int, default=0,
+                    help="also measure this many random-rollout programs (search baseline)")
     ap.add_argument("--records", default=None, help="JSONL log of every measured schedule")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-streams", type=int, default=8)
+    ap.add_argument("--serve-saturation", type=int, default=20000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -461,7 +700,12 @@ def main(argv=None):
     else:
         import __graft_entry__
         __graft_entry__.build()
-        line = run_ours(args, world, rank, local)
+        if args.workload == "batched":
+            line = run_batched(args, world, rank, local)
+        elif args.workload == "serving":
+            line = run_serving(args, world, rank, local)
+        else:
+            line = run_ours(args, world, rank, local)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -146,13 +146,17 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *   PAIRS  param = lanes per row (1, 2, 4, 8), one aligned pair of entries per
  *          lane per step, FMA count = the warp's longest share
  *   MERGE  merge-path split with deterministic carries (param ignored)
+ *   WARP   param = geometry 0..3: warp-private shared-memory pipelines of
+ *          32-row tiles (bulk copies per warp, no block-wide barrier), one
+ *          thread per row, one DFMA per entry
  * Fails with SPMV_EINVAL while captured graphs exist (they hold the old
  * kernels' tables). */
 enum {
     SPMV_VARIANT_TILE = 0,
     SPMV_VARIANT_VECTOR = 1,
     SPMV_VARIANT_MERGE = 2,
-    SPMV_VARIANT_PAIRS = 3
+    SPMV_VARIANT_PAIRS = 3,
+    SPMV_VARIANT_WARP = 4
 };
 /* Sets the variant of both products. */
 int spmv_part_set_variant(spmv_part* part, int variant, int param);
@@ -285,7 +289,8 @@ typedef struct spmv_batch spmv_batch;
 enum {
     SPMV_BQ_COUNT = 0, SPMV_BQ_TOTAL_ROWS = 1, SPMV_BQ_TOTAL_NNZ = 2, SPMV_BQ_ITEMS = 3,
     SPMV_BQ_ALG_BYTES = 4,   /* 12 B/entry + 4 B/row pointer + 16 B/row (x read, y written) */
-    SPMV_BQ_OFFSET = 5, SPMV_BQ_N = 6, SPMV_BQ_NNZ = 7, SPMV_BQ_LANES = 8   /* of matrix m */
+    SPMV_BQ_OFFSET = 5, SPMV_BQ_N = 6, SPMV_BQ_NNZ = 7, SPMV_BQ_LANES = 8,  /* of matrix m */
+    SPMV_BQ_DEVICE_BYTES = 9   /* device memory the batch holds */
 };
 int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr,
                       const int32_t* const* col_idx, const double* const* vals,
@@ -299,6 +304,54 @@ int spmv_batch_run(spmv_batch* batch, const double* x_dev, double* y_dev, cudaSt
 /* The same products as one launch per matrix (only matrix m if m >= 0). */
 int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, double* y_dev,
                             cudaStream_t s);
+
+/*
+ * Serving: SpMV requests over the matrices of a resident batch, with
+ * continuous batching.  A request names a matrix, a width k in 1..8 (right-
+ * hand sides) and a 64-bit seed; its X (n x k) is drawn on the device: element
+ * (i, j) is 2 u - 1 with u = (SplitMix64(seed, 8 i + j) >> 11) * 2^-53, where
+ * SplitMix64(s, t) is the SplitMix64 output for state s + (t + 1) * golden
+ * (Steele, Lea and Flood).  Not part of the paper's method: a serving loop
+ * around its SpMV.
+ * spmv_serve_create: n_streams (1..64) stream slots, one block in flight per
+ *   slot; budget_bytes covers the resident matrices plus a pool from which
+ *   every in-flight block takes 128 n bytes (X and Y, n x 8 doubles each);
+ *   SPMV_ENOMEM when the budget is below the resident matrices.
+ * spmv_serve_run: runs n_req requests open loop against their arrival times
+ *   (seconds from the call, non-decreasing), on the host thread, until all
+ *   completed.  BATCHED merges the oldest requests of one matrix into one
+ *   block of total width <= 8 whenever a slot and pool memory are free;
+ *   requests arriving while blocks run join at the next turn of the loop.
+ *   PLAIN launches every request alone (one block per request).  Outputs:
+ *   latency_s[r] = observed completion - arrival; hash_out[r] (optional) an
+ *   order-independent 64-bit hash of the bits of request r's Y; stats (6
+ *   int64, optional): blocks launched, most blocks in flight, launches that
+ *   waited for pool memory, peak pool bytes, elapsed ns, requests admitted
+ *   while blocks were in flight.  Each column of a block is summed in the
+ *   same order whatever the block's partners, so Y (and the hash) of a
+ *   request is the same alone and in any mix.  SPMV_ETIMEOUT if no request
+ *   completes for 30 s after the last arrival.
+ * spmv_serve_single: one request alone on stream s into caller buffers
+ *   x_dev, y_dev (n x 8 doubles each, row-major; columns >= width of Y are
+ *   unspecified).
+ */
+typedef struct spmv_server spmv_server;
+enum { SPMV_SERVE_BATCHED = 0, SPMV_SERVE_PLAIN = 1 };
+int spmv_serve_create(spmv_batch* matrices, int n_streams, int64_t budget_bytes,
+                      spmv_server** out);
+int spmv_serve_destroy(spmv_server* server);
+int spmv_serve_run(spmv_server* server, int64_t n_req, const int32_t* matrix,
+                   const int32_t* width, const uint64_t* seed, const double* arrival_s,
+                   int mode, double* latency_s, uint64_t* hash_out, int64_t* stats);
+int spmv_serve_single(spmv_server* server, int matrix, int width, uint64_t seed,
+                      double* y_dev, double* x_dev, cudaStream_t s);
+
+/* Self-test of the bounded device waits: one thread waits on an mbarrier
+ * that nothing ever completes; the wait gives up after limit_ns (1e3..2e9)
+ * and *status_out receives 6 (the magnitude of SPMV_ETIMEOUT) -- the status
+ * every kernel of the library reports through its error word when a wait
+ * runs out.  Synchronises; leaves the context usable. */
+int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out);
 
 /* Thread-local message describing the last failure of this thread. */
 const char* spmv_last_error(void);

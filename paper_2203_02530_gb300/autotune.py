@@ -21,6 +21,7 @@ CACHE = os.environ.get("SPMV_TUNE_CACHE",
 CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
               + [(spmv.VARIANT_VECTOR, w) for w in (2, 4, 8)]
               + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8)]
+              + [(spmv.VARIANT_WARP, g) for g in range(4)]
               + [(spmv.VARIANT_MERGE, 0)])
 
 
@@ -84,3 +85,41 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
                       "times": {"%d,%d,%d" % k: t for k, t in times.items()}}
         _save_cache(cache_path, cache)
     return out
+
+
+def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(1, 2, 4, 8, 16),
+               reps=5):
+    """Lanes per row for the matrices of a batch, timed on the persistent
+    launch itself (one launch per matrix would be dominated by launch
+    latency for small matrices): first one value for every matrix, then one
+    value per class of mean row length (< 4, < 8, < 16, < 32, >= 32), each
+    class tried with the others fixed.  Returns the list chosen."""
+    run = lambda: spmv.spmv_batch_run(batch.h, x_dev, y_dev, stream)
+    best_v, best_t = None, None
+    for v in lanes:
+        spmv.spmv_batch_set_lanes(batch.h, -1, v)
+        t = time_loop(run, stream, reps, warmup=2)
+        if best_t is None or t < best_t:
+            best_v, best_t = v, t
+    chosen = [best_v] * batch.count
+    spmv.spmv_batch_set_lanes(batch.h, -1, best_v)
+    if mean_row_lengths is not None:
+        edges = [4, 8, 16, 32]
+        cls = [sum(mrl >= e for e in edges) for mrl in mean_row_lengths]
+        for c in sorted(set(cls)):
+            members = [m for m in range(batch.count) if cls[m] == c]
+            cur_v, cur_t = chosen[members[0]], best_t
+            for v in lanes:
+                if v == cur_v:
+                    continue
+                for m in members:
+                    spmv.spmv_batch_set_lanes(batch.h, m, v)
+                t = time_loop(run, stream, reps, warmup=2)
+                if t < cur_t:
+                    cur_v, cur_t = v, t
+                for m in members:
+                    spmv.spmv_batch_set_lanes(batch.h, m, cur_v)
+            for m in members:
+                chosen[m] = cur_v
+            best_t = cur_t
+    return chosen

@@ -141,6 +141,14 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
                    "merge product");
         return me > mb ? 2 : 0;
     }
+    if (var == SPMV_VARIANT_WARP) {
+        const std::vector<int64_t>& wo = remote ? pt->rwtile_off : pt->lwtile_off;
+        const int wb = (int)(p < 0 ? 0 : wo[p]);
+        const int we = (int)(p < 0 ? wo[pt->P] : wo[p + 1]);
+        check_cuda(spmvk::launch_warp(a, remote ? pt->rwtiles : pt->lwtiles, wb, we, param, pt->num_sms, s),
+                   "warp product");
+        return we > wb;
+    }
     const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
     if (var == SPMV_VARIANT_VECTOR || var == SPMV_VARIANT_PAIRS) {
         const std::vector<int64_t>& bo = remote ? pt->rblock_off : pt->lblock_off;
@@ -288,6 +296,7 @@ int spmv_part_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, 
     API_TRY
     if (granularity != SPMV_COARSE && granularity != SPMV_PER_PARTITION)
         fail(SPMV_EINVAL, "granularity %d", granularity);
+    spmvk::validate_csr(n, row_ptr, col_idx, vals, P);   // before any CUDA call
     pt = new spmv_part();
     pt->P = P;
     pt->gran = granularity;
@@ -522,6 +531,11 @@ static void prepare_variant(spmv_part* pt, int variant, int param) {
     } else if (variant == SPMV_VARIANT_PAIRS) {
         if (param != 1 && param != 2 && param != 4 && param != 8)
             fail(SPMV_EINVAL, "lanes per row %d not in {1,2,4,8}", param);
+    } else if (variant == SPMV_VARIANT_WARP) {
+        const int cap = spmvk::warp_tile_cap(param);
+        if (cap < 0) fail(SPMV_EINVAL, "warp geometry %d not in [0, 4)", param);
+        check_cuda(cudaDeviceSynchronize(), "synchronize");
+        if (!pt->lwtiles || pt->wtile_cap != cap) spmvk::build_warp_tiles(pt, cap);
     } else if (variant == SPMV_VARIANT_MERGE) {
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
@@ -764,6 +778,17 @@ int spmv_csr_error(int64_t* out) {
     int h = 0;
     check_cuda(spmvk::read_clear_csr_error(&h), "error word");
     *out = h;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out) {
+    API_TRY
+    need(status_out != nullptr, SPMV_EINVAL, "status_out is NULL");
+    if (limit_ns < 1000 || limit_ns > 2000000000) fail(SPMV_EINVAL, "limit %lld ns not in [1e3, 2e9]", (long long)limit_ns);
+    int st = 0;
+    check_cuda(spmvk::selftest_wait_timeout((uint64_t)limit_ns, &st), "self-test");
+    *status_out = st;
     API_CATCH
     return SPMV_OK;
 }

@@ -72,6 +72,10 @@ cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin,
                         int tile_end, const TileGeom& g, int num_sms, cudaStream_t s);
 cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
                           int lanes, int num_sms, cudaStream_t s);
+cudaError_t launch_warp(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
+                        int param, int num_sms, cudaStream_t s);
+int warp_tile_cap(int param);
+cudaError_t selftest_wait_timeout(uint64_t limit_ns, int* status_host);
 cudaError_t launch_pairs(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
                          int lanes, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begin,

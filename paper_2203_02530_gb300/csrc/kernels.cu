@@ -464,6 +464,177 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* 
 }
 
 // ------------------------------------------------------------------------
+// Warp-private pipelines: every warp owns an ST-stage ring of 32-row tiles
+// (values, columns, row pointers) in shared memory, filled by bulk copies its
+// lane 0 issues against the warp's own mbarriers.  There is no block-wide
+// barrier after set-up, so warps never wait for each other.  One thread per
+// row, exactly one DFMA per entry in storage order (the FMA loop runs the
+// warp's longest row), CH gathers of x in flight per chunk.  A row longer
+// than a stage (TILE_LONG) is summed by the 32 lanes from global memory with
+// a fixed butterfly.
+// ------------------------------------------------------------------------
+template <int WARPS, int CAP, int ST, int CH>
+__global__ void __launch_bounds__(WARPS * 32, 1) csr_warp_kernel(CsrArgs a, const Tile* __restrict__ tiles,
+                                                                int tile_begin, int tile_end) {
+    using L = TileLayout<32, CAP>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[WARPS][ST];
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    unsigned char* ring = smem + (size_t)w * ST * L::BYTES;
+    const int first = tile_begin + (int)blockIdx.x * WARPS + w;
+    const int stride = (int)gridDim.x * WARPS;
+    if (lane == 0) {
+        for (int s = 0; s < ST; ++s) mbar_init(smem_u32(&bars[w][s]), 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+
+    auto issue = [&](int j) {   // lane 0 only
+        const int t = first + j * stride;
+        if (t >= tile_end) return;
+        const int s = j % ST;
+        const Tile d = tiles[t];
+        const uint32_t bar = smem_u32(&bars[w][s]);
+        if (d.flags & TILE_LONG) {
+            mbar_arrive_expect_tx(bar, 0);
+            return;
+        }
+        const int va = d.k0 & ~1, vb = (d.k1 + 1) & ~1;
+        const int ca = d.k0 & ~3, cb = (d.k1 + 3) & ~3;
+        const int pa = d.r0 & ~3, pb = (d.r1 + 4) & ~3;
+        const uint32_t vbytes = (uint32_t)(vb - va) * 8u;
+        const uint32_t cbytes = (uint32_t)(cb - ca) * 4u;
+        const uint32_t pbytes = (uint32_t)(pb - pa) * 4u;
+        unsigned char* st = ring + (size_t)s * L::BYTES;
+        mbar_arrive_expect_tx(bar, vbytes + cbytes + pbytes);
+        if (vbytes) bulk_g2s_hint(smem_u32(st + L::VAL_OFF), a.val + va, vbytes, bar, pol_stream);
+        if (cbytes) bulk_g2s_hint(smem_u32(st + L::COL_OFF), a.col + ca, cbytes, bar, pol_stream);
+        bulk_g2s_hint(smem_u32(st + L::PTR_OFF), a.ptr + pa, pbytes, bar, pol_stream);
+    };
+
+    if (lane == 0)
+        for (int j = 0; j < ST - 1; ++j) issue(j);
+    int j = 0;
+    bool aborted = false;
+    for (;; ++j) {
+        const int t = first + j * stride;
+        if (t >= tile_end) break;
+        if (lane == 0) {
+            fence_proxy_async_smem();   // stage (j-1) % ST was released by the warp
+            issue(j + ST - 1);
+        }
+        const int s = j % ST;
+        const bool ok = mbar_wait_bounded(smem_u32(&bars[w][s]), (uint32_t)((j / ST) & 1), kWaitLimitNs);
+        if (__any_sync(0xffffffffu, !ok)) {
+            aborted = true;
+            break;
+        }
+        const Tile d = tiles[t];
+        const double* xb = a.x + d.xoff;
+        if (d.flags & TILE_LONG) {
+            double part = 0.0;
+            for (int k = d.k0 + lane; k < d.k1; k += 32)
+                part = fma(__ldg(a.val + k), ldg_keep(xb + __ldg(a.col + k), pol_keep), part);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == 0) store_row(a, d.r0, part);
+        } else {
+            const unsigned char* st = ring + (size_t)s * L::BYTES;
+            const double* vs = reinterpret_cast<const double*>(st + L::VAL_OFF);
+            const int32_t* cs = reinterpret_cast<const int32_t*>(st + L::COL_OFF);
+            const int32_t* ps = reinterpret_cast<const int32_t*>(st + L::PTR_OFF);
+            const int va = d.k0 & ~1, ca = d.k0 & ~3, pa = d.r0 & ~3;
+            const int dc = va - ca;
+            const int row = d.r0 + lane;
+            int kb = 0, cnt = 0;
+            if (row < d.r1) {
+                kb = ps[row - pa] - va;
+                cnt = ps[row + 1 - pa] - va - kb;
+            }
+            const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+            double sum = 0.0;
+            for (int base = 0; base < wmax; base += CH) {
+                double xv[CH], vv[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const bool m = base + u < cnt;
+                    const int k = kb + base + u;
+                    const int c = m ? cs[k + dc] : 0;
+                    vv[u] = m ? vs[k] : 0.0;
+                    xv[u] = ldg_keep(xb + c, pol_keep);
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (base + u >= wmax) break;   // warp-uniform
+                    const double t0 = fma(vv[u], xv[u], sum);
+                    sum = (base + u < cnt) ? t0 : sum;
+                }
+            }
+            if (row < d.r1) store_row(a, row, sum);
+        }
+        __syncwarp();   // stage s is free again
+    }
+    if (aborted && lane == 0) {
+        atomicExch(a.err, kErrTimeout);
+        for (int jj = j + 1; jj < j + ST; ++jj) {
+            if (first + jj * stride >= tile_end) break;
+            mbar_wait_bounded(smem_u32(&bars[w][jj % ST]), (uint32_t)((jj / ST) & 1), kDrainLimitNs);
+        }
+    }
+}
+
+template <int WARPS, int CAP, int ST, int CH>
+static cudaError_t run_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int num_sms, cudaStream_t s) {
+    using L = TileLayout<32, CAP>;
+    const size_t smem = (size_t)WARPS * ST * L::BYTES;
+    static unsigned long long configured = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured >> dev & 1ull)) {
+        e = cudaFuncSetAttribute(csr_warp_kernel<WARPS, CAP, ST, CH>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ull << dev;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_warp_kernel<WARPS, CAP, ST, CH>, WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int grid = num_sms * occ;
+    const int need = (te - tb + WARPS - 1) / WARPS;
+    if (grid > need) grid = need;
+    csr_warp_kernel<WARPS, CAP, ST, CH><<<grid, WARPS * 32, smem, s>>>(a, tiles, tb, te);
+    return cudaGetLastError();
+}
+
+// Warp-tile geometries: (warps per CTA, entries per stage, stages, gathers per chunk).
+int warp_tile_cap(int param) {
+    switch (param) {
+        case 0: return 896;    // 32 rows x 28 entries
+        case 1: return 896;
+        case 2: return 896;
+        case 3: return 1792;   // rows up to 56 entries
+        default: return -1;
+    }
+}
+
+cudaError_t launch_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int param, int num_sms,
+                        cudaStream_t s) {
+    if (te <= tb) return cudaSuccess;
+    switch (param) {
+        case 0: return run_warp<8, 896, 2, 16>(a, tiles, tb, te, num_sms, s);    // 175 KB, 1 CTA
+        case 1: return run_warp<4, 896, 2, 16>(a, tiles, tb, te, num_sms, s);    // 88 KB, 2 CTAs
+        case 2: return run_warp<10, 896, 2, 16>(a, tiles, tb, te, num_sms, s);   // 219 KB, 1 CTA
+        case 3: return run_warp<4, 1792, 2, 16>(a, tiles, tb, te, num_sms, s);   // 174 KB, 1 CTA
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------------
 // Pair-per-lane CSR: V lanes share a row; the row's entries are covered by
 // aligned pairs [k, k+1) (k even) and lane h takes pairs h, h+V, h+2V, ...
 // Each pair is one 16-byte load of values and one 8-byte load of columns.
@@ -556,6 +727,35 @@ cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, i
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Self-test of the bounded wait: one thread waits on an mbarrier that no
+// copy and no thread ever completes; the wait gives up after limit_ns and
+// the kernel reports SPMV_ETIMEOUT's magnitude through `status`.
+// ------------------------------------------------------------------------
+__global__ void selftest_wait_kernel(uint64_t limit_ns, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait_bounded(smem_u32(&bar), 0u, limit_ns);
+        *status = ok ? 0 : kErrTimeout;
+    }
+}
+
+cudaError_t selftest_wait_timeout(uint64_t limit_ns, int* status_host) {
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e != cudaSuccess) return e;
+    selftest_wait_kernel<<<1, 32>>>(limit_ns, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(status_host, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e;
 }
 
 }  // namespace spmvk

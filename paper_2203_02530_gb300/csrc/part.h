@@ -88,6 +88,12 @@ struct spmv_part {
     spmvk::Tile* rblocks = nullptr;
     std::vector<int64_t> lblock_off;  // P+1
     std::vector<int64_t> rblock_off;  // P+1
+    // 32-row tiles of the warp-pipeline kernel (built on first use)
+    spmvk::Tile* lwtiles = nullptr;
+    spmvk::Tile* rwtiles = nullptr;
+    std::vector<int64_t> lwtile_off;  // P+1
+    std::vector<int64_t> rwtile_off;  // P+1
+    int wtile_cap = 0;
     // merge-path tiles (built on first use of the merge variant)
     spmvk::MergeTile* lmtiles = nullptr;
     spmvk::MergeTile* rmtiles = nullptr;
@@ -118,10 +124,12 @@ struct spmv_part {
 };
 
 namespace spmvk {
+void validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* vals, int P);
 void build_plan(spmv_part* pt, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                 const double* vals);
 void build_tiles(spmv_part* pt, const TileGeom& g);
 void build_merge_tiles(spmv_part* pt);
+void build_warp_tiles(spmv_part* pt, int cap);
 void* dev_alloc(spmv_part* pt, size_t bytes);
 void free_plan(spmv_part* pt);
 }  // namespace spmvk

@@ -86,9 +86,26 @@ void free_plan(spmv_part* pt) {
     pt->device_bytes = 0;
 }
 
+void validate_csr(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, int P) {
+    if (n < 0) fail(SPMV_EINVAL, "n = %lld < 0", (long long)n);
+    if (n >= (int64_t(1) << 31)) fail(SPMV_EBOUNDS, "n = %lld needs 64-bit columns", (long long)n);
+    if (P < 1) fail(SPMV_EINVAL, "P = %d < 1", P);
+    if (P > 1024) fail(SPMV_EBOUNDS, "P = %d above the limit 1024", P);
+    if (!rp) fail(SPMV_EINVAL, "row_ptr is NULL");
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) fail(SPMV_EINVAL, "row_ptr decreases at row %lld", (long long)i);
+    const int64_t nnz = rp[n] - rp[0];
+    if (nnz >= (int64_t(1) << 31) - 64) fail(SPMV_EBOUNDS, "nnz = %lld too large", (long long)nnz);
+    if (nnz > 0 && (!ci || !va)) fail(SPMV_EINVAL, "col_idx or vals is NULL");
+    for (int64_t k = rp[0]; k < rp[n]; ++k)
+        if (ci[k] < 0 || ci[k] >= n)
+            fail(SPMV_EINVAL, "column %d out of range at entry %lld", ci[k], (long long)(k - rp[0]));
+}
+
 void build_plan(spmv_part* pt, int64_t n, const int64_t* rp, const int32_t* ci,
                 const double* va) {
     const int P = pt->P;
+    validate_csr(n, rp, ci, va, P);
     if (n < 0) fail(SPMV_EINVAL, "n = %lld < 0", (long long)n);
     if (n >= (int64_t(1) << 31)) fail(SPMV_EBOUNDS, "n = %lld needs 64-bit columns", (long long)n);
     if (P < 1) fail(SPMV_EINVAL, "P = %d < 1", P);
@@ -326,6 +343,30 @@ void build_merge_tiles(spmv_part* pt) {
                    "merge partition");
     }
     check_cuda(cudaDeviceSynchronize(), "merge partition");
+}
+
+// Tiles of at most 32 rows and `cap` entries (one warp each).
+void build_warp_tiles(spmv_part* pt, int cap) {
+    const int P = pt->P;
+    const std::vector<int32_t> l_ptr = download(pt->l_ptr, (size_t)pt->n + 1);
+    const std::vector<int32_t> rr_ptr = download(pt->rr_ptr, (size_t)pt->n_rr + 1);
+    const TileGeom g{32, cap, 2, 16, 1};
+    std::vector<Tile> lt, rt;
+    pt->lwtile_off.assign(P + 1, 0);
+    pt->rwtile_off.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        pt->lwtile_off[p] = (int64_t)lt.size();
+        tile_range(l_ptr, pt->bounds[p], pt->bounds[p + 1], (int32_t)pt->bounds[p], g, lt);
+        pt->rwtile_off[p] = (int64_t)rt.size();
+        tile_range(rr_ptr, pt->rr_off[p], pt->rr_off[p + 1], 0, g, rt);
+    }
+    pt->lwtile_off[P] = (int64_t)lt.size();
+    pt->rwtile_off[P] = (int64_t)rt.size();
+    free_one(pt, pt->lwtiles);
+    free_one(pt, pt->rwtiles);
+    pt->lwtiles = upload(pt, lt);
+    pt->rwtiles = upload(pt, rt);
+    pt->wtile_cap = cap;
 }
 
 }  // namespace spmvk

@@ -1,0 +1,498 @@
+// Serving runtime: SpMV requests over matrices resident in HBM, with
+// continuous batching.
+//
+// A request names a matrix of a resident batch, a width k (1..8 right-hand
+// sides) and a seed; its X (n x k) is drawn on the device from the seed with
+// SplitMix64, so no input crosses PCIe/C2C.  The loop runs open-loop against
+// the requests' arrival times: arrived requests queue per matrix; whenever a
+// stream slot and budget memory are free, the oldest requests of a matrix
+// are merged into one multi-RHS block (total width <= 8) and launched; a
+// request arriving while blocks run is admitted at the next turn of the
+// loop, so blocks of different matrices overlap on the device.  Completion
+// is observed through events; latency = observed completion - arrival.
+//
+// Each column of a block is summed by the same lanes in the same order
+// whatever the block's width and partners, so a request's Y is bit-identical
+// alone and in any mix (checked through an order-independent 64-bit hash of
+// its bits).
+#include "batch.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+using spmvk::BatchMat;
+
+namespace {
+
+constexpr int kMaxW = 8;          // widest block
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------- device
+// SplitMix64 (Steele, Lea and Flood): element t of the stream of `seed`.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t t) {
+    uint64_t z = seed + (t + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// U[-1, 1) from the top 53 bits.
+__device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t t) {
+    return (double)(splitmix64(seed, t) >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+}
+
+struct BlockReq {
+    uint64_t seed;
+    int col0;     // first column of the request in the block
+    int width;
+    int index;    // request index (hash slot)
+    int pad;
+};
+
+struct BlockDesc {
+    BlockReq req[kMaxW];
+    int n_req;
+    int width;
+};
+
+// X[i, c] for every column of every request of the block (row-major, ld 8):
+// request r's element (i, j) is U(seed_r, 8 i + j).
+__global__ void gen_x_kernel(double* __restrict__ X, int n, BlockDesc b) {
+    const int64_t total = (int64_t)n * kMaxW;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / kMaxW), c = (int)(e % kMaxW);
+        double v = 0.0;
+        for (int r = 0; r < b.n_req; ++r) {
+            const BlockReq q = b.req[r];
+            if (c >= q.col0 && c < q.col0 + q.width)
+                v = uniform_pm1(q.seed, (uint64_t)i * kMaxW + (uint64_t)(c - q.col0));
+        }
+        X[e] = v;
+    }
+}
+
+// Y[:, 0..W) = A X[:, 0..W): V lanes per row, lane h takes entries
+// kb + h, kb + h + V, ...; each column accumulates in entry order, then a
+// fixed xor-butterfly over the V lanes.
+template <int V, int W>
+__global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restrict__ ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const double* __restrict__ X,
+                                                        double* __restrict__ Y, int n) {
+    constexpr int GROUPS = kThreads / V;
+    const int lane = threadIdx.x % V;
+    for (int rbase = (int)blockIdx.x * GROUPS; rbase < n; rbase += (int)gridDim.x * GROUPS) {
+        const int row = rbase + (int)threadIdx.x / V;
+        double acc[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = 0.0;
+        if (row < n) {
+            const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+            for (int k = kb + lane; k < ke; k += V) {
+                const double a = __ldg(val + k);
+                const double* xr = X + (int64_t)__ldg(col + k) * kMaxW;
+#pragma unroll
+                for (int c = 0; c < W; ++c) acc[c] = fma(a, __ldg(xr + c), acc[c]);
+            }
+        }
+#pragma unroll
+        for (int off = V / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off, V);
+        if (row < n && lane == 0) {
+#pragma unroll
+            for (int c = 0; c < W; ++c) Y[(int64_t)row * kMaxW + c] = acc[c];
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 33)) * 0xFF51AFD7ED558CCDull;
+    z = (z ^ (z >> 33)) * 0xC4CEB9FE1A85EC53ull;
+    return z ^ (z >> 33);
+}
+
+// Order-independent hash of each request's columns of Y: the sum (mod 2^64)
+// of mix64(bits + position); equal hashes <=> (almost surely) equal bits.
+__global__ void hash_kernel(const double* __restrict__ Y, int n, BlockDesc b,
+                            unsigned long long* __restrict__ hashes) {
+    for (int r = 0; r < b.n_req; ++r) {
+        const BlockReq q = b.req[r];
+        unsigned long long h = 0;
+        const int64_t total = (int64_t)n * q.width;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int i = (int)(e / q.width), j = (int)(e % q.width);
+            const uint64_t bits = (uint64_t)__double_as_longlong(Y[(int64_t)i * kMaxW + q.col0 + j]);
+            h += mix64(bits + (uint64_t)e * 0x9E3779B97F4A7C15ull);
+        }
+        for (int off = 16; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(hashes + q.index, h);
+    }
+}
+
+template <int V>
+cudaError_t launch_spmm_w(int W, const int32_t* ptr, const int32_t* col, const double* val, const double* X,
+                          double* Y, int n, int grid, cudaStream_t s) {
+    switch (W) {
+        case 1: spmm_kernel<V, 1><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        case 2: spmm_kernel<V, 2><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        case 3: spmm_kernel<V, 3><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        case 4: spmm_kernel<V, 4><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        case 5: spmm_kernel<V, 5><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        case 6: spmm_kernel<V, 6><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        case 7: spmm_kernel<V, 7><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+        default: spmm_kernel<V, 8><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pool
+// First-fit allocator over one device region: the admission budget.
+class Pool {
+   public:
+    void init(char* base, size_t bytes) {
+        base_ = base;
+        free_.clear();
+        free_[0] = bytes;
+        cap_ = bytes;
+        used_ = peak_ = 0;
+    }
+    // offset of a block of `bytes` (rounded to 256), or -1 when none fits
+    long long alloc(size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return (long long)off;
+            }
+        }
+        return -1;
+    }
+    void release(long long off, size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        used_ -= bytes;
+        auto it = free_.emplace((size_t)off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    char* ptr(long long off) const { return base_ + off; }
+    size_t peak() const { return peak_; }
+    size_t capacity() const { return cap_; }
+
+   private:
+    char* base_ = nullptr;
+    std::map<size_t, size_t> free_;
+    size_t cap_ = 0, used_ = 0, peak_ = 0;
+};
+
+}  // namespace
+
+struct spmv_server {
+    spmv_batch* mats = nullptr;
+    int n_streams = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> lanes;             // lanes per row per matrix
+    char* pool_base = nullptr;
+    size_t pool_bytes = 0;
+    Pool pool;
+    unsigned long long* d_hash = nullptr;
+    size_t hash_cap = 0;
+    int num_sms = 0;
+};
+
+namespace {
+
+int sfail(int code, const std::string& m) {
+    spmvk::set_last_error(m);
+    return code;
+}
+
+cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, double* Y,
+                         unsigned long long* hashes, cudaStream_t s) {
+    spmv_batch* bt = sv->mats;
+    const BatchMat& M = bt->mats[m];
+    const int n = M.n;
+    if (n == 0) return cudaSuccess;
+    int g = (int)std::min<int64_t>(((int64_t)n * kMaxW + kThreads - 1) / kThreads, (int64_t)sv->num_sms * 8);
+    gen_x_kernel<<<g, kThreads, 0, s>>>(X, n, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int32_t* ptr = bt->ptr + M.ptr_off;
+    const int32_t* col = bt->col + M.ent_off;
+    const double* val = bt->val + M.ent_off;
+    const int V = sv->lanes[m];
+    int grid = (int)std::min<int64_t>((n + (kThreads / V) - 1) / (kThreads / V), (int64_t)sv->num_sms * 8);
+    switch (V) {
+        case 1: e = launch_spmm_w<1>(b.width, ptr, col, val, X, Y, n, grid, s); break;
+        case 2: e = launch_spmm_w<2>(b.width, ptr, col, val, X, Y, n, grid, s); break;
+        case 4: e = launch_spmm_w<4>(b.width, ptr, col, val, X, Y, n, grid, s); break;
+        default: e = launch_spmm_w<8>(b.width, ptr, col, val, X, Y, n, grid, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    if (hashes) {
+        hash_kernel<<<std::min(g, sv->num_sms * 4), kThreads, 0, s>>>(Y, n, b, hashes);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace
+
+#define SERVE_TRY try {
+#define SERVE_CATCH                                              \
+    }                                                            \
+    catch (const spmvk::Fail& f) {                               \
+        return sfail(f.code, f.msg);                             \
+    }                                                            \
+    catch (const std::bad_alloc&) {                              \
+        return sfail(SPMV_ENOMEM, "host allocation failed");     \
+    }                                                            \
+    catch (...) {                                                \
+        return sfail(SPMV_EINVAL, "unexpected exception");       \
+    }
+
+extern "C" {
+
+int spmv_serve_create(spmv_batch* mats, int n_streams, int64_t budget_bytes, spmv_server** out) {
+    if (!out) return sfail(SPMV_EINVAL, "out is NULL");
+    *out = nullptr;
+    spmv_server* sv = nullptr;
+    SERVE_TRY
+    if (!mats) spmvk::fail(SPMV_EINVAL, "matrices are NULL");
+    if (n_streams < 1 || n_streams > 64) spmvk::fail(SPMV_EINVAL, "n_streams = %d", n_streams);
+    const int64_t resident = (int64_t)mats->device_bytes;
+    if (budget_bytes <= resident) spmvk::fail(SPMV_ENOMEM, "budget %lld below the resident matrices (%lld)",
+                                              (long long)budget_bytes, (long long)resident);
+    sv = new spmv_server();
+    sv->mats = mats;
+    sv->n_streams = n_streams;
+    sv->num_sms = mats->num_sms;
+    for (int m = 0; m < mats->count; ++m) {
+        const double mean = mats->n[m] ? (double)mats->nnz[m] / (double)mats->n[m] : 0.0;
+        sv->lanes.push_back(mean < 6 ? 1 : mean < 24 ? 2 : mean < 64 ? 4 : 8);
+    }
+    // the pool holds the X/Y blocks of every block in flight; beyond what
+    // the slots can ever hold at once the budget is never used, so it is
+    // not taken
+    size_t max_block = 0;
+    for (int m = 0; m < mats->count; ++m)
+        max_block = std::max(max_block, ((size_t)2 * mats->n[m] * kMaxW * sizeof(double) + 255) & ~size_t(255));
+    sv->pool_bytes = std::min((size_t)(budget_bytes - resident),
+                              std::max<size_t>(4096, max_block * (size_t)n_streams));
+    spmvk::check_cuda(cudaMalloc(reinterpret_cast<void**>(&sv->pool_base), sv->pool_bytes), "pool");
+    sv->pool.init(sv->pool_base, sv->pool_bytes);
+    sv->streams.resize(n_streams);
+    sv->events.resize(n_streams);
+    for (int i = 0; i < n_streams; ++i) {
+        spmvk::check_cuda(cudaStreamCreateWithFlags(&sv->streams[i], cudaStreamNonBlocking), "stream");
+        spmvk::check_cuda(cudaEventCreateWithFlags(&sv->events[i], cudaEventDisableTiming), "event");
+    }
+    *out = sv;
+    sv = nullptr;
+    return SPMV_OK;
+    }
+    catch (const spmvk::Fail& f) {
+        if (sv) spmv_serve_destroy(sv);
+        return sfail(f.code, f.msg);
+    }
+    catch (...) {
+        if (sv) spmv_serve_destroy(sv);
+        return sfail(SPMV_ENOMEM, "server creation failed");
+    }
+}
+
+int spmv_serve_destroy(spmv_server* sv) {
+    if (!sv) return SPMV_OK;
+    cudaDeviceSynchronize();
+    for (auto s : sv->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : sv->events)
+        if (e) cudaEventDestroy(e);
+    if (sv->pool_base) cudaFree(sv->pool_base);
+    if (sv->d_hash) cudaFree(sv->d_hash);
+    delete sv;
+    return SPMV_OK;
+}
+
+int spmv_serve_single(spmv_server* sv, int matrix, int width, uint64_t seed, double* y_dev,
+                      double* x_dev, cudaStream_t s) {
+    SERVE_TRY
+    if (!sv) spmvk::fail(SPMV_EINVAL, "server is NULL");
+    if (matrix < 0 || matrix >= sv->mats->count) spmvk::fail(SPMV_EINVAL, "matrix %d", matrix);
+    if (width < 1 || width > kMaxW) spmvk::fail(SPMV_EINVAL, "width %d", width);
+    if (!y_dev || !x_dev) spmvk::fail(SPMV_EINVAL, "buffers are NULL");
+    BlockDesc b{};
+    b.n_req = 1;
+    b.width = width;
+    b.req[0] = BlockReq{seed, 0, width, 0, 0};
+    spmvk::check_cuda(launch_block(sv, matrix, b, x_dev, y_dev, nullptr, s), "single request");
+    SERVE_CATCH
+    return SPMV_OK;
+}
+
+int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const int32_t* width,
+                   const uint64_t* seed, const double* arrival_s, int mode, double* latency_s,
+                   uint64_t* hash_out, int64_t* stats) {
+    SERVE_TRY
+    if (!sv) spmvk::fail(SPMV_EINVAL, "server is NULL");
+    if (n_req < 0 || (n_req > 0 && (!matrix || !width || !seed || !arrival_s || !latency_s)))
+        spmvk::fail(SPMV_EINVAL, "request arrays are NULL");
+    if (mode != SPMV_SERVE_BATCHED && mode != SPMV_SERVE_PLAIN) spmvk::fail(SPMV_EINVAL, "mode %d", mode);
+    const int M = sv->mats->count;
+    for (int64_t r = 0; r < n_req; ++r) {
+        if (matrix[r] < 0 || matrix[r] >= M) spmvk::fail(SPMV_EINVAL, "request %lld: matrix %d", (long long)r, matrix[r]);
+        if (width[r] < 1 || width[r] > kMaxW) spmvk::fail(SPMV_EINVAL, "request %lld: width %d", (long long)r, width[r]);
+        if (r && arrival_s[r] < arrival_s[r - 1]) spmvk::fail(SPMV_EINVAL, "arrivals must be non-decreasing");
+    }
+    for (int m = 0; m < M; ++m)
+        if ((size_t)2 * sv->mats->mats[m].n * kMaxW * sizeof(double) + 256 > sv->pool.capacity())
+            spmvk::fail(SPMV_ENOMEM, "matrix %d: one block of it exceeds the budget", m);
+    if (hash_out) {
+        if ((size_t)n_req > sv->hash_cap) {
+            if (sv->d_hash) cudaFree(sv->d_hash);
+            sv->d_hash = nullptr;
+            spmvk::check_cuda(cudaMalloc(reinterpret_cast<void**>(&sv->d_hash), (size_t)n_req * 8 + 8), "hashes");
+            sv->hash_cap = (size_t)n_req;
+        }
+        spmvk::check_cuda(cudaMemset(sv->d_hash, 0, (size_t)n_req * 8 + 8), "hashes");
+    }
+    struct Inflight {
+        bool busy = false;
+        std::vector<int64_t> reqs;
+        long long off = -1;
+        size_t bytes = 0;
+    };
+    std::vector<Inflight> slot(sv->n_streams);
+    std::vector<std::deque<int64_t>> pending(M);
+    int64_t next = 0, done = 0, blocks = 0, waits_mem = 0, max_inflight = 0, admitted_while_busy = 0;
+    int rr = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    auto now_s = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    int64_t queued = 0;
+    int64_t last_done = 0;
+    double last_progress = 0.0;
+    while (done < n_req) {
+        const double now = now_s();
+        if (done != last_done) {
+            last_done = done;
+            last_progress = now;
+        } else if (now - last_progress > 30.0 && next >= n_req) {
+            spmvk::fail(SPMV_ETIMEOUT, "no request completed for 30 s");
+        }
+        // admission of the requests that have arrived
+        int busy_now = 0;
+        for (auto& sl : slot) busy_now += sl.busy;
+        while (next < n_req && arrival_s[next] <= now) {
+            pending[matrix[next]].push_back(next);
+            if (busy_now) ++admitted_while_busy;
+            ++next;
+            ++queued;
+        }
+        // completions
+        for (int i = 0; i < sv->n_streams; ++i) {
+            Inflight& sl = slot[i];
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sv->events[i]);
+            if (q == cudaErrorNotReady) continue;
+            spmvk::check_cuda(q, "block completion");
+            const double t = now_s();
+            for (int64_t r : sl.reqs) latency_s[r] = t - arrival_s[r];
+            done += (int64_t)sl.reqs.size();
+            sv->pool.release(sl.off, sl.bytes);
+            sl.busy = false;
+            sl.reqs.clear();
+        }
+        // launches: one block per free slot, matrices taken round robin
+        if (queued > 0) {
+            for (int i = 0; i < sv->n_streams && queued > 0; ++i) {
+                if (slot[i].busy) continue;
+                int m = -1;
+                for (int k = 0; k < M; ++k) {
+                    const int c = (rr + k) % M;
+                    if (!pending[c].empty()) {
+                        m = c;
+                        break;
+                    }
+                }
+                if (m < 0) break;
+                rr = (m + 1) % M;
+                const int n = sv->mats->mats[m].n;
+                const size_t bytes = (size_t)2 * n * kMaxW * sizeof(double);
+                const long long off = sv->pool.alloc(bytes);
+                if (off < 0) {   // over budget: wait for memory to free up
+                    ++waits_mem;
+                    break;
+                }
+                BlockDesc b{};
+                int wsum = 0;
+                std::vector<int64_t> reqs;
+                auto& q = pending[m];
+                while (!q.empty() && b.n_req < kMaxW) {
+                    const int64_t r = q.front();
+                    if (wsum + width[r] > kMaxW) break;
+                    b.req[b.n_req++] = BlockReq{seed[r], wsum, width[r], (int)r, 0};
+                    wsum += width[r];
+                    reqs.push_back(r);
+                    q.pop_front();
+                    if (mode == SPMV_SERVE_PLAIN) break;   // one request per launch
+                }
+                b.width = wsum;
+                queued -= (int64_t)reqs.size();
+                double* X = reinterpret_cast<double*>(sv->pool.ptr(off));
+                double* Y = X + (size_t)n * kMaxW;
+                spmvk::check_cuda(launch_block(sv, m, b, X, Y, hash_out ? sv->d_hash : nullptr,
+                                               sv->streams[i]),
+                                  "block launch");
+                spmvk::check_cuda(cudaEventRecord(sv->events[i], sv->streams[i]), "event");
+                slot[i].busy = true;
+                slot[i].reqs = std::move(reqs);
+                slot[i].off = off;
+                slot[i].bytes = bytes;
+                ++blocks;
+            }
+        }
+        int64_t inflight = 0;
+        for (auto& sl : slot) inflight += sl.busy;
+        max_inflight = std::max(max_inflight, inflight);
+    }
+    const double elapsed = now_s();
+    if (hash_out && n_req > 0)
+        spmvk::check_cuda(cudaMemcpy(hash_out, sv->d_hash, (size_t)n_req * 8, cudaMemcpyDeviceToHost), "hashes");
+    if (stats) {
+        stats[0] = blocks;
+        stats[1] = max_inflight;
+        stats[2] = waits_mem;
+        stats[3] = (int64_t)sv->pool.peak();
+        stats[4] = (int64_t)(elapsed * 1e9);
+        stats[5] = admitted_while_busy;
+    }
+    SERVE_CATCH
+    return SPMV_OK;
+}
+
+}  // extern "C"

@@ -21,11 +21,14 @@ OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
 COARSE, PER_PARTITION = 0, 1
 RUN_EAGER, RUN_CAPTURE, RUN_REPLAY = 0, 1, 2
-VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS = 0, 1, 2, 3
+VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP = 0, 1, 2, 3, 4
+SERVE_BATCHED, SERVE_PLAIN = 0, 1
 (Q_N, Q_P, Q_GRANULARITY, Q_NNZ, Q_NNZ_LOCAL, Q_NNZ_REMOTE, Q_N_SEND, Q_N_HALO,
  Q_N_REMOTE_ROWS, Q_N_OPS, Q_N_EDGES, Q_ALG_BYTES, Q_ALG_BYTES_LOCAL,
  Q_DEVICE_BYTES, Q_LAST_RECORDS, Q_LAST_WAITS, Q_ERROR, Q_LOCAL_VARIANT,
  Q_N_LOCAL_TILES, Q_LAST_LAUNCHES, Q_REMOTE_VARIANT) = range(21)
+(BQ_COUNT, BQ_TOTAL_ROWS, BQ_TOTAL_NNZ, BQ_ITEMS, BQ_ALG_BYTES, BQ_OFFSET, BQ_N, BQ_NNZ,
+ BQ_LANES, BQ_DEVICE_BYTES) = range(10)
 (X_BOUNDS, X_L_PTR, X_L_COL, X_L_VAL, X_R_PTR, X_R_COL, X_R_VAL, X_HALO,
  X_SEND_IDX, X_HALO_OFF, X_SEG_OFF, X_SENDBUF, X_RECVBUF) = range(13)
 _X_DTYPE = {X_BOUNDS: np.int64, X_L_PTR: np.int64, X_L_COL: np.int32,
@@ -75,6 +78,17 @@ def _load():
         "spmv_csr_merge": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_merge_noalloc": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_error": [P64],
+        "spmv_batch_create": [i32, vp, vp, vp, vp, ctypes.POINTER(vp)],
+        "spmv_batch_destroy": [vp],
+        "spmv_batch_set_lanes": [vp, i32, i32],
+        "spmv_batch_query": [vp, i32, i32, P64],
+        "spmv_batch_run": [vp, vp, vp, vp],
+        "spmv_batch_run_separate": [vp, i32, vp, vp, vp],
+        "spmv_serve_create": [vp, i32, i64, ctypes.POINTER(vp)],
+        "spmv_serve_destroy": [vp],
+        "spmv_serve_run": [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp],
+        "spmv_serve_single": [vp, i32, i32, ctypes.c_uint64, vp, vp, vp],
+        "spmv_selftest_wait_timeout": [i64, P64],
         "spmv_last_error": [],
     }
     for name, args in sig.items():
@@ -223,6 +237,12 @@ def spmv_csr_merge_noalloc(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_
                                       _ptr(vals_dev), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
 
 
+def spmv_selftest_wait_timeout(limit_ns):
+    out = ctypes.c_int64()
+    _check(lib.spmv_selftest_wait_timeout(int(limit_ns), ctypes.byref(out)))
+    return out.value
+
+
 def spmv_csr_error():
     out = ctypes.c_int64()
     _check(lib.spmv_csr_error(ctypes.byref(out)))
@@ -268,3 +288,124 @@ class Part:
 
     def run(self, order, stream_of_op, streams, x, y, flags=RUN_EAGER, graph=0):
         return spmv_schedule_run(self.h, order, stream_of_op, streams, x, y, flags, graph)
+
+
+def spmv_batch_create(mats):
+    """mats: list of (n, row_ptr, col_idx, vals) host CSR; returns (handle,
+    arrays kept alive until the call returns)."""
+    keep = []
+    ns = np.array([int(m[0]) for m in mats], dtype=np.int64)
+    ptrs = (ctypes.c_void_p * len(mats))()
+    cols = (ctypes.c_void_p * len(mats))()
+    vals = (ctypes.c_void_p * len(mats))()
+    for i, (n, rp, ci, va) in enumerate(mats):
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        va = np.ascontiguousarray(va, dtype=np.float64)
+        keep += [rp, ci, va]
+        ptrs[i] = rp.ctypes.data
+        cols[i] = ci.ctypes.data if ci.size else None
+        vals[i] = va.ctypes.data if va.size else None
+    h = ctypes.c_void_p()
+    _check(lib.spmv_batch_create(len(mats), _ptr(ns), ptrs, cols, vals, ctypes.byref(h)))
+    return h
+
+
+def spmv_batch_destroy(h):
+    _check(lib.spmv_batch_destroy(h))
+
+
+def spmv_batch_set_lanes(h, m, lanes):
+    _check(lib.spmv_batch_set_lanes(h, int(m), int(lanes)))
+
+
+def spmv_batch_query(h, what, m=-1):
+    out = ctypes.c_int64()
+    _check(lib.spmv_batch_query(h, int(what), int(m), ctypes.byref(out)))
+    return out.value
+
+
+def spmv_batch_run(h, x_dev, y_dev, stream):
+    _check(lib.spmv_batch_run(h, _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_batch_run_separate(h, m, x_dev, y_dev, stream):
+    _check(lib.spmv_batch_run_separate(h, int(m), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+class Batch:
+    """Owns one batch handle (many independent CSR matrices)."""
+
+    def __init__(self, mats):
+        self.h = spmv_batch_create(mats)
+        self.count = len(mats)
+
+    def close(self):
+        if self.h is not None:
+            spmv_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def query(self, what, m=-1):
+        return spmv_batch_query(self.h, what, m)
+
+    def offsets(self):
+        return [self.query(BQ_OFFSET, m) for m in range(self.count)] + [self.query(BQ_TOTAL_ROWS)]
+
+
+def spmv_serve_create(batch_handle, n_streams, budget_bytes):
+    h = ctypes.c_void_p()
+    _check(lib.spmv_serve_create(batch_handle, int(n_streams), int(budget_bytes), ctypes.byref(h)))
+    return h
+
+
+def spmv_serve_destroy(h):
+    _check(lib.spmv_serve_destroy(h))
+
+
+def spmv_serve_run(h, matrix, width, seed, arrival_s, mode=SERVE_BATCHED, want_hash=True):
+    """Run requests open loop; returns (latency_s, hashes or None, stats dict)."""
+    m = np.ascontiguousarray(matrix, dtype=np.int32)
+    w = np.ascontiguousarray(width, dtype=np.int32)
+    sd = np.ascontiguousarray(seed, dtype=np.uint64)
+    t = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    lat = np.zeros(m.size, dtype=np.float64)
+    hs = np.zeros(m.size, dtype=np.uint64) if want_hash else None
+    st = np.zeros(6, dtype=np.int64)
+    _check(lib.spmv_serve_run(h, m.size, _ptr(m), _ptr(w), _ptr(sd), _ptr(t), int(mode), _ptr(lat),
+                              _ptr(hs) if hs is not None else None, _ptr(st)))
+    keys = ["blocks", "max_inflight", "waits_for_memory", "peak_pool_bytes", "elapsed_ns",
+            "admitted_while_busy"]
+    return lat, hs, dict(zip(keys, (int(v) for v in st)))
+
+
+def spmv_serve_single(h, matrix, width, seed, y_dev, x_dev, stream):
+    _check(lib.spmv_serve_single(h, int(matrix), int(width), ctypes.c_uint64(int(seed)),
+                                 _ptr(y_dev), _ptr(x_dev), _stream(stream)))
+
+
+class Server:
+    """Owns one serving runtime over a Batch of resident matrices."""
+
+    def __init__(self, batch, n_streams=8, budget_bytes=40 << 30):
+        self.batch = batch
+        self.h = spmv_serve_create(batch.h, n_streams, budget_bytes)
+
+    def close(self):
+        if self.h is not None:
+            spmv_serve_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, matrix, width, seed, arrival_s, mode=SERVE_BATCHED, want_hash=True):
+        return spmv_serve_run(self.h, matrix, width, seed, arrival_s, mode, want_hash)

@@ -118,26 +118,30 @@ def _fill_rows(rng, n, lengths, local_frac, window):
     nnz = int(row_ptr[-1])
     rows = np.repeat(np.arange(n, dtype=np.int64), lengths)
 
-    def draw(r):
+    def draw(r, frac=local_frac):
         """One column per entry of row array r."""
         lo = np.maximum(r - window, 0)
         hi = np.minimum(r + window, n - 1)
-        loc = rng.random(r.size) < local_frac
+        loc = rng.random(r.size) < frac
         c = rng.integers(0, n, size=r.size)
         c[loc] = lo[loc] + (rng.random(int(loc.sum())) * (hi[loc] - lo[loc] + 1)).astype(np.int64)
         return c
 
     cols = draw(rows)
-    for _ in range(200):
-        # rows stay grouped and ascending; sort columns within each row
-        order = np.lexsort((cols, rows))
-        cols = cols[order]
+    for rnd in range(400):
+        # rows stay grouped and ascending; sort columns within each row by
+        # sorting the combined key row * n + column
+        key = rows * n + cols
+        key.sort()
+        cols = key - rows * n
+        del key
         dup = np.zeros(nnz, dtype=bool)
         dup[1:] = (cols[1:] == cols[:-1]) & (rows[1:] == rows[:-1])
         if not dup.any():
             break
         redo = np.nonzero(dup)[0]
-        cols[redo] = draw(rows[redo])
+        # a row longer than its window allows ends with uniform redraws
+        cols[redo] = draw(rows[redo], local_frac if rnd < 20 else 0.0)
     else:
         raise RuntimeError("could not make columns distinct")
     return row_ptr, cols.astype(np.int32)
@@ -157,8 +161,9 @@ def powerlaw(n=4_000_000, seed=3, alpha=2.0, cap=4096, mult=3,
 
 
 def zipf_random(n, seed=0, mult=2, cap=4096):
-    """Zipf-row random matrix of the batched mix (mean about 10 nnz/row)."""
-    return powerlaw(n, seed=seed, mult=mult, cap=min(cap, n))
+    """Zipf-row random matrix of the batched mix (mean about 10 nnz/row);
+    rows hold at most min(cap, n/4) entries."""
+    return powerlaw(n, seed=seed, mult=mult, cap=max(1, min(cap, n // 4)))
 
 
 def band(n=150_000, nnz=1_500_000, half_width=37_500, seed=7):
@@ -247,6 +252,55 @@ def batch_mix(count=256, seed=5, n_lo=1e3, n_hi=1e6):
         else:
             out.append(("zipf", zipf_random(int(round(target)), seed=s)))
     return out
+
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed, t):
+    """SplitMix64 (Steele, Lea and Flood) output for state seed + (t+1)*golden,
+    elementwise over uint64 arrays t (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(t, dtype=np.uint64) + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def request_x(seed, n, width):
+    """X (n x width) of a serving request: element (i, j) = 2u - 1 with
+    u = (splitmix64(seed, 8 i + j) >> 11) * 2^-53."""
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    j = np.arange(width, dtype=np.uint64)[None, :]
+    z = splitmix64(seed, i * np.uint64(8) + j)
+    return (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 * 2.0 - 1.0
+
+
+def serve_mix(count=64, seed=6, n_lo=1e4, n_hi=2e6, total_bytes=1.5e9):
+    """Resident matrices of the serving workload: n log-uniform in
+    [n_lo, n_hi], alternating 7-point stencils and power-law rows, with every
+    n scaled by one factor so the CSR bytes total about total_bytes."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=count))
+    est = sum((104.0 if i % 2 == 0 else 146.0) * n for i, n in enumerate(ns))
+    ns = ns * min(1.0, total_bytes / est)
+    out = []
+    for i, n in enumerate(ns):
+        s = int(rng.integers(0, 2**31 - 1))
+        if i % 2 == 0:
+            g = max(2, int(round(n ** (1.0 / 3.0))))
+            out.append(("7pt", stencil_7pt(g, seed=s)))
+        else:
+            out.append(("powerlaw", zipf_random(max(16, int(round(n))), seed=s)))
+    return out
+
+
+def poisson_arrivals(rate, duration_s, seed=7):
+    """Arrival times (s) of a Poisson process of `rate` per second."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=int(rate * duration_s * 1.2) + 16)
+    t = np.cumsum(gaps)
+    return t[t < duration_s]
 
 
 def csr_nbytes(n, nnz):

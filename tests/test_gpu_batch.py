@@ -1,0 +1,92 @@
+"""Batched products (many independent CSR matrices in one persistent
+launch) against the oracle and against one launch per matrix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02530_gb300 import workloads as W
+from tests.gpu_util import assert_fp64_close, dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    mats = [W.laplacian_5pt(17), W.stencil_7pt(9, seed=1), W.powerlaw(5000, seed=2, cap=2000),
+            W.random_csr(1, density=1.0, seed=3, empty_rows=False),
+            (0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0)),
+            W.random_csr(300, density=0.05, seed=4, duplicates=True, shuffle_cols=True),
+            (50, np.zeros(51, np.int64), np.zeros(0, np.int32), np.zeros(0)),
+            W.stencil_27pt(0, seed=5, dims=(5, 7, 11)), W.zipf_random(3000, seed=6)]
+    return mats
+
+
+def _oracle(mats, x, offs):
+    want, scale = np.zeros(offs[-1]), np.zeros(offs[-1])
+    for m, (n, rp, ci, va) in enumerate(mats):
+        xs = x[offs[m]:offs[m] + n]
+        want[offs[m]:offs[m] + n] = oracle.csr_spmv(n, rp, ci, va, xs)
+        scale[offs[m]:offs[m] + n] = oracle.csr_absdot(n, rp, ci, va, xs)
+    return want, scale
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32, "mixed"])
+def test_batch_matches_oracle_and_separate_launches(lanes):
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = _mix()
+    with spmv.Batch(mats) as b:
+        offs = b.offsets()
+        assert offs[-1] == sum(m[0] for m in mats)
+        if lanes == "mixed":
+            for m in range(b.count):
+                spmv.spmv_batch_set_lanes(b.h, m, [1, 2, 4, 8, 16, 32][m % 6])
+        else:
+            spmv.spmv_batch_set_lanes(b.h, -1, lanes)
+        x = W.uniform_x(offs[-1], seed=9)
+        want, scale = _oracle(mats, x, offs)
+        s = torch.cuda.Stream()
+        x_d = dev(x)
+        y1 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
+        y2 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
+        spmv.spmv_batch_run(b.h, x_d, y1, s)
+        spmv.spmv_batch_run_separate(b.h, -1, x_d, y2, s)
+        s.synchronize()
+        a1, a2 = y1.cpu().numpy(), y2.cpu().numpy()
+        assert np.array_equal(a1, a2), "batched and separate launches differ"
+        assert_fp64_close(a1, want, scale, "batch lanes=%s" % lanes)
+        spmv.spmv_batch_run(b.h, x_d, y1, s)   # ticket reset between launches
+        s.synchronize()
+        assert np.array_equal(y1.cpu().numpy(), a1)
+
+
+def test_batch_rejects_bad_arguments():
+    from paper_2203_02530_gb300 import spmv
+    torch_cuda()
+    with spmv.Batch(_mix()[:3]) as b:
+        with pytest.raises(spmv.SpmvError):
+            spmv.spmv_batch_set_lanes(b.h, 0, 3)
+        with pytest.raises(spmv.SpmvError):
+            spmv.spmv_batch_set_lanes(b.h, 7, 2)
+        with pytest.raises(spmv.SpmvError):
+            spmv.spmv_batch_query(b.h, spmv.BQ_N, 5)
+    with pytest.raises(spmv.SpmvError):
+        spmv.Batch([(2, np.array([0, 1, 2]), np.array([0, 9], np.int32), np.ones(2))])
+
+
+def test_batch_autotune_keeps_results():
+    from paper_2203_02530_gb300 import autotune, spmv
+    torch = torch_cuda()
+    mats = _mix()
+    with spmv.Batch(mats) as b:
+        offs = b.offsets()
+        x = W.uniform_x(offs[-1], seed=10)
+        want, scale = _oracle(mats, x, offs)
+        s = torch.cuda.Stream()
+        x_d = dev(x)
+        y = torch.empty(offs[-1], dtype=torch.float64, device="cuda")
+        chosen = autotune.tune_batch(b, x_d, y, s)
+        assert len(chosen) == len(mats)
+        assert [b.query(spmv.BQ_LANES, m) for m in range(b.count)] == chosen
+        spmv.spmv_batch_run(b.h, x_d, y, s)
+        s.synchronize()
+        assert_fp64_close(y.cpu().numpy(), want, scale, "tuned batch")

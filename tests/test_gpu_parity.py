@@ -67,7 +67,8 @@ def case(name):
 
 
 VARIANTS = ([("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)]
-            + [("pairs", v) for v in (1, 2, 4, 8)] + [("merge", 0)])
+            + [("pairs", v) for v in (1, 2, 4, 8)] + [("warp", g) for g in range(4)]
+            + [("merge", 0)])
 
 
 def make_part(n, rp, ci, va, P, gran=0):
@@ -79,7 +80,8 @@ def set_variant(part, v):
     from paper_2203_02530_gb300 import spmv
     kind, param = v
     part.set_variant({"tile": spmv.VARIANT_TILE, "vector": spmv.VARIANT_VECTOR,
-                      "merge": spmv.VARIANT_MERGE, "pairs": spmv.VARIANT_PAIRS}[kind], param)
+                      "merge": spmv.VARIANT_MERGE, "pairs": spmv.VARIANT_PAIRS,
+                      "warp": spmv.VARIANT_WARP}[kind], param)
 
 
 def run_default(part, x_d, y_d, stream):
@@ -443,3 +445,20 @@ def test_full_size_powerlaw_4M_per_partition():
             part.run(order, [0] * 32, [s], x_d, y_d, spmv.RUN_EAGER)
             s.synchronize()
             assert_fp64_close(y_d.cpu().numpy(), want, scale, "powerlaw %s" % (variant,))
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A wait that nothing completes gives up after its limit and reports
+    the timeout status; the device stays usable afterwards."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    assert spmv.spmv_selftest_wait_timeout(2_000_000) == 6
+    n, rp, ci, va, P, x = case("lap64")
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P) as part:
+        run_default(part, dev(x), y_d, s)
+        s.synchronize()
+        assert_fp64_close(y_d.cpu().numpy(), want, scale, "after the timeout self-test")
+        assert part.query(spmv.Q_ERROR) == 0

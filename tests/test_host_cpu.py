@@ -85,3 +85,56 @@ def test_enumerator_small_dags():
 def test_canonicalize():
     # op 2 comes first and its stream becomes 0; op 0 then opens stream 1
     assert E.canonicalize([2, 0, 1, 3], [1, 1, 0, 3]) == [1, 1, 0, 2]
+
+
+def test_splitmix64_published_first_output():
+    """SplitMix64 seeded with 0 first returns 0xE220A8397B1DCDAF (the
+    generator of the serving requests' inputs)."""
+    import numpy as np
+    from paper_2203_02530_gb300 import workloads as W
+    assert int(W.splitmix64(0, np.array([0], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+    x = W.request_x(99, 1000, 8)
+    assert x.min() >= -1.0 and x.max() < 1.0 and abs(x.mean()) < 0.05
+
+
+def test_malformed_csr_rejected_before_any_cuda_call(libpath):
+    """Host-side fault injection: bad plans are refused with SPMV_EINVAL /
+    SPMV_EBOUNDS before the library touches the GPU."""
+    import numpy as np
+    from paper_2203_02530_gb300 import spmv
+    bad = [(2, [0, 1, 2], [0, 5], [1.0, 1.0], 1, spmv.EINVAL),     # column out of range
+           (2, [0, 2, 1], [0, 1], [1.0, 1.0], 1, spmv.EINVAL),     # decreasing row_ptr
+           (2, [0, 1, 2], [0, 1], [1.0, 1.0], 0, spmv.EINVAL),     # P < 1
+           (2, [0, 1, 2], [0, 1], [1.0, 1.0], 2000, spmv.EBOUNDS),  # P above the limit
+           (-1, [0], [], [], 1, spmv.EINVAL)]
+    for n, rp, ci, va, P, code in bad:
+        with pytest.raises(spmv.SpmvError) as e:
+            spmv.spmv_part_create(n, np.array(rp), np.array(ci, dtype=np.int32), np.array(va), P)
+        assert e.value.code == code, (n, rp, P)
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_part_create(2, np.array([0, 1, 2]), np.array([0, 1], np.int32), np.ones(2), 1, 7)
+    assert e.value.code == spmv.EINVAL
+
+
+def test_record_log_resumes_without_remeasuring(tmp_path):
+    """Checkpoint/resume of a search: measured programs are read back from
+    the JSONL log and not measured again."""
+    from paper_2203_02530_gb300 import search
+    path = str(tmp_path / "log.jsonl")
+    rec = search.Recorder(path, meta={"workload": "t"})
+    rec.put([0, 1, 2, 3], [0, 0, 0, 0], 1.5e-4)
+    rec.put([1, 0, 2, 3], [0, 1, 0, 1], 1.2e-4)
+    again = search.Recorder(path)
+    assert again.get([0, 1, 2, 3], [0, 0, 0, 0]) == 1.5e-4
+    assert again.get((1, 0, 2, 3), (0, 1, 0, 1)) == 1.2e-4
+    assert again.get([0, 2, 1, 3], [0, 0, 0, 0]) is None
+    calls = []
+
+    class FakePart:
+        def run(self, *a, **k):
+            calls.append(a)
+            raise AssertionError("must not measure a recorded program")
+
+    ev = search.graph_evaluator(FakePart(), [None], None, None, recorder=again)
+    assert ev([0, 1, 2, 3], [0, 0, 0, 0]) == 1.5e-4
+    assert not calls
