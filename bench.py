@@ -689,7 +689,7 @@ def main(argv=None):
     ap.add_argument("--records", default=None, help="JSONL log of every measured schedule")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--serve-streams", type=int, default=8)
+    ap.add_argument("--serve-streams", type=int, default=32)
     ap.add_argument("--serve-saturation", type=int, default=20000)
     args = ap.parse_args(argv)
     if args.warmup < 3:

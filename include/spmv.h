@@ -144,7 +144,8 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *   VECTOR param = lanes per row (2..32), 4 entries per lane per step with
  *          128-bit loads
  *   PAIRS  param = lanes per row (1, 2, 4, 8), one aligned pair of entries per
- *          lane per step, FMA count = the warp's longest share
+ *          lane per step, FMA count = the warp's longest share; 102 / 104:
+ *          2 / 4 lanes with fewer pairs in flight and 8 CTAs per SM
  *   MERGE  merge-path split with deterministic carries (param ignored)
  *   WARP   param = geometry 0..3: warp-private shared-memory pipelines of
  *          32-row tiles (bulk copies per warp, no block-wide barrier), one

@@ -20,7 +20,7 @@ CACHE = os.environ.get("SPMV_TUNE_CACHE",
 
 CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
               + [(spmv.VARIANT_VECTOR, w) for w in (2, 4, 8)]
-              + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8)]
+              + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8, 102, 104)]
               + [(spmv.VARIANT_WARP, g) for g in range(4)]
               + [(spmv.VARIANT_MERGE, 0)])
 

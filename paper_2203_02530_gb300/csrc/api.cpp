@@ -529,8 +529,8 @@ static void prepare_variant(spmv_part* pt, int variant, int param) {
         if (param != 2 && param != 4 && param != 8 && param != 16 && param != 32)
             fail(SPMV_EINVAL, "vector width %d not in {2,4,8,16,32}", param);
     } else if (variant == SPMV_VARIANT_PAIRS) {
-        if (param != 1 && param != 2 && param != 4 && param != 8)
-            fail(SPMV_EINVAL, "lanes per row %d not in {1,2,4,8}", param);
+        if (param != 1 && param != 2 && param != 4 && param != 8 && param != 102 && param != 104)
+            fail(SPMV_EINVAL, "pair variant %d not in {1,2,4,8,102,104}", param);
     } else if (variant == SPMV_VARIANT_WARP) {
         const int cap = spmvk::warp_tile_cap(param);
         if (cap < 0) fail(SPMV_EINVAL, "warp geometry %d not in [0, 4)", param);

@@ -644,9 +644,9 @@ cudaError_t launch_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int
 // partial sums meet in a fixed xor-butterfly.  For a 27-entry row and V = 2
 // this is 14 FMA instructions + 1 add per 16 rows.
 // ------------------------------------------------------------------------
-template <int V, int U>
-__global__ void __launch_bounds__(256, 4) csr_pair_kernel(CsrArgs a, const Tile* __restrict__ tiles,
-                                                       int tile_begin, int tile_end) {
+template <int V, int U, int MINB>
+__global__ void __launch_bounds__(256, MINB) csr_pair_kernel(CsrArgs a, const Tile* __restrict__ tiles,
+                                                          int tile_begin, int tile_end) {
     constexpr int GROUPS = 256 / V;
     const uint64_t pol_keep = policy_evict_last();
     const int lane = threadIdx.x % V;
@@ -703,11 +703,16 @@ cudaError_t launch_pairs(const CsrArgs& a, const Tile* tiles, int tile_begin, in
     if (tile_end <= tile_begin) return cudaSuccess;
     int grid = num_sms * 8;
     if (grid > tile_end - tile_begin) grid = tile_end - tile_begin;
+    // lanes 1/2/4/8: 4 pairs in flight per lane (up to 64 registers);
+    // 102/104: 2 or 4 lanes with 2 pairs in flight in 32 registers, so 8
+    // CTAs (64 warps) fit on an SM
     switch (lanes) {
-        case 1: csr_pair_kernel<1, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 2: csr_pair_kernel<2, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 4: csr_pair_kernel<4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 8: csr_pair_kernel<8, 2><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 1: csr_pair_kernel<1, 4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 2: csr_pair_kernel<2, 4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 4: csr_pair_kernel<4, 4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 8: csr_pair_kernel<8, 2, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 102: csr_pair_kernel<2, 2, 8><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 104: csr_pair_kernel<4, 2, 8><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -63,31 +63,46 @@ struct BlockDesc {
 // X[i, c] for every column of every request of the block (row-major, ld 8):
 // request r's element (i, j) is U(seed_r, 8 i + j).
 __global__ void gen_x_kernel(double* __restrict__ X, int n, BlockDesc b) {
-    const int64_t total = (int64_t)n * kMaxW;
+    const int W = b.width;
+    const int64_t total = (int64_t)n * W;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / kMaxW), c = (int)(e % kMaxW);
+        const int i = (int)(e / W), c = (int)(e % W);
         double v = 0.0;
         for (int r = 0; r < b.n_req; ++r) {
             const BlockReq q = b.req[r];
             if (c >= q.col0 && c < q.col0 + q.width)
                 v = uniform_pm1(q.seed, (uint64_t)i * kMaxW + (uint64_t)(c - q.col0));
         }
-        X[e] = v;
+        X[(int64_t)i * kMaxW + c] = v;
     }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 33)) * 0xFF51AFD7ED558CCDull;
+    z = (z ^ (z >> 33)) * 0xC4CEB9FE1A85EC53ull;
+    return z ^ (z >> 33);
 }
 
 // Y[:, 0..W) = A X[:, 0..W): V lanes per row, lane h takes entries
 // kb + h, kb + h + V, ...; each column accumulates in entry order, then a
 // fixed xor-butterfly over the V lanes.
+// With `hashes`, every request of the block also gets the order-independent
+// hash of its columns: sum (mod 2^64) over its elements (i, j) of
+// mix64(bits(y_ij) + (i * width + j) * golden), accumulated per thread and
+// added once per warp.
 template <int V, int W>
 __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restrict__ ptr,
                                                         const int32_t* __restrict__ col,
                                                         const double* __restrict__ val,
                                                         const double* __restrict__ X,
-                                                        double* __restrict__ Y, int n) {
+                                                        double* __restrict__ Y, int n, BlockDesc b,
+                                                        unsigned long long* __restrict__ hashes) {
     constexpr int GROUPS = kThreads / V;
     const int lane = threadIdx.x % V;
+    unsigned long long h[kMaxW];
+#pragma unroll
+    for (int r = 0; r < kMaxW; ++r) h[r] = 0;
     for (int rbase = (int)blockIdx.x * GROUPS; rbase < n; rbase += (int)gridDim.x * GROUPS) {
         const int row = rbase + (int)threadIdx.x / V;
         double acc[W];
@@ -109,48 +124,47 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restric
         if (row < n && lane == 0) {
 #pragma unroll
             for (int c = 0; c < W; ++c) Y[(int64_t)row * kMaxW + c] = acc[c];
+            if (hashes) {
+#pragma unroll
+                for (int r = 0; r < kMaxW; ++r) {
+                    if (r >= b.n_req) break;
+                    const BlockReq q = b.req[r];
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        if (c >= q.col0 && c < q.col0 + q.width) {
+                            const uint64_t e = (uint64_t)row * q.width + (uint64_t)(c - q.col0);
+                            h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * 0x9E3779B97F4A7C15ull);
+                        }
+                    }
+                }
+            }
         }
     }
-}
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 33)) * 0xFF51AFD7ED558CCDull;
-    z = (z ^ (z >> 33)) * 0xC4CEB9FE1A85EC53ull;
-    return z ^ (z >> 33);
-}
-
-// Order-independent hash of each request's columns of Y: the sum (mod 2^64)
-// of mix64(bits + position); equal hashes <=> (almost surely) equal bits.
-__global__ void hash_kernel(const double* __restrict__ Y, int n, BlockDesc b,
-                            unsigned long long* __restrict__ hashes) {
-    for (int r = 0; r < b.n_req; ++r) {
-        const BlockReq q = b.req[r];
-        unsigned long long h = 0;
-        const int64_t total = (int64_t)n * q.width;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-             e += (int64_t)gridDim.x * blockDim.x) {
-            const int i = (int)(e / q.width), j = (int)(e % q.width);
-            const uint64_t bits = (uint64_t)__double_as_longlong(Y[(int64_t)i * kMaxW + q.col0 + j]);
-            h += mix64(bits + (uint64_t)e * 0x9E3779B97F4A7C15ull);
+    if (hashes) {
+        for (int r = 0; r < b.n_req; ++r) {
+            unsigned long long v = h[r];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + b.req[r].index, v);
         }
-        for (int off = 16; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(hashes + q.index, h);
     }
 }
 
 template <int V>
-cudaError_t launch_spmm_w(int W, const int32_t* ptr, const int32_t* col, const double* val, const double* X,
-                          double* Y, int n, int grid, cudaStream_t s) {
-    switch (W) {
-        case 1: spmm_kernel<V, 1><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        case 2: spmm_kernel<V, 2><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        case 3: spmm_kernel<V, 3><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        case 4: spmm_kernel<V, 4><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        case 5: spmm_kernel<V, 5><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        case 6: spmm_kernel<V, 6><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        case 7: spmm_kernel<V, 7><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
-        default: spmm_kernel<V, 8><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n); break;
+cudaError_t launch_spmm_w(const BlockDesc& b, const int32_t* ptr, const int32_t* col, const double* val,
+                          const double* X, double* Y, int n, int grid, unsigned long long* hashes,
+                          cudaStream_t s) {
+#define SPMM_W(w) spmm_kernel<V, w><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n, b, hashes)
+    switch (b.width) {
+        case 1: SPMM_W(1); break;
+        case 2: SPMM_W(2); break;
+        case 3: SPMM_W(3); break;
+        case 4: SPMM_W(4); break;
+        case 5: SPMM_W(5); break;
+        case 6: SPMM_W(6); break;
+        case 7: SPMM_W(7); break;
+        default: SPMM_W(8); break;
     }
+#undef SPMM_W
     return cudaGetLastError();
 }
 
@@ -236,7 +250,7 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     const BatchMat& M = bt->mats[m];
     const int n = M.n;
     if (n == 0) return cudaSuccess;
-    int g = (int)std::min<int64_t>(((int64_t)n * kMaxW + kThreads - 1) / kThreads, (int64_t)sv->num_sms * 8);
+    int g = (int)std::min<int64_t>(((int64_t)n * b.width + kThreads - 1) / kThreads, (int64_t)sv->num_sms * 8);
     gen_x_kernel<<<g, kThreads, 0, s>>>(X, n, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -246,15 +260,10 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     const int V = sv->lanes[m];
     int grid = (int)std::min<int64_t>((n + (kThreads / V) - 1) / (kThreads / V), (int64_t)sv->num_sms * 8);
     switch (V) {
-        case 1: e = launch_spmm_w<1>(b.width, ptr, col, val, X, Y, n, grid, s); break;
-        case 2: e = launch_spmm_w<2>(b.width, ptr, col, val, X, Y, n, grid, s); break;
-        case 4: e = launch_spmm_w<4>(b.width, ptr, col, val, X, Y, n, grid, s); break;
-        default: e = launch_spmm_w<8>(b.width, ptr, col, val, X, Y, n, grid, s); break;
-    }
-    if (e != cudaSuccess) return e;
-    if (hashes) {
-        hash_kernel<<<std::min(g, sv->num_sms * 4), kThreads, 0, s>>>(Y, n, b, hashes);
-        e = cudaGetLastError();
+        case 1: e = launch_spmm_w<1>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
+        case 2: e = launch_spmm_w<2>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
+        case 4: e = launch_spmm_w<4>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
+        default: e = launch_spmm_w<8>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
     }
     return e;
 }

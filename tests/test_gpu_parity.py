@@ -67,7 +67,7 @@ def case(name):
 
 
 VARIANTS = ([("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)]
-            + [("pairs", v) for v in (1, 2, 4, 8)] + [("warp", g) for g in range(4)]
+            + [("pairs", v) for v in (1, 2, 4, 8, 102, 104)] + [("warp", g) for g in range(4)]
             + [("merge", 0)])
 
 
