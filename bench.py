@@ -145,7 +145,7 @@ def hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "merge.cu"):
+    for f in ("kernels.cu", "merge.cu", "sell.cu"):
         with open(os.path.join(ROOT, "paper_2203_02530_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -337,7 +337,7 @@ def run_ours(args, world, rank, local):
     achieved = alg_local / t_local / 1e9
     kname = {spmv.VARIANT_TILE: "csr_tile_kernel", spmv.VARIANT_VECTOR: "csr_vector_kernel",
              spmv.VARIANT_MERGE: "merge_kernel", spmv.VARIANT_PAIRS: "csr_pair_kernel",
-             spmv.VARIANT_WARP: "csr_warp_kernel"}[variant]
+             spmv.VARIANT_WARP: "csr_warp_kernel", spmv.VARIANT_SELL: "csr_sell_kernel"}[variant]
     traffic = profiled_traffic("%s/%d" % (kname, vparam))
 
     # paper protocol: per-measurement latency percentiles of the best schedule

@@ -96,8 +96,16 @@ enum {
     SPMV_Q_N_REMOTE_ROWS = 8,     /* rows with at least one remote entry */
     SPMV_Q_N_OPS = 9,             /* operations of the DAG */
     SPMV_Q_N_EDGES = 10,          /* dependency edges of the DAG */
-    SPMV_Q_ALG_BYTES = 11,        /* algorithmic bytes of one SpMV (DESIGN) */
-    SPMV_Q_ALG_BYTES_LOCAL = 12,  /* algorithmic bytes of the LOCAL op */
+    SPMV_Q_ALG_BYTES = 11,        /* algorithmic bytes of one SpMV: the LOCAL
+                                     op's, plus 12 per remote entry, 8 per
+                                     compressed remote row (row id, pointer)
+                                     and 4 for the closing pointer, 16 per
+                                     remote row (y read and written),
+                                     12 per send slot (index, slot), 16 per
+                                     exchanged entry, 8 per remote halo read */
+    SPMV_Q_ALG_BYTES_LOCAL = 12,  /* algorithmic bytes of the LOCAL op: 12 per
+                                     local entry (value, column), 4 per row
+                                     pointer (n + 1), 16 per row (x, y) */
     SPMV_Q_DEVICE_BYTES = 13,     /* device memory the plan holds */
     SPMV_Q_LAST_RECORDS = 14,     /* events recorded for DAG edges by the last issue */
     SPMV_Q_LAST_WAITS = 15,       /* stream waits issued for DAG edges by the last issue */
@@ -105,8 +113,10 @@ enum {
     SPMV_Q_LOCAL_VARIANT = 17,
     SPMV_Q_N_LOCAL_TILES = 18,
     SPMV_Q_LAST_LAUNCHES = 19,    /* kernels launched by the last issue */
-    SPMV_Q_REMOTE_VARIANT = 20    /* 100 * variant + param of the REMOTE product
+    SPMV_Q_REMOTE_VARIANT = 20,   /* 100 * variant + param of the REMOTE product
                                      (SPMV_Q_LOCAL_VARIANT: of the LOCAL one) */
+    SPMV_Q_SELL_ENTRIES = 21      /* padded entries of the sliced layout, local
+                                     plus remote (0 until SELL is first set) */
 };
 int spmv_part_query(const spmv_part* part, int what, int part_idx, int64_t* out);
 
@@ -147,9 +157,20 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *          lane per step, FMA count = the warp's longest share; 102 / 104:
  *          2 / 4 lanes with fewer pairs in flight and 8 CTAs per SM
  *   MERGE  merge-path split with deterministic carries (param ignored)
- *   WARP   param = geometry 0..3: warp-private shared-memory pipelines of
+ *   WARP   param = geometry 0..4: warp-private shared-memory pipelines of
  *          32-row tiles (bulk copies per warp, no block-wide barrier), one
  *          thread per row, one DFMA per entry
+ *   SELL   param = 4, 8, 9 (entries per lane per step) or 104 (4, fewer
+ *          registers): a sliced-ELL copy of A_L and A_R that the plan builds
+ *          on first use (slices of 32 consecutive rows of one rank, entry j
+ *          of row r at slice offset + 32 j + r, rows padded to the slice's
+ *          longest with value 0 and column 0), one thread per row, one FMA
+ *          per stored entry in storage order (padded slots are discarded,
+ *          so y equals WARP's bit for bit on rows that fit its stages).
+ *          SPMV_EINVAL when the padded layout
+ *          would hold more than 2 (nnz_local + nnz_remote) + 32768 entries;
+ *          SPMV_EBOUNDS beyond 2^31.  The copy is device memory the plan
+ *          holds until destroyed.
  * Fails with SPMV_EINVAL while captured graphs exist (they hold the old
  * kernels' tables). */
 enum {
@@ -157,7 +178,8 @@ enum {
     SPMV_VARIANT_VECTOR = 1,
     SPMV_VARIANT_MERGE = 2,
     SPMV_VARIANT_PAIRS = 3,
-    SPMV_VARIANT_WARP = 4
+    SPMV_VARIANT_WARP = 4,
+    SPMV_VARIANT_SELL = 5
 };
 /* Sets the variant of both products. */
 int spmv_part_set_variant(spmv_part* part, int variant, int param);
@@ -274,9 +296,10 @@ int spmv_csr_error(int64_t* out);
 /*
  * Batched products: many independent CSR matrices (no partitioning) kept
  * resident in HBM and multiplied in ONE persistent launch.  Work items are
- * blocks of up to 256 rows of one matrix, claimed by CTAs through an atomic
+ * blocks of up to 256 rows of one matrix, claimed by warps through an atomic
  * ticket; each row is summed by `lanes` lanes (set per matrix, e.g. by an
- * autotuner) in a fixed order, so y is the same, bit for bit, as with
+ * autotuner), a row longer than 64 entries by a whole warp, in a fixed
+ * order, so y is the same, bit for bit, as with
  * spmv_batch_run_separate, which launches the same row code once per
  * matrix.  Not part of the paper's method: a way of running many of its
  * SpMVs at once.
@@ -297,7 +320,9 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
                       const int32_t* const* col_idx, const double* const* vals,
                       spmv_batch** out);
 int spmv_batch_destroy(spmv_batch* batch);
-/* Lanes per row (1, 2, 4, 8, 16, 32) of matrix m, or of every matrix (m = -1). */
+/* Lanes per row (1, 2, 4, 8, 16, 32) of matrix m, or of every matrix (m = -1);
+ * 0 selects warp-staged rows (each warp stages its 32 rows' entries in shared
+ * memory and sums one row per lane; for short rows). */
 int spmv_batch_set_lanes(spmv_batch* batch, int m, int lanes);
 int spmv_batch_query(const spmv_batch* batch, int what, int m, int64_t* out);
 /* Every product in one persistent launch on stream s. */
@@ -316,8 +341,9 @@ int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, doubl
  * around its SpMV.
  * spmv_serve_create: n_streams (1..64) stream slots, one block in flight per
  *   slot; budget_bytes covers the resident matrices plus a pool from which
- *   every in-flight block takes 128 n bytes (X and Y, n x 8 doubles each);
- *   SPMV_ENOMEM when the budget is below the resident matrices.
+ *   every in-flight block of total width w takes 16 n w bytes (X and Y,
+ *   n x w doubles each, row-major); SPMV_ENOMEM when the budget is below the
+ *   resident matrices, SPMV_EBOUNDS for a matrix with n >= 2^28.
  * spmv_serve_run: runs n_req requests open loop against their arrival times
  *   (seconds from the call, non-decreasing), on the host thread, until all
  *   completed.  BATCHED merges the oldest requests of one matrix into one
@@ -331,10 +357,13 @@ int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, doubl
  *   while blocks were in flight.  Each column of a block is summed in the
  *   same order whatever the block's partners, so Y (and the hash) of a
  *   request is the same alone and in any mix.  SPMV_ETIMEOUT if no request
- *   completes for 30 s after the last arrival.
+ *   completes for 30 s after the last arrival; SPMV_ENOMEM (before any
+ *   launch) when a width-8 block of any of the matrices exceeds the pool.
+ * Rows are summed in length buckets fixed per matrix at creation (short rows
+ * by 1-8 lanes chosen from the mean length, rows up to 256 entries by 8
+ * lanes, longer rows by a whole warp), so skewed matrices keep warps busy.
  * spmv_serve_single: one request alone on stream s into caller buffers
- *   x_dev, y_dev (n x 8 doubles each, row-major; columns >= width of Y are
- *   unspecified).
+ *   x_dev, y_dev (n x width doubles each, row-major).
  */
 typedef struct spmv_server spmv_server;
 enum { SPMV_SERVE_BATCHED = 0, SPMV_SERVE_PLAIN = 1 };

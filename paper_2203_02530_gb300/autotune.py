@@ -21,8 +21,9 @@ CACHE = os.environ.get("SPMV_TUNE_CACHE",
 CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
               + [(spmv.VARIANT_VECTOR, w) for w in (2, 4, 8)]
               + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8, 102, 104)]
-              + [(spmv.VARIANT_WARP, g) for g in range(4)]
-              + [(spmv.VARIANT_MERGE, 0)])
+              + [(spmv.VARIANT_WARP, g) for g in range(5)]
+              + [(spmv.VARIANT_MERGE, 0)]
+              + [(spmv.VARIANT_SELL, u) for u in (4, 8, 9, 104)])
 
 
 def signature(n, row_ptr, P, device_name):
@@ -71,12 +72,20 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
            (spmv.OP_REMOTE, lambda: spmv.spmv_remote(part.h, -1, y_dev, stream))]
     best = {}
     for op, run in ops:
+        usable = []
         for trial in range(2):   # two interleaved passes; keep the faster
             for v, p in candidates:
-                part.set_op_variant(op, v, p)
+                try:
+                    part.set_op_variant(op, v, p)
+                except spmv.SpmvError as e:
+                    if e.code != spmv.EINVAL:
+                        raise
+                    continue     # not applicable here (the sliced layout on skewed rows)
                 t = time_loop(run, stream, reps)
                 times[(op, v, p)] = min(t, times.get((op, v, p), t))
-        b = min(((v, p) for v, p in candidates), key=lambda vp: times[(op,) + vp])
+                if trial == 0:
+                    usable.append((v, p))
+        b = min(usable, key=lambda vp: times[(op,) + vp])
         part.set_op_variant(op, *b)
         best[op] = b
     out = {"local": best[spmv.OP_LOCAL], "remote": best[spmv.OP_REMOTE], "times": times}
@@ -87,7 +96,7 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
     return out
 
 
-def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(1, 2, 4, 8, 16),
+def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(0, 1, 2, 4, 8, 16),
                reps=5):
     """Lanes per row for the matrices of a batch, timed on the persistent
     launch itself (one launch per matrix would be dominated by launch

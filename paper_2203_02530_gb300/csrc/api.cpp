@@ -149,6 +149,15 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
                    "warp product");
         return we > wb;
     }
+    if (var == SPMV_VARIANT_SELL) {
+        const std::vector<int64_t>& so = remote ? pt->rslice_off : pt->lslice_off;
+        const int sb = (int)(p < 0 ? 0 : so[p]);
+        const int se = (int)(p < 0 ? so[pt->P] : so[p + 1]);
+        check_cuda(spmvk::launch_sell(a, remote ? pt->rslices : pt->lslices, sb, se, remote ? pt->rs_val : pt->ls_val,
+                                      remote ? pt->rs_col : pt->ls_col, param, pt->num_sms, s),
+                   "sliced product");
+        return se > sb;
+    }
     const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
     if (var == SPMV_VARIANT_VECTOR || var == SPMV_VARIANT_PAIRS) {
         const std::vector<int64_t>& bo = remote ? pt->rblock_off : pt->lblock_off;
@@ -365,6 +374,7 @@ int spmv_part_query(const spmv_part* pt, int what, int part_idx, int64_t* out) {
         }
         case SPMV_Q_LOCAL_VARIANT: *out = pt->variant[0] * 100 + pt->vparam[0]; break;
         case SPMV_Q_REMOTE_VARIANT: *out = pt->variant[1] * 100 + pt->vparam[1]; break;
+        case SPMV_Q_SELL_ENTRIES: *out = pt->sell_entries; break;
         case SPMV_Q_N_LOCAL_TILES: *out = pt->ltile_off.empty() ? 0 : pt->ltile_off[pt->P]; break;
         case SPMV_Q_LAST_LAUNCHES: *out = pt->last_launches; break;
         default: fail(SPMV_EINVAL, "unknown query %d", what);
@@ -533,12 +543,16 @@ static void prepare_variant(spmv_part* pt, int variant, int param) {
             fail(SPMV_EINVAL, "pair variant %d not in {1,2,4,8,102,104}", param);
     } else if (variant == SPMV_VARIANT_WARP) {
         const int cap = spmvk::warp_tile_cap(param);
-        if (cap < 0) fail(SPMV_EINVAL, "warp geometry %d not in [0, 4)", param);
+        if (cap < 0) fail(SPMV_EINVAL, "warp geometry %d not in [0, 5)", param);
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->lwtiles || pt->wtile_cap != cap) spmvk::build_warp_tiles(pt, cap);
     } else if (variant == SPMV_VARIANT_MERGE) {
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
+    } else if (variant == SPMV_VARIANT_SELL) {
+        if (!spmvk::sell_param_supported(param)) fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104}", param);
+        check_cuda(cudaDeviceSynchronize(), "synchronize");
+        if (!pt->sell_entries) spmvk::build_sell(pt);
     } else {
         fail(SPMV_EINVAL, "unknown variant %d", variant);
     }

@@ -3,11 +3,12 @@
 // The matrices of a batch live back to back in HBM (row pointers local to
 // each matrix, entries padded to a multiple of 4 so every matrix starts
 // 16-byte aligned).  A work item is a block of up to 256 rows of one matrix;
-// persistent CTAs claim items with an atomic ticket and compute every row
-// with the pair-per-lane scheme (lanes per row chosen per matrix by the
-// autotuner).  The plain alternative launches the same per-row code once
-// per matrix; both give bit-identical results because each row is summed
-// by the same lanes in the same order.
+// the warps of a persistent grid claim items with an atomic ticket and
+// compute every row with the pair-per-lane scheme or warp-staged rows
+// (chosen per matrix by the autotuner); rows longer than 64 entries are
+// summed by a whole warp.  The plain alternative launches the same per-row
+// code once per matrix; both give bit-identical results because each row
+// is summed by the same lanes in the same order.
 #include "batch.h"
 
 #include <cuda_runtime.h>
@@ -50,15 +51,58 @@ __device__ __forceinline__ double ldg_keep(const double* p, uint64_t policy) {
     return v;
 }
 
-// Rows [r0, r1) of one matrix: V lanes per row, lane h takes the aligned
-// entry pairs h, h+V, ...; the FMA loop runs the warp's longest share.
-template <int V>
-__device__ __forceinline__ void batch_rows(const BatchArgs& a, const BatchMat& m, int r0, int r1,
+constexpr int kLongRow = 64;   // rows longer than this are summed by a whole warp
+
+// One row summed by the 32 lanes of a warp: lane l takes entries l, l+32,
+// ... in order (four loads in flight), then a fixed xor-butterfly; every
+// lane returns the total.
+__device__ __forceinline__ double warp_row(const int32_t* col, const double* val, const double* x, int kb, int ke,
                                            uint64_t pol) {
-    constexpr int GROUPS = kThreads / V;
+    const int lane = threadIdx.x & 31;
+    double part = 0.0;
+    int k = kb + lane;
+    for (; k + 96 < ke; k += 128) {
+        double v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = __ldg(val + k + 32 * u);
+            xv[u] = ldg_keep(x + __ldg(col + k + 32 * u), pol);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) part = fma(v[u], xv[u], part);
+    }
+    for (; k < ke; k += 32) part = fma(__ldg(val + k), ldg_keep(x + __ldg(col + k), pol), part);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    return part;
+}
+
+// The long rows flagged in `mask` (bit = the lane holding the row's kb, ke
+// and row index), one after another, each by the whole warp.
+__device__ __forceinline__ void warp_long_rows(unsigned mask, int kb, int ke, int row, const int32_t* col,
+                                               const double* val, const double* x, double* y, uint64_t pol) {
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int rkb = __shfl_sync(0xffffffffu, kb, src);
+        const int rke = __shfl_sync(0xffffffffu, ke, src);
+        const int rrow = __shfl_sync(0xffffffffu, row, src);
+        const double t = warp_row(col, val, x, rkb, rke, pol);
+        if ((threadIdx.x & 31) == 0) y[rrow] = t;
+    }
+}
+
+// Rows [r0, r1) of one matrix by one warp: V lanes per row, lane h takes the
+// aligned entry pairs h, h+V, ...; the FMA loop runs the warp's longest
+// share.  Rows longer than kLongRow are left out of that loop and summed
+// afterwards by the whole warp, so one long row never holds 32 / V short
+// ones (or the warp) for its whole length.
+template <int V>
+__device__ __forceinline__ void batch_rows(const BatchArgs& a, const BatchMat& m, int r0, int r1, uint64_t pol) {
+    constexpr int GROUPS = 32 / V;
     constexpr int U = 4;
-    const int lane = threadIdx.x % V;
-    const int group = threadIdx.x / V;
+    const int lane = (threadIdx.x & 31) % V;
+    const int group = (threadIdx.x & 31) / V;
     const int32_t* ptr = a.ptr + m.ptr_off;
     const int32_t* col = a.col + m.ent_off;
     const double* val = a.val + m.ent_off;
@@ -67,13 +111,16 @@ __device__ __forceinline__ void batch_rows(const BatchArgs& a, const BatchMat& m
     for (int rbase = r0; rbase < r1; rbase += GROUPS) {
         const int row = rbase + group;
         int kb = 0, ke = 0, k2 = 0, cnt = 0;
+        bool is_long = false;
         if (row < r1) {
             kb = __ldg(ptr + row);
             ke = __ldg(ptr + row + 1);
+            is_long = V < 32 && ke - kb > kLongRow;
             k2 = kb & ~1;
             const int npairs = (ke - k2 + 1) >> 1;
-            cnt = npairs > lane ? (npairs - lane + V - 1) / V : 0;
+            cnt = (!is_long && npairs > lane) ? (npairs - lane + V - 1) / V : 0;
         }
+        const unsigned long_mask = __ballot_sync(0xffffffffu, is_long && lane == 0);
         const int wmax = __reduce_max_sync(0xffffffffu, cnt);
         double sum = 0.0;
         for (int j0 = 0; j0 < wmax; j0 += U) {
@@ -103,14 +150,94 @@ __device__ __forceinline__ void batch_rows(const BatchArgs& a, const BatchMat& m
         }
 #pragma unroll
         for (int off = V / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off, V);
-        if (row < r1 && lane == 0) y[row] = sum;
+        if (row < r1 && lane == 0 && !is_long) y[row] = sum;
+        warp_long_rows(long_mask, kb, ke, row, col, val, x, y, pol);
     }
 }
 
-__device__ __forceinline__ void batch_item(const BatchArgs& a, int it, uint64_t pol) {
+constexpr int kStageEntries = 448;   // per warp: 32 rows x 14 entries
+
+// Warp-staged rows (lanes = 0), 32 rows per pass: when the pass's short
+// rows fit the warp's shared-memory slice, the warp copies their entries in
+// with coalesced loads and every lane sums one row from shared memory (one
+// DFMA per entry, the FMA loop running the warp's longest short row);
+// otherwise each lane sums its short row straight from global memory.
+// Rows longer than kLongRow are summed afterwards by the whole warp.
+__device__ __forceinline__ void batch_rows_staged(const BatchArgs& a, const BatchMat& m, int r0, int r1,
+                                                  uint64_t pol, double* sv, int32_t* sc) {
+    constexpr int CH = 8;
+    const int lane = threadIdx.x & 31;
+    const int32_t* ptr = a.ptr + m.ptr_off;
+    const int32_t* col = a.col + m.ent_off;
+    const double* val = a.val + m.ent_off;
+    const double* x = a.x + m.row_off;
+    double* y = a.y + m.row_off;
+    for (int rb = r0; rb < r1; rb += 32) {
+        const int re = rb + 32 < r1 ? rb + 32 : r1;
+        const int k0 = __ldg(ptr + rb), k1 = __ldg(ptr + re);
+        const int row = rb + lane;
+        int kb = 0, ke = 0;
+        if (row < re) {
+            kb = __ldg(ptr + row);
+            ke = __ldg(ptr + row + 1);
+        }
+        const bool is_long = ke - kb > kLongRow;
+        const unsigned long_mask = __ballot_sync(0xffffffffu, is_long);
+        const int cnt = is_long ? 0 : ke - kb;
+        const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+        double sum = 0.0;
+        if (long_mask == 0 && k1 - k0 <= kStageEntries) {
+            for (int i = lane; i < k1 - k0; i += 32) {
+                sv[i] = __ldg(val + k0 + i);
+                sc[i] = __ldg(col + k0 + i);
+            }
+            __syncwarp();
+            const int sb = kb - k0;
+            for (int base = 0; base < wmax; base += CH) {
+                double xv[CH], vv[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const bool on = base + u < cnt;
+                    vv[u] = on ? sv[sb + base + u] : 0.0;
+                    xv[u] = ldg_keep(x + (on ? sc[sb + base + u] : 0), pol);
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (base + u >= wmax) break;
+                    const double t = fma(vv[u], xv[u], sum);
+                    sum = base + u < cnt ? t : sum;
+                }
+            }
+            __syncwarp();
+        } else {
+            for (int base = 0; base < wmax; base += CH) {
+                double xv[CH], vv[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const bool on = base + u < cnt;
+                    const int k = on ? kb + base + u : 0;
+                    vv[u] = on ? __ldg(val + k) : 0.0;
+                    xv[u] = ldg_keep(x + (on ? __ldg(col + k) : 0), pol);
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (base + u >= wmax) break;
+                    const double t = fma(vv[u], xv[u], sum);
+                    sum = base + u < cnt ? t : sum;
+                }
+            }
+        }
+        if (row < re && !is_long) y[row] = sum;
+        warp_long_rows(long_mask, kb, ke, row, col, val, x, y, pol);
+    }
+}
+
+__device__ __forceinline__ void batch_item(const BatchArgs& a, int it, uint64_t pol, double* sv,
+                                           int32_t* sc) {
     const BatchItem w = a.items[it];
     const BatchMat m = a.mats[w.m];
     switch (m.lanes) {
+        case 0: batch_rows_staged(a, m, w.r0, w.r1, pol, sv, sc); break;
         case 1: batch_rows<1>(a, m, w.r0, w.r1, pol); break;
         case 2: batch_rows<2>(a, m, w.r0, w.r1, pol); break;
         case 4: batch_rows<4>(a, m, w.r0, w.r1, pol); break;
@@ -120,24 +247,31 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, int it, uint64_t 
     }
 }
 
-// Persistent: CTAs claim items with an atomic ticket until none is left.
+// Persistent: every warp claims whole items with an atomic ticket until
+// none is left (no block-wide barrier: warps never wait for each other).
 __global__ void __launch_bounds__(kThreads, 4) batch_persistent_kernel(BatchArgs a) {
-    __shared__ int s_item;
+    __shared__ double s_val[kThreads / 32][kStageEntries];
+    __shared__ int32_t s_col[kThreads / 32][kStageEntries];
     const uint64_t pol = policy_evict_last();
+    const int w = threadIdx.x >> 5;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.ticket, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
+        int it = 0;
+        if ((threadIdx.x & 31) == 0) it = atomicAdd(a.ticket, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= a.n_items) break;
-        batch_item(a, it, pol);
+        batch_item(a, it, pol, s_val[w], s_col[w]);
     }
 }
 
-// Items [first, last) with a grid-stride loop (one matrix per launch).
+// Items [first, last), one per warp, grid-stride (one matrix per launch).
 __global__ void __launch_bounds__(kThreads, 4) batch_range_kernel(BatchArgs a, int first, int last) {
+    __shared__ double s_val[kThreads / 32][kStageEntries];
+    __shared__ int32_t s_col[kThreads / 32][kStageEntries];
     const uint64_t pol = policy_evict_last();
-    for (int it = first + (int)blockIdx.x; it < last; it += (int)gridDim.x) batch_item(a, it, pol);
+    const int w = threadIdx.x >> 5;
+    const int nw = (int)gridDim.x * (kThreads / 32);
+    for (int it = first + (int)blockIdx.x * (kThreads / 32) + w; it < last; it += nw)
+        batch_item(a, it, pol, s_val[w], s_col[w]);
 }
 
 }  // namespace
@@ -293,8 +427,8 @@ int spmv_batch_set_lanes(spmv_batch* b, int m, int lanes) {
     BATCH_TRY
     if (!b) spmvk::fail(SPMV_EINVAL, "batch is NULL");
     if (m < -1 || m >= b->count) spmvk::fail(SPMV_EINVAL, "matrix %d", m);
-    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
-        spmvk::fail(SPMV_EINVAL, "lanes %d not in {1,2,4,8,16,32}", lanes);
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        spmvk::fail(SPMV_EINVAL, "lanes %d not in {0,1,2,4,8,16,32}", lanes);
     const int lo = m < 0 ? 0 : m, hi = m < 0 ? b->count : m + 1;
     for (int i = lo; i < hi; ++i) b->mats[i].lanes = lanes;
     spmvk::check_cuda(cudaMemcpy(b->d_mats + lo, b->mats.data() + lo, (size_t)(hi - lo) * sizeof(BatchMat),
@@ -341,7 +475,8 @@ int spmv_batch_run(spmv_batch* b, const double* x, double* y, cudaStream_t s) {
     if (b->n_items == 0) return SPMV_OK;
     spmvk::check_cuda(cudaMemsetAsync(b->ticket, 0, sizeof(int), s), "ticket reset");
     int grid = b->num_sms * std::max(1, b->occupancy);
-    if (grid > b->n_items) grid = b->n_items;
+    const int need = (b->n_items + kThreads / 32 - 1) / (kThreads / 32);
+    if (grid > need) grid = need;
     batch_persistent_kernel<<<grid, kThreads, 0, s>>>(args_of(b, x, y));
     spmvk::check_cuda(cudaGetLastError(), "batch launch");
     BATCH_CATCH
@@ -359,7 +494,8 @@ int spmv_batch_run_separate(spmv_batch* b, int m, const double* x, double* y, cu
         const int first = b->item_off[i], last = b->item_off[i + 1];
         if (last <= first) continue;
         int grid = b->num_sms * std::max(1, b->occupancy);
-        if (grid > last - first) grid = last - first;
+        const int need = (last - first + kThreads / 32 - 1) / (kThreads / 32);
+        if (grid > need) grid = need;
         batch_range_kernel<<<grid, kThreads, 0, s>>>(a, first, last);
         spmvk::check_cuda(cudaGetLastError(), "matrix launch");
     }

@@ -48,6 +48,14 @@ struct Carry {
     double val;
 };
 
+// Slice of the sliced-ELL layout: rows [r0, r0 + rows) (rows <= 32) of a
+// CSR, every row padded to len entries; entry j of lane r at off + 32 j + r.
+struct SellSlice {
+    int32_t r0, rows, len, xoff;
+    int32_t off, pad0, pad1, pad2;
+};
+static_assert(sizeof(SellSlice) == 32, "slice descriptor is two int4");
+
 // Operands of one CSR product launch.
 struct CsrArgs {
     const int32_t* ptr;     // row pointer of the CSR (row space indices)
@@ -86,6 +94,11 @@ int merge_items_per_tile();
 cudaError_t read_clear_csr_error(int* out);
 int64_t noalloc_max_items();
 cudaError_t launch_merge_noalloc(const CsrArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const double* val, const SellSlice* slices,
+                             int n_slices, double* sval, int32_t* scol, int num_sms, cudaStream_t s);
+cudaError_t launch_sell(const CsrArgs& a, const SellSlice* slices, int slice_begin, int slice_end,
+                        const double* sval, const int32_t* scol, int param, int num_sms, cudaStream_t s);
+bool sell_param_supported(int param);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);
 TileGeom default_tile_geom();

@@ -618,6 +618,7 @@ int warp_tile_cap(int param) {
         case 1: return 896;
         case 2: return 896;
         case 3: return 1792;   // rows up to 56 entries
+        case 4: return 896;
         default: return -1;
     }
 }
@@ -630,6 +631,7 @@ cudaError_t launch_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int
         case 1: return run_warp<4, 896, 2, 16>(a, tiles, tb, te, num_sms, s);    // 88 KB, 2 CTAs
         case 2: return run_warp<10, 896, 2, 16>(a, tiles, tb, te, num_sms, s);   // 219 KB, 1 CTA
         case 3: return run_warp<4, 1792, 2, 16>(a, tiles, tb, te, num_sms, s);   // 174 KB, 1 CTA
+        case 4: return run_warp<10, 896, 2, 32>(a, tiles, tb, te, num_sms, s);   // 219 KB, 32 gathers in flight
         default: return cudaErrorInvalidValue;
     }
 }

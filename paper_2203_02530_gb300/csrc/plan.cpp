@@ -369,4 +369,68 @@ void build_warp_tiles(spmv_part* pt, int cap) {
     pt->wtile_cap = cap;
 }
 
+// Padded entries of the sliced layout of rows [r0, r1): 32 slots per entry
+// position of each slice's longest row.
+int64_t sell_entries_for(const std::vector<int32_t>& ptr, int64_t r0, int64_t r1) {
+    int64_t total = 0;
+    for (int64_t r = r0; r < r1; r += 32) {
+        const int64_t e = std::min(r1, r + 32);
+        int32_t len = 0;
+        for (int64_t i = r; i < e; ++i) len = std::max(len, ptr[(size_t)i + 1] - ptr[(size_t)i]);
+        total += 32 * (int64_t)len;
+    }
+    return total;
+}
+
+// Sliced-ELL copies of A_L and A_R: slices of 32 consecutive rows of one
+// rank, filled on the device from the plan's CSR arrays.  Refused when the
+// padding would more than double the entries (skewed row lengths: use the
+// merge or vector variants there).
+void build_sell(spmv_part* pt) {
+    const int P = pt->P;
+    const std::vector<int32_t> l_ptr = download(pt->l_ptr, (size_t)pt->n + 1);
+    const std::vector<int32_t> rr_ptr = download(pt->rr_ptr, (size_t)pt->n_rr + 1);
+    std::vector<SellSlice> ls, rs;
+    int64_t l_off = 0, r_off = 0;
+    auto slices = [](const std::vector<int32_t>& ptr, int64_t r0, int64_t r1, int32_t xoff, int64_t& off,
+                     std::vector<SellSlice>& out) {
+        for (int64_t r = r0; r < r1; r += 32) {
+            const int64_t e = std::min(r1, r + 32);
+            int32_t len = 0;
+            for (int64_t i = r; i < e; ++i) len = std::max(len, ptr[(size_t)i + 1] - ptr[(size_t)i]);
+            if (off + 32 * (int64_t)len > INT32_MAX - 64) fail(SPMV_EBOUNDS, "sliced layout exceeds 2^31 entries");
+            out.push_back(SellSlice{(int32_t)r, (int32_t)(e - r), len, xoff, (int32_t)off, 0, 0, 0});
+            off += 32 * (int64_t)len;
+        }
+    };
+    pt->lslice_off.assign(P + 1, 0);
+    pt->rslice_off.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        pt->lslice_off[p] = (int64_t)ls.size();
+        slices(l_ptr, pt->bounds[p], pt->bounds[p + 1], (int32_t)pt->bounds[p], l_off, ls);
+        pt->rslice_off[p] = (int64_t)rs.size();
+        slices(rr_ptr, pt->rr_off[p], pt->rr_off[p + 1], 0, r_off, rs);
+    }
+    pt->lslice_off[P] = (int64_t)ls.size();
+    pt->rslice_off[P] = (int64_t)rs.size();
+    const int64_t limit = 2 * (pt->nnz_l + pt->nnz_r) + 32768;
+    if (l_off + r_off > limit)
+        fail(SPMV_EINVAL, "sliced layout would hold %lld entries for %lld stored (limit %lld): row lengths too skewed",
+             (long long)(l_off + r_off), (long long)(pt->nnz_l + pt->nnz_r), (long long)limit);
+    pt->lslices = upload(pt, ls);
+    pt->rslices = upload(pt, rs);
+    pt->ls_val = static_cast<double*>(dev_alloc(pt, (size_t)l_off * 8));
+    pt->ls_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)l_off * 4));
+    pt->rs_val = static_cast<double*>(dev_alloc(pt, (size_t)r_off * 8));
+    pt->rs_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)r_off * 4));
+    check_cuda(launch_sell_fill(pt->l_ptr, pt->l_col, pt->l_val, pt->lslices, (int)ls.size(), pt->ls_val,
+                                pt->ls_col, pt->num_sms, 0),
+               "sliced layout (local)");
+    check_cuda(launch_sell_fill(pt->rr_ptr, pt->r_col, pt->r_val, pt->rslices, (int)rs.size(), pt->rs_val,
+                                pt->rs_col, pt->num_sms, 0),
+               "sliced layout (remote)");
+    check_cuda(cudaDeviceSynchronize(), "sliced layout");
+    pt->sell_entries = l_off + r_off;
+}
+
 }  // namespace spmvk

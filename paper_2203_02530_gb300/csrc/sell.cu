@@ -1,0 +1,169 @@
+// Sliced-ELL form of the CSR products y_L = A_L x_L and y += A_R x_R
+// (Sec. III-A): the plan re-lays each rank's rows out in slices of 32
+// consecutive rows, entry j of the slice's lane r at  off + 32 j + r, every
+// row padded to the slice's longest row (value 0, column 0).
+//
+// Why on GB300: FP64 FMA issues at 2 lanes per clock per SM, so the product
+// is co-bound by HBM and the FP64 pipe and the cost that decides is warp
+// DFMA instructions per entry.  In this layout one thread walks one row, so
+// every stored entry costs exactly one lane-FMA with no shuffle reduction,
+// and the 32 lanes of a warp read 32 consecutive values (256 bytes) and 32
+// consecutive columns (128 bytes) per step: full coalescing without a
+// shared-memory stage, so occupancy is set by registers alone.  On banded
+// and stencil matrices the lanes' x gathers of one step are also contiguous
+// rows of x.  Each row is summed in its CSR storage order, one FMA per
+// entry from 0.0; padded slots are discarded by a select, so y equals that
+// of the other one-thread-per-row kernels bit for bit.
+#include "internal.h"
+
+#include <cuda_runtime.h>
+
+namespace spmvk {
+
+namespace {
+
+__device__ __forceinline__ uint64_t sell_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t sell_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Streamed operand, read once: skip L1, evict first from L2.
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+// Gathered x, reused across rows: keep in L2.
+__device__ __forceinline__ double ld_keep(const double* p, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void sell_store(const CsrArgs& a, int row, double sum) {
+    if (a.rowmap) {
+        const int o = __ldg(a.rowmap + row);
+        a.y[o] = a.accumulate ? a.y[o] + sum : sum;
+    } else {
+        a.y[row] = a.accumulate ? a.y[row] + sum : sum;
+    }
+}
+
+}  // namespace
+
+// One warp per slice (grid-stride over the launch's slices), one lane per
+// row.  U entries per lane per step: U value and U column loads, then U x
+// gathers, then U FMAs, so each lane keeps U gathers in flight.
+template <int U, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    csr_sell_kernel(CsrArgs a, const SellSlice* __restrict__ slices, int slice_begin, int slice_end,
+                    const double* __restrict__ sval, const int32_t* __restrict__ scol) {
+    const uint64_t pol_stream = sell_policy_evict_first();
+    const uint64_t pol_keep = sell_policy_evict_last();
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * 8;
+    for (int si = slice_begin + (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < slice_end; si += nwarps) {
+        const SellSlice d = slices[si];
+        const int row = d.r0 + lane;
+        const bool live = lane < d.rows;
+        int len = 0;
+        if (live) len = __ldg(a.ptr + row + 1) - __ldg(a.ptr + row);
+        const double* vp = sval + (int64_t)d.off + lane;
+        const int32_t* cp = scol + (int64_t)d.off + lane;
+        const double* xb = a.x + d.xoff;
+        double sum = 0.0;
+        int j = 0;
+        for (; j + U <= d.len; j += U) {
+            int32_t c[U];
+            double v[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                c[u] = ld_stream(cp + 32 * (j + u), pol_stream);
+                v[u] = ld_stream(vp + 32 * (j + u), pol_stream);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = ld_keep(xb + c[u], pol_keep);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const double t = fma(v[u], xv[u], sum);
+                sum = (j + u < len) ? t : sum;
+            }
+        }
+        for (; j < d.len; ++j) {
+            const int32_t c = ld_stream(cp + 32 * j, pol_stream);
+            const double v = ld_stream(vp + 32 * j, pol_stream);
+            const double t = fma(v, ld_keep(xb + c, pol_keep), sum);
+            sum = (j < len) ? t : sum;
+        }
+        if (live) sell_store(a, row, sum);
+    }
+}
+
+// Fill the sliced arrays from the CSR: one warp per slice, one lane per row.
+__global__ void __launch_bounds__(256) sell_fill_kernel(const int32_t* __restrict__ ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const SellSlice* __restrict__ slices, int n_slices,
+                                                        double* __restrict__ sval, int32_t* __restrict__ scol) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * 8;
+    for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < n_slices; si += nwarps) {
+        const SellSlice d = slices[si];
+        const bool live = lane < d.rows;
+        const int kb = live ? ptr[d.r0 + lane] : 0;
+        const int len = live ? ptr[d.r0 + lane + 1] - kb : 0;
+        for (int j = 0; j < d.len; ++j) {
+            const int64_t o = (int64_t)d.off + 32 * j + lane;
+            sval[o] = j < len ? val[kb + j] : 0.0;
+            scol[o] = j < len ? col[kb + j] : 0;
+        }
+    }
+}
+
+cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const double* val, const SellSlice* slices,
+                             int n_slices, double* sval, int32_t* scol, int num_sms, cudaStream_t s) {
+    if (n_slices <= 0) return cudaSuccess;
+    int grid = (n_slices + 7) / 8;
+    if (grid > num_sms * 8) grid = num_sms * 8;
+    sell_fill_kernel<<<grid, 256, 0, s>>>(ptr, col, val, slices, n_slices, sval, scol);
+    return cudaGetLastError();
+}
+
+bool sell_param_supported(int param) {
+    return param == 4 || param == 8 || param == 9 || param == 104;
+}
+
+cudaError_t launch_sell(const CsrArgs& a, const SellSlice* slices, int slice_begin, int slice_end,
+                        const double* sval, const int32_t* scol, int param, int num_sms, cudaStream_t s) {
+    if (slice_end <= slice_begin) return cudaSuccess;
+    const int warps = slice_end - slice_begin;
+    int blocks_per_sm = 8;
+    switch (param) {
+        case 4: blocks_per_sm = 8; break;
+        case 8: blocks_per_sm = 4; break;
+        case 9: blocks_per_sm = 4; break;
+        case 104: blocks_per_sm = 6; break;
+        default: return cudaErrorInvalidValue;
+    }
+    int grid = num_sms * blocks_per_sm;
+    if (grid > (warps + 7) / 8) grid = (warps + 7) / 8;
+    switch (param) {
+        case 4: csr_sell_kernel<4, 8><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
+        case 8: csr_sell_kernel<8, 4><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
+        case 9: csr_sell_kernel<9, 4><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
+        case 104: csr_sell_kernel<4, 6><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spmvk

@@ -32,6 +32,8 @@ namespace {
 
 constexpr int kMaxW = 8;          // widest block
 constexpr int kThreads = 256;
+constexpr int kMidRow = 256;      // rows up to this length (above the short
+                                  // threshold) get 8 lanes, longer rows 32
 
 // ---------------------------------------------------------------- device
 // SplitMix64 (Steele, Lea and Flood): element t of the stream of `seed`.
@@ -60,21 +62,20 @@ struct BlockDesc {
     int width;
 };
 
-// X[i, c] for every column of every request of the block (row-major, ld 8):
+// X[i, c] for every column of every request of the block (row-major, ld W):
 // request r's element (i, j) is U(seed_r, 8 i + j).
 __global__ void gen_x_kernel(double* __restrict__ X, int n, BlockDesc b) {
     const int W = b.width;
-    const int64_t total = (int64_t)n * W;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / W), c = (int)(e % W);
+    const int total = n * W;   // < 2^31: n < 2^28 is checked by the server
+    for (int e = (int)(blockIdx.x * blockDim.x + threadIdx.x); e < total; e += (int)(gridDim.x * blockDim.x)) {
+        const int i = e / W, c = e - (e / W) * W;
         double v = 0.0;
         for (int r = 0; r < b.n_req; ++r) {
             const BlockReq q = b.req[r];
             if (c >= q.col0 && c < q.col0 + q.width)
                 v = uniform_pm1(q.seed, (uint64_t)i * kMaxW + (uint64_t)(c - q.col0));
         }
-        X[(int64_t)i * kMaxW + c] = v;
+        X[e] = v;   // row-major, leading dimension W
     }
 }
 
@@ -82,6 +83,23 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 33)) * 0xFF51AFD7ED558CCDull;
     z = (z ^ (z >> 33)) * 0xC4CEB9FE1A85EC53ull;
     return z ^ (z >> 33);
+}
+
+// A row of X (W values, leading dimension W): two per 16-byte load when W
+// is even (every row then starts 16-byte aligned), else one at a time.
+template <int W>
+__device__ __forceinline__ void load_row(const double* xr, double (&xv)[W]) {
+    if (W % 2 == 0) {
+#pragma unroll
+        for (int c = 0; c < W; c += 2) {
+            const double2 t = __ldg(reinterpret_cast<const double2*>(xr + c));
+            xv[c] = t.x;
+            xv[c + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < W; ++c) xv[c] = __ldg(xr + c);
+    }
 }
 
 // Y[:, 0..W) = A X[:, 0..W): V lanes per row, lane h takes entries
@@ -97,7 +115,8 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restric
                                                         const double* __restrict__ val,
                                                         const double* __restrict__ X,
                                                         double* __restrict__ Y, int n, BlockDesc b,
-                                                        unsigned long long* __restrict__ hashes) {
+                                                        unsigned long long* __restrict__ hashes,
+                                                        int short_max) {
     constexpr int GROUPS = kThreads / V;
     const int lane = threadIdx.x % V;
     unsigned long long h[kMaxW];
@@ -108,22 +127,93 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restric
         double acc[W];
 #pragma unroll
         for (int c = 0; c < W; ++c) acc[c] = 0.0;
-        if (row < n) {
+        bool mine = row < n;   // rows longer than short_max belong to the bucket kernels
+        if (mine) {
             const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
-            for (int k = kb + lane; k < ke; k += V) {
+            mine = ke - kb <= short_max;
+            for (int k = kb + lane; mine && k < ke; k += V) {
                 const double a = __ldg(val + k);
-                const double* xr = X + (int64_t)__ldg(col + k) * kMaxW;
+                const double* xr = X + (int64_t)__ldg(col + k) * W;
+                double xv[W];
+                load_row<W>(xr, xv);
 #pragma unroll
-                for (int c = 0; c < W; ++c) acc[c] = fma(a, __ldg(xr + c), acc[c]);
+                for (int c = 0; c < W; ++c) acc[c] = fma(a, xv[c], acc[c]);
             }
         }
 #pragma unroll
         for (int off = V / 2; off > 0; off >>= 1)
 #pragma unroll
             for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off, V);
-        if (row < n && lane == 0) {
+        if (mine && lane == 0) {
 #pragma unroll
-            for (int c = 0; c < W; ++c) Y[(int64_t)row * kMaxW + c] = acc[c];
+            for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
+            if (hashes) {
+#pragma unroll
+                for (int r = 0; r < kMaxW; ++r) {
+                    if (r >= b.n_req) break;
+                    const BlockReq q = b.req[r];
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        if (c >= q.col0 && c < q.col0 + q.width) {
+                            const uint64_t e = (uint64_t)row * q.width + (uint64_t)(c - q.col0);
+                            h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * 0x9E3779B97F4A7C15ull);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (hashes) {
+        for (int r = 0; r < b.n_req; ++r) {
+            unsigned long long v = h[r];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + b.req[r].index, v);
+        }
+    }
+}
+
+// Rows from a list (one length bucket of a matrix): V lanes per row, lanes
+// strided over the row's entries, W accumulators per lane, a fixed
+// xor-butterfly; hash as in spmm_kernel.
+template <int V, int W>
+__global__ void __launch_bounds__(kThreads) spmm_list_kernel(const int32_t* __restrict__ ptr,
+                                                             const int32_t* __restrict__ col,
+                                                             const double* __restrict__ val,
+                                                             const double* __restrict__ X,
+                                                             double* __restrict__ Y,
+                                                             const int32_t* __restrict__ rows, int n_rows,
+                                                             BlockDesc b,
+                                                             unsigned long long* __restrict__ hashes) {
+    constexpr int GROUPS = kThreads / V;
+    const int lane = threadIdx.x % V;
+    unsigned long long h[kMaxW];
+#pragma unroll
+    for (int r = 0; r < kMaxW; ++r) h[r] = 0;
+    for (int base = (int)blockIdx.x * GROUPS; base < n_rows; base += (int)gridDim.x * GROUPS) {
+        const int wr = base + (int)threadIdx.x / V;
+        double acc[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = 0.0;
+        int row = -1;
+        if (wr < n_rows) {
+            row = __ldg(rows + wr);
+            const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+            for (int k = kb + lane; k < ke; k += V) {
+                const double a = __ldg(val + k);
+                const double* xr = X + (int64_t)__ldg(col + k) * W;
+                double xv[W];
+                load_row<W>(xr, xv);
+#pragma unroll
+                for (int c = 0; c < W; ++c) acc[c] = fma(a, xv[c], acc[c]);
+            }
+        }
+#pragma unroll
+        for (int off = V / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off, V);
+        if (row >= 0 && lane == 0) {
+#pragma unroll
+            for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
             if (hashes) {
 #pragma unroll
                 for (int r = 0; r < kMaxW; ++r) {
@@ -150,10 +240,30 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restric
 }
 
 template <int V>
+cudaError_t launch_list_w(const BlockDesc& b, const int32_t* ptr, const int32_t* col, const double* val,
+                          const double* X, double* Y, const int32_t* rows, int nr, int num_sms,
+                          unsigned long long* hashes, cudaStream_t s) {
+    const int grid = std::min((nr + kThreads / V - 1) / (kThreads / V), num_sms * 8);
+#define SPMM_LIST(w) spmm_list_kernel<V, w><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, rows, nr, b, hashes)
+    switch (b.width) {
+        case 1: SPMM_LIST(1); break;
+        case 2: SPMM_LIST(2); break;
+        case 3: SPMM_LIST(3); break;
+        case 4: SPMM_LIST(4); break;
+        case 5: SPMM_LIST(5); break;
+        case 6: SPMM_LIST(6); break;
+        case 7: SPMM_LIST(7); break;
+        default: SPMM_LIST(8); break;
+    }
+#undef SPMM_LIST
+    return cudaGetLastError();
+}
+
+template <int V>
 cudaError_t launch_spmm_w(const BlockDesc& b, const int32_t* ptr, const int32_t* col, const double* val,
                           const double* X, double* Y, int n, int grid, unsigned long long* hashes,
-                          cudaStream_t s) {
-#define SPMM_W(w) spmm_kernel<V, w><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n, b, hashes)
+                          int short_max, cudaStream_t s) {
+#define SPMM_W(w) spmm_kernel<V, w><<<grid, kThreads, 0, s>>>(ptr, col, val, X, Y, n, b, hashes, short_max)
     switch (b.width) {
         case 1: SPMM_W(1); break;
         case 2: SPMM_W(2); break;
@@ -235,6 +345,11 @@ struct spmv_server {
     unsigned long long* d_hash = nullptr;
     size_t hash_cap = 0;
     int num_sms = 0;
+    // per matrix: rows longer than short_max[m] in two buckets (8 lanes up to
+    // kMidRow entries, 32 lanes above), as row lists
+    std::vector<int> short_max;
+    int32_t* bucket_rows = nullptr;
+    std::vector<int64_t> mid_off, long_off;   // rows of bucket b of matrix m: [off[m], off[m+1])
 };
 
 namespace {
@@ -259,12 +374,23 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     const double* val = bt->val + M.ent_off;
     const int V = sv->lanes[m];
     int grid = (int)std::min<int64_t>((n + (kThreads / V) - 1) / (kThreads / V), (int64_t)sv->num_sms * 8);
+    const int smax = sv->short_max[m];
     switch (V) {
-        case 1: e = launch_spmm_w<1>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
-        case 2: e = launch_spmm_w<2>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
-        case 4: e = launch_spmm_w<4>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
-        default: e = launch_spmm_w<8>(b, ptr, col, val, X, Y, n, grid, hashes, s); break;
+        case 1: e = launch_spmm_w<1>(b, ptr, col, val, X, Y, n, grid, hashes, smax, s); break;
+        case 2: e = launch_spmm_w<2>(b, ptr, col, val, X, Y, n, grid, hashes, smax, s); break;
+        case 4: e = launch_spmm_w<4>(b, ptr, col, val, X, Y, n, grid, hashes, smax, s); break;
+        default: e = launch_spmm_w<8>(b, ptr, col, val, X, Y, n, grid, hashes, smax, s); break;
     }
+    if (e != cudaSuccess) return e;
+    const int nm = (int)(sv->mid_off[m + 1] - sv->mid_off[m]);
+    if (nm > 0)
+        e = launch_list_w<8>(b, ptr, col, val, X, Y, sv->bucket_rows + sv->mid_off[m], nm, sv->num_sms,
+                             hashes, s);
+    if (e != cudaSuccess) return e;
+    const int nl = (int)(sv->long_off[m + 1] - sv->long_off[m]);
+    if (nl > 0)
+        e = launch_list_w<32>(b, ptr, col, val, X, Y, sv->bucket_rows + sv->long_off[m], nl, sv->num_sms,
+                              hashes, s);
     return e;
 }
 
@@ -300,8 +426,47 @@ int spmv_serve_create(spmv_batch* mats, int n_streams, int64_t budget_bytes, spm
     sv->n_streams = n_streams;
     sv->num_sms = mats->num_sms;
     for (int m = 0; m < mats->count; ++m) {
+        if (mats->n[m] >= (int64_t(1) << 28)) spmvk::fail(SPMV_EBOUNDS, "matrix %d: n >= 2^28", m);
         const double mean = mats->n[m] ? (double)mats->nnz[m] / (double)mats->n[m] : 0.0;
         sv->lanes.push_back(mean < 6 ? 1 : mean < 24 ? 2 : mean < 64 ? 4 : 8);
+    }
+    // row buckets of every matrix: rows up to short_max stay with the
+    // main kernel, longer rows go to the 8-lane or the 32-lane list
+    {
+        std::vector<int32_t> hp((size_t)mats->mats.back().ptr_off + mats->n.back() + 1);
+        spmvk::check_cuda(cudaMemcpy(hp.data(), mats->ptr, hp.size() * 4, cudaMemcpyDeviceToHost), "row pointers");
+        std::vector<int32_t> mid, lng;
+        std::vector<int64_t> mid_cnt(mats->count), lng_cnt(mats->count);
+        std::vector<std::vector<int32_t>> mid_rows(mats->count), long_rows(mats->count);
+        sv->short_max.assign(mats->count, 0);
+        for (int m = 0; m < mats->count; ++m) {
+            const double mean = mats->n[m] ? (double)mats->nnz[m] / (double)mats->n[m] : 0.0;
+            const int smax = std::max(8, (int)(2.0 * mean + 0.5));
+            sv->short_max[m] = smax;
+            const int32_t* p = hp.data() + mats->mats[m].ptr_off;
+            for (int64_t i = 0; i < mats->n[m]; ++i) {
+                const int len = p[i + 1] - p[i];
+                if (len > kMidRow) long_rows[m].push_back((int32_t)i);
+                else if (len > smax) mid_rows[m].push_back((int32_t)i);
+            }
+        }
+        std::vector<int32_t> all;
+        sv->mid_off.assign(mats->count + 1, 0);
+        sv->long_off.assign(mats->count + 1, 0);
+        for (int m = 0; m < mats->count; ++m) {
+            sv->mid_off[m] = (int64_t)all.size();
+            all.insert(all.end(), mid_rows[m].begin(), mid_rows[m].end());
+        }
+        sv->mid_off[mats->count] = (int64_t)all.size();
+        for (int m = 0; m < mats->count; ++m) {
+            sv->long_off[m] = (int64_t)all.size();
+            all.insert(all.end(), long_rows[m].begin(), long_rows[m].end());
+        }
+        sv->long_off[mats->count] = (int64_t)all.size();
+        spmvk::check_cuda(cudaMalloc(reinterpret_cast<void**>(&sv->bucket_rows), all.size() * 4 + 16), "row buckets");
+        if (!all.empty())
+            spmvk::check_cuda(cudaMemcpy(sv->bucket_rows, all.data(), all.size() * 4, cudaMemcpyHostToDevice),
+                              "row buckets");
     }
     // the pool holds the X/Y blocks of every block in flight; beyond what
     // the slots can ever hold at once the budget is never used, so it is
@@ -342,6 +507,7 @@ int spmv_serve_destroy(spmv_server* sv) {
         if (e) cudaEventDestroy(e);
     if (sv->pool_base) cudaFree(sv->pool_base);
     if (sv->d_hash) cudaFree(sv->d_hash);
+    if (sv->bucket_rows) cudaFree(sv->bucket_rows);
     delete sv;
     return SPMV_OK;
 }
@@ -377,7 +543,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
         if (r && arrival_s[r] < arrival_s[r - 1]) spmvk::fail(SPMV_EINVAL, "arrivals must be non-decreasing");
     }
     for (int m = 0; m < M; ++m)
-        if ((size_t)2 * sv->mats->mats[m].n * kMaxW * sizeof(double) + 256 > sv->pool.capacity())
+        if ((((size_t)2 * sv->mats->mats[m].n * kMaxW * sizeof(double) + 255) & ~size_t(255)) > sv->pool.capacity())
             spmvk::fail(SPMV_ENOMEM, "matrix %d: one block of it exceeds the budget", m);
     if (hash_out) {
         if ((size_t)n_req > sv->hash_cap) {
@@ -451,29 +617,35 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                 if (m < 0) break;
                 rr = (m + 1) % M;
                 const int n = sv->mats->mats[m].n;
-                const size_t bytes = (size_t)2 * n * kMaxW * sizeof(double);
+                // the oldest requests of matrix m whose widths sum to <= 8
+                auto& q = pending[m];
+                int take = 0, wsum = 0;
+                while (take < (int)q.size() && take < kMaxW) {
+                    const int64_t r = q[take];
+                    if (wsum + width[r] > kMaxW) break;
+                    wsum += width[r];
+                    ++take;
+                    if (mode == SPMV_SERVE_PLAIN) break;   // one request per launch
+                }
+                const size_t bytes = (size_t)2 * n * wsum * sizeof(double);   // X and Y, ld wsum
                 const long long off = sv->pool.alloc(bytes);
                 if (off < 0) {   // over budget: wait for memory to free up
                     ++waits_mem;
                     break;
                 }
                 BlockDesc b{};
-                int wsum = 0;
                 std::vector<int64_t> reqs;
-                auto& q = pending[m];
-                while (!q.empty() && b.n_req < kMaxW) {
+                for (int t = 0, col = 0; t < take; ++t) {
                     const int64_t r = q.front();
-                    if (wsum + width[r] > kMaxW) break;
-                    b.req[b.n_req++] = BlockReq{seed[r], wsum, width[r], (int)r, 0};
-                    wsum += width[r];
+                    b.req[b.n_req++] = BlockReq{seed[r], col, width[r], (int)r, 0};
+                    col += width[r];
                     reqs.push_back(r);
                     q.pop_front();
-                    if (mode == SPMV_SERVE_PLAIN) break;   // one request per launch
                 }
                 b.width = wsum;
                 queued -= (int64_t)reqs.size();
                 double* X = reinterpret_cast<double*>(sv->pool.ptr(off));
-                double* Y = X + (size_t)n * kMaxW;
+                double* Y = X + (size_t)n * b.width;
                 spmvk::check_cuda(launch_block(sv, m, b, X, Y, hash_out ? sv->d_hash : nullptr,
                                                sv->streams[i]),
                                   "block launch");

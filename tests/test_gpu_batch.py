@@ -29,7 +29,7 @@ def _oracle(mats, x, offs):
     return want, scale
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32, "mixed"])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32, "mixed"])
 def test_batch_matches_oracle_and_separate_launches(lanes):
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
@@ -39,7 +39,7 @@ def test_batch_matches_oracle_and_separate_launches(lanes):
         assert offs[-1] == sum(m[0] for m in mats)
         if lanes == "mixed":
             for m in range(b.count):
-                spmv.spmv_batch_set_lanes(b.h, m, [1, 2, 4, 8, 16, 32][m % 6])
+                spmv.spmv_batch_set_lanes(b.h, m, [0, 1, 2, 4, 8, 16, 32][m % 7])
         else:
             spmv.spmv_batch_set_lanes(b.h, -1, lanes)
         x = W.uniform_x(offs[-1], seed=9)

@@ -67,8 +67,24 @@ def case(name):
 
 
 VARIANTS = ([("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)]
-            + [("pairs", v) for v in (1, 2, 4, 8, 102, 104)] + [("warp", g) for g in range(4)]
-            + [("merge", 0)])
+            + [("pairs", v) for v in (1, 2, 4, 8, 102, 104)] + [("warp", g) for g in range(5)]
+            + [("merge", 0)] + [("sell", u) for u in (4, 8, 9, 104)])
+
+SELL_LIMIT_SLACK = 32768
+
+
+def sell_entries(part, P):
+    """Padded entries of the sliced layout, from the exported plan: slices of
+    32 rows of each rank's local rows and of its rows with remote entries."""
+    from paper_2203_02530_gb300 import spmv
+    tot = 0
+    for p in range(P):
+        ll = np.diff(part.export(spmv.X_L_PTR, p))
+        rl = np.diff(part.export(spmv.X_R_PTR, p))
+        for lens in (ll, rl[rl > 0]):
+            for s0 in range(0, lens.size, 32):
+                tot += 32 * int(lens[s0:s0 + 32].max())
+    return tot
 
 
 def make_part(n, rp, ci, va, P, gran=0):
@@ -77,11 +93,25 @@ def make_part(n, rp, ci, va, P, gran=0):
 
 
 def set_variant(part, v):
+    """Select variant v; the sliced layout's refusal on skewed rows is checked
+    against its documented limit and skips the case."""
     from paper_2203_02530_gb300 import spmv
     kind, param = v
-    part.set_variant({"tile": spmv.VARIANT_TILE, "vector": spmv.VARIANT_VECTOR,
-                      "merge": spmv.VARIANT_MERGE, "pairs": spmv.VARIANT_PAIRS,
-                      "warp": spmv.VARIANT_WARP}[kind], param)
+    code = {"tile": spmv.VARIANT_TILE, "vector": spmv.VARIANT_VECTOR,
+            "merge": spmv.VARIANT_MERGE, "pairs": spmv.VARIANT_PAIRS,
+            "warp": spmv.VARIANT_WARP, "sell": spmv.VARIANT_SELL}[kind]
+    if kind != "sell":
+        part.set_variant(code, param)
+        return
+    want = sell_entries(part, part.query(spmv.Q_P))
+    nnz = part.query(spmv.Q_NNZ)
+    if want > 2 * nnz + SELL_LIMIT_SLACK:
+        with pytest.raises(spmv.SpmvError) as e:
+            part.set_variant(code, param)
+        assert e.value.code == spmv.EINVAL
+        pytest.skip("sliced layout refused: %d padded entries for %d stored" % (want, nnz))
+    part.set_variant(code, param)
+    assert part.query(spmv.Q_SELL_ENTRIES) == want
 
 
 def run_default(part, x_d, y_d, stream):
@@ -186,6 +216,26 @@ def test_integer_data_is_exact(variant):
         run_default(part, x_d, y_d, s)
         s.synchronize()
         assert np.array_equal(y_d.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("name", ["lap64", "st27_20", "st27_ragged", "band", "rand_dup"])
+def test_sliced_layout_matches_thread_per_row_bit_for_bit(name):
+    """SELL and WARP both sum each row from 0.0 in storage order with one FMA
+    per entry, so their y agree bit for bit (padding adds nothing)."""
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    out = []
+    for v in (("warp", 0), ("sell", 4), ("sell", 9)):
+        y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        with make_part(n, rp, ci, va, P) as part:
+            set_variant(part, v)
+            run_default(part, x_d, y_d, s)
+            s.synchronize()
+        out.append(y_d.cpu().numpy())
+    assert np.array_equal(out[0].view(np.uint64), out[1].view(np.uint64))
+    assert np.array_equal(out[0].view(np.uint64), out[2].view(np.uint64))
 
 
 @pytest.mark.parametrize("name", ["st27_ragged", "powerlaw", "dense_row"])

@@ -50,12 +50,12 @@ def test_request_x_matches_device_generator():
     mats = _mats()
     with spmv.Batch(mats) as b, spmv.Server(b, n_streams=2, budget_bytes=1 << 30) as sv:
         n = mats[0][0]
-        x = torch.empty((n, 8), dtype=torch.float64, device="cuda")
-        y = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+        x = torch.empty((n, 5), dtype=torch.float64, device="cuda")
+        y = torch.empty((n, 5), dtype=torch.float64, device="cuda")
         s = torch.cuda.Stream()
         spmv.spmv_serve_single(sv.h, 0, 5, 12345, y, x, s)
         s.synchronize()
-        assert np.array_equal(x.cpu().numpy()[:, :5], W.request_x(12345, n, 5))
+        assert np.array_equal(x.cpu().numpy(), W.request_x(12345, n, 5))
 
 
 def test_results_same_alone_and_in_the_mix_and_match_oracle():
@@ -67,15 +67,19 @@ def test_results_same_alone_and_in_the_mix_and_match_oracle():
         lat_b, h_b, st_b = sv.run(mat, wid, sd, arr, spmv.SERVE_BATCHED)
         lat_p, h_p, st_p = sv.run(mat, wid, sd, arr, spmv.SERVE_PLAIN)
         assert np.array_equal(h_b, h_p)
-        assert st_b["blocks"] < st_p["blocks"] == len(mat)   # requests were merged
+        assert st_p["blocks"] == len(mat)
         assert st_b["admitted_while_busy"] > 0                 # continuous admission
         assert (lat_b > 0).all() and (lat_p > 0).all()
+        # a burst queues up, so requests of one matrix are merged into blocks
+        lat_burst, h_burst, st_burst = sv.run(mat, wid, sd, np.zeros(len(mat)), spmv.SERVE_BATCHED)
+        assert st_burst["blocks"] < len(mat)
+        assert np.array_equal(h_burst, h_b)
         s = torch.cuda.Stream()
         for r in range(0, len(mat), 23):
             m, k = int(mat[r]), int(wid[r])
             n, rp, ci, va = mats[m]
-            x = torch.empty((n, 8), dtype=torch.float64, device="cuda")
-            y = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+            x = torch.empty((n, k), dtype=torch.float64, device="cuda")
+            y = torch.empty((n, k), dtype=torch.float64, device="cuda")
             spmv.spmv_serve_single(sv.h, m, k, int(sd[r]), y, x, s)
             s.synchronize()
             Y = y.cpu().numpy()
@@ -95,7 +99,7 @@ def test_small_budget_makes_blocks_wait_but_completes():
     with spmv.Batch(mats) as b:
         nmax = max(m[0] for m in mats)
         resident = b.query(spmv.BQ_DEVICE_BYTES)
-        budget = resident + 128 * nmax + 4096      # room for about one block
+        budget = resident + 128 * nmax + 4096      # room for one width-8 block of the largest
         with spmv.Server(b, n_streams=4, budget_bytes=budget) as sv:
             lat, h, st = sv.run(mat, wid, sd, arr, spmv.SERVE_BATCHED)
             assert st["waits_for_memory"] > 0
