@@ -491,6 +491,7 @@ def run_batched(args, world, rank, local):
         cpu = {"value": round(alg * reps / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "%d passes over all 256 matrices (plain CSR products), single-threaded C "
                          "oracle, %.1f s (nproc=%d)" % (reps, secs, os.cpu_count() or 0)}
+    launches = spmv.spmv_batch_query(b.h, spmv.BQ_LAUNCHES, -1)
     b.close()
     if rank != 0:
         return None
@@ -514,7 +515,9 @@ def run_batched(args, world, rank, local):
                               "bit_identical_to_batched": identical},
         "speedup_vs_separate_graph": round(t_graph / t_b, 3),
         "speedup_vs_separate_eager": round(t_sep / t_b, 3),
-        "roofline": {"bound": "hbm", "kernel": "batch_persistent_kernel",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("batch_sliced_persistent_kernel" if all(l == spmv.BATCH_SLICED for l in lanes)
+                                else "batch_persistent_kernel"),
                      "achieved": round(alg / t_b / 1e9, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(alg / t_b / 1e9 / peak, 4), "traffic": None, "peak_kind": peak_kind},
         "latency_us": {"p50": round(benchmark.percentile(meas, 50) * 1e6, 2),
@@ -523,7 +526,8 @@ def run_batched(args, world, rank, local):
         "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
                 "ms_per_step": round(t_e2e * 1e3, 4)},
-        "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
+        "cpu_baseline": cpu, "clocks": clocks,
+        "gpu_launches": args.steps * launches,
     }
 
 

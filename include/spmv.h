@@ -162,15 +162,15 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *          thread per row, one DFMA per entry
  *   SELL   param = 4, 8, 9 (entries per lane per step) or 104 (4, fewer
  *          registers): a sliced-ELL copy of A_L and A_R that the plan builds
- *          on first use (slices of 32 consecutive rows of one rank, entry j
- *          of row r at slice offset + 32 j + r, rows padded to the slice's
- *          longest with value 0 and column 0), one thread per row, one FMA
- *          per stored entry in storage order (padded slots are discarded,
- *          so y equals WARP's bit for bit on rows that fit its stages).
- *          SPMV_EINVAL when the padded layout
- *          would hold more than 2 (nnz_local + nnz_remote) + 32768 entries;
- *          SPMV_EBOUNDS beyond 2^31.  The copy is device memory the plan
- *          holds until destroyed.
+ *          on first use and holds until destroyed.  Per rank, rows longer
+ *          than 64 entries are summed by a whole warp each; the others sit
+ *          in slices of 32 positions (entry j of position r at slice offset
+ *          + 32 j + r, padded to the slice's longest row with value 0 and
+ *          column 0), in natural row order when that pads by at most 1/8
+ *          (+1024 entries), else sorted by length.  One thread per short
+ *          row, one FMA per stored entry in storage order (padded slots
+ *          discarded), so y equals WARP's bit for bit on matrices without
+ *          long rows.  SPMV_EBOUNDS beyond 2^31 padded entries.
  * Fails with SPMV_EINVAL while captured graphs exist (they hold the old
  * kernels' tables). */
 enum {
@@ -295,7 +295,8 @@ int spmv_csr_error(int64_t* out);
 
 /*
  * Batched products: many independent CSR matrices (no partitioning) kept
- * resident in HBM and multiplied in ONE persistent launch.  Work items are
+ * resident in HBM and multiplied in one persistent launch per layout
+ * (CSR modes, sliced layout).  Work items are
  * blocks of up to 256 rows of one matrix, claimed by warps through an atomic
  * ticket; each row is summed by `lanes` lanes (set per matrix, e.g. by an
  * autotuner), a row longer than 64 entries by a whole warp, in a fixed
@@ -314,7 +315,8 @@ enum {
     SPMV_BQ_COUNT = 0, SPMV_BQ_TOTAL_ROWS = 1, SPMV_BQ_TOTAL_NNZ = 2, SPMV_BQ_ITEMS = 3,
     SPMV_BQ_ALG_BYTES = 4,   /* 12 B/entry + 4 B/row pointer + 16 B/row (x read, y written) */
     SPMV_BQ_OFFSET = 5, SPMV_BQ_N = 6, SPMV_BQ_NNZ = 7, SPMV_BQ_LANES = 8,  /* of matrix m */
-    SPMV_BQ_DEVICE_BYTES = 9   /* device memory the batch holds */
+    SPMV_BQ_DEVICE_BYTES = 9,  /* device memory the batch holds */
+    SPMV_BQ_LAUNCHES = 10      /* kernels one spmv_batch_run launches (0-2) */
 };
 int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr,
                       const int32_t* const* col_idx, const double* const* vals,
@@ -322,10 +324,19 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
 int spmv_batch_destroy(spmv_batch* batch);
 /* Lanes per row (1, 2, 4, 8, 16, 32) of matrix m, or of every matrix (m = -1);
  * 0 selects warp-staged rows (each warp stages its 32 rows' entries in shared
- * memory and sums one row per lane; for short rows). */
+ * memory and sums one row per lane; for short rows); SPMV_BATCH_SLICED (64)
+ * a sliced layout built on first use (a second copy of the matrix in device
+ * memory): slices of 32 rows, one row per lane, entry j of lane r at
+ * slice offset + 32 j + r, rows padded to the slice's longest with value 0;
+ * natural row order when that pads by at most 1/8 and no row exceeds 64
+ * entries, else rows sorted by length with the longer-than-64 rows summed
+ * by whole warps.  Synchronises the device (no launch of the batch may be
+ * in flight). */
+enum { SPMV_BATCH_SLICED = 64 };
 int spmv_batch_set_lanes(spmv_batch* batch, int m, int lanes);
 int spmv_batch_query(const spmv_batch* batch, int what, int m, int64_t* out);
-/* Every product in one persistent launch on stream s. */
+/* Every product on stream s: one persistent launch over the sliced-layout
+ * matrices and one over the others (either left out when it has no work). */
 int spmv_batch_run(spmv_batch* batch, const double* x_dev, double* y_dev, cudaStream_t s);
 /* The same products as one launch per matrix (only matrix m if m >= 0). */
 int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, double* y_dev,
@@ -361,7 +372,11 @@ int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, doubl
  *   launch) when a width-8 block of any of the matrices exceeds the pool.
  * Rows are summed in length buckets fixed per matrix at creation (short rows
  * by 1-8 lanes chosen from the mean length, rows up to 256 entries by 8
- * lanes, longer rows by a whole warp), so skewed matrices keep warps busy.
+ * lanes, longer rows by a whole warp), so skewed matrices keep warps busy;
+ * a matrix whose batch layout is SPMV_BATCH_SLICED when a block is launched
+ * is summed over that layout instead (one thread per row, its long rows by
+ * whole warps).  Choose the layouts before creating the server: the budget
+ * counts the batch's device memory at creation.
  * spmv_serve_single: one request alone on stream s into caller buffers
  *   x_dev, y_dev (n x width doubles each, row-major).
  */

@@ -96,7 +96,7 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
     return out
 
 
-def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(0, 1, 2, 4, 8, 16),
+def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(0, 1, 2, 4, 8, 16, 64),
                reps=5):
     """Lanes per row for the matrices of a batch, timed on the persistent
     launch itself (one launch per matrix would be dominated by launch

@@ -150,13 +150,14 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         return we > wb;
     }
     if (var == SPMV_VARIANT_SELL) {
-        const std::vector<int64_t>& so = remote ? pt->rslice_off : pt->lslice_off;
-        const int sb = (int)(p < 0 ? 0 : so[p]);
-        const int se = (int)(p < 0 ? so[pt->P] : so[p + 1]);
-        check_cuda(spmvk::launch_sell(a, remote ? pt->rslices : pt->lslices, sb, se, remote ? pt->rs_val : pt->ls_val,
-                                      remote ? pt->rs_col : pt->ls_col, param, pt->num_sms, s),
-                   "sliced product");
-        return se > sb;
+        const spmv_part::SellPart& sp = pt->sell[remote ? 1 : 0];
+        spmvk::SellArgs sa{sp.slices, sp.longs, sp.val, sp.col, sp.len, sp.perm, 0, 0, 0, 0};
+        sa.slice_begin = (int)(p < 0 ? 0 : sp.slice_off[p]);
+        sa.slice_end = (int)(p < 0 ? sp.slice_off[pt->P] : sp.slice_off[p + 1]);
+        sa.long_begin = (int)(p < 0 ? 0 : sp.long_off[p]);
+        sa.long_end = (int)(p < 0 ? sp.long_off[pt->P] : sp.long_off[p + 1]);
+        check_cuda(spmvk::launch_sell(a, sa, param, pt->num_sms, s), "sliced product");
+        return (sa.slice_end > sa.slice_begin || sa.long_end > sa.long_begin) ? 1 : 0;
     }
     const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
     if (var == SPMV_VARIANT_VECTOR || var == SPMV_VARIANT_PAIRS) {
@@ -552,7 +553,7 @@ static void prepare_variant(spmv_part* pt, int variant, int param) {
     } else if (variant == SPMV_VARIANT_SELL) {
         if (!spmvk::sell_param_supported(param)) fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104}", param);
         check_cuda(cudaDeviceSynchronize(), "synchronize");
-        if (!pt->sell_entries) spmvk::build_sell(pt);
+        if (!pt->sell_built) spmvk::build_sell(pt);
     } else {
         fail(SPMV_EINVAL, "unknown variant %d", variant);
     }

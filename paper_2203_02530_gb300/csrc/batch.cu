@@ -24,9 +24,10 @@ namespace {
 constexpr int kItemRows = 256;
 constexpr int kThreads = 256;
 
-struct BatchItem {
-    int m, r0, r1, pad;
-};
+using spmvk::BatchItem;
+using spmvk::BSlice;
+
+constexpr int kSliced = 64;   // lanes value selecting the sliced layout
 
 struct BatchArgs {
     const int32_t* ptr;
@@ -34,6 +35,7 @@ struct BatchArgs {
     const double* val;
     const BatchMat* mats;
     const BatchItem* items;
+    const int* order;         // claim order of the persistent launch
     const double* x;
     double* y;
     int n_items;
@@ -48,6 +50,17 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
 __device__ __forceinline__ double ldg_keep(const double* p, uint64_t policy) {
     double v;
     asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(policy));
+    return v;
+}
+// Streamed operands of the sliced layout, read once: not kept in L1.
+__device__ __forceinline__ double ld_stream(const double* p) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 
@@ -232,38 +245,157 @@ __device__ __forceinline__ void batch_rows_staged(const BatchArgs& a, const Batc
     }
 }
 
+// Slices [s0, s1) of a matrix's sliced layout, two at a time: one lane per
+// row of each, one FMA per stored entry in storage order (padded slots
+// discarded by a select).  Each round issues U slots of both slices' values
+// and columns, then their 2U gathers, so a warp keeps 2U entries per lane in
+// flight even when rows are short.
+__device__ __forceinline__ void batch_slices(const BatchArgs& a, const BatchMat& m, int s0, int s1, uint64_t pol) {
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const double* x = a.x + m.row_off;
+    double* y = a.y + m.row_off;
+    for (int si = s0; si < s1; si += 2) {
+        const bool two = si + 1 < s1;
+        const BSlice d0 = m.s_slices[si];
+        const BSlice d1 = two ? m.s_slices[si + 1] : BSlice{0, 0, 0, 0};
+        const int len0 = lane < d0.rows ? (int)m.s_len[d0.pos0 + lane] : 0;
+        const int len1 = lane < d1.rows ? (int)m.s_len[d1.pos0 + lane] : 0;
+        const double* vp0 = m.s_val + (int64_t)d0.off + lane;
+        const int32_t* cp0 = m.s_col + (int64_t)d0.off + lane;
+        const double* vp1 = m.s_val + (int64_t)d1.off + lane;
+        const int32_t* cp1 = m.s_col + (int64_t)d1.off + lane;
+        const int lmax = d0.len > d1.len ? d0.len : d1.len;
+        double sum0 = 0.0, sum1 = 0.0;
+        for (int j0 = 0; j0 < lmax; j0 += U) {
+            int32_t c0[U], c1[U];
+            double v0[U], v1[U], x0[U], x1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int ja = j0 + u < d0.len ? j0 + u : d0.len - 1;   // clamped: in this slice
+                const int jb = j0 + u < d1.len ? j0 + u : d1.len - 1;
+                c0[u] = ja >= 0 ? ld_stream(cp0 + 32 * ja) : 0;
+                v0[u] = ja >= 0 ? ld_stream(vp0 + 32 * ja) : 0.0;
+                c1[u] = jb >= 0 ? ld_stream(cp1 + 32 * jb) : 0;
+                v1[u] = jb >= 0 ? ld_stream(vp1 + 32 * jb) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                x0[u] = ldg_keep(x + c0[u], pol);
+                x1[u] = ldg_keep(x + c1[u], pol);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j0 + u < d0.len) {   // uniform over the warp
+                    const double t = fma(v0[u], x0[u], sum0);
+                    sum0 = j0 + u < len0 ? t : sum0;
+                }
+                if (j0 + u < d1.len) {
+                    const double t = fma(v1[u], x1[u], sum1);
+                    sum1 = j0 + u < len1 ? t : sum1;
+                }
+            }
+        }
+        if (lane < d0.rows) y[m.s_perm ? __ldg(m.s_perm + d0.pos0 + lane) : d0.pos0 + lane] = sum0;
+        if (lane < d1.rows) y[m.s_perm ? __ldg(m.s_perm + d1.pos0 + lane) : d1.pos0 + lane] = sum1;
+    }
+}
+
+// Long rows at positions [p0, p1) of a matrix's sliced layout, each by the
+// whole warp straight from the CSR arrays.
+__device__ __forceinline__ void batch_long(const BatchArgs& a, const BatchMat& m, int p0, int p1, uint64_t pol) {
+    const int32_t* ptr = a.ptr + m.ptr_off;
+    const int32_t* col = a.col + m.ent_off;
+    const double* val = a.val + m.ent_off;
+    const double* x = a.x + m.row_off;
+    double* y = a.y + m.row_off;
+    for (int pos = p0; pos < p1; ++pos) {
+        const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
+        const double t = warp_row(col, val, x, __ldg(ptr + row), __ldg(ptr + row + 1), pol);
+        if ((threadIdx.x & 31) == 0) y[row] = t;
+    }
+}
+
+// Items of the CSR modes (kind 0).
 __device__ __forceinline__ void batch_item(const BatchArgs& a, int it, uint64_t pol, double* sv,
                                            int32_t* sc) {
     const BatchItem w = a.items[it];
     const BatchMat m = a.mats[w.m];
     switch (m.lanes) {
-        case 0: batch_rows_staged(a, m, w.r0, w.r1, pol, sv, sc); break;
-        case 1: batch_rows<1>(a, m, w.r0, w.r1, pol); break;
-        case 2: batch_rows<2>(a, m, w.r0, w.r1, pol); break;
-        case 4: batch_rows<4>(a, m, w.r0, w.r1, pol); break;
-        case 8: batch_rows<8>(a, m, w.r0, w.r1, pol); break;
-        case 16: batch_rows<16>(a, m, w.r0, w.r1, pol); break;
-        default: batch_rows<32>(a, m, w.r0, w.r1, pol); break;
+        case 0: batch_rows_staged(a, m, w.a, w.b, pol, sv, sc); break;
+        case 1: batch_rows<1>(a, m, w.a, w.b, pol); break;
+        case 2: batch_rows<2>(a, m, w.a, w.b, pol); break;
+        case 4: batch_rows<4>(a, m, w.a, w.b, pol); break;
+        case 8: batch_rows<8>(a, m, w.a, w.b, pol); break;
+        case 16: batch_rows<16>(a, m, w.a, w.b, pol); break;
+        default: batch_rows<32>(a, m, w.a, w.b, pol); break;
     }
 }
 
-// Persistent: every warp claims whole items with an atomic ticket until
-// none is left (no block-wide barrier: warps never wait for each other).
+// Items of the sliced layout (kinds 1 and 2).
+__device__ __forceinline__ void batch_item_sliced(const BatchArgs& a, int it, uint64_t pol) {
+    const BatchItem w = a.items[it];
+    const BatchMat m = a.mats[w.m];
+    if (w.kind == 1)
+        batch_long(a, m, w.a, w.b, pol);
+    else
+        batch_slices(a, m, w.a, w.b, pol);
+}
+
+// Fill the sliced layout of one matrix from its CSR arrays: one warp per
+// slice, one lane per position.
+__global__ void __launch_bounds__(256) batch_slice_fill_kernel(const int32_t* __restrict__ ptr,
+                                                               const int32_t* __restrict__ col,
+                                                               const double* __restrict__ val, BatchMat m,
+                                                               double* __restrict__ s_val,
+                                                               int32_t* __restrict__ s_col) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)gridDim.x * 8;
+    for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < m.n_slices; si += nw) {
+        const BSlice d = m.s_slices[si];
+        const int pos = d.pos0 + lane;
+        const bool live = lane < d.rows;
+        const int row = live ? (m.s_perm ? m.s_perm[pos] : pos) : 0;
+        const int kb = live ? ptr[row] : 0;
+        const int len = live ? ptr[row + 1] - kb : 0;
+        for (int j = 0; j < d.len; ++j) {
+            const int64_t o = (int64_t)d.off + 32 * j + lane;
+            s_val[o] = j < len ? val[kb + j] : 0.0;
+            s_col[o] = j < len ? col[kb + j] : 0;
+        }
+    }
+}
+
+// Persistent: every warp claims whole items (order[0 .. n_items)) with an
+// atomic ticket until none is left (no block-wide barrier: warps never wait
+// for each other).  One kernel for the CSR modes (shared-memory slices for
+// the staged mode), one for the sliced layout (no shared memory).
 __global__ void __launch_bounds__(kThreads, 4) batch_persistent_kernel(BatchArgs a) {
     __shared__ double s_val[kThreads / 32][kStageEntries];
     __shared__ int32_t s_col[kThreads / 32][kStageEntries];
     const uint64_t pol = policy_evict_last();
     const int w = threadIdx.x >> 5;
     for (;;) {
-        int it = 0;
-        if ((threadIdx.x & 31) == 0) it = atomicAdd(a.ticket, 1);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= a.n_items) break;
-        batch_item(a, it, pol, s_val[w], s_col[w]);
+        int t = 0;
+        if ((threadIdx.x & 31) == 0) t = atomicAdd(a.ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.n_items) break;
+        batch_item(a, __ldg(a.order + t), pol, s_val[w], s_col[w]);
     }
 }
 
-// Items [first, last), one per warp, grid-stride (one matrix per launch).
+__global__ void __launch_bounds__(kThreads, 4) batch_sliced_persistent_kernel(BatchArgs a) {
+    const uint64_t pol = policy_evict_last();
+    for (;;) {
+        int t = 0;
+        if ((threadIdx.x & 31) == 0) t = atomicAdd(a.ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.n_items) break;
+        batch_item_sliced(a, __ldg(a.order + t), pol);
+    }
+}
+
+// Items [first, last) of one matrix, one per warp, grid-stride.
 __global__ void __launch_bounds__(kThreads, 4) batch_range_kernel(BatchArgs a, int first, int last) {
     __shared__ double s_val[kThreads / 32][kStageEntries];
     __shared__ int32_t s_col[kThreads / 32][kStageEntries];
@@ -272,6 +404,13 @@ __global__ void __launch_bounds__(kThreads, 4) batch_range_kernel(BatchArgs a, i
     const int nw = (int)gridDim.x * (kThreads / 32);
     for (int it = first + (int)blockIdx.x * (kThreads / 32) + w; it < last; it += nw)
         batch_item(a, it, pol, s_val[w], s_col[w]);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) batch_sliced_range_kernel(BatchArgs a, int first, int last) {
+    const uint64_t pol = policy_evict_last();
+    const int nw = (int)gridDim.x * (kThreads / 32);
+    for (int it = first + (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); it < last; it += nw)
+        batch_item_sliced(a, it, pol);
 }
 
 }  // namespace
@@ -297,6 +436,140 @@ void bfree(spmv_batch* b) {
     b->allocs.clear();
 }
 
+void brelease(spmv_batch* b, void* p, size_t bytes) {
+    for (size_t i = 0; i < b->allocs.size(); ++i)
+        if (b->allocs[i] == p) {
+            cudaFree(p);
+            b->allocs.erase(b->allocs.begin() + (long)i);
+            b->device_bytes -= bytes + 256;
+            return;
+        }
+}
+
+// Item table of the current modes: each matrix's CSR or sliced items, and
+// the claim order of the persistent launch (items of long rows first: they
+// are the heaviest, so they do not end up in the tail).
+void upload_items(spmv_batch* b) {
+    std::vector<BatchItem> all;
+    b->item_off.assign(b->count + 1, 0);
+    for (int m = 0; m < b->count; ++m) {
+        b->item_off[m] = (int)all.size();
+        const auto& src = b->mats[m].lanes == kSliced ? b->sliced_items[m] : b->csr_items[m];
+        all.insert(all.end(), src.begin(), src.end());
+    }
+    b->item_off[b->count] = (int)all.size();
+    b->order.clear();
+    for (int i = 0; i < (int)all.size(); ++i)
+        if (all[i].kind == 1) b->order.push_back(i);
+    for (int i = 0; i < (int)all.size(); ++i)
+        if (all[i].kind == 2) b->order.push_back(i);
+    b->n_sliced_items = (int)b->order.size();
+    for (int i = 0; i < (int)all.size(); ++i)
+        if (all[i].kind == 0) b->order.push_back(i);
+    if (all.size() > b->items_cap) {
+        if (b->d_items) brelease(b, b->d_items, b->items_cap * sizeof(BatchItem));
+        if (b->d_order) brelease(b, b->d_order, b->items_cap * sizeof(int));
+        b->items_cap = all.size();
+        b->d_items = balloc(b, b->items_cap * sizeof(BatchItem));
+        b->d_order = static_cast<int*>(balloc(b, b->items_cap * sizeof(int)));
+    }
+    b->n_items = (int)all.size();
+    if (!all.empty()) {
+        spmvk::check_cuda(cudaMemcpy(b->d_items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice),
+                          "items");
+        spmvk::check_cuda(cudaMemcpy(b->d_order, b->order.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice),
+                          "item order");
+    }
+}
+
+// Sliced layout of matrix m.  Natural row order when no row is longer than
+// kLongRow and padding to each 32-row slice's longest row adds at most 1/8;
+// otherwise rows sorted by length (descending, stable), the rows longer than
+// kLongRow first (summed by whole warps), the rest in slices of similar
+// lengths.  Items: up to 32 long rows or 4096 of their entries, 8 slices.
+void build_sliced(spmv_batch* b, int m) {
+    BatchMat& M = b->mats[m];
+    const int n = M.n;
+    std::vector<int32_t> hp((size_t)n + 1, 0);
+    if (n > 0)
+        spmvk::check_cuda(cudaMemcpy(hp.data(), b->ptr + M.ptr_off, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost),
+                          "row pointers");
+    std::vector<int32_t> len((size_t)n);
+    for (int i = 0; i < n; ++i) len[i] = hp[i + 1] - hp[i];
+    const int64_t nnz = hp[n];
+    bool natural = true;
+    int64_t padded = 0;
+    for (int r = 0; r < n; r += 32) {
+        int mx = 0;
+        for (int i = r; i < std::min(n, r + 32); ++i) mx = std::max(mx, len[i]);
+        if (mx > kLongRow) natural = false;
+        padded += 32 * (int64_t)mx;
+    }
+    if (padded > nnz + nnz / 8 + 1024) natural = false;
+    std::vector<int32_t> perm;
+    int n_long = 0;
+    if (!natural) {
+        perm.resize((size_t)n);
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t p, int32_t q) { return len[p] > len[q]; });
+        while (n_long < n && len[perm[n_long]] > kLongRow) ++n_long;
+    }
+    auto L = [&](int pos) { return len[natural ? pos : perm[pos]]; };
+    std::vector<BSlice> sl;
+    std::vector<uint8_t> slen((size_t)n, 0);
+    int64_t off = 0;
+    for (int p0 = n_long; p0 < n; p0 += 32) {
+        const int e = std::min(n, p0 + 32);
+        int mx = 0;
+        for (int pos = p0; pos < e; ++pos) {
+            slen[pos] = (uint8_t)L(pos);
+            mx = std::max(mx, L(pos));
+        }
+        if (off + 32 * (int64_t)mx > INT32_MAX - 64) spmvk::fail(SPMV_EBOUNDS, "matrix %d: sliced layout too large", m);
+        sl.push_back(BSlice{p0, e - p0, mx, (int32_t)off});
+        off += 32 * (int64_t)mx;
+    }
+    double* s_val = static_cast<double*>(balloc(b, (size_t)off * 8));
+    int32_t* s_col = static_cast<int32_t*>(balloc(b, (size_t)off * 4));
+    uint8_t* s_len = static_cast<uint8_t*>(balloc(b, (size_t)n));
+    BSlice* s_sl = static_cast<BSlice*>(balloc(b, sl.size() * sizeof(BSlice)));
+    int32_t* s_perm = nullptr;
+    if (n > 0) spmvk::check_cuda(cudaMemcpy(s_len, slen.data(), (size_t)n, cudaMemcpyHostToDevice), "lengths");
+    if (!sl.empty())
+        spmvk::check_cuda(cudaMemcpy(s_sl, sl.data(), sl.size() * sizeof(BSlice), cudaMemcpyHostToDevice), "slices");
+    if (!natural) {
+        s_perm = static_cast<int32_t*>(balloc(b, (size_t)n * 4));
+        spmvk::check_cuda(cudaMemcpy(s_perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice), "row order");
+    }
+    M.s_val = s_val;
+    M.s_col = s_col;
+    M.s_len = s_len;
+    M.s_perm = s_perm;
+    M.s_slices = s_sl;
+    M.n_long = n_long;
+    M.n_slices = (int)sl.size();
+    if (!sl.empty()) {
+        int grid = ((int)sl.size() + 7) / 8;
+        if (grid > b->num_sms * 8) grid = b->num_sms * 8;
+        batch_slice_fill_kernel<<<grid, 256>>>(b->ptr + M.ptr_off, b->col + M.ent_off, b->val + M.ent_off, M,
+                                               s_val, s_col);
+        spmvk::check_cuda(cudaGetLastError(), "sliced fill");
+        spmvk::check_cuda(cudaDeviceSynchronize(), "sliced fill");
+    }
+    std::vector<BatchItem>& items = b->sliced_items[m];
+    items.clear();
+    for (int p = 0; p < n_long;) {
+        int e = p;
+        int64_t ent = 0;
+        while (e < n_long && e - p < 32 && ent < 4096) ent += L(e++);
+        items.push_back(BatchItem{m, 1, p, e});
+        p = e;
+    }
+    for (int s0 = 0; s0 < (int)sl.size(); s0 += 8)
+        items.push_back(BatchItem{m, 2, s0, std::min((int)sl.size(), s0 + 8)});
+    b->sliced_built[m] = 1;
+}
+
 BatchArgs args_of(spmv_batch* b, const double* x, double* y) {
     BatchArgs a{};
     a.ptr = b->ptr;
@@ -304,6 +577,7 @@ BatchArgs args_of(spmv_batch* b, const double* x, double* y) {
     a.val = b->val;
     a.mats = b->d_mats;
     a.items = static_cast<const BatchItem*>(b->d_items);
+    a.order = b->d_order;
     a.x = x;
     a.y = y;
     a.n_items = b->n_items;
@@ -340,6 +614,9 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
     b->count = count;
     spmvk::check_cuda(cudaGetDevice(&b->device), "cudaGetDevice");
     spmvk::check_cuda(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device), "SMs");
+    spmvk::check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occupancy_sliced,
+                                                                    batch_sliced_persistent_kernel, kThreads, 0),
+                      "occupancy");
     spmvk::check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occupancy, batch_persistent_kernel,
                                                                     kThreads, 0),
                       "occupancy");
@@ -370,8 +647,9 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
     std::vector<int32_t> hptr((size_t)ptr_total);
     std::vector<int32_t> hcol((size_t)ent_total, 0);
     std::vector<double> hval((size_t)ent_total, 0.0);
-    std::vector<BatchItem> items;
-    b->item_off.assign(count + 1, 0);
+    b->csr_items.assign(count, {});
+    b->sliced_items.assign(count, {});
+    b->sliced_built.assign(count, 0);
     for (int m = 0; m < count; ++m) {
         const BatchMat& M = b->mats[m];
         const int64_t base = n[m] > 0 ? row_ptr[m][0] : 0;
@@ -381,26 +659,20 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
             hcol[(size_t)(M.ent_off + k)] = col_idx[m][base + k];
             hval[(size_t)(M.ent_off + k)] = vals[m][base + k];
         }
-        b->item_off[m] = (int)items.size();
         for (int64_t r = 0; r < n[m]; r += kItemRows)
-            items.push_back(BatchItem{m, (int)r, (int)std::min<int64_t>(n[m], r + kItemRows), 0});
+            b->csr_items[m].push_back(BatchItem{m, 0, (int)r, (int)std::min<int64_t>(n[m], r + kItemRows)});
     }
-    b->item_off[count] = (int)items.size();
-    b->n_items = (int)items.size();
     b->ptr = static_cast<int32_t*>(balloc(b, hptr.size() * 4));
     b->col = static_cast<int32_t*>(balloc(b, hcol.size() * 4));
     b->val = static_cast<double*>(balloc(b, hval.size() * 8));
     b->d_mats = static_cast<BatchMat*>(balloc(b, b->mats.size() * sizeof(BatchMat)));
-    b->d_items = balloc(b, items.size() * sizeof(BatchItem));
-    b->ticket = static_cast<int*>(balloc(b, sizeof(int)));
+    b->ticket = static_cast<int*>(balloc(b, 2 * sizeof(int)));
     spmvk::check_cuda(cudaMemcpy(b->ptr, hptr.data(), hptr.size() * 4, cudaMemcpyHostToDevice), "upload");
     spmvk::check_cuda(cudaMemcpy(b->col, hcol.data(), hcol.size() * 4, cudaMemcpyHostToDevice), "upload");
     spmvk::check_cuda(cudaMemcpy(b->val, hval.data(), hval.size() * 8, cudaMemcpyHostToDevice), "upload");
     spmvk::check_cuda(cudaMemcpy(b->d_mats, b->mats.data(), b->mats.size() * sizeof(BatchMat),
                                  cudaMemcpyHostToDevice), "upload");
-    if (!items.empty())
-        spmvk::check_cuda(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem),
-                                     cudaMemcpyHostToDevice), "upload");
+    upload_items(b);
     *out = b;
     b = nullptr;
     return SPMV_OK;
@@ -427,13 +699,21 @@ int spmv_batch_set_lanes(spmv_batch* b, int m, int lanes) {
     BATCH_TRY
     if (!b) spmvk::fail(SPMV_EINVAL, "batch is NULL");
     if (m < -1 || m >= b->count) spmvk::fail(SPMV_EINVAL, "matrix %d", m);
-    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
-        spmvk::fail(SPMV_EINVAL, "lanes %d not in {0,1,2,4,8,16,32}", lanes);
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 &&
+        lanes != kSliced)
+        spmvk::fail(SPMV_EINVAL, "lanes %d not in {0,1,2,4,8,16,32,64}", lanes);
+    spmvk::check_cuda(cudaDeviceSynchronize(), "synchronize");   // no launch may read the tables
     const int lo = m < 0 ? 0 : m, hi = m < 0 ? b->count : m + 1;
-    for (int i = lo; i < hi; ++i) b->mats[i].lanes = lanes;
+    bool changed = false;
+    for (int i = lo; i < hi; ++i) {
+        if (lanes == kSliced && !b->sliced_built[i]) build_sliced(b, i);
+        changed = changed || ((b->mats[i].lanes == kSliced) != (lanes == kSliced));
+        b->mats[i].lanes = lanes;
+    }
     spmvk::check_cuda(cudaMemcpy(b->d_mats + lo, b->mats.data() + lo, (size_t)(hi - lo) * sizeof(BatchMat),
                                  cudaMemcpyHostToDevice),
                       "lanes");
+    if (changed) upload_items(b);
     BATCH_CATCH
     return SPMV_OK;
 }
@@ -448,6 +728,9 @@ int spmv_batch_query(const spmv_batch* b, int what, int m, int64_t* out) {
         case SPMV_BQ_TOTAL_ROWS: *out = b->total_rows; break;
         case SPMV_BQ_TOTAL_NNZ: *out = b->total_nnz; break;
         case SPMV_BQ_ITEMS: *out = b->n_items; break;
+        case SPMV_BQ_LAUNCHES:
+            *out = (b->n_sliced_items > 0) + (b->n_items > b->n_sliced_items);
+            break;
         case SPMV_BQ_ALG_BYTES:
             // entries, row pointers, x read, y written, over every matrix
             *out = 12 * b->total_nnz + 4 * (b->total_rows + b->count) + 16 * b->total_rows;
@@ -473,12 +756,28 @@ int spmv_batch_run(spmv_batch* b, const double* x, double* y, cudaStream_t s) {
     if (!b) spmvk::fail(SPMV_EINVAL, "batch is NULL");
     if (b->total_rows > 0 && (!x || !y)) spmvk::fail(SPMV_EINVAL, "x_dev or y_dev is NULL");
     if (b->n_items == 0) return SPMV_OK;
-    spmvk::check_cuda(cudaMemsetAsync(b->ticket, 0, sizeof(int), s), "ticket reset");
-    int grid = b->num_sms * std::max(1, b->occupancy);
-    const int need = (b->n_items + kThreads / 32 - 1) / (kThreads / 32);
-    if (grid > need) grid = need;
-    batch_persistent_kernel<<<grid, kThreads, 0, s>>>(args_of(b, x, y));
-    spmvk::check_cuda(cudaGetLastError(), "batch launch");
+    spmvk::check_cuda(cudaMemsetAsync(b->ticket, 0, 2 * sizeof(int), s), "ticket reset");
+    const int n_sl = b->n_sliced_items, n_csr = b->n_items - b->n_sliced_items;
+    if (n_sl > 0) {
+        BatchArgs a = args_of(b, x, y);
+        a.n_items = n_sl;
+        int grid = b->num_sms * std::max(1, b->occupancy_sliced);
+        const int need = (n_sl + kThreads / 32 - 1) / (kThreads / 32);
+        if (grid > need) grid = need;
+        batch_sliced_persistent_kernel<<<grid, kThreads, 0, s>>>(a);
+        spmvk::check_cuda(cudaGetLastError(), "batch launch (sliced)");
+    }
+    if (n_csr > 0) {
+        BatchArgs a = args_of(b, x, y);
+        a.order += n_sl;
+        a.n_items = n_csr;
+        a.ticket += 1;
+        int grid = b->num_sms * std::max(1, b->occupancy);
+        const int need = (n_csr + kThreads / 32 - 1) / (kThreads / 32);
+        if (grid > need) grid = need;
+        batch_persistent_kernel<<<grid, kThreads, 0, s>>>(a);
+        spmvk::check_cuda(cudaGetLastError(), "batch launch");
+    }
     BATCH_CATCH
     return SPMV_OK;
 }
@@ -493,10 +792,14 @@ int spmv_batch_run_separate(spmv_batch* b, int m, const double* x, double* y, cu
     for (int i = lo; i < hi; ++i) {
         const int first = b->item_off[i], last = b->item_off[i + 1];
         if (last <= first) continue;
-        int grid = b->num_sms * std::max(1, b->occupancy);
+        const bool sliced = b->mats[i].lanes == kSliced;
+        int grid = b->num_sms * std::max(1, sliced ? b->occupancy_sliced : b->occupancy);
         const int need = (last - first + kThreads / 32 - 1) / (kThreads / 32);
         if (grid > need) grid = need;
-        batch_range_kernel<<<grid, kThreads, 0, s>>>(a, first, last);
+        if (sliced)
+            batch_sliced_range_kernel<<<grid, kThreads, 0, s>>>(a, first, last);
+        else
+            batch_range_kernel<<<grid, kThreads, 0, s>>>(a, first, last);
         spmvk::check_cuda(cudaGetLastError(), "matrix launch");
     }
     BATCH_CATCH

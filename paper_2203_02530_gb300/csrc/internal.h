@@ -48,13 +48,32 @@ struct Carry {
     double val;
 };
 
-// Slice of the sliced-ELL layout: rows [r0, r0 + rows) (rows <= 32) of a
-// CSR, every row padded to len entries; entry j of lane r at off + 32 j + r.
+// Slice of the sliced-ELL layout: positions [p0, p0 + rows) (rows <= 32) of
+// the layout's row order, every row padded to len entries; entry j of lane r
+// at off + 32 j + r.
 struct SellSlice {
-    int32_t r0, rows, len, xoff;
+    int32_t p0, rows, len, xoff;
     int32_t off, pad0, pad1, pad2;
 };
 static_assert(sizeof(SellSlice) == 32, "slice descriptor is two int4");
+
+// A row longer than kSellLong entries: summed by a whole warp from the CSR.
+struct SellLong {
+    int32_t row, xoff;
+};
+constexpr int kSellLong = 64;
+constexpr uint8_t kSellLenLong = 0xFF;   // length code of a long row inside a slice
+
+// Sliced layout of one CSR product (local or remote), all ranks.
+struct SellArgs {
+    const SellSlice* slices;
+    const SellLong* longs;
+    const double* val;
+    const int32_t* col;
+    const uint8_t* len;      // per position: entries, or kSellLenLong
+    const int32_t* perm;     // per position: row; nullptr = position is the row
+    int slice_begin, slice_end, long_begin, long_end;
+};
 
 // Operands of one CSR product launch.
 struct CsrArgs {
@@ -95,9 +114,9 @@ cudaError_t read_clear_csr_error(int* out);
 int64_t noalloc_max_items();
 cudaError_t launch_merge_noalloc(const CsrArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const double* val, const SellSlice* slices,
-                             int n_slices, double* sval, int32_t* scol, int num_sms, cudaStream_t s);
-cudaError_t launch_sell(const CsrArgs& a, const SellSlice* slices, int slice_begin, int slice_end,
-                        const double* sval, const int32_t* scol, int param, int num_sms, cudaStream_t s);
+                             int n_slices, const uint8_t* len, const int32_t* perm, double* sval, int32_t* scol,
+                             int num_sms, cudaStream_t s);
+cudaError_t launch_sell(const CsrArgs& a, const SellArgs& s, int param, int num_sms, cudaStream_t st);
 bool sell_param_supported(int param);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);

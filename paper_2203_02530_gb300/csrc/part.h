@@ -102,16 +102,21 @@ struct spmv_part {
     std::vector<int64_t> lmtile_off;  // P+1
     std::vector<int64_t> rmtile_off;  // P+1
 
-    // sliced-ELL copies of A_L and A_R (built on first use of that variant)
-    spmvk::SellSlice* lslices = nullptr;
-    spmvk::SellSlice* rslices = nullptr;
-    std::vector<int64_t> lslice_off;  // P+1
-    std::vector<int64_t> rslice_off;  // P+1
-    double* ls_val = nullptr;
-    int32_t* ls_col = nullptr;
-    double* rs_val = nullptr;
-    int32_t* rs_col = nullptr;
-    int64_t sell_entries = 0;         // padded entries, local + remote (0: not built)
+    // sliced-ELL copies of A_L [0] and A_R [1] (built on first use of that
+    // variant): slices and long rows per rank, row order per position
+    struct SellPart {
+        spmvk::SellSlice* slices = nullptr;
+        spmvk::SellLong* longs = nullptr;
+        double* val = nullptr;
+        int32_t* col = nullptr;
+        uint8_t* len = nullptr;
+        int32_t* perm = nullptr;          // nullptr: every rank in natural order
+        std::vector<int64_t> slice_off;   // P+1
+        std::vector<int64_t> long_off;    // P+1
+        std::vector<char> sorted;         // per rank
+    } sell[2];
+    bool sell_built = false;
+    int64_t sell_entries = 0;         // padded entries, local + remote
 
     // product variant of the LOCAL [0] and REMOTE [1] operations
     int variant[2] = {SPMV_VARIANT_TILE, SPMV_VARIANT_TILE};
@@ -142,7 +147,6 @@ void build_tiles(spmv_part* pt, const TileGeom& g);
 void build_merge_tiles(spmv_part* pt);
 void build_warp_tiles(spmv_part* pt, int cap);
 void build_sell(spmv_part* pt);
-int64_t sell_entries_for(const std::vector<int32_t>& ptr, int64_t r0, int64_t r1);
 void* dev_alloc(spmv_part* pt, size_t bytes);
 void free_plan(spmv_part* pt);
 }  // namespace spmvk

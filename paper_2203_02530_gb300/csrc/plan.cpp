@@ -369,68 +369,96 @@ void build_warp_tiles(spmv_part* pt, int cap) {
     pt->wtile_cap = cap;
 }
 
-// Padded entries of the sliced layout of rows [r0, r1): 32 slots per entry
-// position of each slice's longest row.
-int64_t sell_entries_for(const std::vector<int32_t>& ptr, int64_t r0, int64_t r1) {
-    int64_t total = 0;
-    for (int64_t r = r0; r < r1; r += 32) {
-        const int64_t e = std::min(r1, r + 32);
-        int32_t len = 0;
-        for (int64_t i = r; i < e; ++i) len = std::max(len, ptr[(size_t)i + 1] - ptr[(size_t)i]);
-        total += 32 * (int64_t)len;
+// Sliced layout of one CSR (row pointer `ptr` over rows [0, rows)), rank p
+// owning rows [rb[p], rb[p+1]) with x offset xo[p].  Per rank: rows longer
+// than kSellLong go to the long list; the rest stay in natural order when
+// padding every 32-position slice to its longest row adds at most 1/8 (+1024)
+// entries, else they are sorted by length (descending, stable) behind the
+// long rows.  Returns the padded entry count.
+static int64_t build_sell_part(spmv_part* pt, spmv_part::SellPart& sp, const std::vector<int32_t>& ptr,
+                               const std::vector<int64_t>& rb, const std::vector<int32_t>& xo,
+                               const int32_t* d_ptr, const int32_t* d_col, const double* d_val) {
+    const int P = pt->P;
+    const int64_t rows = rb[P];
+    std::vector<SellSlice> slices;
+    std::vector<SellLong> longs;
+    std::vector<uint8_t> len((size_t)rows, 0);
+    std::vector<int32_t> perm;   // position -> row
+    perm.reserve((size_t)rows);
+    bool any_sorted = false;
+    int64_t off = 0;
+    sp.slice_off.assign(P + 1, 0);
+    sp.long_off.assign(P + 1, 0);
+    sp.sorted.assign(P, 0);
+    std::vector<int32_t> order;
+    for (int p = 0; p < P; ++p) {
+        const int64_t r0 = rb[p], r1 = rb[p + 1];
+        auto L = [&](int64_t r) { return ptr[(size_t)r + 1] - ptr[(size_t)r]; };
+        // natural order: long rows are holes in their slices
+        int64_t short_nnz = 0, nat = 0;
+        for (int64_t r = r0; r < r1; r += 32) {
+            int32_t mx = 0;
+            for (int64_t i = r; i < std::min(r1, r + 32); ++i)
+                if (L(i) <= kSellLong) mx = std::max(mx, L(i));
+            nat += 32 * (int64_t)mx;
+        }
+        for (int64_t i = r0; i < r1; ++i)
+            if (L(i) <= kSellLong) short_nnz += L(i);
+        const bool sorted = nat > short_nnz + short_nnz / 8 + 1024;
+        sp.sorted[p] = sorted;
+        order.resize((size_t)(r1 - r0));
+        for (int64_t i = r0; i < r1; ++i) order[(size_t)(i - r0)] = (int32_t)i;
+        if (sorted) {
+            any_sorted = true;
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return L(a) > L(b); });
+        }
+        perm.insert(perm.end(), order.begin(), order.end());   // identity for natural ranks
+        sp.long_off[p] = (int64_t)longs.size();
+        for (int64_t q = 0; q < r1 - r0; ++q) {
+            const int32_t r = order[(size_t)q];
+            if (L(r) > kSellLong) longs.push_back(SellLong{r, xo[p]});
+            len[(size_t)(r0 + q)] = L(r) > kSellLong ? kSellLenLong : (uint8_t)L(r);
+        }
+        // slices: sorted ranks skip their leading long rows
+        const int64_t first = sorted ? r0 + (int64_t)(longs.size() - sp.long_off[p]) : r0;
+        sp.slice_off[p] = (int64_t)slices.size();
+        for (int64_t q = first; q < r1; q += 32) {
+            const int64_t e = std::min(r1, q + 32);
+            int32_t mx = 0;
+            for (int64_t i = q; i < e; ++i)
+                if (len[(size_t)i] != kSellLenLong) mx = std::max<int32_t>(mx, len[(size_t)i]);
+            if (off + 32 * (int64_t)mx > INT32_MAX - 64) fail(SPMV_EBOUNDS, "sliced layout exceeds 2^31 entries");
+            slices.push_back(SellSlice{(int32_t)q, (int32_t)(e - q), mx, xo[p], (int32_t)off, 0, 0, 0});
+            off += 32 * (int64_t)mx;
+        }
     }
-    return total;
+    sp.slice_off[P] = (int64_t)slices.size();
+    sp.long_off[P] = (int64_t)longs.size();
+    sp.slices = upload(pt, slices);
+    sp.longs = upload(pt, longs);
+    sp.len = upload(pt, len);
+    sp.perm = any_sorted ? upload(pt, perm) : nullptr;
+    sp.val = static_cast<double*>(dev_alloc(pt, (size_t)off * 8));
+    sp.col = static_cast<int32_t*>(dev_alloc(pt, (size_t)off * 4));
+    check_cuda(launch_sell_fill(d_ptr, d_col, d_val, sp.slices, (int)slices.size(), sp.len, sp.perm, sp.val, sp.col,
+                                pt->num_sms, 0),
+               "sliced layout");
+    return off;
 }
 
-// Sliced-ELL copies of A_L and A_R: slices of 32 consecutive rows of one
-// rank, filled on the device from the plan's CSR arrays.  Refused when the
-// padding would more than double the entries (skewed row lengths: use the
-// merge or vector variants there).
+// Sliced-ELL copies of A_L and A_R (see build_sell_part), filled on the
+// device from the plan's CSR arrays.
 void build_sell(spmv_part* pt) {
     const int P = pt->P;
     const std::vector<int32_t> l_ptr = download(pt->l_ptr, (size_t)pt->n + 1);
     const std::vector<int32_t> rr_ptr = download(pt->rr_ptr, (size_t)pt->n_rr + 1);
-    std::vector<SellSlice> ls, rs;
-    int64_t l_off = 0, r_off = 0;
-    auto slices = [](const std::vector<int32_t>& ptr, int64_t r0, int64_t r1, int32_t xoff, int64_t& off,
-                     std::vector<SellSlice>& out) {
-        for (int64_t r = r0; r < r1; r += 32) {
-            const int64_t e = std::min(r1, r + 32);
-            int32_t len = 0;
-            for (int64_t i = r; i < e; ++i) len = std::max(len, ptr[(size_t)i + 1] - ptr[(size_t)i]);
-            if (off + 32 * (int64_t)len > INT32_MAX - 64) fail(SPMV_EBOUNDS, "sliced layout exceeds 2^31 entries");
-            out.push_back(SellSlice{(int32_t)r, (int32_t)(e - r), len, xoff, (int32_t)off, 0, 0, 0});
-            off += 32 * (int64_t)len;
-        }
-    };
-    pt->lslice_off.assign(P + 1, 0);
-    pt->rslice_off.assign(P + 1, 0);
-    for (int p = 0; p < P; ++p) {
-        pt->lslice_off[p] = (int64_t)ls.size();
-        slices(l_ptr, pt->bounds[p], pt->bounds[p + 1], (int32_t)pt->bounds[p], l_off, ls);
-        pt->rslice_off[p] = (int64_t)rs.size();
-        slices(rr_ptr, pt->rr_off[p], pt->rr_off[p + 1], 0, r_off, rs);
-    }
-    pt->lslice_off[P] = (int64_t)ls.size();
-    pt->rslice_off[P] = (int64_t)rs.size();
-    const int64_t limit = 2 * (pt->nnz_l + pt->nnz_r) + 32768;
-    if (l_off + r_off > limit)
-        fail(SPMV_EINVAL, "sliced layout would hold %lld entries for %lld stored (limit %lld): row lengths too skewed",
-             (long long)(l_off + r_off), (long long)(pt->nnz_l + pt->nnz_r), (long long)limit);
-    pt->lslices = upload(pt, ls);
-    pt->rslices = upload(pt, rs);
-    pt->ls_val = static_cast<double*>(dev_alloc(pt, (size_t)l_off * 8));
-    pt->ls_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)l_off * 4));
-    pt->rs_val = static_cast<double*>(dev_alloc(pt, (size_t)r_off * 8));
-    pt->rs_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)r_off * 4));
-    check_cuda(launch_sell_fill(pt->l_ptr, pt->l_col, pt->l_val, pt->lslices, (int)ls.size(), pt->ls_val,
-                                pt->ls_col, pt->num_sms, 0),
-               "sliced layout (local)");
-    check_cuda(launch_sell_fill(pt->rr_ptr, pt->r_col, pt->r_val, pt->rslices, (int)rs.size(), pt->rs_val,
-                                pt->rs_col, pt->num_sms, 0),
-               "sliced layout (remote)");
+    std::vector<int32_t> lxo(P), rxo(P, 0);
+    for (int p = 0; p < P; ++p) lxo[p] = (int32_t)pt->bounds[p];
+    int64_t e = build_sell_part(pt, pt->sell[0], l_ptr, pt->bounds, lxo, pt->l_ptr, pt->l_col, pt->l_val);
+    e += build_sell_part(pt, pt->sell[1], rr_ptr, pt->rr_off, rxo, pt->rr_ptr, pt->r_col, pt->r_val);
     check_cuda(cudaDeviceSynchronize(), "sliced layout");
-    pt->sell_entries = l_off + r_off;
+    pt->sell_entries = e;
+    pt->sell_built = true;
 }
 
 }  // namespace spmvk

@@ -1,7 +1,11 @@
 // Sliced-ELL form of the CSR products y_L = A_L x_L and y += A_R x_R
 // (Sec. III-A): the plan re-lays each rank's rows out in slices of 32
-// consecutive rows, entry j of the slice's lane r at  off + 32 j + r, every
-// row padded to the slice's longest row (value 0, column 0).
+// positions, entry j of the slice's lane r at off + 32 j + r, every row
+// padded to the slice's longest row (value 0, column 0).  A rank keeps its
+// natural row order when that pads little; otherwise its rows are sorted by
+// length, so a slice holds rows of similar length (a row permutation maps
+// positions back to rows).  Rows longer than 64 entries are summed by whole
+// warps instead.
 //
 // Why on GB300: FP64 FMA issues at 2 lanes per clock per SM, so the product
 // is co-bound by HBM and the FP64 pipe and the cost that decides is warp
@@ -11,9 +15,9 @@
 // consecutive columns (128 bytes) per step: full coalescing without a
 // shared-memory stage, so occupancy is set by registers alone.  On banded
 // and stencil matrices the lanes' x gathers of one step are also contiguous
-// rows of x.  Each row is summed in its CSR storage order, one FMA per
-// entry from 0.0; padded slots are discarded by a select, so y equals that
-// of the other one-thread-per-row kernels bit for bit.
+// rows of x.  Each short row is summed in its CSR storage order, one FMA
+// per entry from 0.0; padded slots are discarded by a select, so y equals
+// that of the other one-thread-per-row kernels bit for bit.
 #include "internal.h"
 
 #include <cuda_runtime.h>
@@ -61,25 +65,56 @@ __device__ __forceinline__ void sell_store(const CsrArgs& a, int row, double sum
 
 }  // namespace
 
-// One warp per slice (grid-stride over the launch's slices), one lane per
-// row.  U entries per lane per step: U value and U column loads, then U x
-// gathers, then U FMAs, so each lane keeps U gathers in flight.
+// One warp per work unit, grid-stride: units [0, n_long) are the launch's
+// long rows (each summed by the whole warp: lane l takes entries l, l+32,
+// ... in order, then a fixed xor-butterfly), the rest its slices (one lane
+// per row, U entries per lane per step: U value and U column loads, then U
+// x gathers, then U FMAs, so each lane keeps U gathers in flight).  Long
+// rows come first so that the heaviest units start in the first wave.
 template <int U, int MINB>
-__global__ void __launch_bounds__(256, MINB)
-    csr_sell_kernel(CsrArgs a, const SellSlice* __restrict__ slices, int slice_begin, int slice_end,
-                    const double* __restrict__ sval, const int32_t* __restrict__ scol) {
+__global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs sa) {
     const uint64_t pol_stream = sell_policy_evict_first();
     const uint64_t pol_keep = sell_policy_evict_last();
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)gridDim.x * 8;
-    for (int si = slice_begin + (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < slice_end; si += nwarps) {
-        const SellSlice d = slices[si];
-        const int row = d.r0 + lane;
-        const bool live = lane < d.rows;
+    const int n_long = sa.long_end - sa.long_begin;
+    const int n_units = n_long + (sa.slice_end - sa.slice_begin);
+    for (int u0 = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); u0 < n_units; u0 += nwarps) {
+        if (u0 < n_long) {
+            const SellLong L = sa.longs[sa.long_begin + u0];
+            const int kb = __ldg(a.ptr + L.row), ke = __ldg(a.ptr + L.row + 1);
+            const double* xb = a.x + L.xoff;
+            double part = 0.0;
+            int k = kb + lane;
+            for (; k + 96 < ke; k += 128) {
+                double v[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    v[u] = ld_stream(a.val + k + 32 * u, pol_stream);
+                    xv[u] = ld_keep(xb + ld_stream(a.col + k + 32 * u, pol_stream), pol_keep);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) part = fma(v[u], xv[u], part);
+            }
+            for (; k < ke; k += 32)
+                part = fma(ld_stream(a.val + k, pol_stream), ld_keep(xb + ld_stream(a.col + k, pol_stream), pol_keep),
+                           part);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == 0) sell_store(a, L.row, part);
+            continue;
+        }
+        const SellSlice d = sa.slices[sa.slice_begin + u0 - n_long];
+        const int pos = d.p0 + lane;
         int len = 0;
-        if (live) len = __ldg(a.ptr + row + 1) - __ldg(a.ptr + row);
-        const double* vp = sval + (int64_t)d.off + lane;
-        const int32_t* cp = scol + (int64_t)d.off + lane;
+        bool store = false;
+        if (lane < d.rows) {
+            const int code = sa.len[pos];
+            store = code != kSellLenLong;
+            len = store ? code : 0;
+        }
+        const double* vp = sa.val + (int64_t)d.off + lane;
+        const int32_t* cp = sa.col + (int64_t)d.off + lane;
         const double* xb = a.x + d.xoff;
         double sum = 0.0;
         int j = 0;
@@ -105,23 +140,28 @@ __global__ void __launch_bounds__(256, MINB)
             const double t = fma(v, ld_keep(xb + c, pol_keep), sum);
             sum = (j < len) ? t : sum;
         }
-        if (live) sell_store(a, row, sum);
+        if (store) sell_store(a, sa.perm ? __ldg(sa.perm + pos) : pos, sum);
     }
 }
 
-// Fill the sliced arrays from the CSR: one warp per slice, one lane per row.
+// Fill the sliced arrays from the CSR: one warp per slice, one lane per
+// position (a long row's slots, if it sits in a slice, stay padding).
 __global__ void __launch_bounds__(256) sell_fill_kernel(const int32_t* __restrict__ ptr,
                                                         const int32_t* __restrict__ col,
                                                         const double* __restrict__ val,
                                                         const SellSlice* __restrict__ slices, int n_slices,
+                                                        const uint8_t* __restrict__ lens,
+                                                        const int32_t* __restrict__ perm,
                                                         double* __restrict__ sval, int32_t* __restrict__ scol) {
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)gridDim.x * 8;
     for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < n_slices; si += nwarps) {
         const SellSlice d = slices[si];
-        const bool live = lane < d.rows;
-        const int kb = live ? ptr[d.r0 + lane] : 0;
-        const int len = live ? ptr[d.r0 + lane + 1] - kb : 0;
+        const int pos = d.p0 + lane;
+        const bool live = lane < d.rows && lens[pos] != kSellLenLong;
+        const int row = live ? (perm ? perm[pos] : pos) : 0;
+        const int kb = live ? ptr[row] : 0;
+        const int len = live ? ptr[row + 1] - kb : 0;
         for (int j = 0; j < d.len; ++j) {
             const int64_t o = (int64_t)d.off + 32 * j + lane;
             sval[o] = j < len ? val[kb + j] : 0.0;
@@ -131,11 +171,12 @@ __global__ void __launch_bounds__(256) sell_fill_kernel(const int32_t* __restric
 }
 
 cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const double* val, const SellSlice* slices,
-                             int n_slices, double* sval, int32_t* scol, int num_sms, cudaStream_t s) {
+                             int n_slices, const uint8_t* len, const int32_t* perm, double* sval, int32_t* scol,
+                             int num_sms, cudaStream_t s) {
     if (n_slices <= 0) return cudaSuccess;
     int grid = (n_slices + 7) / 8;
     if (grid > num_sms * 8) grid = num_sms * 8;
-    sell_fill_kernel<<<grid, 256, 0, s>>>(ptr, col, val, slices, n_slices, sval, scol);
+    sell_fill_kernel<<<grid, 256, 0, s>>>(ptr, col, val, slices, n_slices, len, perm, sval, scol);
     return cudaGetLastError();
 }
 
@@ -143,10 +184,9 @@ bool sell_param_supported(int param) {
     return param == 4 || param == 8 || param == 9 || param == 104;
 }
 
-cudaError_t launch_sell(const CsrArgs& a, const SellSlice* slices, int slice_begin, int slice_end,
-                        const double* sval, const int32_t* scol, int param, int num_sms, cudaStream_t s) {
-    if (slice_end <= slice_begin) return cudaSuccess;
-    const int warps = slice_end - slice_begin;
+cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, int num_sms, cudaStream_t st) {
+    const int units = (sa.long_end - sa.long_begin) + (sa.slice_end - sa.slice_begin);
+    if (units <= 0) return cudaSuccess;
     int blocks_per_sm = 8;
     switch (param) {
         case 4: blocks_per_sm = 8; break;
@@ -156,12 +196,12 @@ cudaError_t launch_sell(const CsrArgs& a, const SellSlice* slices, int slice_beg
         default: return cudaErrorInvalidValue;
     }
     int grid = num_sms * blocks_per_sm;
-    if (grid > (warps + 7) / 8) grid = (warps + 7) / 8;
+    if (grid > (units + 7) / 8) grid = (units + 7) / 8;
     switch (param) {
-        case 4: csr_sell_kernel<4, 8><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
-        case 8: csr_sell_kernel<8, 4><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
-        case 9: csr_sell_kernel<9, 4><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
-        case 104: csr_sell_kernel<4, 6><<<grid, 256, 0, s>>>(a, slices, slice_begin, slice_end, sval, scol); break;
+        case 4: csr_sell_kernel<4, 8><<<grid, 256, 0, st>>>(a, sa); break;
+        case 8: csr_sell_kernel<8, 4><<<grid, 256, 0, st>>>(a, sa); break;
+        case 9: csr_sell_kernel<9, 4><<<grid, 256, 0, st>>>(a, sa); break;
+        case 104: csr_sell_kernel<4, 6><<<grid, 256, 0, st>>>(a, sa); break;
     }
     return cudaGetLastError();
 }

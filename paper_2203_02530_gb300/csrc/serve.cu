@@ -27,10 +27,12 @@
 #include <vector>
 
 using spmvk::BatchMat;
+using spmvk::BSlice;
 
 namespace {
 
 constexpr int kMaxW = 8;          // widest block
+constexpr int kBatchSliced = 64;  // batch lanes value of the sliced layout
 constexpr int kThreads = 256;
 constexpr int kMidRow = 256;      // rows up to this length (above the short
                                   // threshold) get 8 lanes, longer rows 32
@@ -102,6 +104,35 @@ __device__ __forceinline__ void load_row(const double* xr, double (&xv)[W]) {
     }
 }
 
+// Hash of row `row`'s W values into the per-request sums h (definition below).
+template <int W>
+__device__ __forceinline__ void hash_row(const BlockDesc& b, int row, const double (&acc)[W],
+                                         unsigned long long (&h)[kMaxW]) {
+#pragma unroll
+    for (int r = 0; r < kMaxW; ++r) {
+        if (r >= b.n_req) break;
+        const BlockReq q = b.req[r];
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (c >= q.col0 && c < q.col0 + q.width) {
+                const uint64_t e = (uint64_t)row * q.width + (uint64_t)(c - q.col0);
+                h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * 0x9E3779B97F4A7C15ull);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void flush_hash(const BlockDesc& b, const unsigned long long (&h)[kMaxW],
+                                           unsigned long long* hashes) {
+#pragma unroll
+    for (int r = 0; r < kMaxW; ++r) {
+        if (r >= b.n_req) break;
+        unsigned long long v = h[r];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + b.req[r].index, v);
+    }
+}
+
 // Y[:, 0..W) = A X[:, 0..W): V lanes per row, lane h takes entries
 // kb + h, kb + h + V, ...; each column accumulates in entry order, then a
 // fixed xor-butterfly over the V lanes.
@@ -147,29 +178,10 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restric
         if (mine && lane == 0) {
 #pragma unroll
             for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
-            if (hashes) {
-#pragma unroll
-                for (int r = 0; r < kMaxW; ++r) {
-                    if (r >= b.n_req) break;
-                    const BlockReq q = b.req[r];
-#pragma unroll
-                    for (int c = 0; c < W; ++c) {
-                        if (c >= q.col0 && c < q.col0 + q.width) {
-                            const uint64_t e = (uint64_t)row * q.width + (uint64_t)(c - q.col0);
-                            h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * 0x9E3779B97F4A7C15ull);
-                        }
-                    }
-                }
-            }
+            if (hashes) hash_row<W>(b, row, acc, h);
         }
     }
-    if (hashes) {
-        for (int r = 0; r < b.n_req; ++r) {
-            unsigned long long v = h[r];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + b.req[r].index, v);
-        }
-    }
+    if (hashes) flush_hash(b, h, hashes);
 }
 
 // Rows from a list (one length bucket of a matrix): V lanes per row, lanes
@@ -214,29 +226,143 @@ __global__ void __launch_bounds__(kThreads) spmm_list_kernel(const int32_t* __re
         if (row >= 0 && lane == 0) {
 #pragma unroll
             for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
-            if (hashes) {
+            if (hashes) hash_row<W>(b, row, acc, h);
+        }
+    }
+    if (hashes) flush_hash(b, h, hashes);
+}
+
+// Y = A X over the matrix's sliced layout (the batch's, see
+// spmv_batch_set_lanes): one warp per slice, one lane per row, each column
+// accumulated in entry order (padded slots discarded by a select), two
+// entries' gathers in flight per lane.
+template <int W>
+__global__ void __launch_bounds__(kThreads) spmm_sliced_kernel(BatchMat m, const double* __restrict__ X,
+                                                               double* __restrict__ Y, BlockDesc b,
+                                                               unsigned long long* __restrict__ hashes) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long h[kMaxW];
 #pragma unroll
-                for (int r = 0; r < kMaxW; ++r) {
-                    if (r >= b.n_req) break;
-                    const BlockReq q = b.req[r];
+    for (int r = 0; r < kMaxW; ++r) h[r] = 0;
+    const int nw = (int)gridDim.x * (kThreads / 32);
+    for (int si = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); si < m.n_slices; si += nw) {
+        const BSlice d = m.s_slices[si];
+        const int pos = d.pos0 + lane;
+        const bool live = lane < d.rows;
+        const int len = live ? (int)m.s_len[pos] : 0;
+        const double* vp = m.s_val + (int64_t)d.off + lane;
+        const int32_t* cp = m.s_col + (int64_t)d.off + lane;
+        double acc[W];
 #pragma unroll
-                    for (int c = 0; c < W; ++c) {
-                        if (c >= q.col0 && c < q.col0 + q.width) {
-                            const uint64_t e = (uint64_t)row * q.width + (uint64_t)(c - q.col0);
-                            h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * 0x9E3779B97F4A7C15ull);
-                        }
-                    }
+        for (int c = 0; c < W; ++c) acc[c] = 0.0;
+        for (int j = 0; j < d.len; j += 2) {
+            const int j1 = j + 1 < d.len ? j + 1 : j;
+            const double a0 = __ldg(vp + 32 * j), a1 = __ldg(vp + 32 * j1);
+            const int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * j1);
+            double x0[W], x1[W];
+            load_row<W>(X + (int64_t)c0 * W, x0);
+            load_row<W>(X + (int64_t)c1 * W, x1);
+            const bool on0 = j < len, on1 = j + 1 < len;
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                const double t = fma(a0, x0[c], acc[c]);
+                acc[c] = on0 ? t : acc[c];
+            }
+            if (j + 1 < d.len) {   // uniform over the warp
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    const double t = fma(a1, x1[c], acc[c]);
+                    acc[c] = on1 ? t : acc[c];
                 }
             }
         }
-    }
-    if (hashes) {
-        for (int r = 0; r < b.n_req; ++r) {
-            unsigned long long v = h[r];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + b.req[r].index, v);
+        if (live) {
+            const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
+#pragma unroll
+            for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
+            if (hashes) hash_row<W>(b, row, acc, h);
         }
     }
+    if (hashes) flush_hash(b, h, hashes);
+}
+
+// The sliced layout's long rows (positions [0, n_long)), one per warp: lane
+// l takes entries l, l+32, ... of the row, W accumulators each, then a fixed
+// xor-butterfly.
+template <int W>
+__global__ void __launch_bounds__(kThreads) spmm_long_kernel(const int32_t* __restrict__ ptr,
+                                                             const int32_t* __restrict__ col,
+                                                             const double* __restrict__ val, BatchMat m,
+                                                             const double* __restrict__ X, double* __restrict__ Y,
+                                                             BlockDesc b, unsigned long long* __restrict__ hashes) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long h[kMaxW];
+#pragma unroll
+    for (int r = 0; r < kMaxW; ++r) h[r] = 0;
+    const int nw = (int)gridDim.x * (kThreads / 32);
+    for (int pos = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); pos < m.n_long; pos += nw) {
+        const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
+        const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+        double acc[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = 0.0;
+        for (int k = kb + lane; k < ke; k += 32) {
+            const double a = __ldg(val + k);
+            double xv[W];
+            load_row<W>(X + (int64_t)__ldg(col + k) * W, xv);
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] = fma(a, xv[c], acc[c]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
+            if (hashes) hash_row<W>(b, row, acc, h);
+        }
+    }
+    if (hashes) flush_hash(b, h, hashes);
+}
+
+cudaError_t launch_sliced(const BlockDesc& b, const int32_t* ptr, const int32_t* col, const double* val,
+                          const BatchMat& M, const double* X, double* Y, int num_sms, unsigned long long* hashes,
+                          cudaStream_t s) {
+    constexpr int WPB = kThreads / 32;
+    if (M.n_slices > 0) {
+        const int grid = std::min((M.n_slices + WPB - 1) / WPB, num_sms * 8);
+#define SPMM_SL(w) spmm_sliced_kernel<w><<<grid, kThreads, 0, s>>>(M, X, Y, b, hashes)
+        switch (b.width) {
+            case 1: SPMM_SL(1); break;
+            case 2: SPMM_SL(2); break;
+            case 3: SPMM_SL(3); break;
+            case 4: SPMM_SL(4); break;
+            case 5: SPMM_SL(5); break;
+            case 6: SPMM_SL(6); break;
+            case 7: SPMM_SL(7); break;
+            default: SPMM_SL(8); break;
+        }
+#undef SPMM_SL
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (M.n_long > 0) {
+        const int grid = std::min((M.n_long + WPB - 1) / WPB, num_sms * 8);
+#define SPMM_LG(w) spmm_long_kernel<w><<<grid, kThreads, 0, s>>>(ptr, col, val, M, X, Y, b, hashes)
+        switch (b.width) {
+            case 1: SPMM_LG(1); break;
+            case 2: SPMM_LG(2); break;
+            case 3: SPMM_LG(3); break;
+            case 4: SPMM_LG(4); break;
+            case 5: SPMM_LG(5); break;
+            case 6: SPMM_LG(6); break;
+            case 7: SPMM_LG(7); break;
+            default: SPMM_LG(8); break;
+        }
+#undef SPMM_LG
+    }
+    return cudaGetLastError();
 }
 
 template <int V>
@@ -372,6 +498,7 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     const int32_t* ptr = bt->ptr + M.ptr_off;
     const int32_t* col = bt->col + M.ent_off;
     const double* val = bt->val + M.ent_off;
+    if (M.lanes == kBatchSliced) return launch_sliced(b, ptr, col, val, M, X, Y, sv->num_sms, hashes, s);
     const int V = sv->lanes[m];
     int grid = (int)std::min<int64_t>((n + (kThreads / V) - 1) / (kThreads / V), (int64_t)sv->num_sms * 8);
     const int smax = sv->short_max[m];

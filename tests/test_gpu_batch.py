@@ -29,7 +29,7 @@ def _oracle(mats, x, offs):
     return want, scale
 
 
-@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32, "mixed"])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32, 64, "mixed"])
 def test_batch_matches_oracle_and_separate_launches(lanes):
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
@@ -39,7 +39,7 @@ def test_batch_matches_oracle_and_separate_launches(lanes):
         assert offs[-1] == sum(m[0] for m in mats)
         if lanes == "mixed":
             for m in range(b.count):
-                spmv.spmv_batch_set_lanes(b.h, m, [0, 1, 2, 4, 8, 16, 32][m % 7])
+                spmv.spmv_batch_set_lanes(b.h, m, [0, 1, 2, 4, 8, 16, 32, 64][m % 8])
         else:
             spmv.spmv_batch_set_lanes(b.h, -1, lanes)
         x = W.uniform_x(offs[-1], seed=9)
@@ -90,3 +90,31 @@ def test_batch_autotune_keeps_results():
         spmv.spmv_batch_run(b.h, x_d, y, s)
         s.synchronize()
         assert_fp64_close(y.cpu().numpy(), want, scale, "tuned batch")
+
+
+def test_sliced_mode_round_trip_and_long_rows():
+    """The sliced layout (natural order for stencils, length-sorted with
+    whole-warp long rows for skewed matrices) gives the oracle's y; switching
+    modes back and forth keeps every mode's result."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = [W.stencil_7pt(12, seed=1), W.zipf_random(20000, seed=2), W.laplacian_5pt(33),
+            W.powerlaw(6000, seed=3, cap=3000)]
+    with spmv.Batch(mats) as b:
+        offs = b.offsets()
+        x = W.uniform_x(offs[-1], seed=12)
+        want, scale = _oracle(mats, x, offs)
+        s = torch.cuda.Stream()
+        x_d = dev(x)
+        y = torch.empty(offs[-1], dtype=torch.float64, device="cuda")
+        res = {}
+        for lanes in (spmv.BATCH_SLICED, 1, spmv.BATCH_SLICED, 0):
+            spmv.spmv_batch_set_lanes(b.h, -1, lanes)
+            assert b.query(spmv.BQ_LANES, 1) == lanes
+            spmv.spmv_batch_run(b.h, x_d, y, s)
+            s.synchronize()
+            a = y.cpu().numpy()
+            assert_fp64_close(a, want, scale, "lanes %d" % lanes)
+            if lanes in res:
+                assert np.array_equal(a, res[lanes])
+            res[lanes] = a

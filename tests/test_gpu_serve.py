@@ -58,37 +58,41 @@ def test_request_x_matches_device_generator():
         assert np.array_equal(x.cpu().numpy(), W.request_x(12345, n, 5))
 
 
-def test_results_same_alone_and_in_the_mix_and_match_oracle():
+@pytest.mark.parametrize("layout", ["buckets", "sliced"])
+def test_results_same_alone_and_in_the_mix_and_match_oracle(layout):
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
     mats = _mats()
     mat, wid, sd, arr = _requests(400, len(mats), 11, 0.02)
-    with spmv.Batch(mats) as b, spmv.Server(b, n_streams=4, budget_bytes=1 << 30) as sv:
-        lat_b, h_b, st_b = sv.run(mat, wid, sd, arr, spmv.SERVE_BATCHED)
-        lat_p, h_p, st_p = sv.run(mat, wid, sd, arr, spmv.SERVE_PLAIN)
-        assert np.array_equal(h_b, h_p)
-        assert st_p["blocks"] == len(mat)
-        assert st_b["admitted_while_busy"] > 0                 # continuous admission
-        assert (lat_b > 0).all() and (lat_p > 0).all()
-        # a burst queues up, so requests of one matrix are merged into blocks
-        lat_burst, h_burst, st_burst = sv.run(mat, wid, sd, np.zeros(len(mat)), spmv.SERVE_BATCHED)
-        assert st_burst["blocks"] < len(mat)
-        assert np.array_equal(h_burst, h_b)
-        s = torch.cuda.Stream()
-        for r in range(0, len(mat), 23):
-            m, k = int(mat[r]), int(wid[r])
-            n, rp, ci, va = mats[m]
-            x = torch.empty((n, k), dtype=torch.float64, device="cuda")
-            y = torch.empty((n, k), dtype=torch.float64, device="cuda")
-            spmv.spmv_serve_single(sv.h, m, k, int(sd[r]), y, x, s)
-            s.synchronize()
-            Y = y.cpu().numpy()
-            assert host_hash(Y, k) == h_b[r], "request %d differs alone and in the mix" % r
-            X = W.request_x(int(sd[r]), n, k)
-            for j in range(k):
-                want = oracle.csr_spmv(n, rp, ci, va, X[:, j])
-                scale = oracle.csr_absdot(n, rp, ci, va, X[:, j])
-                assert_fp64_close(Y[:, j], want, scale, "request %d column %d" % (r, j))
+    with spmv.Batch(mats) as b:
+        if layout == "sliced":
+            spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        with spmv.Server(b, n_streams=4, budget_bytes=1 << 30) as sv:
+            lat_b, h_b, st_b = sv.run(mat, wid, sd, arr, spmv.SERVE_BATCHED)
+            lat_p, h_p, st_p = sv.run(mat, wid, sd, arr, spmv.SERVE_PLAIN)
+            assert np.array_equal(h_b, h_p)
+            assert st_p["blocks"] == len(mat)
+            assert st_b["admitted_while_busy"] > 0                 # continuous admission
+            assert (lat_b > 0).all() and (lat_p > 0).all()
+            # a burst queues up, so requests of one matrix are merged into blocks
+            lat_burst, h_burst, st_burst = sv.run(mat, wid, sd, np.zeros(len(mat)), spmv.SERVE_BATCHED)
+            assert st_burst["blocks"] < len(mat)
+            assert np.array_equal(h_burst, h_b)
+            s = torch.cuda.Stream()
+            for r in range(0, len(mat), 23):
+                m, k = int(mat[r]), int(wid[r])
+                n, rp, ci, va = mats[m]
+                x = torch.empty((n, k), dtype=torch.float64, device="cuda")
+                y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+                spmv.spmv_serve_single(sv.h, m, k, int(sd[r]), y, x, s)
+                s.synchronize()
+                Y = y.cpu().numpy()
+                assert host_hash(Y, k) == h_b[r], "request %d differs alone and in the mix" % r
+                X = W.request_x(int(sd[r]), n, k)
+                for j in range(k):
+                    want = oracle.csr_spmv(n, rp, ci, va, X[:, j])
+                    scale = oracle.csr_absdot(n, rp, ci, va, X[:, j])
+                    assert_fp64_close(Y[:, j], want, scale, "request %d column %d" % (r, j))
 
 
 def test_small_budget_makes_blocks_wait_but_completes():
