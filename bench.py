@@ -434,7 +434,8 @@ def run_batched(args, world, rank, local):
     y_s = torch.empty(total, dtype=torch.float64, device=dev)
     s = torch.cuda.Stream(device=dev)
     mrl = [(int(m[1][-1]) / m[0]) if m[0] else 0.0 for m in mats]
-    lanes = autotune.tune_batch(b, x_d, y_b, s, mean_row_lengths=mrl)
+    tune_log = []
+    lanes = autotune.tune_batch(b, x_d, y_b, s, mean_row_lengths=mrl, log=tune_log)
     alg = b.query(spmv.BQ_ALG_BYTES)
     batched = lambda: spmv.spmv_batch_run(b.h, x_d, y_b, s)
     separate = lambda: spmv.spmv_batch_run_separate(b.h, -1, x_d, y_s, s)
@@ -527,6 +528,7 @@ def run_batched(args, world, rank, local):
                 "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
                 "ms_per_step": round(t_e2e * 1e3, 4)},
         "cpu_baseline": cpu, "clocks": clocks,
+        "autotune_us": {k: round(t * 1e6, 1) for k, t in tune_log},
         "gpu_launches": args.steps * launches,
     }
 
@@ -544,6 +546,8 @@ def run_serving(args, world, rank, local):
     mix = W.serve_mix(64, seed=6)
     mats = [m for _, m in mix]
     b = spmv.Batch(mats)
+    if args.serve_layout == "sliced":
+        spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
     sv = spmv.Server(b, n_streams=args.serve_streams, budget_bytes=40 << 30)
     rate = args.serve_rate
     arr = W.poisson_arrivals(rate, args.serve_seconds, seed=7)
@@ -576,7 +580,8 @@ def run_serving(args, world, rank, local):
         lat, _, st = sv.run(mat[:nsat], wid[:nsat], sd[:nsat], np.zeros(nsat), mode, want_hash=False)
         el = st["elapsed_ns"] * 1e-9
         sat[name] = {"throughput_req_s": round(nsat / el, 1),
-                     "gbs": round(req_bytes[:nsat].sum() / el / 1e9, 2), "blocks": st["blocks"]}
+                     "gbs": round(req_bytes[:nsat].sum() / el / 1e9, 2), "blocks": st["blocks"],
+                     "launches": spmv.spmv_serve_launches(sv.h)}
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -606,21 +611,24 @@ def run_serving(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals (%g req/s for %g s, %d requests) over 64 resident "
                                "matrices (7-point stencils and power-law rows, %.2f GB), width 1..8, "
-                               "budget 40 GB, %d stream slots" % (rate, args.serve_seconds, count,
-                                                                   total / 1e9, args.serve_streams),
+                               "budget 40 GB, %d stream slots, %s layout" % (
+                                   rate, args.serve_seconds, count, total / 1e9, args.serve_streams,
+                                   args.serve_layout),
                    "value": "saturation throughput of the served form (all requests present at t=0)"},
         "open_loop": out, "saturation": sat,
         "served_vs_plain_saturation": round(sat["served"]["gbs"] / sat["plain"]["gbs"], 3),
         "results_identical_served_vs_plain": same,
         "latency_us": {"p50": out["served"]["p50_us"], "p99": out["served"]["p99_us"],
                        "protocol": "arrival to observed completion, open loop"},
-        "roofline": {"bound": "hbm", "kernel": "spmm_kernel", "achieved": value, "peak": peak,
+        "roofline": {"bound": "hbm",
+                     "kernel": "spmm_sliced_kernel" if args.serve_layout == "sliced" else "spmm_kernel",
+                     "achieved": value, "peak": peak,
                      "unit": "GB/s", "frac": round(value / peak, 4), "traffic": None,
                      "peak_kind": peak_kind, "note": "per-request algorithmic bytes at saturation"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
                 "note": "inputs are drawn on the device from each request's seed; the host reads "
                         "one 8-byte hash per request"},
-        "cpu_baseline": cpu, "gpu_launches": 3 * sat["served"]["blocks"],
+        "cpu_baseline": cpu, "gpu_launches": sat["served"]["launches"],
     }
 
 
@@ -695,6 +703,7 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-streams", type=int, default=32)
     ap.add_argument("--serve-saturation", type=int, default=20000)
+    ap.add_argument("--serve-layout", choices=["sliced", "buckets"], default="sliced")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -360,6 +360,9 @@ int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, doubl
  *   completed.  BATCHED merges the oldest requests of one matrix into one
  *   block of total width <= 8 whenever a slot and pool memory are free;
  *   requests arriving while blocks run join at the next turn of the loop.
+ *   When every matrix is in the sliced layout, BATCHED goes further: a free
+ *   slot takes up to 64 such blocks, across matrices, as one group run by
+ *   one launch per kernel kind (X generation, slices, long rows).
  *   PLAIN launches every request alone (one block per request).  Outputs:
  *   latency_s[r] = observed completion - arrival; hash_out[r] (optional) an
  *   order-independent 64-bit hash of the bits of request r's Y; stats (6
@@ -388,6 +391,9 @@ int spmv_serve_destroy(spmv_server* server);
 int spmv_serve_run(spmv_server* server, int64_t n_req, const int32_t* matrix,
                    const int32_t* width, const uint64_t* seed, const double* arrival_s,
                    int mode, double* latency_s, uint64_t* hash_out, int64_t* stats);
+/* Kernels launched by the last spmv_serve_run (every block's X generator
+ * and products). */
+int spmv_serve_launches(const spmv_server* server, int64_t* out);
 int spmv_serve_single(spmv_server* server, int matrix, int width, uint64_t seed,
                       double* y_dev, double* x_dev, cudaStream_t s);
 

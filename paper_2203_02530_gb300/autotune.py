@@ -97,17 +97,20 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
 
 
 def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(0, 1, 2, 4, 8, 16, 64),
-               reps=5):
+               reps=5, log=None):
     """Lanes per row for the matrices of a batch, timed on the persistent
     launch itself (one launch per matrix would be dominated by launch
     latency for small matrices): first one value for every matrix, then one
     value per class of mean row length (< 4, < 8, < 16, < 32, >= 32), each
-    class tried with the others fixed.  Returns the list chosen."""
+    class tried with the others fixed.  Returns the list chosen; `log`, if
+    given, receives (description, seconds) for every timing."""
     run = lambda: spmv.spmv_batch_run(batch.h, x_dev, y_dev, stream)
     best_v, best_t = None, None
     for v in lanes:
         spmv.spmv_batch_set_lanes(batch.h, -1, v)
         t = time_loop(run, stream, reps, warmup=2)
+        if log is not None:
+            log.append(("all %d" % v, t))
         if best_t is None or t < best_t:
             best_v, best_t = v, t
     chosen = [best_v] * batch.count
@@ -124,6 +127,8 @@ def tune_batch(batch, x_dev, y_dev, stream, mean_row_lengths=None, lanes=(0, 1, 
                 for m in members:
                     spmv.spmv_batch_set_lanes(batch.h, m, v)
                 t = time_loop(run, stream, reps, warmup=2)
+                if log is not None:
+                    log.append(("class %d -> %d" % (c, v), t))
                 if t < cur_t:
                     cur_v, cur_t = v, t
                 for m in members:

@@ -451,21 +451,33 @@ void brelease(spmv_batch* b, void* p, size_t bytes) {
 // are the heaviest, so they do not end up in the tail).
 void upload_items(spmv_batch* b) {
     std::vector<BatchItem> all;
+    std::vector<int64_t> cost;   // estimated work per item (entries plus 8 per row)
     b->item_off.assign(b->count + 1, 0);
     for (int m = 0; m < b->count; ++m) {
         b->item_off[m] = (int)all.size();
-        const auto& src = b->mats[m].lanes == kSliced ? b->sliced_items[m] : b->csr_items[m];
+        const bool sl = b->mats[m].lanes == kSliced;
+        const auto& src = sl ? b->sliced_items[m] : b->csr_items[m];
+        const auto& cst = sl ? b->sliced_cost[m] : b->csr_cost[m];
         all.insert(all.end(), src.begin(), src.end());
+        cost.insert(cost.end(), cst.begin(), cst.end());
     }
     b->item_off[b->count] = (int)all.size();
+    // claim order: matrix by matrix, so that the warps in flight share a
+    // few matrices' x in L2 (taking heavy items of every matrix first would
+    // spread the gathers over all of them); within a matrix its heaviest
+    // items (the long rows) first, so they do not end up in the tail
     b->order.clear();
     for (int i = 0; i < (int)all.size(); ++i)
-        if (all[i].kind == 1) b->order.push_back(i);
-    for (int i = 0; i < (int)all.size(); ++i)
-        if (all[i].kind == 2) b->order.push_back(i);
+        if (all[i].kind != 0) b->order.push_back(i);
     b->n_sliced_items = (int)b->order.size();
     for (int i = 0; i < (int)all.size(); ++i)
         if (all[i].kind == 0) b->order.push_back(i);
+    auto first = [&](int p, int q) {
+        if (all[p].m != all[q].m) return all[p].m < all[q].m;
+        return cost[p] > cost[q];
+    };
+    std::stable_sort(b->order.begin(), b->order.begin() + b->n_sliced_items, first);
+    std::stable_sort(b->order.begin() + b->n_sliced_items, b->order.end(), first);
     if (all.size() > b->items_cap) {
         if (b->d_items) brelease(b, b->d_items, b->items_cap * sizeof(BatchItem));
         if (b->d_order) brelease(b, b->d_order, b->items_cap * sizeof(int));
@@ -557,16 +569,25 @@ void build_sliced(spmv_batch* b, int m) {
         spmvk::check_cuda(cudaDeviceSynchronize(), "sliced fill");
     }
     std::vector<BatchItem>& items = b->sliced_items[m];
+    std::vector<int64_t>& cost = b->sliced_cost[m];
     items.clear();
-    for (int p = 0; p < n_long;) {
+    cost.clear();
+    for (int p = 0; p < n_long;) {   // up to 32 long rows or 4096 of their entries
         int e = p;
         int64_t ent = 0;
         while (e < n_long && e - p < 32 && ent < 4096) ent += L(e++);
         items.push_back(BatchItem{m, 1, p, e});
+        cost.push_back(ent + ent / 2 + 8 * (e - p));
         p = e;
     }
-    for (int s0 = 0; s0 < (int)sl.size(); s0 += 8)
-        items.push_back(BatchItem{m, 2, s0, std::min((int)sl.size(), s0 + 8)});
+    for (int s0 = 0; s0 < (int)sl.size();) {   // up to 8 slices or 4096 padded slots
+        int s1 = s0;
+        int64_t slots = 0;
+        while (s1 < (int)sl.size() && s1 - s0 < 8 && slots < 4096) slots += 32 * (int64_t)sl[s1++].len;
+        items.push_back(BatchItem{m, 2, s0, s1});
+        cost.push_back(slots + 8 * 32 * (int64_t)(s1 - s0));
+        s0 = s1;
+    }
     b->sliced_built[m] = 1;
 }
 
@@ -649,6 +670,8 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
     std::vector<double> hval((size_t)ent_total, 0.0);
     b->csr_items.assign(count, {});
     b->sliced_items.assign(count, {});
+    b->csr_cost.assign(count, {});
+    b->sliced_cost.assign(count, {});
     b->sliced_built.assign(count, 0);
     for (int m = 0; m < count; ++m) {
         const BatchMat& M = b->mats[m];
@@ -659,8 +682,11 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
             hcol[(size_t)(M.ent_off + k)] = col_idx[m][base + k];
             hval[(size_t)(M.ent_off + k)] = vals[m][base + k];
         }
-        for (int64_t r = 0; r < n[m]; r += kItemRows)
-            b->csr_items[m].push_back(BatchItem{m, 0, (int)r, (int)std::min<int64_t>(n[m], r + kItemRows)});
+        for (int64_t r = 0; r < n[m]; r += kItemRows) {
+            const int64_t e = std::min<int64_t>(n[m], r + kItemRows);
+            b->csr_items[m].push_back(BatchItem{m, 0, (int)r, (int)e});
+            b->csr_cost[m].push_back((row_ptr[m][e] - row_ptr[m][r]) + 8 * (e - r));
+        }
     }
     b->ptr = static_cast<int32_t*>(balloc(b, hptr.size() * 4));
     b->col = static_cast<int32_t*>(balloc(b, hcol.size() * 4));

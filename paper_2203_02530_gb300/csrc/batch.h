@@ -52,6 +52,7 @@ struct spmv_batch {
     std::vector<int64_t> nnz;            // entries per matrix
     std::vector<int> item_off;           // count+1 item offsets per matrix
     std::vector<std::vector<spmvk::BatchItem>> csr_items, sliced_items;   // per matrix
+    std::vector<std::vector<int64_t>> csr_cost, sliced_cost;              // estimated work per item
     std::vector<int> order;              // claim order of the persistent launch
     std::vector<char> sliced_built;      // per matrix
     int* d_order = nullptr;

@@ -64,21 +64,25 @@ struct BlockDesc {
     int width;
 };
 
-// X[i, c] for every column of every request of the block (row-major, ld W):
-// request r's element (i, j) is U(seed_r, 8 i + j).
-__global__ void gen_x_kernel(double* __restrict__ X, int n, BlockDesc b) {
-    const int W = b.width;
+// X[i, c] for every column of every request of a block (row-major, ld W):
+// request r's element (i, j) is U(seed_r, 8 i + j).  Elements e0, e0 + step, ...
+__device__ __forceinline__ void gen_x(double* __restrict__ X, int n, int W, const BlockReq* req, int n_req,
+                                      int e0, int step) {
     const int total = n * W;   // < 2^31: n < 2^28 is checked by the server
-    for (int e = (int)(blockIdx.x * blockDim.x + threadIdx.x); e < total; e += (int)(gridDim.x * blockDim.x)) {
+    for (int e = e0; e < total; e += step) {
         const int i = e / W, c = e - (e / W) * W;
         double v = 0.0;
-        for (int r = 0; r < b.n_req; ++r) {
-            const BlockReq q = b.req[r];
+        for (int r = 0; r < n_req; ++r) {
+            const BlockReq q = req[r];
             if (c >= q.col0 && c < q.col0 + q.width)
                 v = uniform_pm1(q.seed, (uint64_t)i * kMaxW + (uint64_t)(c - q.col0));
         }
         X[e] = v;   // row-major, leading dimension W
     }
+}
+
+__global__ void gen_x_kernel(double* __restrict__ X, int n, BlockDesc b) {
+    gen_x(X, n, b.width, b.req, b.n_req, (int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x));
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -106,12 +110,12 @@ __device__ __forceinline__ void load_row(const double* xr, double (&xv)[W]) {
 
 // Hash of row `row`'s W values into the per-request sums h (definition below).
 template <int W>
-__device__ __forceinline__ void hash_row(const BlockDesc& b, int row, const double (&acc)[W],
+__device__ __forceinline__ void hash_row(const BlockReq* req, int n_req, int row, const double (&acc)[W],
                                          unsigned long long (&h)[kMaxW]) {
 #pragma unroll
     for (int r = 0; r < kMaxW; ++r) {
-        if (r >= b.n_req) break;
-        const BlockReq q = b.req[r];
+        if (r >= n_req) break;
+        const BlockReq q = req[r];
 #pragma unroll
         for (int c = 0; c < W; ++c) {
             if (c >= q.col0 && c < q.col0 + q.width) {
@@ -122,14 +126,15 @@ __device__ __forceinline__ void hash_row(const BlockDesc& b, int row, const doub
     }
 }
 
-__device__ __forceinline__ void flush_hash(const BlockDesc& b, const unsigned long long (&h)[kMaxW],
+__device__ __forceinline__ void flush_hash(const BlockReq* req, int n_req, unsigned long long (&h)[kMaxW],
                                            unsigned long long* hashes) {
 #pragma unroll
     for (int r = 0; r < kMaxW; ++r) {
-        if (r >= b.n_req) break;
+        if (r >= n_req) break;
         unsigned long long v = h[r];
+        h[r] = 0;
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + b.req[r].index, v);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(hashes + req[r].index, v);
     }
 }
 
@@ -178,10 +183,10 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(const int32_t* __restric
         if (mine && lane == 0) {
 #pragma unroll
             for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
-            if (hashes) hash_row<W>(b, row, acc, h);
+            if (hashes) hash_row<W>(b.req, b.n_req, row, acc, h);
         }
     }
-    if (hashes) flush_hash(b, h, hashes);
+    if (hashes) flush_hash(b.req, b.n_req, h, hashes);
 }
 
 // Rows from a list (one length bucket of a matrix): V lanes per row, lanes
@@ -226,110 +231,222 @@ __global__ void __launch_bounds__(kThreads) spmm_list_kernel(const int32_t* __re
         if (row >= 0 && lane == 0) {
 #pragma unroll
             for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
-            if (hashes) hash_row<W>(b, row, acc, h);
+            if (hashes) hash_row<W>(b.req, b.n_req, row, acc, h);
         }
     }
-    if (hashes) flush_hash(b, h, hashes);
+    if (hashes) flush_hash(b.req, b.n_req, h, hashes);
 }
 
-// Y = A X over the matrix's sliced layout (the batch's, see
-// spmv_batch_set_lanes): one warp per slice, one lane per row, each column
+// One slice of the matrix's sliced layout (the batch's, see
+// spmv_batch_set_lanes), Y = A X on its rows: one lane per row, each column
 // accumulated in entry order (padded slots discarded by a select), two
-// entries' gathers in flight per lane.
+// entries' gathers in flight per lane; with `hashes`, the rows' hash terms
+// go into h.
+template <int W>
+__device__ __forceinline__ void sliced_unit(const BatchMat& m, int si, const double* __restrict__ X,
+                                            double* __restrict__ Y, const BlockReq* req, int n_req,
+                                            unsigned long long* hashes, unsigned long long (&h)[kMaxW]) {
+    const int lane = threadIdx.x & 31;
+    const BSlice d = m.s_slices[si];
+    const int pos = d.pos0 + lane;
+    const bool live = lane < d.rows;
+    const int len = live ? (int)m.s_len[pos] : 0;
+    const double* vp = m.s_val + (int64_t)d.off + lane;
+    const int32_t* cp = m.s_col + (int64_t)d.off + lane;
+    double acc[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] = 0.0;
+    for (int j = 0; j < d.len; j += 2) {
+        const int j1 = j + 1 < d.len ? j + 1 : j;
+        const double a0 = __ldg(vp + 32 * j), a1 = __ldg(vp + 32 * j1);
+        const int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * j1);
+        double x0[W], x1[W];
+        load_row<W>(X + (int64_t)c0 * W, x0);
+        load_row<W>(X + (int64_t)c1 * W, x1);
+        const bool on0 = j < len, on1 = j + 1 < len;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const double t = fma(a0, x0[c], acc[c]);
+            acc[c] = on0 ? t : acc[c];
+        }
+        if (j + 1 < d.len) {   // uniform over the warp
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                const double t = fma(a1, x1[c], acc[c]);
+                acc[c] = on1 ? t : acc[c];
+            }
+        }
+    }
+    if (live) {
+        const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
+#pragma unroll
+        for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
+        if (hashes) hash_row<W>(req, n_req, row, acc, h);
+    }
+}
+
+// The sliced layout's long row at position pos, by the whole warp: lane l
+// takes entries l, l+32, ... in order (four in flight), W accumulators
+// each, then a fixed xor-butterfly.
+template <int W>
+__device__ __forceinline__ void long_unit(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, const BatchMat& m, int pos,
+                                          const double* __restrict__ X, double* __restrict__ Y,
+                                          const BlockReq* req, int n_req, unsigned long long* hashes,
+                                          unsigned long long (&h)[kMaxW]) {
+    const int lane = threadIdx.x & 31;
+    const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
+    const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+    double acc[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] = 0.0;
+    int k = kb + lane;
+    for (; k + 96 < ke; k += 128) {   // four entries per lane in flight
+        double a[4], xv[4][W];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = __ldg(val + k + 32 * u);
+            load_row<W>(X + (int64_t)__ldg(col + k + 32 * u) * W, xv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] = fma(a[u], xv[u][c], acc[c]);
+    }
+    for (; k < ke; k += 32) {
+        const double a = __ldg(val + k);
+        double xv[W];
+        load_row<W>(X + (int64_t)__ldg(col + k) * W, xv);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(a, xv[c], acc[c]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
+        if (hashes) hash_row<W>(req, n_req, row, acc, h);
+    }
+}
+
+// One block over the sliced layout: one warp per slice (grid-stride).
 template <int W>
 __global__ void __launch_bounds__(kThreads) spmm_sliced_kernel(BatchMat m, const double* __restrict__ X,
                                                                double* __restrict__ Y, BlockDesc b,
                                                                unsigned long long* __restrict__ hashes) {
-    const int lane = threadIdx.x & 31;
     unsigned long long h[kMaxW];
 #pragma unroll
     for (int r = 0; r < kMaxW; ++r) h[r] = 0;
     const int nw = (int)gridDim.x * (kThreads / 32);
-    for (int si = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); si < m.n_slices; si += nw) {
-        const BSlice d = m.s_slices[si];
-        const int pos = d.pos0 + lane;
-        const bool live = lane < d.rows;
-        const int len = live ? (int)m.s_len[pos] : 0;
-        const double* vp = m.s_val + (int64_t)d.off + lane;
-        const int32_t* cp = m.s_col + (int64_t)d.off + lane;
-        double acc[W];
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = 0.0;
-        for (int j = 0; j < d.len; j += 2) {
-            const int j1 = j + 1 < d.len ? j + 1 : j;
-            const double a0 = __ldg(vp + 32 * j), a1 = __ldg(vp + 32 * j1);
-            const int c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * j1);
-            double x0[W], x1[W];
-            load_row<W>(X + (int64_t)c0 * W, x0);
-            load_row<W>(X + (int64_t)c1 * W, x1);
-            const bool on0 = j < len, on1 = j + 1 < len;
-#pragma unroll
-            for (int c = 0; c < W; ++c) {
-                const double t = fma(a0, x0[c], acc[c]);
-                acc[c] = on0 ? t : acc[c];
-            }
-            if (j + 1 < d.len) {   // uniform over the warp
-#pragma unroll
-                for (int c = 0; c < W; ++c) {
-                    const double t = fma(a1, x1[c], acc[c]);
-                    acc[c] = on1 ? t : acc[c];
-                }
-            }
-        }
-        if (live) {
-            const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
-#pragma unroll
-            for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
-            if (hashes) hash_row<W>(b, row, acc, h);
-        }
-    }
-    if (hashes) flush_hash(b, h, hashes);
+    for (int si = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); si < m.n_slices; si += nw)
+        sliced_unit<W>(m, si, X, Y, b.req, b.n_req, hashes, h);
+    if (hashes) flush_hash(b.req, b.n_req, h, hashes);
 }
 
-// The sliced layout's long rows (positions [0, n_long)), one per warp: lane
-// l takes entries l, l+32, ... of the row, W accumulators each, then a fixed
-// xor-butterfly.
+// One block's long rows (positions [0, n_long)), one per warp.
 template <int W>
 __global__ void __launch_bounds__(kThreads) spmm_long_kernel(const int32_t* __restrict__ ptr,
                                                              const int32_t* __restrict__ col,
                                                              const double* __restrict__ val, BatchMat m,
                                                              const double* __restrict__ X, double* __restrict__ Y,
                                                              BlockDesc b, unsigned long long* __restrict__ hashes) {
-    const int lane = threadIdx.x & 31;
     unsigned long long h[kMaxW];
 #pragma unroll
     for (int r = 0; r < kMaxW; ++r) h[r] = 0;
     const int nw = (int)gridDim.x * (kThreads / 32);
-    for (int pos = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); pos < m.n_long; pos += nw) {
-        const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
-        const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
-        double acc[W];
+    for (int pos = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); pos < m.n_long; pos += nw)
+        long_unit<W>(ptr, col, val, m, pos, X, Y, b.req, b.n_req, hashes, h);
+    if (hashes) flush_hash(b.req, b.n_req, h, hashes);
+}
+
+// ---------------------------------------------------------------- groups
+// A group: up to kGroupMax blocks, possibly of different matrices and
+// widths, run by one launch per kernel kind.  Block i's X sits at x_off
+// (doubles from the pool base), its Y right after (n x width each); its
+// slices are the group's units [unit0, next unit0), its long rows the long
+// units [long0, next long0).
+constexpr int kGroupMax = 64;
+
+struct GroupBlock {
+    BlockReq req[kMaxW];
+    long long x_off;
+    int n_req, width, m, n;
+    int unit0, long0, pad0, pad1;
+};
+
+__global__ void gen_group_kernel(double* __restrict__ pool, const GroupBlock* __restrict__ g) {
+    const GroupBlock& b = g[blockIdx.y];
+    gen_x(pool + b.x_off, b.n, b.width, b.req, b.n_req, (int)(blockIdx.x * blockDim.x + threadIdx.x),
+          (int)(gridDim.x * blockDim.x));
+}
+
+// Units [0, units) of a group, one warp per unit (grid-stride); LONG picks
+// the long-row units.  The unit's block is found by binary search over the
+// blocks' first units; each unit's hash terms are flushed before the next.
+template <bool LONG>
+__global__ void __launch_bounds__(kThreads) spmm_group_kernel(const BatchMat* __restrict__ mats,
+                                                              const int32_t* __restrict__ ptr,
+                                                              const int32_t* __restrict__ col,
+                                                              const double* __restrict__ val,
+                                                              double* __restrict__ pool,
+                                                              const GroupBlock* __restrict__ g, int nb, int units,
+                                                              unsigned long long* __restrict__ hashes) {
+    __shared__ int s_first[kGroupMax + 1];
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x) s_first[i] = i < nb ? (LONG ? g[i].long0 : g[i].unit0) : units;
+    __syncthreads();
+    unsigned long long h[kMaxW];
 #pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = 0.0;
-        for (int k = kb + lane; k < ke; k += 32) {
-            const double a = __ldg(val + k);
-            double xv[W];
-            load_row<W>(X + (int64_t)__ldg(col + k) * W, xv);
-#pragma unroll
-            for (int c = 0; c < W; ++c) acc[c] = fma(a, xv[c], acc[c]);
+    for (int r = 0; r < kMaxW; ++r) h[r] = 0;
+    const int nw = (int)gridDim.x * (kThreads / 32);
+    for (int u = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); u < units; u += nw) {
+        int lo = 0, hi = nb - 1;   // the last block whose first unit is <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= u) lo = mid;
+            else hi = mid - 1;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-        if (lane == 0) {
-#pragma unroll
-            for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
-            if (hashes) hash_row<W>(b, row, acc, h);
+        const GroupBlock& b = g[lo];
+        const BatchMat m = mats[b.m];
+        double* X = pool + b.x_off;
+        double* Y = X + (int64_t)b.n * b.width;
+        const int k = u - s_first[lo];
+        if (LONG) {
+            const int32_t* mp = ptr + m.ptr_off;
+            const int32_t* mc = col + m.ent_off;
+            const double* mv = val + m.ent_off;
+            switch (b.width) {
+                case 1: long_unit<1>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 2: long_unit<2>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 3: long_unit<3>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 4: long_unit<4>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 5: long_unit<5>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 6: long_unit<6>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 7: long_unit<7>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                default: long_unit<8>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+            }
+        } else {
+            switch (b.width) {
+                case 1: sliced_unit<1>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 2: sliced_unit<2>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 3: sliced_unit<3>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 4: sliced_unit<4>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 5: sliced_unit<5>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 6: sliced_unit<6>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 7: sliced_unit<7>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                default: sliced_unit<8>(m, k, X, Y, b.req, b.n_req, hashes, h); break;
+            }
         }
+        if (hashes) flush_hash(b.req, b.n_req, h, hashes);
     }
-    if (hashes) flush_hash(b, h, hashes);
 }
 
 cudaError_t launch_sliced(const BlockDesc& b, const int32_t* ptr, const int32_t* col, const double* val,
                           const BatchMat& M, const double* X, double* Y, int num_sms, unsigned long long* hashes,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t& launches) {
     constexpr int WPB = kThreads / 32;
+    launches += (M.n_slices > 0) + (M.n_long > 0);
     if (M.n_slices > 0) {
         const int grid = std::min((M.n_slices + WPB - 1) / WPB, num_sms * 8);
 #define SPMM_SL(w) spmm_sliced_kernel<w><<<grid, kThreads, 0, s>>>(M, X, Y, b, hashes)
@@ -476,6 +593,9 @@ struct spmv_server {
     std::vector<int> short_max;
     int32_t* bucket_rows = nullptr;
     std::vector<int64_t> mid_off, long_off;   // rows of bucket b of matrix m: [off[m], off[m+1])
+    int64_t launches = 0;                      // kernels launched since the last run began
+    // per stream slot: the group table on the device and its pinned staging
+    std::vector<GroupBlock*> d_group, h_group;
 };
 
 namespace {
@@ -491,6 +611,7 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     const BatchMat& M = bt->mats[m];
     const int n = M.n;
     if (n == 0) return cudaSuccess;
+    sv->launches += 2;   // X generator, product over the short rows (or the slices)
     int g = (int)std::min<int64_t>(((int64_t)n * b.width + kThreads - 1) / kThreads, (int64_t)sv->num_sms * 8);
     gen_x_kernel<<<g, kThreads, 0, s>>>(X, n, b);
     cudaError_t e = cudaGetLastError();
@@ -498,7 +619,10 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     const int32_t* ptr = bt->ptr + M.ptr_off;
     const int32_t* col = bt->col + M.ent_off;
     const double* val = bt->val + M.ent_off;
-    if (M.lanes == kBatchSliced) return launch_sliced(b, ptr, col, val, M, X, Y, sv->num_sms, hashes, s);
+    if (M.lanes == kBatchSliced) {
+        sv->launches -= 1;
+        return launch_sliced(b, ptr, col, val, M, X, Y, sv->num_sms, hashes, s, sv->launches);
+    }
     const int V = sv->lanes[m];
     int grid = (int)std::min<int64_t>((n + (kThreads / V) - 1) / (kThreads / V), (int64_t)sv->num_sms * 8);
     const int smax = sv->short_max[m];
@@ -510,6 +634,8 @@ cudaError_t launch_block(spmv_server* sv, int m, const BlockDesc& b, double* X, 
     }
     if (e != cudaSuccess) return e;
     const int nm = (int)(sv->mid_off[m + 1] - sv->mid_off[m]);
+    const int nl_ = (int)(sv->long_off[m + 1] - sv->long_off[m]);
+    sv->launches += (nm > 0) + (nl_ > 0);
     if (nm > 0)
         e = launch_list_w<8>(b, ptr, col, val, X, Y, sv->bucket_rows + sv->mid_off[m], nm, sv->num_sms,
                              hashes, s);
@@ -607,9 +733,15 @@ int spmv_serve_create(spmv_batch* mats, int n_streams, int64_t budget_bytes, spm
     sv->pool.init(sv->pool_base, sv->pool_bytes);
     sv->streams.resize(n_streams);
     sv->events.resize(n_streams);
+    sv->d_group.assign(n_streams, nullptr);
+    sv->h_group.assign(n_streams, nullptr);
     for (int i = 0; i < n_streams; ++i) {
         spmvk::check_cuda(cudaStreamCreateWithFlags(&sv->streams[i], cudaStreamNonBlocking), "stream");
         spmvk::check_cuda(cudaEventCreateWithFlags(&sv->events[i], cudaEventDisableTiming), "event");
+        spmvk::check_cuda(cudaMalloc(reinterpret_cast<void**>(&sv->d_group[i]), kGroupMax * sizeof(GroupBlock)),
+                          "group table");
+        spmvk::check_cuda(cudaMallocHost(reinterpret_cast<void**>(&sv->h_group[i]), kGroupMax * sizeof(GroupBlock)),
+                          "group staging");
     }
     *out = sv;
     sv = nullptr;
@@ -633,9 +765,19 @@ int spmv_serve_destroy(spmv_server* sv) {
     for (auto e : sv->events)
         if (e) cudaEventDestroy(e);
     if (sv->pool_base) cudaFree(sv->pool_base);
+    for (auto p : sv->d_group)
+        if (p) cudaFree(p);
+    for (auto p : sv->h_group)
+        if (p) cudaFreeHost(p);
     if (sv->d_hash) cudaFree(sv->d_hash);
     if (sv->bucket_rows) cudaFree(sv->bucket_rows);
     delete sv;
+    return SPMV_OK;
+}
+
+int spmv_serve_launches(const spmv_server* sv, int64_t* out) {
+    if (!sv || !out) return sfail(SPMV_EINVAL, "NULL argument");
+    *out = sv->launches;
     return SPMV_OK;
 }
 
@@ -664,6 +806,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
         spmvk::fail(SPMV_EINVAL, "request arrays are NULL");
     if (mode != SPMV_SERVE_BATCHED && mode != SPMV_SERVE_PLAIN) spmvk::fail(SPMV_EINVAL, "mode %d", mode);
     const int M = sv->mats->count;
+    sv->launches = 0;
     for (int64_t r = 0; r < n_req; ++r) {
         if (matrix[r] < 0 || matrix[r] >= M) spmvk::fail(SPMV_EINVAL, "request %lld: matrix %d", (long long)r, matrix[r]);
         if (width[r] < 1 || width[r] > kMaxW) spmvk::fail(SPMV_EINVAL, "request %lld: width %d", (long long)r, width[r]);
@@ -684,9 +827,13 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
     struct Inflight {
         bool busy = false;
         std::vector<int64_t> reqs;
-        long long off = -1;
-        size_t bytes = 0;
+        std::vector<std::pair<long long, size_t>> allocs;   // pool blocks (offset, bytes)
     };
+    // grouped launches when every matrix is in the sliced layout: each free
+    // slot takes up to kGroupMax blocks (round robin over the matrices) and
+    // runs them with one launch per kernel kind
+    bool grouped = mode == SPMV_SERVE_BATCHED;
+    for (int m = 0; m < M; ++m) grouped = grouped && sv->mats->mats[m].lanes == kBatchSliced;
     std::vector<Inflight> slot(sv->n_streams);
     std::vector<std::deque<int64_t>> pending(M);
     int64_t next = 0, done = 0, blocks = 0, waits_mem = 0, max_inflight = 0, admitted_while_busy = 0;
@@ -725,14 +872,96 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
             const double t = now_s();
             for (int64_t r : sl.reqs) latency_s[r] = t - arrival_s[r];
             done += (int64_t)sl.reqs.size();
-            sv->pool.release(sl.off, sl.bytes);
+            for (auto& a : sl.allocs) sv->pool.release(a.first, a.second);
             sl.busy = false;
             sl.reqs.clear();
+            sl.allocs.clear();
         }
-        // launches: one block per free slot, matrices taken round robin
+        // launches: one block (or one group of blocks) per free slot,
+        // matrices taken round robin
         if (queued > 0) {
             for (int i = 0; i < sv->n_streams && queued > 0; ++i) {
                 if (slot[i].busy) continue;
+                if (grouped) {
+                    GroupBlock* hg = sv->h_group[i];
+                    int nb = 0, units = 0, longs = 0, max_elems = 0;
+                    bool out_of_memory = false;
+                    while (nb < kGroupMax && queued > 0 && !out_of_memory) {
+                        int m = -1;
+                        for (int k = 0; k < M; ++k) {
+                            const int c = (rr + k) % M;
+                            if (!pending[c].empty()) {
+                                m = c;
+                                break;
+                            }
+                        }
+                        if (m < 0) break;
+                        rr = (m + 1) % M;
+                        const BatchMat& Mm = sv->mats->mats[m];
+                        auto& q = pending[m];
+                        int take = 0, wsum = 0;
+                        while (take < (int)q.size() && take < kMaxW && wsum + width[q[take]] <= kMaxW)
+                            wsum += width[q[take++]];
+                        const size_t bytes = (size_t)2 * Mm.n * wsum * sizeof(double);
+                        const long long off = sv->pool.alloc(bytes);
+                        if (off < 0) {
+                            ++waits_mem;
+                            out_of_memory = true;
+                            break;
+                        }
+                        GroupBlock& gb = hg[nb++];
+                        gb = GroupBlock{};
+                        for (int t = 0, colx = 0; t < take; ++t) {
+                            const int64_t r = q.front();
+                            gb.req[gb.n_req++] = BlockReq{seed[r], colx, width[r], (int)r, 0};
+                            colx += width[r];
+                            slot[i].reqs.push_back(r);
+                            q.pop_front();
+                        }
+                        gb.x_off = off / (long long)sizeof(double);
+                        gb.width = wsum;
+                        gb.m = m;
+                        gb.n = Mm.n;
+                        gb.unit0 = units;
+                        gb.long0 = longs;
+                        units += Mm.n_slices;
+                        longs += Mm.n_long;
+                        max_elems = std::max(max_elems, Mm.n * wsum);
+                        queued -= take;
+                        slot[i].allocs.emplace_back(off, bytes);
+                        ++blocks;
+                    }
+                    if (nb == 0) break;   // no memory: wait for completions
+                    cudaStream_t st = sv->streams[i];
+                    spmvk::check_cuda(cudaMemcpyAsync(sv->d_group[i], hg, (size_t)nb * sizeof(GroupBlock),
+                                                      cudaMemcpyHostToDevice, st),
+                                      "group table");
+                    double* pool = reinterpret_cast<double*>(sv->pool_base);
+                    unsigned long long* hs = hash_out ? sv->d_hash : nullptr;
+                    const spmv_batch* bt = sv->mats;
+                    if (max_elems > 0) {
+                        const int gx = std::max(1, std::min((max_elems + kThreads - 1) / kThreads, sv->num_sms * 2));
+                        gen_group_kernel<<<dim3(gx, nb), kThreads, 0, st>>>(pool, sv->d_group[i]);
+                        ++sv->launches;
+                    }
+                    if (units > 0) {
+                        const int gs = std::min((units + 7) / 8, sv->num_sms * 8);
+                        spmm_group_kernel<false><<<gs, kThreads, 0, st>>>(bt->d_mats, bt->ptr, bt->col, bt->val, pool,
+                                                                         sv->d_group[i], nb, units, hs);
+                        ++sv->launches;
+                    }
+                    if (longs > 0) {
+                        const int gl = std::min((longs + 7) / 8, sv->num_sms * 8);
+                        spmm_group_kernel<true><<<gl, kThreads, 0, st>>>(bt->d_mats, bt->ptr, bt->col, bt->val, pool,
+                                                                        sv->d_group[i], nb, longs, hs);
+                        ++sv->launches;
+                    }
+                    spmvk::check_cuda(cudaGetLastError(), "group launch");
+                    spmvk::check_cuda(cudaEventRecord(sv->events[i], st), "event");
+                    slot[i].busy = true;
+                    if (out_of_memory) break;
+                    continue;
+                }
                 int m = -1;
                 for (int k = 0; k < M; ++k) {
                     const int c = (rr + k) % M;
@@ -779,8 +1008,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                 spmvk::check_cuda(cudaEventRecord(sv->events[i], sv->streams[i]), "event");
                 slot[i].busy = true;
                 slot[i].reqs = std::move(reqs);
-                slot[i].off = off;
-                slot[i].bytes = bytes;
+                slot[i].allocs.emplace_back(off, bytes);
                 ++blocks;
             }
         }

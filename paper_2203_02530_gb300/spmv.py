@@ -89,6 +89,7 @@ def _load():
         "spmv_serve_destroy": [vp],
         "spmv_serve_run": [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp],
         "spmv_serve_single": [vp, i32, i32, ctypes.c_uint64, vp, vp, vp],
+        "spmv_serve_launches": [vp, P64],
         "spmv_selftest_wait_timeout": [i64, P64],
         "spmv_last_error": [],
     }
@@ -383,6 +384,12 @@ def spmv_serve_run(h, matrix, width, seed, arrival_s, mode=SERVE_BATCHED, want_h
     keys = ["blocks", "max_inflight", "waits_for_memory", "peak_pool_bytes", "elapsed_ns",
             "admitted_while_busy"]
     return lat, hs, dict(zip(keys, (int(v) for v in st)))
+
+
+def spmv_serve_launches(h):
+    out = ctypes.c_int64()
+    _check(lib.spmv_serve_launches(h, ctypes.byref(out)))
+    return out.value
 
 
 def spmv_serve_single(h, matrix, width, seed, y_dev, x_dev, stream):

@@ -242,6 +242,60 @@ def test_sliced_layout_matches_thread_per_row_bit_for_bit(name):
     assert np.array_equal(out[0].view(np.uint64), out[2].view(np.uint64))
 
 
+def _lengths_matrix(lens, seed):
+    """Rows of the given lengths with distinct random columns."""
+    rng = np.random.default_rng(seed)
+    n = len(lens)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    ci = np.concatenate([np.sort(rng.choice(n, size=k, replace=False)) for k in lens]).astype(np.int32) \
+        if rp[-1] else np.zeros(0, np.int32)
+    return n, rp, ci, rng.uniform(-1, 1, size=ci.size)
+
+
+@pytest.mark.parametrize("lens_kind", ["all_long", "edge_64_65", "long_and_empty", "one_long_in_natural"])
+@pytest.mark.parametrize("gran", [0, 1])
+def test_sliced_layout_edge_cases(lens_kind, gran):
+    """Rows at and around the 64-entry long-row threshold, ranks made of long
+    rows only, empty rows among long ones, and a single long row inside a
+    natural-order rank (a hole in its slice), coarse and per rank."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    rng = np.random.default_rng(31)
+    n = 700
+    if lens_kind == "all_long":
+        lens = rng.integers(65, 300, size=n)
+    elif lens_kind == "edge_64_65":
+        lens = rng.choice([63, 64, 65, 66], size=n)
+    elif lens_kind == "long_and_empty":
+        lens = np.where(rng.random(n) < 0.5, 0, rng.integers(65, 200, size=n))
+    else:
+        lens = np.full(n, 9)
+        lens[333] = 500
+    n, rp, ci, va = _lengths_matrix(lens, 32)
+    x = W.uniform_x(n, seed=33)
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    P = 3
+    with make_part(n, rp, ci, va, P, gran) as part:
+        set_variant(part, ("sell", 4))
+        if gran == 0:
+            run_default(part, x_d, y_d, s)
+        else:
+            for p in range(P):
+                spmv.spmv_pack(part.h, p, x_d, s)
+            for p in range(P):
+                spmv.spmv_local(part.h, p, x_d, y_d, s)
+                spmv.spmv_halo_copy(part.h, p, s)
+            for p in reversed(range(P)):
+                spmv.spmv_remote(part.h, p, y_d, s)
+        s.synchronize()
+        assert_fp64_close(y_d.cpu().numpy(), want, scale, "sliced %s gran %d" % (lens_kind, gran))
+        assert part.query(spmv.Q_ERROR) == 0
+
+
 @pytest.mark.parametrize("name", ["st27_ragged", "powerlaw", "dense_row"])
 def test_local_and_remote_variants_chosen_separately(name):
     from paper_2203_02530_gb300 import spmv
@@ -325,7 +379,8 @@ def _random_schedule(dag, n_streams, rng):
 
 
 @pytest.mark.parametrize("name,variant", [("st27_ragged", ("tile", 0)), ("powerlaw", ("merge", 0)),
-                                          ("powerlaw", ("tile", 2)), ("band", ("vector", 4))])
+                                          ("powerlaw", ("tile", 2)), ("band", ("vector", 4)),
+                                          ("powerlaw", ("sell", 4)), ("dense_row", ("sell", 9))])
 def test_per_partition_schedules_give_identical_y(name, variant):
     from paper_2203_02530_gb300 import spmv
     from paper_2203_02530_gb300 import schedules as E

@@ -95,12 +95,15 @@ def test_results_same_alone_and_in_the_mix_and_match_oracle(layout):
                     assert_fp64_close(Y[:, j], want, scale, "request %d column %d" % (r, j))
 
 
-def test_small_budget_makes_blocks_wait_but_completes():
+@pytest.mark.parametrize("layout", ["buckets", "sliced"])
+def test_small_budget_makes_blocks_wait_but_completes(layout):
     from paper_2203_02530_gb300 import spmv
     torch_cuda()
     mats = _mats()
     mat, wid, sd, arr = _requests(200, len(mats), 12, 0.0)
     with spmv.Batch(mats) as b:
+        if layout == "sliced":
+            spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
         nmax = max(m[0] for m in mats)
         resident = b.query(spmv.BQ_DEVICE_BYTES)
         budget = resident + 128 * nmax + 4096      # room for one width-8 block of the largest
