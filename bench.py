@@ -200,6 +200,25 @@ def oracle_rate(n, rp, ci, va, x, P, seconds):
     return alg * reps / t / 1e9, reps, t, alg
 
 
+def oracle_parallel_rate(n, rp, ci, va, x, seconds):
+    """The oracle's plain product (the definition, unpartitioned) with its
+    rows shared among all host threads, timed for about `seconds`."""
+    import oracle
+    nnz = int(rp[-1] - rp[0])
+    alg = 12 * nnz + 4 * (n + 1) + 16 * n
+    oracle.csr_spmv_rows_parallel(n, rp, ci, va, x)   # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.csr_spmv_rows_parallel(n, rp, ci, va, x)
+        reps += 1
+        t = time.perf_counter() - t0
+        if t >= seconds:
+            break
+    return {"value": round(alg * reps / t / 1e9, 3), "unit": "GB/s", "cores": oracle.max_threads(),
+            "kind": "oracle", "sample": "%d plain CSR products (rows split over OpenMP threads) of the same "
+                                        "matrix in %.1f s" % (reps, t)}
+
+
 def cpu_alg_bytes(n, nnz_l, nnz_r, n_rr, n_send):
     # the same counting as the library: local entries, row pointers, x, y;
     # remote entries, its compressed rows and y update; pack, exchange, halo
@@ -337,8 +356,9 @@ def run_ours(args, world, rank, local):
     achieved = alg_local / t_local / 1e9
     kname = {spmv.VARIANT_TILE: "csr_tile_kernel", spmv.VARIANT_VECTOR: "csr_vector_kernel",
              spmv.VARIANT_MERGE: "merge_kernel", spmv.VARIANT_PAIRS: "csr_pair_kernel",
-             spmv.VARIANT_WARP: "csr_warp_kernel", spmv.VARIANT_SELL: "csr_sell_kernel"}[variant]
-    traffic = profiled_traffic("%s/%d" % (kname, vparam))
+             spmv.VARIANT_WARP: "csr_warp_kernel", spmv.VARIANT_SELL: "csr_sell_kernel",
+             spmv.VARIANT_SELL16: "csr_sell_kernel"}[variant]
+    traffic = profiled_traffic("%s/%d/%d" % (kname, variant, vparam))
 
     # paper protocol: per-measurement latency percentiles of the best schedule
     meas = benchmark.measurements(step, streams[0], args.measurements)
@@ -364,6 +384,7 @@ def run_ours(args, world, rank, local):
                "sample": "%d full partitioned SpMVs of the same matrix (P=%d) in %.1f s, "
                          "single-threaded C oracle on the host cores (nproc=%d)" % (
                              reps, P, secs, os.cpu_count() or 0)}
+        cpu["all_cores"] = oracle_parallel_rate(n, rp, ci, va, x, args.cpu_seconds / 2)
     part.close()
     if rank != 0:
         return None
@@ -385,10 +406,15 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "alg_bytes_per_step": alg},
         "percent_hbm": round(100.0 * value / world / peak, 2),
-        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_local, "launch_us": round(t_local * 1e6, 2)},
+        "roofline": dict({"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
+                          "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                          "traffic": traffic, "peak_kind": peak_kind,
+                          "alg_bytes_per_launch": alg_local, "launch_us": round(t_local * 1e6, 2)},
+                         **({} if traffic is None else {
+                             "dram_gbs": round(traffic / t_local / 1e9, 1),
+                             "dram_frac": round(traffic / t_local / 1e9 / peak, 4),
+                             "note": "achieved counts the CSR algorithmic bytes; the DRAM traffic of "
+                                     "the launch (ncu) is `traffic`"})),
         "fp64": {"dfma_per_s": round(nnz_l / t_local / 1e9, 1), "unit": "G DFMA/s",
                  "peak": round(fp64_peak / 1e9, 1), "frac": round(nnz_l / t_local / fp64_peak, 4),
                  "note": "2 DFMA/clk/SM at the sampled SM clock"},
@@ -576,9 +602,12 @@ def run_serving(args, world, rank, local):
     # saturation: every request present at t = 0 (the most either form can do)
     nsat = min(count, args.serve_saturation)
     sat = {}
+    req_flops = 2.0 * zz[mat] * wid
     for name, mode in (("served", spmv.SERVE_BATCHED), ("plain", spmv.SERVE_PLAIN)):
         lat, _, st = sv.run(mat[:nsat], wid[:nsat], sd[:nsat], np.zeros(nsat), mode, want_hash=False)
         el = st["elapsed_ns"] * 1e-9
+        if name == "served":
+            sat_flops = req_flops[:nsat].sum() / el
         sat[name] = {"throughput_req_s": round(nsat / el, 1),
                      "gbs": round(req_bytes[:nsat].sum() / el / 1e9, 2), "blocks": st["blocks"],
                      "launches": spmv.spmv_serve_launches(sv.h)}
@@ -603,6 +632,7 @@ def run_serving(args, world, rank, local):
     total = int(sum(zz) * 12 + sum(nn) * 4)
     b.close()
     peak, peak_kind = hbm_peak()
+    fp64_peak = 2.0 * torch.cuda.get_device_properties(local).multi_processor_count * 2070.0e6   # DFMA/s
     value = sat["served"]["gbs"]
     return {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
@@ -620,11 +650,15 @@ def run_serving(args, world, rank, local):
         "results_identical_served_vs_plain": same,
         "latency_us": {"p50": out["served"]["p50_us"], "p99": out["served"]["p99_us"],
                        "protocol": "arrival to observed completion, open loop"},
-        "roofline": {"bound": "hbm",
-                     "kernel": "spmm_sliced_kernel" if args.serve_layout == "sliced" else "spmm_kernel",
-                     "achieved": value, "peak": peak,
-                     "unit": "GB/s", "frac": round(value / peak, 4), "traffic": None,
-                     "peak_kind": peak_kind, "note": "per-request algorithmic bytes at saturation"},
+        "roofline": {"bound": "alu",
+                     "kernel": "spmm_group_kernel" if args.serve_layout == "sliced" else "spmm_kernel",
+                     "achieved": round(sat_flops / 1e12, 4), "peak": round(fp64_peak * 2 / 1e12, 4),
+                     "unit": "TFLOP/s", "frac": round(sat_flops / (fp64_peak * 2), 4), "traffic": None,
+                     "peak_kind": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs at the maximum SM clock",
+                     "note": "2 flops per entry per right-hand side, over the saturation run's elapsed time "
+                             "(all launches and the gaps between them)"},
+        "hbm_fraction": {"achieved": value, "peak": peak, "unit": "GB/s", "frac": round(value / peak, 4),
+                         "peak_kind": peak_kind, "note": "per-request algorithmic bytes at saturation"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
                 "note": "inputs are drawn on the device from each request's seed; the host reads "
                         "one 8-byte hash per request"},

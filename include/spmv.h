@@ -171,6 +171,12 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *          row, one FMA per stored entry in storage order (padded slots
  *          discarded), so y equals WARP's bit for bit on matrices without
  *          long rows.  SPMV_EBOUNDS beyond 2^31 padded entries.
+ *   SELL16 the SELL layout of the LOCAL product with each slot's column
+ *          stored as a 16-bit delta to its row (x index = row + delta):
+ *          10 instead of 12 bytes per slot.  LOCAL only, through
+ *          spmv_part_set_op_variant; SPMV_EINVAL (nothing changed) when a
+ *          local column lies more than 32767 rows from its row, or for the
+ *          REMOTE product.  Same y as SELL, bit for bit.
  * Fails with SPMV_EINVAL while captured graphs exist (they hold the old
  * kernels' tables). */
 enum {
@@ -179,7 +185,8 @@ enum {
     SPMV_VARIANT_MERGE = 2,
     SPMV_VARIANT_PAIRS = 3,
     SPMV_VARIANT_WARP = 4,
-    SPMV_VARIANT_SELL = 5
+    SPMV_VARIANT_SELL = 5,
+    SPMV_VARIANT_SELL16 = 6
 };
 /* Sets the variant of both products. */
 int spmv_part_set_variant(spmv_part* part, int variant, int param);

@@ -43,6 +43,8 @@ def lib():
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         L.orc_csr_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
         L.orc_csr_absdot.argtypes = [i64, vp, vp, vp, vp, vp]
+        L.orc_csr_spmv_rows_parallel.argtypes = [i64, vp, vp, vp, vp, vp, i32]
+        L.orc_max_threads.argtypes = []
         L.orc_plan_create.argtypes = [i64, vp, vp, vp, i32, ctypes.POINTER(vp)]
         L.orc_plan_destroy.argtypes = [vp]
         L.orc_plan_destroy.restype = None
@@ -79,6 +81,23 @@ def csr_spmv(n, row_ptr, col_idx, vals, x):
     if rc:
         raise ValueError("orc_csr_spmv failed: %d" % rc)
     return y
+
+
+def csr_spmv_rows_parallel(n, row_ptr, col_idx, vals, x, threads=0):
+    """csr_spmv with the rows shared among host threads (same result bit for
+    bit); for timing the oracle on every core."""
+    rp, ci, va = _csr(row_ptr, col_idx, vals)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(n, dtype=np.float64)
+    rc = lib().orc_csr_spmv_rows_parallel(n, _p(rp), _p(ci), _p(va), _p(x), _p(y), int(threads))
+    if rc:
+        raise ValueError("orc_csr_spmv_rows_parallel failed: %d" % rc)
+    return y
+
+
+def max_threads():
+    """Threads the parallel product uses by default (1 without OpenMP)."""
+    return int(lib().orc_max_threads())
 
 
 def csr_absdot(n, row_ptr, col_idx, vals, x):

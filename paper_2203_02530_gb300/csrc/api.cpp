@@ -149,14 +149,14 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
                    "warp product");
         return we > wb;
     }
-    if (var == SPMV_VARIANT_SELL) {
+    if (var == SPMV_VARIANT_SELL || var == SPMV_VARIANT_SELL16) {
         const spmv_part::SellPart& sp = pt->sell[remote ? 1 : 0];
-        spmvk::SellArgs sa{sp.slices, sp.longs, sp.val, sp.col, sp.len, sp.perm, 0, 0, 0, 0};
+        spmvk::SellArgs sa{sp.slices, sp.longs, sp.val, sp.col, sp.col16, sp.len, sp.perm, 0, 0, 0, 0};
         sa.slice_begin = (int)(p < 0 ? 0 : sp.slice_off[p]);
         sa.slice_end = (int)(p < 0 ? sp.slice_off[pt->P] : sp.slice_off[p + 1]);
         sa.long_begin = (int)(p < 0 ? 0 : sp.long_off[p]);
         sa.long_end = (int)(p < 0 ? sp.long_off[pt->P] : sp.long_off[p + 1]);
-        check_cuda(spmvk::launch_sell(a, sa, param, pt->num_sms, s), "sliced product");
+        check_cuda(spmvk::launch_sell(a, sa, param, var == SPMV_VARIANT_SELL16, pt->num_sms, s), "sliced product");
         return (sa.slice_end > sa.slice_begin || sa.long_end > sa.long_begin) ? 1 : 0;
     }
     const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
@@ -520,7 +520,7 @@ int spmv_part_dag(const spmv_part* pt, int32_t* edges, int64_t cap_pairs, int64_
 }
 
 // Validates (variant, param) and prepares the tables it needs.
-static void prepare_variant(spmv_part* pt, int variant, int param) {
+static void prepare_variant(spmv_part* pt, int variant, int param, int op_kind) {
     if (!pt->graphs.empty()) fail(SPMV_EINVAL, "destroy the captured graphs before changing the variant");
     if (variant == SPMV_VARIANT_TILE) {
         static const spmvk::TileGeom geoms[] = {{256, 3456, 2, 16, 2},
@@ -550,10 +550,14 @@ static void prepare_variant(spmv_part* pt, int variant, int param) {
     } else if (variant == SPMV_VARIANT_MERGE) {
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
-    } else if (variant == SPMV_VARIANT_SELL) {
+    } else if (variant == SPMV_VARIANT_SELL || variant == SPMV_VARIANT_SELL16) {
         if (!spmvk::sell_param_supported(param)) fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104}", param);
+        if (variant == SPMV_VARIANT_SELL16 && op_kind != SPMV_OP_LOCAL)
+            fail(SPMV_EINVAL, "16-bit column deltas serve the LOCAL product only");
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->sell_built) spmvk::build_sell(pt);
+        if (variant == SPMV_VARIANT_SELL16 && !spmvk::build_sell_delta16(pt))
+            fail(SPMV_EINVAL, "a LOCAL column lies more than 32767 rows from its row: no 16-bit deltas");
     } else {
         fail(SPMV_EINVAL, "unknown variant %d", variant);
     }
@@ -562,7 +566,9 @@ static void prepare_variant(spmv_part* pt, int variant, int param) {
 int spmv_part_set_variant(spmv_part* pt, int variant, int param) {
     API_TRY
     check_part(pt);
-    prepare_variant(pt, variant, param);
+    if (variant == SPMV_VARIANT_SELL16)
+        fail(SPMV_EINVAL, "16-bit column deltas serve the LOCAL product only: use spmv_part_set_op_variant");
+    prepare_variant(pt, variant, param, -1);
     pt->variant[0] = pt->variant[1] = variant;
     pt->vparam[0] = pt->vparam[1] = param;
     API_CATCH
@@ -574,7 +580,7 @@ int spmv_part_set_op_variant(spmv_part* pt, int op_kind, int variant, int param)
     check_part(pt);
     if (op_kind != SPMV_OP_LOCAL && op_kind != SPMV_OP_REMOTE)
         fail(SPMV_EINVAL, "op kind %d has no product variant", op_kind);
-    prepare_variant(pt, variant, param);
+    prepare_variant(pt, variant, param, op_kind);
     const int i = op_kind == SPMV_OP_REMOTE ? 1 : 0;
     pt->variant[i] = variant;
     pt->vparam[i] = param;

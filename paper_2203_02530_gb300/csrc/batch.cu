@@ -255,10 +255,16 @@ __device__ __forceinline__ void batch_slices(const BatchArgs& a, const BatchMat&
     const int lane = threadIdx.x & 31;
     const double* x = a.x + m.row_off;
     double* y = a.y + m.row_off;
+    // the item's slice descriptors (at most 32), one per lane, loaded at once
+    const BSlice mine = s0 + lane < s1 ? m.s_slices[s0 + lane] : BSlice{0, 0, 0, 0};
+    auto desc = [&](int i) {
+        return BSlice{__shfl_sync(0xffffffffu, mine.pos0, i), __shfl_sync(0xffffffffu, mine.rows, i),
+                      __shfl_sync(0xffffffffu, mine.len, i), __shfl_sync(0xffffffffu, mine.off, i)};
+    };
     for (int si = s0; si < s1; si += 2) {
         const bool two = si + 1 < s1;
-        const BSlice d0 = m.s_slices[si];
-        const BSlice d1 = two ? m.s_slices[si + 1] : BSlice{0, 0, 0, 0};
+        const BSlice d0 = desc(si - s0);
+        const BSlice d1 = two ? desc(si + 1 - s0) : BSlice{0, 0, 0, 0};
         const int len0 = lane < d0.rows ? (int)m.s_len[d0.pos0 + lane] : 0;
         const int len1 = lane < d1.rows ? (int)m.s_len[d1.pos0 + lane] : 0;
         const double* vp0 = m.s_val + (int64_t)d0.off + lane;
@@ -320,7 +326,7 @@ __device__ __forceinline__ void batch_long(const BatchArgs& a, const BatchMat& m
 __device__ __forceinline__ void batch_item(const BatchArgs& a, int it, uint64_t pol, double* sv,
                                            int32_t* sc) {
     const BatchItem w = a.items[it];
-    const BatchMat m = a.mats[w.m];
+    const BatchMat& m = a.mats[w.m];   // fields read where used
     switch (m.lanes) {
         case 0: batch_rows_staged(a, m, w.a, w.b, pol, sv, sc); break;
         case 1: batch_rows<1>(a, m, w.a, w.b, pol); break;
@@ -335,7 +341,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, int it, uint64_t 
 // Items of the sliced layout (kinds 1 and 2).
 __device__ __forceinline__ void batch_item_sliced(const BatchArgs& a, int it, uint64_t pol) {
     const BatchItem w = a.items[it];
-    const BatchMat m = a.mats[w.m];
+    const BatchMat& m = a.mats[w.m];   // fields read where used
     if (w.kind == 1)
         batch_long(a, m, w.a, w.b, pol);
     else
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_persistent_kernel(BatchArgs
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) batch_sliced_persistent_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) batch_sliced_persistent_kernel(BatchArgs a) {
     const uint64_t pol = policy_evict_last();
     for (;;) {
         int t = 0;
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_range_kernel(BatchArgs a, i
         batch_item(a, it, pol, s_val[w], s_col[w]);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) batch_sliced_range_kernel(BatchArgs a, int first, int last) {
+__global__ void __launch_bounds__(kThreads, 5) batch_sliced_range_kernel(BatchArgs a, int first, int last) {
     const uint64_t pol = policy_evict_last();
     const int nw = (int)gridDim.x * (kThreads / 32);
     for (int it = first + (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); it < last; it += nw)

@@ -70,6 +70,7 @@ struct SellArgs {
     const SellLong* longs;
     const double* val;
     const int32_t* col;
+    const int16_t* col16;    // column - row deltas (16-bit variant), or nullptr
     const uint8_t* len;      // per position: entries, or kSellLenLong
     const int32_t* perm;     // per position: row; nullptr = position is the row
     int slice_begin, slice_end, long_begin, long_end;
@@ -116,7 +117,10 @@ cudaError_t launch_merge_noalloc(const CsrArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const double* val, const SellSlice* slices,
                              int n_slices, const uint8_t* len, const int32_t* perm, double* sval, int32_t* scol,
                              int num_sms, cudaStream_t s);
-cudaError_t launch_sell(const CsrArgs& a, const SellArgs& s, int param, int num_sms, cudaStream_t st);
+cudaError_t launch_sell(const CsrArgs& a, const SellArgs& s, int param, bool delta16, int num_sms,
+                        cudaStream_t st);
+cudaError_t launch_sell_delta(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
+                              const int32_t* scol, int16_t* scol16, int* bad, int num_sms, cudaStream_t s);
 bool sell_param_supported(int param);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);

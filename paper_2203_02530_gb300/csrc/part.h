@@ -111,6 +111,9 @@ struct spmv_part {
         int32_t* col = nullptr;
         uint8_t* len = nullptr;
         int32_t* perm = nullptr;          // nullptr: every rank in natural order
+        int16_t* col16 = nullptr;         // column - row deltas (LOCAL only), once built
+        int delta_state = 0;              // 0 not checked, 1 built, -1 some delta needs > 16 bits
+        int64_t entries = 0;              // padded slots
         std::vector<int64_t> slice_off;   // P+1
         std::vector<int64_t> long_off;    // P+1
         std::vector<char> sorted;         // per rank
@@ -147,6 +150,7 @@ void build_tiles(spmv_part* pt, const TileGeom& g);
 void build_merge_tiles(spmv_part* pt);
 void build_warp_tiles(spmv_part* pt, int cap);
 void build_sell(spmv_part* pt);
+bool build_sell_delta16(spmv_part* pt);
 void* dev_alloc(spmv_part* pt, size_t bytes);
 void free_plan(spmv_part* pt);
 }  // namespace spmvk

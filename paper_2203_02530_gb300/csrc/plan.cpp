@@ -454,11 +454,34 @@ void build_sell(spmv_part* pt) {
     const std::vector<int32_t> rr_ptr = download(pt->rr_ptr, (size_t)pt->n_rr + 1);
     std::vector<int32_t> lxo(P), rxo(P, 0);
     for (int p = 0; p < P; ++p) lxo[p] = (int32_t)pt->bounds[p];
-    int64_t e = build_sell_part(pt, pt->sell[0], l_ptr, pt->bounds, lxo, pt->l_ptr, pt->l_col, pt->l_val);
-    e += build_sell_part(pt, pt->sell[1], rr_ptr, pt->rr_off, rxo, pt->rr_ptr, pt->r_col, pt->r_val);
+    pt->sell[0].entries = build_sell_part(pt, pt->sell[0], l_ptr, pt->bounds, lxo, pt->l_ptr, pt->l_col, pt->l_val);
+    pt->sell[1].entries = build_sell_part(pt, pt->sell[1], rr_ptr, pt->rr_off, rxo, pt->rr_ptr, pt->r_col, pt->r_val);
     check_cuda(cudaDeviceSynchronize(), "sliced layout");
-    pt->sell_entries = e;
+    pt->sell_entries = pt->sell[0].entries + pt->sell[1].entries;
     pt->sell_built = true;
+}
+
+// 16-bit column deltas of the LOCAL sliced layout (built on first use);
+// false when some |column - row| needs more than 16 bits.
+bool build_sell_delta16(spmv_part* pt) {
+    spmv_part::SellPart& sp = pt->sell[0];
+    if (sp.delta_state != 0) return sp.delta_state > 0;
+    int16_t* c16 = static_cast<int16_t*>(dev_alloc(pt, (size_t)sp.entries * 2));
+    int* bad = static_cast<int*>(dev_alloc(pt, sizeof(int)));
+    const int n_slices = (int)sp.slice_off[pt->P];
+    check_cuda(launch_sell_delta(sp.slices, n_slices, sp.len, sp.perm, sp.col, c16, bad, pt->num_sms, 0),
+               "column deltas");
+    int h = 0;
+    check_cuda(cudaMemcpy(&h, bad, sizeof(int), cudaMemcpyDeviceToHost), "column deltas");
+    free_one(pt, bad);
+    if (h) {
+        free_one(pt, c16);
+        sp.delta_state = -1;
+        return false;
+    }
+    sp.col16 = c16;
+    sp.delta_state = 1;
+    return true;
 }
 
 }  // namespace spmvk

@@ -47,6 +47,11 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+__device__ __forceinline__ int32_t ld_stream(const int16_t* p, uint64_t pol) {
+    int32_t v;   // sign-extended
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s16 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
 // Gathered x, reused across rows: keep in L2.
 __device__ __forceinline__ double ld_keep(const double* p, uint64_t pol) {
     double v;
@@ -71,8 +76,12 @@ __device__ __forceinline__ void sell_store(const CsrArgs& a, int row, double sum
 // per row, U entries per lane per step: U value and U column loads, then U
 // x gathers, then U FMAs, so each lane keeps U gathers in flight).  Long
 // rows come first so that the heaviest units start in the first wave.
-template <int U, int MINB>
+// CT = int32_t: slot columns are the CSR's (x index = xoff + column);
+// CT = int16_t: slot columns are deltas to the row (x index = row + delta),
+// half the index bytes where every |column - row| fits in 16 bits.
+template <int U, int MINB, typename CT>
 __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs sa) {
+    constexpr bool kDelta = sizeof(CT) == 2;
     const uint64_t pol_stream = sell_policy_evict_first();
     const uint64_t pol_keep = sell_policy_evict_last();
     const int lane = threadIdx.x & 31;
@@ -114,8 +123,11 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
             len = store ? code : 0;
         }
         const double* vp = sa.val + (int64_t)d.off + lane;
-        const int32_t* cp = sa.col + (int64_t)d.off + lane;
-        const double* xb = a.x + d.xoff;
+        const CT* cp = (kDelta ? reinterpret_cast<const CT*>(sa.col16) : reinterpret_cast<const CT*>(sa.col)) +
+                       (int64_t)d.off + lane;
+        int row = lane < d.rows ? pos : d.p0;   // lanes past the slice's rows gather x[p0] (padding)
+        if (sa.perm && lane < d.rows) row = __ldg(sa.perm + pos);
+        const double* xb = kDelta ? a.x + row : a.x + d.xoff;
         double sum = 0.0;
         int j = 0;
         for (; j + U <= d.len; j += U) {
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
             const double t = fma(v, ld_keep(xb + c, pol_keep), sum);
             sum = (j < len) ? t : sum;
         }
-        if (store) sell_store(a, sa.perm ? __ldg(sa.perm + pos) : pos, sum);
+        if (store) sell_store(a, row, sum);
     }
 }
 
@@ -170,6 +182,46 @@ __global__ void __launch_bounds__(256) sell_fill_kernel(const int32_t* __restric
     }
 }
 
+// 16-bit column deltas of a filled layout: slot (slice, j, lane) gets
+// xoff + column - row of its row, padding 0; *bad is set when a delta does
+// not fit (the 16-bit copy is then unusable).
+__global__ void __launch_bounds__(256) sell_delta_kernel(const SellSlice* __restrict__ slices, int n_slices,
+                                                         const uint8_t* __restrict__ lens,
+                                                         const int32_t* __restrict__ perm,
+                                                         const int32_t* __restrict__ scol,
+                                                         int16_t* __restrict__ scol16, int* bad) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * 8;
+    for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < n_slices; si += nwarps) {
+        const SellSlice d = slices[si];
+        const int pos = d.p0 + lane;
+        const bool live = lane < d.rows && lens[pos] != kSellLenLong;
+        const int len = live ? lens[pos] : 0;
+        const int row = live ? (perm ? perm[pos] : pos) : 0;
+        for (int j = 0; j < d.len; ++j) {
+            const int64_t o = (int64_t)d.off + 32 * j + lane;
+            int delta = 0;
+            if (j < len) {
+                delta = d.xoff + scol[o] - row;
+                if (delta < -32768 || delta > 32767) {
+                    atomicOr(bad, 1);
+                    delta = 0;
+                }
+            }
+            scol16[o] = (int16_t)delta;
+        }
+    }
+}
+
+cudaError_t launch_sell_delta(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
+                              const int32_t* scol, int16_t* scol16, int* bad, int num_sms, cudaStream_t s) {
+    if (n_slices <= 0) return cudaSuccess;
+    int grid = (n_slices + 7) / 8;
+    if (grid > num_sms * 8) grid = num_sms * 8;
+    sell_delta_kernel<<<grid, 256, 0, s>>>(slices, n_slices, len, perm, scol, scol16, bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const double* val, const SellSlice* slices,
                              int n_slices, const uint8_t* len, const int32_t* perm, double* sval, int32_t* scol,
                              int num_sms, cudaStream_t s) {
@@ -184,7 +236,8 @@ bool sell_param_supported(int param) {
     return param == 4 || param == 8 || param == 9 || param == 104;
 }
 
-cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, int num_sms, cudaStream_t st) {
+cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, bool delta16, int num_sms,
+                        cudaStream_t st) {
     const int units = (sa.long_end - sa.long_begin) + (sa.slice_end - sa.slice_begin);
     if (units <= 0) return cudaSuccess;
     int blocks_per_sm = 8;
@@ -197,12 +250,16 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, int num
     }
     int grid = num_sms * blocks_per_sm;
     if (grid > (units + 7) / 8) grid = (units + 7) / 8;
+#define SELL_LAUNCH(u, b)                                                              \
+    (delta16 ? (csr_sell_kernel<u, b, int16_t><<<grid, 256, 0, st>>>(a, sa), 0)        \
+             : (csr_sell_kernel<u, b, int32_t><<<grid, 256, 0, st>>>(a, sa), 0))
     switch (param) {
-        case 4: csr_sell_kernel<4, 8><<<grid, 256, 0, st>>>(a, sa); break;
-        case 8: csr_sell_kernel<8, 4><<<grid, 256, 0, st>>>(a, sa); break;
-        case 9: csr_sell_kernel<9, 4><<<grid, 256, 0, st>>>(a, sa); break;
-        case 104: csr_sell_kernel<4, 6><<<grid, 256, 0, st>>>(a, sa); break;
+        case 4: SELL_LAUNCH(4, 8); break;
+        case 8: SELL_LAUNCH(8, 4); break;
+        case 9: SELL_LAUNCH(9, 4); break;
+        case 104: SELL_LAUNCH(4, 6); break;
     }
+#undef SELL_LAUNCH
     return cudaGetLastError();
 }
 

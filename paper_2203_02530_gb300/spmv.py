@@ -21,7 +21,8 @@ OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
 COARSE, PER_PARTITION = 0, 1
 RUN_EAGER, RUN_CAPTURE, RUN_REPLAY = 0, 1, 2
-VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP, VARIANT_SELL = 0, 1, 2, 3, 4, 5
+VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP, VARIANT_SELL, VARIANT_SELL16 = (
+    0, 1, 2, 3, 4, 5, 6)
 SERVE_BATCHED, SERVE_PLAIN = 0, 1
 BATCH_SLICED = 64
 (Q_N, Q_P, Q_GRANULARITY, Q_NNZ, Q_NNZ_LOCAL, Q_NNZ_REMOTE, Q_N_SEND, Q_N_HALO,

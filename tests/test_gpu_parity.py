@@ -242,6 +242,49 @@ def test_sliced_layout_matches_thread_per_row_bit_for_bit(name):
     assert np.array_equal(out[0].view(np.uint64), out[2].view(np.uint64))
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_sell16_local_matches_sell_bit_for_bit(name):
+    """16-bit column deltas change only the index bytes: the LOCAL product
+    gives SELL's y bit for bit (and the oracle's within the bound)."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    out = []
+    with make_part(n, rp, ci, va, P) as part:
+        part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_SELL, 4)
+        for v in (spmv.VARIANT_SELL, spmv.VARIANT_SELL16):
+            part.set_op_variant(spmv.OP_LOCAL, v, 9)
+            assert part.query(spmv.Q_LOCAL_VARIANT) == 100 * v + 9
+            y_d = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda")
+            run_default(part, x_d, y_d, s)
+            s.synchronize()
+            out.append(y_d.cpu().numpy()[:n])
+        assert part.query(spmv.Q_ERROR) == 0
+        with pytest.raises(spmv.SpmvError):
+            part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_SELL16, 4)
+        with pytest.raises(spmv.SpmvError):
+            part.set_variant(spmv.VARIANT_SELL16, 4)
+    assert np.array_equal(out[0].view(np.uint64), out[1].view(np.uint64))
+    assert_fp64_close(out[1], want, scale, "%s sell16" % name)
+
+
+def test_sell16_refused_when_a_delta_needs_more_than_16_bits():
+    from paper_2203_02530_gb300 import spmv
+    torch_cuda()
+    n = 70000
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = ((np.arange(n) + 40000) % n).astype(np.int32)   # every column 40000 rows away (mod n)
+    va = np.ones(n)
+    with make_part(n, rp, ci, va, 1) as part:
+        with pytest.raises(spmv.SpmvError) as e:
+            part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL16, 9)
+        assert e.value.code == spmv.EINVAL
+        assert part.query(spmv.Q_LOCAL_VARIANT) // 100 != spmv.VARIANT_SELL16
+
+
 def _lengths_matrix(lens, seed):
     """Rows of the given lengths with distinct random columns."""
     rng = np.random.default_rng(seed)

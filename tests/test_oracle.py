@@ -81,6 +81,18 @@ def test_scipy_csr_matvec():
     assert np.all(np.abs(got_p - want) <= 1e-12 * scale)
 
 
+def test_rows_parallel_product_equals_serial_bit_for_bit():
+    """The timing-only parallel oracle sums every row as the serial one."""
+    import oracle
+    n, rp, ci, va = W.powerlaw(20000, seed=13, cap=500)
+    x = W.uniform_x(n, seed=14)
+    a = csr_spmv(n, rp, ci, va, x)
+    for threads in (0, 1, 3):
+        b = oracle.csr_spmv_rows_parallel(n, rp, ci, va, x, threads)
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    assert oracle.max_threads() >= 1
+
+
 def test_local_plus_remote_exact_on_integers():
     """A = A_L + A_R (Sec. III-A): with small integers every sum is exact, so
     the partitioned product equals the plain one bit for bit."""
