@@ -27,7 +27,10 @@
  *     stated otherwise.
  *   - Work is asynchronous on the given stream(s); no hidden synchronisation
  *     except in spmv_part_create, spmv_part_destroy, spmv_part_export_plan,
- *     spmv_part_query(SPMV_Q_ERROR) and the _host entry points.
+ *     spmv_part_query(SPMV_Q_ERROR), spmv_part_set_variant and
+ *     spmv_part_set_op_variant (which may build a layout), the _host entry
+ *     points, spmv_csr_error, spmv_batch_create / destroy / set_lanes and
+ *     the serving entry points other than spmv_serve_single.
  *   - Indices: column indices are int32 and n < 2^31; the number of nonzeros
  *     must also be below 2^31.
  *   - All FP values and accumulations are IEEE binary64.
@@ -247,6 +250,17 @@ int spmv_graph_destroy(spmv_part* part, int64_t graph_handle);
 int spmv_part_io_buffers(spmv_part* part, double** x_dev_out, double** y_dev_out);
 int spmv_apply_host(spmv_part* part, int64_t graph_handle, const double* x_host,
                     double* y_host, cudaStream_t s);
+/*
+ * The same end-to-end product with the transfers overlapped: x_host's row
+ * blocks are copied in one by one on copy_stream, rank p's LOCAL product
+ * starts on compute_stream as soon as block p has arrived (it reads no other
+ * x), then PACK, COPY and REMOTE for every rank follow on compute_stream and
+ * y comes back on copy_stream; returns after y has arrived.  The two
+ * streams must differ.  Same y as the graph path, bit for bit (the same
+ * kernels on the same rows).  Plan-owned device vectors as above.
+ */
+int spmv_apply_host_pipelined(spmv_part* part, const double* x_host, double* y_host,
+                              cudaStream_t copy_stream, cudaStream_t compute_stream);
 
 /*
  * Plain CSR product y = A x on caller-owned DEVICE arrays with the
@@ -303,14 +317,15 @@ int spmv_csr_error(int64_t* out);
 /*
  * Batched products: many independent CSR matrices (no partitioning) kept
  * resident in HBM and multiplied in one persistent launch per layout
- * (CSR modes, sliced layout).  Work items are
- * blocks of up to 256 rows of one matrix, claimed by warps through an atomic
- * ticket; each row is summed by `lanes` lanes (set per matrix, e.g. by an
- * autotuner), a row longer than 64 entries by a whole warp, in a fixed
- * order, so y is the same, bit for bit, as with
- * spmv_batch_run_separate, which launches the same row code once per
- * matrix.  Not part of the paper's method: a way of running many of its
- * SpMVs at once.
+ * (CSR modes, sliced layout).  Work items are blocks of up to 256 rows of
+ * one matrix (CSR modes) or up to 8 slices or 32 long rows of one matrix
+ * (sliced layout), claimed by warps through an atomic ticket, matrix by
+ * matrix with each matrix's heaviest items first; each row is summed by
+ * `lanes` lanes (set per matrix, e.g. by an autotuner), a row longer than
+ * 64 entries by a whole warp, in a fixed order, so y is the same, bit for
+ * bit, as with spmv_batch_run_separate, which launches the same row code
+ * once per matrix.  Not part of the paper's method: a way of running many
+ * of its SpMVs at once.
  * spmv_batch_create: `count` matrices given as HOST CSR arrays (n[m],
  *   row_ptr[m][n[m]+1] int64, col_idx[m] int32 in [0, n[m]), vals[m]),
  *   copied to the current device.  Errors as spmv_part_create.

@@ -699,6 +699,51 @@ int spmv_part_io_buffers(spmv_part* pt, double** x_out, double** y_out) {
     return SPMV_OK;
 }
 
+int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_host, cudaStream_t copy_stream,
+                              cudaStream_t compute_stream) {
+    API_TRY
+    check_part(pt);
+    need(pt->n == 0 || (x_host && y_host), SPMV_EINVAL, "host buffer is NULL");
+    need(copy_stream != compute_stream, SPMV_EINVAL, "the copy and compute streams must differ");
+    if (pt->n == 0) return SPMV_OK;
+    if (!pt->io_x) {
+        pt->io_x = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
+        pt->io_y = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
+    }
+    const int P = pt->P;
+    while ((int)pt->io_ev.size() < P + 1) {
+        cudaEvent_t e;
+        check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        pt->io_ev.push_back(e);
+    }
+    // x block by block on the copy stream; rank p's LOCAL product starts as
+    // soon as its block has arrived (it reads no other x)
+    int64_t launches = 0;
+    for (int p = 0; p < P; ++p) {
+        const int64_t r0 = pt->bounds[p], r1 = pt->bounds[p + 1];
+        if (r1 > r0)
+            check_cuda(cudaMemcpyAsync(pt->io_x + r0, x_host + r0, (size_t)(r1 - r0) * sizeof(double),
+                                       cudaMemcpyHostToDevice, copy_stream),
+                       "copy x in");
+        check_cuda(cudaEventRecord(pt->io_ev[p], copy_stream), "event");
+        check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[p], 0), "wait");
+        launches += op_local(pt, p, pt->io_x, pt->io_y, compute_stream);
+    }
+    // the rest of the DAG needs all of x: pack, exchange, remote products
+    launches += op_pack(pt, -1, pt->io_x, compute_stream);
+    launches += op_copy(pt, -1, compute_stream);
+    launches += op_remote(pt, -1, pt->io_y, compute_stream);
+    check_cuda(cudaEventRecord(pt->io_ev[P], compute_stream), "event");
+    check_cuda(cudaStreamWaitEvent(copy_stream, pt->io_ev[P], 0), "wait");
+    check_cuda(cudaMemcpyAsync(y_host, pt->io_y, (size_t)pt->n * sizeof(double), cudaMemcpyDeviceToHost,
+                               copy_stream),
+               "copy y out");
+    check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
+    pt->last_launches = launches;
+    API_CATCH
+    return SPMV_OK;
+}
+
 int spmv_apply_host(spmv_part* pt, int64_t handle, const double* x_host, double* y_host, cudaStream_t s) {
     API_TRY
     check_part(pt);

@@ -75,6 +75,7 @@ struct spmv_part {
     int* err = nullptr;               // device error word
     double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
     double* io_y = nullptr;
+    std::vector<cudaEvent_t> io_ev;   // P+1: x block p arrived; products done
 
     // tiles (thread-per-row and vector kernels)
     spmvk::TileGeom geom{};

@@ -78,6 +78,9 @@ void free_plan(spmv_part* pt) {
     for (cudaEvent_t e : pt->join_ev)
         if (e) cudaEventDestroy(e);
     if (pt->fork_ev) cudaEventDestroy(pt->fork_ev);
+    for (cudaEvent_t e : pt->io_ev)
+        if (e) cudaEventDestroy(e);
+    pt->io_ev.clear();
     pt->op_ev.clear();
     pt->join_ev.clear();
     pt->fork_ev = nullptr;

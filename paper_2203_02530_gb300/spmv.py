@@ -77,6 +77,7 @@ def _load():
         "spmv_graph_destroy": [vp, i64],
         "spmv_part_io_buffers": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
         "spmv_apply_host": [vp, i64, vp, vp, vp],
+        "spmv_apply_host_pipelined": [vp, vp, vp, vp, vp],
         "spmv_csr_merge": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_merge_noalloc": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_error": [P64],
@@ -226,6 +227,11 @@ def spmv_part_io_buffers(h):
 def spmv_apply_host(h, graph_handle, x_host, y_host, stream):
     _check(lib.spmv_apply_host(h, int(graph_handle), _ptr(x_host), _ptr(y_host),
                                _stream(stream)))
+
+
+def spmv_apply_host_pipelined(h, x_host, y_host, copy_stream, compute_stream):
+    _check(lib.spmv_apply_host_pipelined(h, _ptr(x_host), _ptr(y_host), _stream(copy_stream),
+                                         _stream(compute_stream)))
 
 
 def spmv_csr_merge(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_dev, stream):

@@ -544,6 +544,32 @@ def test_apply_host_buffers():
             spmv.spmv_apply_host(part.h, g2, xh, yh, s)
 
 
+@pytest.mark.parametrize("name,variant", [("st27_ragged", ("sell", 9)), ("powerlaw", ("sell", 4)),
+                                          ("tiny_P_gt_n", ("vector", 2)), ("empty_rows", ("tile", 0))])
+def test_apply_host_pipelined_matches_graph_path(name, variant):
+    """Block-wise x transfers overlapped with the LOCAL products give the
+    graph path's y bit for bit."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    s, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with make_part(n, rp, ci, va, P) as part:
+        set_variant(part, variant)
+        xi, yi = spmv.spmv_part_io_buffers(part.h)
+        g = part.run([0, 1, 2, 3], [0, 0, 0, 0], [s], xi, yi, spmv.RUN_CAPTURE)
+        xh = torch.from_numpy(x).pin_memory()
+        y1 = torch.full((max(n, 1),), float("nan"), dtype=torch.float64).pin_memory()
+        y2 = torch.full((max(n, 1),), float("nan"), dtype=torch.float64).pin_memory()
+        spmv.spmv_apply_host(part.h, g, xh, y1, s)
+        spmv.spmv_apply_host_pipelined(part.h, xh, y2, s, s2)
+        a, b = y1.numpy()[:n], y2.numpy()[:n]
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+        assert_fp64_close(b, want, scale, "pipelined host path")
+        with pytest.raises(spmv.SpmvError):
+            spmv.spmv_apply_host_pipelined(part.h, xh, y2, s, s)
+
+
 # ------------------------------------------------------------------ full sizes
 def test_full_size_27pt_150_all_schedules():
     """The 3-D 27-point stencil on 150^3 (n = 3 375 000, 89 915 392 entries),
