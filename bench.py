@@ -144,10 +144,16 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """Hash of the product kernels' code (comments and blank lines left out,
+    so that a comment edit does not invalidate a profile)."""
+    import re
     h = hashlib.sha256()
     for f in ("kernels.cu", "merge.cu", "sell.cu"):
-        with open(os.path.join(ROOT, "paper_2203_02530_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2203_02530_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -241,6 +247,10 @@ WORKLOADS = {
     "band": ("the paper's band matrix: 150000 x 150000, 1.5M entries uniform in |i-j| <= 37500, "
              "P=4, 2 streams, all 24 schedules; L2-resident (replay latency)",
              lambda: band(), 4, 2, 0, "exhaustive"),
+    "stencil27_segments": ("27-point stencil 150^3 (n=3375000, nnz=89915392), P=4, per-segment DAG "
+                           "(LOCAL and REMOTE per rank, PACK and COPY per halo segment: 20 ops), "
+                           "2 streams, MCTS-sampled schedules",
+                           lambda: workload(), 4, 2, 2, "mcts"),
 }
 
 
@@ -287,7 +297,8 @@ def run_ours(args, world, rank, local):
     rec = search.Recorder(args.records, meta={"workload": args.workload}) if args.records else None
     if args.records:
         with open(args.records + ".dag.json", "w") as f:
-            json.dump({"n_ops": part.n_ops, "edges": part.dag(), "P": P, "streams": S}, f)
+            json.dump({"n_ops": part.n_ops, "edges": part.dag(), "P": P, "streams": S,
+                       "names": part.op_names()}, f)
     search_cmp = None
     evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec, measurements=3
                                       if mode == "exhaustive" else 1)
@@ -406,7 +417,7 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": desc, "n": n, "nnz": int(rp[-1]), "P": P, "streams": S,
-                   "granularity": "coarse" if gran == 0 else "per-rank",
+                   "granularity": ("coarse", "per-rank", "per-segment")[gran],
                    "search": mode, "schedules_measured": len(sched),
                    "best_order": order, "best_streams": smap,
                    "variant": {"local": list(tuned["local"]), "remote": list(tuned["remote"])},

@@ -56,12 +56,24 @@ typedef enum {
     SPMV_ETIMEOUT = -6   /* a bounded device wait gave up (see SPMV_Q_ERROR) */
 } spmv_status;
 
-/* Operation kinds; op id = part * 4 + kind (coarse granularity: part 0). */
+/* Operation kinds; op id = part * 4 + kind for the coarse (part 0) and
+ * per-partition granularities; see SPMV_PER_SEGMENT for the third. */
 enum { SPMV_OP_PACK = 0, SPMV_OP_LOCAL = 1, SPMV_OP_COPY = 2, SPMV_OP_REMOTE = 3 };
 
 /* Granularity of the operations (Sec. III-A: one Pack vertex for all
- * peers versus one per peer). */
-enum { SPMV_COARSE = 0, SPMV_PER_PARTITION = 1 };
+ * peers versus one per peer).
+ *   SPMV_COARSE        4 ops, each over every rank.
+ *   SPMV_PER_PARTITION 4P ops, op 4p + kind: PACK of source rank p, COPY
+ *                      into destination p, LOCAL / REMOTE of rank p;
+ *                      PACK_q -> COPY_p when q sends to p.
+ *   SPMV_PER_SEGMENT   one PACK and one COPY per halo segment (destination
+ *                      p, source q, nonempty; the per-direction halo ops of
+ *                      a stencil): ops 2p = LOCAL_p, 2p+1 = REMOTE_p, then
+ *                      2P + 2k = PACK and 2P + 2k + 1 = COPY of segment k,
+ *                      segments destination-major then by source;
+ *                      PACK_k -> COPY_k -> REMOTE_p, LOCAL_p -> REMOTE_p.
+ * spmv_part_op_info decodes an op id in every granularity. */
+enum { SPMV_COARSE = 0, SPMV_PER_PARTITION = 1, SPMV_PER_SEGMENT = 2 };
 
 typedef struct spmv_part spmv_part;   /* opaque; owns all plan memory */
 
@@ -76,8 +88,8 @@ typedef struct spmv_part spmv_part;   /* opaque; owns all plan memory */
  *   A_R,p : the other entries, columns renumbered to positions in H_p;
  *   send buffer: destination-major, then source rank, then ascending column,
  *           so destination p's part is x[H_p] and the exchange is one copy.
- * granularity selects SPMV_COARSE (4 ops, each over every rank) or
- * SPMV_PER_PARTITION (4P ops).  Columns within a row may come in any order
+ * granularity selects SPMV_COARSE, SPMV_PER_PARTITION or SPMV_PER_SEGMENT
+ * (above).  Columns within a row may come in any order
  * and may repeat; each entry is kept and summed in the order given.
  * Errors: SPMV_EINVAL for n < 0, P < 1, a decreasing row_ptr, a column out
  * of [0, n), or NULL pointers with n > 0; SPMV_EBOUNDS for n or nnz >=
@@ -145,6 +157,10 @@ int64_t spmv_part_export_len(const spmv_part* part, int what, int part_idx);
 /* Copy array `what` to host_dst (capacity cap elements); synchronises. */
 int spmv_part_export_plan(const spmv_part* part, int what, int part_idx,
                           void* host_dst, int64_t cap);
+
+/* Op id -> kind (SPMV_OP_*), destination rank and source rank (-1 where
+ * the op has none: a coarse op, a per-partition PACK's destination, ...). */
+int spmv_part_op_info(const spmv_part* part, int op, int32_t* kind, int32_t* dst, int32_t* src);
 
 /* DAG of the plan's operations as (src op, dst op) int32 pairs. */
 int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,

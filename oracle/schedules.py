@@ -53,6 +53,22 @@ def per_partition_dag(P, sends):
     return ops, edges
 
 
+def per_segment_dag(P, sends):
+    """One PACK and one COPY per halo segment (destination p, source q), the
+    finer granularity the paper's future work names (per-peer operations,
+    per-direction halos of a stencil).  Op ids: 2p = LOCAL of rank p,
+    2p + 1 = REMOTE of rank p, then for the k-th segment in destination-major,
+    source-minor order 2P + 2k = its PACK and 2P + 2k + 1 = its COPY.
+    Returns (ops, edges, segments)."""
+    segs = [(p, q) for p in range(P) for q in range(P) if q != p and sends(q, p)]
+    ops = list(range(2 * P + 2 * len(segs)))
+    edges = [(2 * p, 2 * p + 1) for p in range(P)]
+    for k, (p, q) in enumerate(segs):
+        edges.append((2 * P + 2 * k, 2 * P + 2 * k + 1))
+        edges.append((2 * P + 2 * k + 1, 2 * p + 1))
+    return ops, edges, segs
+
+
 def paper_fig3c_dag():
     """A reading of the SpMV DAG of Fig. 3c, whose image is not available.
 

@@ -57,6 +57,22 @@ void build_dag(spmv_part* pt) {
         pt->n_ops = 4;
         pt->edges = {{SPMV_OP_PACK, SPMV_OP_COPY}, {SPMV_OP_COPY, SPMV_OP_REMOTE},
                      {SPMV_OP_LOCAL, SPMV_OP_REMOTE}};
+    } else if (pt->gran == SPMV_PER_SEGMENT) {
+        // ops 2p (LOCAL of rank p), 2p+1 (REMOTE of rank p), then for every
+        // nonempty segment k: 2P+2k (its PACK), 2P+2k+1 (its COPY)
+        pt->segs.clear();
+        for (int p = 0; p < P; ++p)
+            for (int q = 0; q < P; ++q) {
+                const int64_t a = pt->seg_off[(size_t)p * P + q], b = pt->seg_off[(size_t)p * P + q + 1];
+                if (q != p && b > a) pt->segs.push_back(spmv_part::Seg{p, q, a, b});
+            }
+        pt->n_ops = 2 * P + 2 * (int)pt->segs.size();
+        for (int p = 0; p < P; ++p) pt->edges.push_back({2 * p, 2 * p + 1});
+        for (size_t k = 0; k < pt->segs.size(); ++k) {
+            const int pack = 2 * P + 2 * (int)k;
+            pt->edges.push_back({pack, pack + 1});
+            pt->edges.push_back({pack + 1, 2 * pt->segs[k].p + 1});
+        }
     } else {
         pt->n_ops = 4 * P;
         for (int p = 0; p < P; ++p) {
@@ -184,7 +200,26 @@ int op_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
     return launch_product(pt, remote_args(pt, y), true, p, s);
 }
 
+// PACK of one halo segment: its send slots [a, b) <- x
+int op_pack_segment(spmv_part* pt, const spmv_part::Seg& g, const double* x, cudaStream_t s) {
+    check_cuda(spmvk::launch_gather(x, pt->send_idx + g.a, nullptr, pt->sendbuf + g.a, g.b - g.a, pt->num_sms, s),
+               "pack segment");
+    return 1;
+}
+
+// COPY of one halo segment: recvbuf[a, b) <- sendbuf[a, b)
+int op_copy_segment(spmv_part* pt, const spmv_part::Seg& g, cudaStream_t s) {
+    check_cuda(spmvk::launch_copy(pt->sendbuf + g.a, pt->recvbuf + g.a, g.b - g.a, pt->num_sms, s), "copy segment");
+    return 1;
+}
+
 int run_op(spmv_part* pt, int op, const double* x, double* y, cudaStream_t s) {
+    if (pt->gran == SPMV_PER_SEGMENT) {
+        const int P = pt->P;
+        if (op < 2 * P) return op % 2 == 0 ? op_local(pt, op / 2, x, y, s) : op_remote(pt, op / 2, y, s);
+        const spmv_part::Seg& g = pt->segs[(size_t)(op - 2 * P) / 2];
+        return (op - 2 * P) % 2 == 0 ? op_pack_segment(pt, g, x, s) : op_copy_segment(pt, g, s);
+    }
     const int kind = op % 4;
     const int p = pt->gran == SPMV_COARSE ? -1 : op / 4;
     switch (kind) {
@@ -304,7 +339,7 @@ int spmv_part_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, 
     *out = nullptr;
     spmv_part* pt = nullptr;
     API_TRY
-    if (granularity != SPMV_COARSE && granularity != SPMV_PER_PARTITION)
+    if (granularity != SPMV_COARSE && granularity != SPMV_PER_PARTITION && granularity != SPMV_PER_SEGMENT)
         fail(SPMV_EINVAL, "granularity %d", granularity);
     spmvk::validate_csr(n, row_ptr, col_idx, vals, P);   // before any CUDA call
     pt = new spmv_part();
@@ -498,6 +533,32 @@ int spmv_part_export_plan(const spmv_part* pt, int what, int p, void* dst, int64
             break;
         }
         default: fail(SPMV_EINVAL, "bad selector %d", what);
+    }
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_part_op_info(const spmv_part* pt, int op, int32_t* kind, int32_t* dst, int32_t* src) {
+    API_TRY
+    check_part(pt);
+    need(kind && dst && src, SPMV_EINVAL, "output pointer is NULL");
+    if (op < 0 || op >= pt->n_ops) fail(SPMV_EINVAL, "op %d not in [0, %d)", op, pt->n_ops);
+    *dst = -1;
+    *src = -1;
+    if (pt->gran == SPMV_COARSE) {
+        *kind = op;
+    } else if (pt->gran == SPMV_PER_PARTITION) {
+        *kind = op % 4;
+        if (*kind == SPMV_OP_PACK) *src = op / 4;
+        else *dst = op / 4;
+    } else if (op < 2 * pt->P) {
+        *kind = op % 2 == 0 ? SPMV_OP_LOCAL : SPMV_OP_REMOTE;
+        *dst = op / 2;
+    } else {
+        const spmv_part::Seg& g = pt->segs[(size_t)(op - 2 * pt->P) / 2];
+        *kind = (op - 2 * pt->P) % 2 == 0 ? SPMV_OP_PACK : SPMV_OP_COPY;
+        *dst = g.p;
+        *src = g.q;
     }
     API_CATCH
     return SPMV_OK;

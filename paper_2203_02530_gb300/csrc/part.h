@@ -126,6 +126,14 @@ struct spmv_part {
     int variant[2] = {SPMV_VARIANT_TILE, SPMV_VARIANT_TILE};
     int vparam[2] = {0, 0};
 
+    // halo segments (destination p, source q, send slots [a, b)), nonempty,
+    // destination-major: the pack/copy ops of the per-segment granularity
+    struct Seg {
+        int p, q;
+        int64_t a, b;
+    };
+    std::vector<Seg> segs;
+
     // DAG of the operations
     int n_ops = 0;
     std::vector<std::pair<int, int>> edges;

@@ -15,7 +15,10 @@
 // consecutive columns (128 bytes) per step: full coalescing without a
 // shared-memory stage, so occupancy is set by registers alone.  On banded
 // and stencil matrices the lanes' x gathers of one step are also contiguous
-// rows of x.  Each short row is summed in its CSR storage order, one FMA
+// rows of x.  Where every |column - row| of the LOCAL product fits 16 bits
+// the columns can be kept as 16-bit deltas to the row instead (64 bytes per
+// step), the 27-point stencil's case.  Each short row is summed in its CSR
+// storage order, one FMA
 // per entry from 0.0; padded slots are discarded by a select, so y equals
 // that of the other one-thread-per-row kernels bit for bit.
 #include "internal.h"

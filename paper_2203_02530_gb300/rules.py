@@ -271,5 +271,8 @@ if __name__ == "__main__":
     ap.add_argument("--title", default="Design rules")
     a = ap.parse_args()
     d = json.load(open(a.dag))
-    names = coarse_names() if d["n_ops"] == 4 else per_rank_names(d["n_ops"] // 4)
+    if "names" in d:
+        names = d["names"]
+    else:
+        names = coarse_names() if d["n_ops"] == 4 else per_rank_names(d["n_ops"] // 4)
     print(report(load_records(a.records), [tuple(e) for e in d["edges"]], names, a.title))

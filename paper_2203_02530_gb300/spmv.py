@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "spmv.h")
 # status codes and selectors (include/spmv.h)
 OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
-COARSE, PER_PARTITION = 0, 1
+COARSE, PER_PARTITION, PER_SEGMENT = 0, 1, 2
 RUN_EAGER, RUN_CAPTURE, RUN_REPLAY = 0, 1, 2
 VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP, VARIANT_SELL, VARIANT_SELL16 = (
     0, 1, 2, 3, 4, 5, 6)
@@ -67,6 +67,7 @@ def _load():
         "spmv_part_export_len": [vp, i32, i32],
         "spmv_part_export_plan": [vp, i32, i32, vp, i64],
         "spmv_part_dag": [vp, vp, i64, P64],
+        "spmv_part_op_info": [vp, i32, vp, vp, vp],
         "spmv_part_set_variant": [vp, i32, i32],
         "spmv_part_set_op_variant": [vp, i32, i32, i32],
         "spmv_pack": [vp, i32, vp, vp],
@@ -258,6 +259,13 @@ def spmv_csr_error():
     return out.value
 
 
+def spmv_part_op_info(h, op):
+    """(kind, destination rank, source rank) of op id `op`; -1 where none."""
+    k, d, sr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.spmv_part_op_info(h, int(op), ctypes.byref(k), ctypes.byref(d), ctypes.byref(sr)))
+    return k.value, d.value, sr.value
+
+
 class Part:
     """Owns one plan handle; methods forward to the functions above."""
 
@@ -284,6 +292,20 @@ class Part:
 
     def dag(self):
         return spmv_part_dag(self.h)
+
+    def op_names(self):
+        """Readable op names: Pack / yL / Copy / yR, with the rank (coarse:
+        none; per partition: the rank; per segment: yL2, Pack1to2, ...)."""
+        base = {OP_PACK: "Pack", OP_LOCAL: "yL", OP_COPY: "Copy", OP_REMOTE: "yR"}
+        out = []
+        for op in range(self.n_ops):
+            k, d, sr = spmv_part_op_info(self.h, op)
+            if d >= 0 and sr >= 0:
+                out.append("%s%dto%d" % (base[k], sr, d))
+            else:
+                r = d if d >= 0 else sr
+                out.append(base[k] + ("" if r < 0 else str(r)))
+        return out
 
     @property
     def n_ops(self):

@@ -421,6 +421,63 @@ def _random_schedule(dag, n_streams, rng):
     return order, smap
 
 
+@pytest.mark.parametrize("name,variant", [("st27_ragged", ("sell", 9)), ("powerlaw", ("sell", 4)),
+                                          ("band", ("vector", 2)), ("tiny_P_gt_n", ("tile", 0)),
+                                          ("lap64", ("pairs", 2))])
+def test_per_segment_granularity(name, variant):
+    """One PACK and one COPY per halo segment: the DAG is the oracle's
+    per-segment reading, op ids decode as documented, every random schedule
+    (eager and captured) gives the same y bit for bit, and the send and
+    receive buffers equal the oracle's."""
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    ref = oracle.OraclePlan(n, rp, ci, va, P)
+    seg = ref.export(oracle.SEG_OFF)
+    ops, oedges, segs = OS.per_segment_dag(P, lambda q, p: seg[p * P + q + 1] > seg[p * P + q])
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    x_d = dev(x)
+    y_d = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, P, spmv.PER_SEGMENT) as part:
+        set_variant(part, variant)
+        assert part.n_ops == len(ops)
+        assert sorted(map(tuple, part.dag())) == sorted(oedges)
+        for op in ops:
+            kind, d, sr = spmv.spmv_part_op_info(part.h, op)
+            if op < 2 * P:
+                assert (kind, d, sr) == ((spmv.OP_LOCAL, spmv.OP_REMOTE)[op % 2], op // 2, -1)
+            else:
+                p_, q_ = segs[(op - 2 * P) // 2]
+                assert (kind, d, sr) == ((spmv.OP_PACK, spmv.OP_COPY)[op % 2], p_, q_)
+        ref.pack(-1, x)
+        ref.copy(-1)
+        dag = E.Dag(len(ops), oedges)
+        rng = random.Random(5)
+        first = None
+        for trial in range(6):
+            order, smap = _random_schedule(dag, 3, rng)
+            y_d.fill_(float("nan"))
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
+            torch.cuda.synchronize()
+            ye = y_d.cpu().numpy()[:n].copy()
+            g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+            y_d.fill_(float("nan"))
+            torch.cuda.synchronize()
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            torch.cuda.synchronize()
+            assert np.array_equal(y_d.cpu().numpy()[:n], ye)
+            spmv.spmv_graph_destroy(part.h, g)
+            if first is None:
+                first = ye
+                assert_fp64_close(ye, want, scale, "%s per segment" % name)
+                assert np.array_equal(part.export(spmv.X_SENDBUF), ref.export(oracle.SENDBUF))
+                assert np.array_equal(part.export(spmv.X_RECVBUF), ref.export(oracle.RECVBUF))
+            assert np.array_equal(ye, first), (order, smap)
+        assert part.query(spmv.Q_ERROR) == 0
+
+
 @pytest.mark.parametrize("name,variant", [("st27_ragged", ("tile", 0)), ("powerlaw", ("merge", 0)),
                                           ("powerlaw", ("tile", 2)), ("band", ("vector", 4)),
                                           ("powerlaw", ("sell", 4)), ("dense_row", ("sell", 9))])

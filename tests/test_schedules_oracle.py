@@ -178,3 +178,45 @@ def test_per_partition_dag_small_count():
             if not mask >> v & 1 and pred[v] & mask == pred[v]:
                 f[mask | 1 << v] = f.get(mask | 1 << v, 0) + f[mask]
     assert n1 == f[(1 << len(ops)) - 1]
+
+
+def test_per_segment_dag_structure():
+    """One PACK and one COPY per (destination, source) segment: each PACK
+    feeds only its COPY, each COPY only its destination's REMOTE, and every
+    REMOTE also waits for its rank's LOCAL."""
+    P = 3
+    sends = lambda q, p: (q, p) != (0, 2)   # every ordered pair but 0 -> 2
+    ops, edges, segs = S.per_segment_dag(P, sends)
+    assert segs == [(p, q) for p in range(P) for q in range(P) if q != p and sends(q, p)]
+    assert len(ops) == 2 * P + 2 * len(segs)
+    E = set(edges)
+    assert len(E) == len(edges) == P + 2 * len(segs)
+    for p in range(P):
+        assert (2 * p, 2 * p + 1) in E
+    for k, (p, q) in enumerate(segs):
+        pack, copy = 2 * P + 2 * k, 2 * P + 2 * k + 1
+        assert (pack, copy) in E and (copy, 2 * p + 1) in E
+        assert [e for e in edges if e[0] == pack] == [(pack, copy)]
+        assert [e for e in edges if e[0] == copy] == [(copy, 2 * p + 1)]
+
+
+def test_per_segment_dag_small_count():
+    """P = 2, both directions, one stream: the library's enumerator, a brute
+    force over all permutations and a subset DP agree on the number of
+    topological orders of the 8-op DAG."""
+    from paper_2203_02530_gb300 import schedules as E
+    ops, edges, segs = S.per_segment_dag(2, lambda q, p: True)
+    assert len(ops) == 8 and len(segs) == 2
+    n1 = S.count_brute_force(ops, edges, 1)
+    pred = {v: 0 for v in ops}
+    for u, v in edges:
+        pred[v] |= 1 << u
+    f = {0: 1}
+    for mask in range(1 << len(ops)):
+        if mask not in f:
+            continue
+        for v in ops:
+            if not mask >> v & 1 and pred[v] & mask == pred[v]:
+                f[mask | 1 << v] = f.get(mask | 1 << v, 0) + f[mask]
+    assert n1 == f[(1 << len(ops)) - 1]
+    assert E.count_schedules(E.Dag(len(ops), edges), 1) == n1
