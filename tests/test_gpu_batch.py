@@ -99,7 +99,7 @@ def test_sliced_mode_round_trip_and_long_rows():
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
     mats = [W.stencil_7pt(12, seed=1), W.zipf_random(20000, seed=2), W.laplacian_5pt(33),
-            W.powerlaw(6000, seed=3, cap=3000)]
+            W.powerlaw(6000, seed=3, cap=3000), W.random_csr(50000, density=0.0001, seed=4)]
     with spmv.Batch(mats) as b:
         offs = b.offsets()
         x = W.uniform_x(offs[-1], seed=12)
