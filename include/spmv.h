@@ -31,6 +31,9 @@
  *     spmv_part_set_op_variant (which may build a layout), the _host entry
  *     points, spmv_csr_error, spmv_batch_create / destroy / set_lanes and
  *     the serving entry points other than spmv_serve_single.
+ *   - A plan computes one product at a time: its send and receive buffers
+ *     are shared by all of its launches, so two executions of the same plan
+ *     must not overlap on the GPU.  Different plans are independent.
  *   - Indices: column indices are int32 and n < 2^31; the number of nonzeros
  *     must also be below 2^31.
  *   - All FP values and accumulations are IEEE binary64.
