@@ -7,6 +7,7 @@ are cached in a JSON file keyed by a matrix signature (size, entries, row
 length statistics, ranks) and the device name, so a plan of the same shape
 skips the search.
 """
+import hashlib
 import json
 import os
 
@@ -61,6 +62,8 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
     """Pick the fastest variant for each of part's products (LOCAL, then
     REMOTE) and apply them.  Returns {"local": (variant, param),
     "remote": (variant, param), "times": {(op, variant, param): seconds}}."""
+    if sig:   # a cached choice holds only for the same candidate set
+        sig = "%s cands=%s" % (sig, hashlib.sha256(repr(list(candidates)).encode()).hexdigest()[:12])
     cache = _load_cache(cache_path) if (use_cache and sig) else {}
     if sig and sig in cache and "local" in cache[sig]:
         e = cache[sig]
