@@ -131,3 +131,47 @@ def test_serving_rejects_bad_requests():
                 sv.run([7], [1], [1], [0.0])
             with pytest.raises(spmv.SpmvError):
                 sv.run([0, 0], [1, 1], [1, 2], [0.1, 0.0])
+
+
+@pytest.mark.parametrize("layout", ["buckets", "sliced"])
+def test_serving_empty_and_one_row_matrices(layout):
+    """Requests on a matrix with no rows, a 1 x 1 matrix and a matrix whose
+    rows are all empty complete, with the oracle's (empty or zero) results,
+    alone and mixed with ordinary requests."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = [(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0)),
+            W.random_csr(1, density=1.0, seed=3, empty_rows=False),
+            (40, np.zeros(41, np.int64), np.zeros(0, np.int32), np.zeros(0)),
+            W.laplacian_5pt(20)]
+    rng = np.random.default_rng(21)
+    cnt = 60
+    mat = rng.integers(0, len(mats), size=cnt).astype(np.int32)
+    wid = rng.integers(1, 9, size=cnt).astype(np.int32)
+    sd = rng.integers(0, 2**63, size=cnt, dtype=np.uint64)
+    with spmv.Batch(mats) as b:
+        if layout == "sliced":
+            spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        with spmv.Server(b, n_streams=3, budget_bytes=1 << 30) as sv:
+            lat_b, h_b, _ = sv.run(mat, wid, sd, np.zeros(cnt), spmv.SERVE_BATCHED)
+            lat_p, h_p, _ = sv.run(mat, wid, sd, np.zeros(cnt), spmv.SERVE_PLAIN)
+            assert np.array_equal(h_b, h_p)
+            assert (lat_b > 0).all() and (lat_p > 0).all()
+            s = torch.cuda.Stream()
+            for r in range(cnt):
+                m, k = int(mat[r]), int(wid[r])
+                n, rp, ci, va = mats[m]
+                if n == 0:
+                    assert h_b[r] == 0
+                    continue
+                x = torch.empty((n, k), dtype=torch.float64, device="cuda")
+                y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+                spmv.spmv_serve_single(sv.h, m, k, int(sd[r]), y, x, s)
+                s.synchronize()
+                Y = y.cpu().numpy()
+                assert host_hash(Y, k) == h_b[r]
+                X = W.request_x(int(sd[r]), n, k)
+                for j in range(k):
+                    want = oracle.csr_spmv(n, rp, ci, va, X[:, j])
+                    scale = oracle.csr_absdot(n, rp, ci, va, X[:, j])
+                    assert_fp64_close(Y[:, j], want, scale, "request %d column %d" % (r, j))
