@@ -722,6 +722,8 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
 int spmv_batch_destroy(spmv_batch* b) {
     if (!b) return SPMV_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    for (cudaEvent_t ev : b->io_ev)
+        if (ev) cudaEventDestroy(ev);
     bfree(b);
     delete b;
     return e == cudaSuccess ? SPMV_OK : bfail(SPMV_ECUDA, cudaGetErrorString(e));
@@ -810,6 +812,72 @@ int spmv_batch_run(spmv_batch* b, const double* x, double* y, cudaStream_t s) {
         batch_persistent_kernel<<<grid, kThreads, 0, s>>>(a);
         spmvk::check_cuda(cudaGetLastError(), "batch launch");
     }
+    BATCH_CATCH
+    return SPMV_OK;
+}
+
+int spmv_batch_run_host(spmv_batch* b, const double* x_host, double* y_host, int chunks, cudaStream_t s_in,
+                        cudaStream_t s_compute, cudaStream_t s_out) {
+    BATCH_TRY
+    if (!b) spmvk::fail(SPMV_EINVAL, "batch is NULL");
+    if (b->total_rows > 0 && (!x_host || !y_host)) spmvk::fail(SPMV_EINVAL, "host buffer is NULL");
+    if (chunks < 1 || chunks > 64) spmvk::fail(SPMV_EINVAL, "chunks = %d not in [1, 64]", chunks);
+    if (s_in == s_compute || s_out == s_compute || s_in == s_out) spmvk::fail(SPMV_EINVAL, "the streams must differ");
+    if (b->total_rows == 0) return SPMV_OK;
+    if (!b->io_x) {
+        b->io_x = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
+        b->io_y = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
+    }
+    while ((int)b->io_ev.size() < 2 * chunks) {
+        cudaEvent_t e;
+        spmvk::check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        b->io_ev.push_back(e);
+    }
+    // chunks of whole matrices with about equal rows: x of chunk c goes in
+    // on s_in, its products run on s_compute once it has arrived, and its y
+    // goes back on s_out while later chunks are still moving or computing
+    const BatchArgs a = args_of(b, b->io_x, b->io_y);
+    int m0 = 0;
+    for (int c = 0; c < chunks && m0 < b->count; ++c) {
+        const long long target = b->total_rows * (long long)(c + 1) / chunks;
+        int m1 = m0 + 1;
+        while (m1 < b->count && b->mats[m1 - 1].row_off + b->n[m1 - 1] < target) ++m1;
+        if (c == chunks - 1) m1 = b->count;
+        const long long r0 = b->mats[m0].row_off;
+        const long long r1 = b->mats[m1 - 1].row_off + b->n[m1 - 1];
+        cudaEvent_t in_ev = b->io_ev[2 * c], out_ev = b->io_ev[2 * c + 1];
+        if (r1 > r0)
+            spmvk::check_cuda(cudaMemcpyAsync(b->io_x + r0, x_host + r0, (size_t)(r1 - r0) * sizeof(double),
+                                              cudaMemcpyHostToDevice, s_in),
+                              "copy x in");
+        spmvk::check_cuda(cudaEventRecord(in_ev, s_in), "event");
+        spmvk::check_cuda(cudaStreamWaitEvent(s_compute, in_ev, 0), "wait");
+        for (int i = m0; i < m1; ++i) {   // consecutive matrices of one layout share a launch
+            int j = i + 1;
+            const bool sliced = b->mats[i].lanes == kSliced;
+            while (j < m1 && (b->mats[j].lanes == kSliced) == sliced) ++j;
+            const int first = b->item_off[i], last = b->item_off[j];
+            if (last > first) {
+                int grid = b->num_sms * std::max(1, sliced ? b->occupancy_sliced : b->occupancy);
+                const int need = (last - first + kThreads / 32 - 1) / (kThreads / 32);
+                if (grid > need) grid = need;
+                if (sliced)
+                    batch_sliced_range_kernel<<<grid, kThreads, 0, s_compute>>>(a, first, last);
+                else
+                    batch_range_kernel<<<grid, kThreads, 0, s_compute>>>(a, first, last);
+                spmvk::check_cuda(cudaGetLastError(), "chunk launch");
+            }
+            i = j - 1;
+        }
+        spmvk::check_cuda(cudaEventRecord(out_ev, s_compute), "event");
+        spmvk::check_cuda(cudaStreamWaitEvent(s_out, out_ev, 0), "wait");
+        if (r1 > r0)
+            spmvk::check_cuda(cudaMemcpyAsync(y_host + r0, b->io_y + r0, (size_t)(r1 - r0) * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s_out),
+                              "copy y out");
+        m0 = m1;
+    }
+    spmvk::check_cuda(cudaStreamSynchronize(s_out), "synchronize");
     BATCH_CATCH
     return SPMV_OK;
 }

@@ -64,6 +64,9 @@ struct spmv_batch {
     spmvk::BatchMat* d_mats = nullptr;
     void* d_items = nullptr;
     int* ticket = nullptr;
+    double* io_x = nullptr;              // device vectors of the host-buffer path (built on first use)
+    double* io_y = nullptr;
+    std::vector<cudaEvent_t> io_ev;      // per chunk: x arrived, y computed
     int n_items = 0;
     size_t device_bytes = 0;
     std::vector<void*> allocs;

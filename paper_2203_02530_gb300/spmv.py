@@ -88,6 +88,7 @@ def _load():
         "spmv_batch_query": [vp, i32, i32, P64],
         "spmv_batch_run": [vp, vp, vp, vp],
         "spmv_batch_run_separate": [vp, i32, vp, vp, vp],
+        "spmv_batch_run_host": [vp, vp, vp, i32, vp, vp, vp],
         "spmv_serve_create": [vp, i32, i64, ctypes.POINTER(vp)],
         "spmv_serve_destroy": [vp],
         "spmv_serve_run": [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp],
@@ -358,6 +359,11 @@ def spmv_batch_query(h, what, m=-1):
 
 def spmv_batch_run(h, x_dev, y_dev, stream):
     _check(lib.spmv_batch_run(h, _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_batch_run_host(h, x_host, y_host, chunks, s_in, s_compute, s_out):
+    _check(lib.spmv_batch_run_host(h, _ptr(x_host), _ptr(y_host), int(chunks), _stream(s_in),
+                                   _stream(s_compute), _stream(s_out)))
 
 
 def spmv_batch_run_separate(h, m, x_dev, y_dev, stream):

@@ -118,3 +118,31 @@ def test_sliced_mode_round_trip_and_long_rows():
             if lanes in res:
                 assert np.array_equal(a, res[lanes])
             res[lanes] = a
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 64])
+def test_batch_run_host_matches_device_run(chunks):
+    """Chunked host-buffer runs (x in, products, y out overlapped) give the
+    device run's y bit for bit, in both layouts."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = _mix()
+    with spmv.Batch(mats) as b:
+        offs = b.offsets()
+        x = W.uniform_x(offs[-1], seed=13)
+        s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        x_d = dev(x)
+        y_d = torch.empty(offs[-1], dtype=torch.float64, device="cuda")
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.full((offs[-1],), float("nan"), dtype=torch.float64).pin_memory()
+        for lanes in (2, spmv.BATCH_SLICED):
+            spmv.spmv_batch_set_lanes(b.h, -1, lanes)
+            spmv.spmv_batch_run(b.h, x_d, y_d, s_c)
+            s_c.synchronize()
+            spmv.spmv_batch_run_host(b.h, xh, yh, chunks, s_in, s_c, s_out)
+            a, h = y_d.cpu().numpy(), yh.numpy()
+            assert np.array_equal(a.view(np.uint64), h.view(np.uint64)), lanes
+        with pytest.raises(spmv.SpmvError):
+            spmv.spmv_batch_run_host(b.h, xh, yh, chunks, s_c, s_c, s_out)
+        with pytest.raises(spmv.SpmvError):
+            spmv.spmv_batch_run_host(b.h, xh, yh, 0, s_in, s_c, s_out)
