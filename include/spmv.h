@@ -382,9 +382,9 @@ int spmv_batch_run(spmv_batch* batch, const double* x_dev, double* y_dev, cudaSt
 /* End to end through HOST buffers (x_host, y_host: the concatenated vectors,
  * pinned for full speed): the matrices are cut into `chunks` (1..64) runs of
  * whole matrices with about equal rows; chunk c's x is copied in on s_in,
- * its products run on s_compute once it has arrived (one launch per run of
- * matrices in the same layout, the same row code as spmv_batch_run, so the
- * same y bit for bit), and its y is copied out on s_out while later chunks
+ * its products run on s_compute once it has arrived (the persistent kernels
+ * of spmv_batch_run over the chunk's items, so the same y bit for bit), and
+ * its y is copied out on s_out while later chunks
  * are still in flight.  The three streams must differ.  Returns after y has
  * arrived.  Uses batch-owned device vectors (allocated on first use). */
 int spmv_batch_run_host(spmv_batch* batch, const double* x_host, double* y_host, int chunks,

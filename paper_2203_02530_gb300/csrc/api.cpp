@@ -779,6 +779,8 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
     }
     // x block by block on the copy stream; rank p's LOCAL product starts as
     // soon as its block has arrived (it reads no other x)
+    // (every copy in is issued before any wait, so that streams sharing a
+    // hardware queue never hold a copy behind a wait)
     int64_t launches = 0;
     for (int p = 0; p < P; ++p) {
         const int64_t r0 = pt->bounds[p], r1 = pt->bounds[p + 1];
@@ -787,6 +789,8 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
                                        cudaMemcpyHostToDevice, copy_stream),
                        "copy x in");
         check_cuda(cudaEventRecord(pt->io_ev[p], copy_stream), "event");
+    }
+    for (int p = 0; p < P; ++p) {
         check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[p], 0), "wait");
         launches += op_local(pt, p, pt->io_x, pt->io_y, compute_stream);
     }

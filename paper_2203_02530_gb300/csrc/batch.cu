@@ -484,6 +484,17 @@ void upload_items(spmv_batch* b) {
     };
     std::stable_sort(b->order.begin(), b->order.begin() + b->n_sliced_items, first);
     std::stable_sort(b->order.begin() + b->n_sliced_items, b->order.end(), first);
+    // where each matrix's items start in either part of the order (the
+    // host-buffer path claims one run of matrices at a time)
+    b->order_off.assign(2 * (b->count + 1), 0);
+    for (int part = 0; part < 2; ++part) {
+        const int lo = part == 0 ? 0 : b->n_sliced_items, hi = part == 0 ? b->n_sliced_items : (int)all.size();
+        int t = lo;
+        for (int m = 0; m <= b->count; ++m) {
+            while (t < hi && all[b->order[t]].m < m) ++t;
+            b->order_off[part * (b->count + 1) + m] = t;
+        }
+    }
     if (all.size() > b->items_cap) {
         if (b->d_items) brelease(b, b->d_items, b->items_cap * sizeof(BatchItem));
         if (b->d_order) brelease(b, b->d_order, b->items_cap * sizeof(int));
@@ -827,6 +838,7 @@ int spmv_batch_run_host(spmv_batch* b, const double* x_host, double* y_host, int
     if (!b->io_x) {
         b->io_x = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
         b->io_y = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
+        b->io_tickets = static_cast<int*>(balloc(b, 4 * 64 * sizeof(int)));
     }
     while ((int)b->io_ev.size() < 2 * chunks) {
         cudaEvent_t e;
@@ -835,47 +847,63 @@ int spmv_batch_run_host(spmv_batch* b, const double* x_host, double* y_host, int
     }
     // chunks of whole matrices with about equal rows: x of chunk c goes in
     // on s_in, its products run on s_compute once it has arrived, and its y
-    // goes back on s_out while later chunks are still moving or computing
+    // goes back on s_out while later chunks are still moving or computing.
+    // Issued phase by phase (all copies in, all products, all copies out) so
+    // that streams sharing a hardware queue never hold a copy behind a wait.
     const BatchArgs a = args_of(b, b->io_x, b->io_y);
-    int m0 = 0;
-    for (int c = 0; c < chunks && m0 < b->count; ++c) {
+    struct Chunk {
+        int m0, m1;
+        long long r0, r1;
+    };
+    std::vector<Chunk> ch;
+    for (int c = 0, m0 = 0; c < chunks && m0 < b->count; ++c) {
         const long long target = b->total_rows * (long long)(c + 1) / chunks;
         int m1 = m0 + 1;
         while (m1 < b->count && b->mats[m1 - 1].row_off + b->n[m1 - 1] < target) ++m1;
         if (c == chunks - 1) m1 = b->count;
-        const long long r0 = b->mats[m0].row_off;
-        const long long r1 = b->mats[m1 - 1].row_off + b->n[m1 - 1];
-        cudaEvent_t in_ev = b->io_ev[2 * c], out_ev = b->io_ev[2 * c + 1];
-        if (r1 > r0)
-            spmvk::check_cuda(cudaMemcpyAsync(b->io_x + r0, x_host + r0, (size_t)(r1 - r0) * sizeof(double),
+        ch.push_back(Chunk{m0, m1, b->mats[m0].row_off, b->mats[m1 - 1].row_off + b->n[m1 - 1]});
+        m0 = m1;
+    }
+    for (size_t c = 0; c < ch.size(); ++c) {
+        if (ch[c].r1 > ch[c].r0)
+            spmvk::check_cuda(cudaMemcpyAsync(b->io_x + ch[c].r0, x_host + ch[c].r0,
+                                              (size_t)(ch[c].r1 - ch[c].r0) * sizeof(double),
                                               cudaMemcpyHostToDevice, s_in),
                               "copy x in");
-        spmvk::check_cuda(cudaEventRecord(in_ev, s_in), "event");
-        spmvk::check_cuda(cudaStreamWaitEvent(s_compute, in_ev, 0), "wait");
-        for (int i = m0; i < m1; ++i) {   // consecutive matrices of one layout share a launch
-            int j = i + 1;
-            const bool sliced = b->mats[i].lanes == kSliced;
-            while (j < m1 && (b->mats[j].lanes == kSliced) == sliced) ++j;
-            const int first = b->item_off[i], last = b->item_off[j];
-            if (last > first) {
-                int grid = b->num_sms * std::max(1, sliced ? b->occupancy_sliced : b->occupancy);
-                const int need = (last - first + kThreads / 32 - 1) / (kThreads / 32);
-                if (grid > need) grid = need;
-                if (sliced)
-                    batch_sliced_range_kernel<<<grid, kThreads, 0, s_compute>>>(a, first, last);
-                else
-                    batch_range_kernel<<<grid, kThreads, 0, s_compute>>>(a, first, last);
-                spmvk::check_cuda(cudaGetLastError(), "chunk launch");
-            }
-            i = j - 1;
+        spmvk::check_cuda(cudaEventRecord(b->io_ev[2 * c], s_in), "event");
+    }
+    // each chunk's items are a contiguous run of the claim order (per
+    // layout), run by the persistent kernels with a ticket of their own
+    spmvk::check_cuda(cudaMemsetAsync(b->io_tickets, 0, (size_t)4 * ch.size() * sizeof(int), s_compute),
+                      "chunk tickets");
+    const int cp1 = b->count + 1;
+    for (size_t c = 0; c < ch.size(); ++c) {
+        spmvk::check_cuda(cudaStreamWaitEvent(s_compute, b->io_ev[2 * c], 0), "wait");
+        for (int part = 0; part < 2; ++part) {
+            const int o0 = b->order_off[part * cp1 + ch[c].m0], o1 = b->order_off[part * cp1 + ch[c].m1];
+            if (o1 <= o0) continue;
+            BatchArgs pa = a;
+            pa.order = b->d_order + o0;
+            pa.n_items = o1 - o0;
+            pa.ticket = b->io_tickets + 4 * c + 2 * part;
+            int grid = b->num_sms * std::max(1, part == 0 ? b->occupancy_sliced : b->occupancy);
+            const int need = (o1 - o0 + kThreads / 32 - 1) / (kThreads / 32);
+            if (grid > need) grid = need;
+            if (part == 0)
+                batch_sliced_persistent_kernel<<<grid, kThreads, 0, s_compute>>>(pa);
+            else
+                batch_persistent_kernel<<<grid, kThreads, 0, s_compute>>>(pa);
+            spmvk::check_cuda(cudaGetLastError(), "chunk launch");
         }
-        spmvk::check_cuda(cudaEventRecord(out_ev, s_compute), "event");
-        spmvk::check_cuda(cudaStreamWaitEvent(s_out, out_ev, 0), "wait");
-        if (r1 > r0)
-            spmvk::check_cuda(cudaMemcpyAsync(y_host + r0, b->io_y + r0, (size_t)(r1 - r0) * sizeof(double),
+        spmvk::check_cuda(cudaEventRecord(b->io_ev[2 * c + 1], s_compute), "event");
+    }
+    for (size_t c = 0; c < ch.size(); ++c) {
+        spmvk::check_cuda(cudaStreamWaitEvent(s_out, b->io_ev[2 * c + 1], 0), "wait");
+        if (ch[c].r1 > ch[c].r0)
+            spmvk::check_cuda(cudaMemcpyAsync(y_host + ch[c].r0, b->io_y + ch[c].r0,
+                                              (size_t)(ch[c].r1 - ch[c].r0) * sizeof(double),
                                               cudaMemcpyDeviceToHost, s_out),
                               "copy y out");
-        m0 = m1;
     }
     spmvk::check_cuda(cudaStreamSynchronize(s_out), "synchronize");
     BATCH_CATCH

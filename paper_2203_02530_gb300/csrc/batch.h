@@ -67,6 +67,8 @@ struct spmv_batch {
     double* io_x = nullptr;              // device vectors of the host-buffer path (built on first use)
     double* io_y = nullptr;
     std::vector<cudaEvent_t> io_ev;      // per chunk: x arrived, y computed
+    int* io_tickets = nullptr;           // per chunk: a ticket per layout (4 ints)
+    std::vector<int> order_off;          // 2 x (count+1): start of matrix m's items in each part of `order`
     int n_items = 0;
     size_t device_bytes = 0;
     std::vector<void*> allocs;
