@@ -772,15 +772,32 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
         pt->io_y = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
     }
     const int P = pt->P;
-    while ((int)pt->io_ev.size() < P + 1) {
+    while ((int)pt->io_ev.size() < 2 * P + 1) {
         cudaEvent_t e;
         check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         pt->io_ev.push_back(e);
     }
+    if (pt->io_free.empty()) {   // once per plan: the remote-free run of every rank
+        std::vector<int32_t> rr((size_t)pt->n_rr);
+        if (pt->n_rr)
+            check_cuda(cudaMemcpy(rr.data(), pt->rr_row, rr.size() * 4, cudaMemcpyDeviceToHost), "remote rows");
+        for (int p = 0; p < P; ++p) {
+            int64_t prev = pt->bounds[p], best_a = prev, best_b = prev;
+            for (int64_t k = pt->rr_off[p]; k <= pt->rr_off[p + 1]; ++k) {
+                const int64_t next = k < pt->rr_off[p + 1] ? (int64_t)rr[(size_t)k] : pt->bounds[p + 1];
+                if (next - prev > best_b - best_a) {
+                    best_a = prev;
+                    best_b = next;
+                }
+                prev = next + 1;
+            }
+            pt->io_free.push_back({best_a, best_b});
+        }
+    }
     // x block by block on the copy stream; rank p's LOCAL product starts as
-    // soon as its block has arrived (it reads no other x)
-    // (every copy in is issued before any wait, so that streams sharing a
-    // hardware queue never hold a copy behind a wait)
+    // soon as its block has arrived (it reads no other x).  Every copy in is
+    // issued before any wait, so that streams sharing a hardware queue never
+    // hold a copy behind a wait.
     int64_t launches = 0;
     for (int p = 0; p < P; ++p) {
         const int64_t r0 = pt->bounds[p], r1 = pt->bounds[p + 1];
@@ -793,16 +810,32 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
     for (int p = 0; p < P; ++p) {
         check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[p], 0), "wait");
         launches += op_local(pt, p, pt->io_x, pt->io_y, compute_stream);
+        check_cuda(cudaEventRecord(pt->io_ev[P + p], compute_stream), "event");
     }
     // the rest of the DAG needs all of x: pack, exchange, remote products
     launches += op_pack(pt, -1, pt->io_x, compute_stream);
     launches += op_copy(pt, -1, compute_stream);
     launches += op_remote(pt, -1, pt->io_y, compute_stream);
-    check_cuda(cudaEventRecord(pt->io_ev[P], compute_stream), "event");
-    check_cuda(cudaStreamWaitEvent(copy_stream, pt->io_ev[P], 0), "wait");
-    check_cuda(cudaMemcpyAsync(y_host, pt->io_y, (size_t)pt->n * sizeof(double), cudaMemcpyDeviceToHost,
-                               copy_stream),
-               "copy y out");
+    check_cuda(cudaEventRecord(pt->io_ev[2 * P], compute_stream), "event");
+    // y: each rank's remote-free run as soon as its LOCAL product is done
+    // (overlapping the other ranks' products), the rest after REMOTE
+    auto copy_out = [&](int64_t a, int64_t b) {
+        if (b > a)
+            check_cuda(cudaMemcpyAsync(y_host + a, pt->io_y + a, (size_t)(b - a) * sizeof(double),
+                                       cudaMemcpyDeviceToHost, copy_stream),
+                       "copy y out");
+    };
+    for (int p = 0; p < P; ++p) {
+        check_cuda(cudaStreamWaitEvent(copy_stream, pt->io_ev[P + p], 0), "wait");
+        copy_out(pt->io_free[p].first, pt->io_free[p].second);
+    }
+    check_cuda(cudaStreamWaitEvent(copy_stream, pt->io_ev[2 * P], 0), "wait");
+    int64_t from = 0;
+    for (int p = 0; p < P; ++p) {
+        copy_out(from, pt->io_free[p].first);
+        from = std::max(from, pt->io_free[p].second);
+    }
+    copy_out(from, pt->n);
     check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
     pt->last_launches = launches;
     API_CATCH

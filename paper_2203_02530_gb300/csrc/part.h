@@ -75,7 +75,10 @@ struct spmv_part {
     int* err = nullptr;               // device error word
     double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
     double* io_y = nullptr;
-    std::vector<cudaEvent_t> io_ev;   // P+1: x block p arrived; products done
+    std::vector<cudaEvent_t> io_ev;   // 2P+1: x block p arrived; LOCAL p done; products done
+    // per rank: the longest run [a, b) of rows without remote entries (final
+    // after the rank's LOCAL product; the host path copies it out early)
+    std::vector<std::pair<int64_t, int64_t>> io_free;
 
     // tiles (thread-per-row and vector kernels)
     spmvk::TileGeom geom{};
