@@ -443,11 +443,14 @@ def run_ours(args, world, rank, local):
                        "measurements": len(meas), "protocol": "0.01 s of samples each"},
         "schedule_spread": round(spread, 4),
         "search_vs_random": search_cmp,
-        "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
+        "e2e": {"value": round(alg / min(t_e2e, t_e2e_graph) / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
-                "ms_per_step": round(t_e2e * 1e3, 4), "path": "spmv_apply_host_pipelined",
-                "graph_path": {"value": round(alg / t_e2e_graph / 1e9, 2),
-                               "ms_per_step": round(t_e2e_graph * 1e3, 4), "path": "spmv_apply_host"}},
+                "ms_per_step": round(min(t_e2e, t_e2e_graph) * 1e3, 4),
+                "path": "spmv_apply_host_pipelined" if t_e2e <= t_e2e_graph else "spmv_apply_host",
+                "paths": {"spmv_apply_host_pipelined": {"value": round(alg / t_e2e / 1e9, 2),
+                                                        "ms_per_step": round(t_e2e * 1e3, 4)},
+                          "spmv_apply_host": {"value": round(alg / t_e2e_graph / 1e9, 2),
+                                              "ms_per_step": round(t_e2e_graph * 1e3, 4)}}},
         "cpu_baseline": cpu,
         "clocks": clocks, "remeasured": remeasured,
         "gpu_launches": launches_per_step * args.steps,
