@@ -445,6 +445,9 @@ int spmv_serve_destroy(spmv_server* server);
 int spmv_serve_run(spmv_server* server, int64_t n_req, const int32_t* matrix,
                    const int32_t* width, const uint64_t* seed, const double* arrival_s,
                    int mode, double* latency_s, uint64_t* hash_out, int64_t* stats);
+/* Most blocks a grouped launch takes (1..64, default 64): smaller groups
+ * finish sooner, larger ones launch less.  SPMV_EINVAL outside the range. */
+int spmv_serve_set_group_max(spmv_server* server, int max_blocks);
 /* Kernels launched by the last spmv_serve_run (every block's X generator
  * and products). */
 int spmv_serve_launches(const spmv_server* server, int64_t* out);

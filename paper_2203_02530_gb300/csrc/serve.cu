@@ -594,6 +594,7 @@ struct spmv_server {
     int32_t* bucket_rows = nullptr;
     std::vector<int64_t> mid_off, long_off;   // rows of bucket b of matrix m: [off[m], off[m+1])
     int64_t launches = 0;                      // kernels launched since the last run began
+    int group_max = kGroupMax;                 // blocks per group (grouped launches)
     // per stream slot: the group table on the device and its pinned staging
     std::vector<GroupBlock*> d_group, h_group;
 };
@@ -775,6 +776,14 @@ int spmv_serve_destroy(spmv_server* sv) {
     return SPMV_OK;
 }
 
+int spmv_serve_set_group_max(spmv_server* sv, int max_blocks) {
+    if (!sv) return sfail(SPMV_EINVAL, "server is NULL");
+    if (max_blocks < 1 || max_blocks > kGroupMax)
+        return sfail(SPMV_EINVAL, "group size " + std::to_string(max_blocks) + " not in [1, 64]");
+    sv->group_max = max_blocks;
+    return SPMV_OK;
+}
+
 int spmv_serve_launches(const spmv_server* sv, int64_t* out) {
     if (!sv || !out) return sfail(SPMV_EINVAL, "NULL argument");
     *out = sv->launches;
@@ -886,7 +895,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                     GroupBlock* hg = sv->h_group[i];
                     int nb = 0, units = 0, longs = 0, max_elems = 0;
                     bool out_of_memory = false;
-                    while (nb < kGroupMax && queued > 0 && !out_of_memory) {
+                    while (nb < sv->group_max && queued > 0 && !out_of_memory) {
                         int m = -1;
                         for (int k = 0; k < M; ++k) {
                             const int c = (rr + k) % M;

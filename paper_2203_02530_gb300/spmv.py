@@ -94,6 +94,7 @@ def _load():
         "spmv_serve_run": [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp],
         "spmv_serve_single": [vp, i32, i32, ctypes.c_uint64, vp, vp, vp],
         "spmv_serve_launches": [vp, P64],
+        "spmv_serve_set_group_max": [vp, i32],
         "spmv_selftest_wait_timeout": [i64, P64],
         "spmv_last_error": [],
     }
@@ -419,6 +420,10 @@ def spmv_serve_run(h, matrix, width, seed, arrival_s, mode=SERVE_BATCHED, want_h
     keys = ["blocks", "max_inflight", "waits_for_memory", "peak_pool_bytes", "elapsed_ns",
             "admitted_while_busy"]
     return lat, hs, dict(zip(keys, (int(v) for v in st)))
+
+
+def spmv_serve_set_group_max(h, max_blocks):
+    _check(lib.spmv_serve_set_group_max(h, int(max_blocks)))
 
 
 def spmv_serve_launches(h):
