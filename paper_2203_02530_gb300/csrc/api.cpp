@@ -167,7 +167,8 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
     }
     if (var == SPMV_VARIANT_SELL || var == SPMV_VARIANT_SELL16) {
         const spmv_part::SellPart& sp = pt->sell[remote ? 1 : 0];
-        spmvk::SellArgs sa{sp.slices, sp.longs, sp.val, sp.col, sp.col16, sp.len, sp.perm, 0, 0, 0, 0};
+        spmvk::SellArgs sa{sp.slices, sp.longs, sp.val,  sp.col,         sp.col16,     sp.len, sp.perm,
+                           0,         0,        0,       0,       sp.long_part, sp.long_cnt};
         sa.slice_begin = (int)(p < 0 ? 0 : sp.slice_off[p]);
         sa.slice_end = (int)(p < 0 ? sp.slice_off[pt->P] : sp.slice_off[p + 1]);
         sa.long_begin = (int)(p < 0 ? 0 : sp.long_off[p]);

@@ -57,11 +57,18 @@ struct SellSlice {
 };
 static_assert(sizeof(SellSlice) == 32, "slice descriptor is two int4");
 
-// A row longer than kSellLong entries: summed by a whole warp from the CSR.
+// A piece of a row longer than kSellLong entries: entries [k0, k1) of the
+// CSR row, summed by a whole warp.  A row longer than kSellChunk entries is
+// cut into nparts pieces; each writes its partial sum to slot `slot` of the
+// partial array, and the warp that finishes a row's last piece (counter
+// cidx) adds the row's partials in piece order and stores the row.
 struct SellLong {
-    int32_t row, xoff;
+    int32_t row, xoff, k0, k1;
+    int32_t slot, first, nparts, cidx;
 };
+static_assert(sizeof(SellLong) == 32, "long-row piece is two int4");
 constexpr int kSellLong = 64;
+constexpr int kSellChunk = 512;
 constexpr uint8_t kSellLenLong = 0xFF;   // length code of a long row inside a slice
 
 // Sliced layout of one CSR product (local or remote), all ranks.
@@ -74,6 +81,8 @@ struct SellArgs {
     const uint8_t* len;      // per position: entries, or kSellLenLong
     const int32_t* perm;     // per position: row; nullptr = position is the row
     int slice_begin, slice_end, long_begin, long_end;
+    double* long_part;       // partial sums of the pieces of cut rows
+    int* long_cnt;           // per cut row: pieces done (zero between launches)
 };
 
 // Operands of one CSR product launch.

@@ -116,6 +116,8 @@ struct spmv_part {
         uint8_t* len = nullptr;
         int32_t* perm = nullptr;          // nullptr: every rank in natural order
         int16_t* col16 = nullptr;         // column - row deltas (LOCAL only), once built
+        double* long_part = nullptr;      // partial sums of cut long rows
+        int* long_cnt = nullptr;          // pieces done per cut long row
         int delta_state = 0;              // 0 not checked, 1 built, -1 some delta needs > 16 bits
         int64_t entries = 0;              // padded slots
         std::vector<int64_t> slice_off;   // P+1

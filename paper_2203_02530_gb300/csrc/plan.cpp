@@ -385,6 +385,7 @@ static int64_t build_sell_part(spmv_part* pt, spmv_part::SellPart& sp, const std
     const int64_t rows = rb[P];
     std::vector<SellSlice> slices;
     std::vector<SellLong> longs;
+    int64_t n_slots = 0, n_cut = 0;   // partial-sum slots and cut rows
     std::vector<uint8_t> len((size_t)rows, 0);
     std::vector<int32_t> perm;   // position -> row
     perm.reserve((size_t)rows);
@@ -417,13 +418,29 @@ static int64_t build_sell_part(spmv_part* pt, spmv_part::SellPart& sp, const std
         }
         perm.insert(perm.end(), order.begin(), order.end());   // identity for natural ranks
         sp.long_off[p] = (int64_t)longs.size();
+        int64_t n_long_rows = 0;
         for (int64_t q = 0; q < r1 - r0; ++q) {
             const int32_t r = order[(size_t)q];
-            if (L(r) > kSellLong) longs.push_back(SellLong{r, xo[p]});
+            if (L(r) > kSellLong) {
+                ++n_long_rows;
+                // pieces of at most kSellChunk entries, so that one very long
+                // row does not keep one warp busy for the whole launch
+                const int32_t kb = ptr[(size_t)r], ke = ptr[(size_t)r + 1];
+                const int32_t np = (ke - kb + kSellChunk - 1) / kSellChunk;
+                if (np == 1) {
+                    longs.push_back(SellLong{r, xo[p], kb, ke, -1, -1, 1, -1});
+                } else {
+                    for (int32_t c = 0; c < np; ++c)
+                        longs.push_back(SellLong{r, xo[p], kb + c * kSellChunk, std::min(ke, kb + (c + 1) * kSellChunk),
+                                                 (int32_t)n_slots + c, (int32_t)n_slots, np, (int32_t)n_cut});
+                    n_slots += np;
+                    ++n_cut;
+                }
+            }
             len[(size_t)(r0 + q)] = L(r) > kSellLong ? kSellLenLong : (uint8_t)L(r);
         }
         // slices: sorted ranks skip their leading long rows
-        const int64_t first = sorted ? r0 + (int64_t)(longs.size() - sp.long_off[p]) : r0;
+        const int64_t first = sorted ? r0 + n_long_rows : r0;
         sp.slice_off[p] = (int64_t)slices.size();
         for (int64_t q = first; q < r1; q += 32) {
             const int64_t e = std::min(r1, q + 32);
@@ -439,6 +456,8 @@ static int64_t build_sell_part(spmv_part* pt, spmv_part::SellPart& sp, const std
     sp.long_off[P] = (int64_t)longs.size();
     sp.slices = upload(pt, slices);
     sp.longs = upload(pt, longs);
+    sp.long_part = static_cast<double*>(dev_alloc(pt, (size_t)n_slots * sizeof(double)));
+    sp.long_cnt = static_cast<int*>(dev_alloc(pt, (size_t)n_cut * sizeof(int)));   // zeroed
     sp.len = upload(pt, len);
     sp.perm = any_sorted ? upload(pt, perm) : nullptr;
     sp.val = static_cast<double*>(dev_alloc(pt, (size_t)off * 8));

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
     for (int u0 = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); u0 < n_units; u0 += nwarps) {
         if (u0 < n_long) {
             const SellLong L = sa.longs[sa.long_begin + u0];
-            const int kb = __ldg(a.ptr + L.row), ke = __ldg(a.ptr + L.row + 1);
+            const int kb = L.k0, ke = L.k1;
             const double* xb = a.x + L.xoff;
             double part = 0.0;
             int k = kb + lane;
@@ -113,7 +113,23 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
                            part);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-            if (lane == 0) sell_store(a, L.row, part);
+            if (lane == 0) {
+                if (L.nparts == 1) {
+                    sell_store(a, L.row, part);
+                } else {
+                    // publish this piece, then the warp that completes the row
+                    // adds its pieces in piece order (independent of timing)
+                    sa.long_part[L.slot] = part;
+                    __threadfence();
+                    if (atomicAdd(sa.long_cnt + L.cidx, 1) == L.nparts - 1) {
+                        __threadfence();
+                        double sum = 0.0;
+                        for (int i = 0; i < L.nparts; ++i) sum += __ldcg(sa.long_part + L.first + i);
+                        sell_store(a, L.row, sum);
+                        sa.long_cnt[L.cidx] = 0;   // ready for the next launch
+                    }
+                }
+            }
             continue;
         }
         const SellSlice d = sa.slices[sa.slice_begin + u0 - n_long];

@@ -296,12 +296,14 @@ def _lengths_matrix(lens, seed):
     return n, rp, ci, rng.uniform(-1, 1, size=ci.size)
 
 
-@pytest.mark.parametrize("lens_kind", ["all_long", "edge_64_65", "long_and_empty", "one_long_in_natural"])
+@pytest.mark.parametrize("lens_kind", ["all_long", "edge_64_65", "long_and_empty", "one_long_in_natural",
+                                       "cut_rows"])
 @pytest.mark.parametrize("gran", [0, 1])
 def test_sliced_layout_edge_cases(lens_kind, gran):
     """Rows at and around the 64-entry long-row threshold, ranks made of long
-    rows only, empty rows among long ones, and a single long row inside a
-    natural-order rank (a hole in its slice), coarse and per rank."""
+    rows only, empty rows among long ones, a single long row inside a
+    natural-order rank (a hole in its slice), and rows cut into 512-entry
+    pieces, coarse and per rank; twice, so the pieces' counters are reset."""
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
     rng = np.random.default_rng(31)
@@ -312,9 +314,12 @@ def test_sliced_layout_edge_cases(lens_kind, gran):
         lens = rng.choice([63, 64, 65, 66], size=n)
     elif lens_kind == "long_and_empty":
         lens = np.where(rng.random(n) < 0.5, 0, rng.integers(65, 200, size=n))
-    else:
+    elif lens_kind == "one_long_in_natural":
         lens = np.full(n, 9)
         lens[333] = 500
+    else:   # rows cut into 512-entry pieces, including exact multiples
+        lens = rng.integers(1, 20, size=3000)
+        lens[::37] = rng.choice([513, 1024, 1025, 2999], size=lens[::37].size)
     n, rp, ci, va = _lengths_matrix(lens, 32)
     x = W.uniform_x(n, seed=33)
     want, scale = reference(n, rp, ci, va, x)
@@ -335,7 +340,12 @@ def test_sliced_layout_edge_cases(lens_kind, gran):
             for p in reversed(range(P)):
                 spmv.spmv_remote(part.h, p, y_d, s)
         s.synchronize()
-        assert_fp64_close(y_d.cpu().numpy(), want, scale, "sliced %s gran %d" % (lens_kind, gran))
+        y1 = y_d.cpu().numpy().copy()
+        assert_fp64_close(y1, want, scale, "sliced %s gran %d" % (lens_kind, gran))
+        y_d.fill_(float("nan"))
+        run_default(part, x_d, y_d, s)
+        s.synchronize()
+        assert np.array_equal(y_d.cpu().numpy(), y1)
         assert part.query(spmv.Q_ERROR) == 0
 
 
