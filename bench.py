@@ -370,6 +370,8 @@ def run_ours(args, world, rank, local):
              spmv.VARIANT_WARP: "csr_warp_kernel", spmv.VARIANT_SELL: "csr_sell_kernel",
              spmv.VARIANT_SELL16: "csr_sell_kernel"}[variant]
     traffic = profiled_traffic("%s/%d/%d" % (kname, variant, vparam))
+    if traffic is None:   # the layout's bytes, measured with another param of the variant
+        traffic = profiled_traffic("%s/%d" % (kname, variant))
 
     # paper protocol: per-measurement latency percentiles of the best schedule
     meas = benchmark.measurements(step, streams[0], args.measurements)
