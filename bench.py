@@ -300,8 +300,10 @@ def run_ours(args, world, rank, local):
             json.dump({"n_ops": part.n_ops, "edges": part.dag(), "P": P, "streams": S,
                        "names": part.op_names()}, f)
     search_cmp = None
+    # the minimum of a few 0.01 s measurements per program, so that a host
+    # hiccup during one measurement does not masquerade as a slow program
     evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec, measurements=3
-                                      if mode == "exhaustive" else 1)
+                                      if mode == "exhaustive" else 2)
     if mode == "exhaustive":
         sched = search.exhaustive(part, streams, evaluate)
     elif mode == "mcts":
