@@ -78,6 +78,13 @@ def test_results_same_alone_and_in_the_mix_and_match_oracle(layout):
             lat_burst, h_burst, st_burst = sv.run(mat, wid, sd, np.zeros(len(mat)), spmv.SERVE_BATCHED)
             assert st_burst["blocks"] < len(mat)
             assert np.array_equal(h_burst, h_b)
+            # smaller groups (sliced layout: grouped launches) give the same results
+            spmv.spmv_serve_set_group_max(sv.h, 2)
+            _, h_g2, _ = sv.run(mat, wid, sd, np.zeros(len(mat)), spmv.SERVE_BATCHED)
+            assert np.array_equal(h_g2, h_b)
+            with pytest.raises(spmv.SpmvError):
+                spmv.spmv_serve_set_group_max(sv.h, 65)
+            spmv.spmv_serve_set_group_max(sv.h, 64)
             s = torch.cuda.Stream()
             for r in range(0, len(mat), 23):
                 m, k = int(mat[r]), int(wid[r])
