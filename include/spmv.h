@@ -448,6 +448,11 @@ int spmv_serve_run(spmv_server* server, int64_t n_req, const int32_t* matrix,
 /* Most blocks a grouped launch takes (1..64, default 64): smaller groups
  * finish sooner, larger ones launch less.  SPMV_EINVAL outside the range. */
 int spmv_serve_set_group_max(spmv_server* server, int max_blocks);
+/* The bits of the binary64 value m * 2^-52 - 1 (the 2 u - 1 above, for the
+ * 53-bit draw m = SplitMix64(...) >> 11; only the low 53 bits of m are read),
+ * computed on the host by the integer construction the device generator runs.
+ * Exact, so it equals converting m to double and subtracting 1; no GPU. */
+uint64_t spmv_serve_pm1_bits(uint64_t m);
 /* Kernels launched by the last spmv_serve_run (every block's X generator
  * and products). */
 int spmv_serve_launches(const spmv_server* server, int64_t* out);

@@ -38,16 +38,39 @@ constexpr int kMidRow = 256;      // rows up to this length (above the short
                                   // threshold) get 8 lanes, longer rows 32
 
 // ---------------------------------------------------------------- device
-// SplitMix64 (Steele, Lea and Flood): element t of the stream of `seed`.
-__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t t) {
-    uint64_t z = seed + (t + 1) * 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 (Steele, Lea and Flood) output function; element t of the
+// stream of `seed` is splitmix_out(seed + (t + 1) * kGolden).
+__host__ __device__ __forceinline__ uint64_t splitmix_out(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
-// U[-1, 1) from the top 53 bits.
-__device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t t) {
-    return (double)(splitmix64(seed, t) >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+
+__host__ __device__ __forceinline__ int clz64(uint64_t a) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)a);
+#else
+    return a ? __builtin_clzll(a) : 64;
+#endif
+}
+
+// The IEEE-754 bits of m * 2^-52 - 1 for a 53-bit m (the uniform draw on
+// [-1, 1) from the top 53 bits of a SplitMix64 output), built with integer
+// operations only.  The value is exact in binary64 (a multiple of 2^-52 of
+// magnitude at most 1), so this equals converting m and subtracting; it keeps
+// the generator off the FP64 pipe, which the multi-RHS products saturate.
+// With a = |m - 2^52| and b its top bit, the value is +-a * 2^-52: the
+// significand is a shifted up to bit 52 and the biased exponent 1023 + b - 52;
+// a = 0 gives +0.
+__host__ __device__ __forceinline__ uint64_t pm1_bits_from_u53(uint64_t m) {
+    const int64_t t = (int64_t)m - (int64_t(1) << 52);
+    const uint64_t s = (uint64_t)(t >> 63);           // all ones when t < 0
+    const uint64_t a = ((uint64_t)t ^ s) - s;         // |t|, at most 2^52
+    const int b = 63 - clz64(a);                      // 0 .. 52 when a > 0
+    const uint64_t bits = ((a << ((52 - b) & 63)) + ((uint64_t)(970 + b) << 52)) | (s << 63);
+    return a ? bits : 0ull;
 }
 
 struct BlockReq {
@@ -65,20 +88,31 @@ struct BlockDesc {
 };
 
 // X[i, c] for every column of every request of a block (row-major, ld W):
-// request r's element (i, j) is U(seed_r, 8 i + j).  Elements e0, e0 + step, ...
+// request r's element (i, j) is U(seed_r, 8 i + j), columns of no request 0.
+// Thread `tid` of `nthreads` (nthreads >= W) owns column tid mod W and rows
+// tid / W, tid / W + R, ... with R = nthreads / W, so consecutive threads
+// write consecutive elements and the counter advances by a constant.
 __device__ __forceinline__ void gen_x(double* __restrict__ X, int n, int W, const BlockReq* req, int n_req,
-                                      int e0, int step) {
-    const int total = n * W;   // < 2^31: n < 2^28 is checked by the server
-    for (int e = e0; e < total; e += step) {
-        const int i = e / W, c = e - (e / W) * W;
-        double v = 0.0;
-        for (int r = 0; r < n_req; ++r) {
-            const BlockReq q = req[r];
-            if (c >= q.col0 && c < q.col0 + q.width)
-                v = uniform_pm1(q.seed, (uint64_t)i * kMaxW + (uint64_t)(c - q.col0));
-        }
-        X[e] = v;   // row-major, leading dimension W
+                                      int tid, int nthreads) {
+    const int R = nthreads / W;
+    if (tid >= R * W) return;
+    const int c = tid % W;
+    int i = tid / W;
+    uint64_t seed = 0;
+    int j = -1;
+    for (int r = 0; r < n_req; ++r) {
+        const BlockReq q = req[r];
+        if (c >= q.col0 && c < q.col0 + q.width) { seed = q.seed; j = c - q.col0; }
     }
+    if (j < 0) {
+        for (; i < n; i += R) X[(int64_t)i * W + c] = 0.0;
+        return;
+    }
+    uint64_t z = seed + ((uint64_t)i * kMaxW + (uint64_t)j + 1) * kGolden;
+    const uint64_t dz = (uint64_t)R * kMaxW * kGolden;
+#pragma unroll 4
+    for (; i < n; i += R, z += dz)
+        X[(int64_t)i * W + c] = __longlong_as_double((long long)pm1_bits_from_u53(splitmix_out(z) >> 11));
 }
 
 __global__ void gen_x_kernel(double* __restrict__ X, int n, BlockDesc b) {
@@ -120,7 +154,7 @@ __device__ __forceinline__ void hash_row(const BlockReq* req, int n_req, int row
         for (int c = 0; c < W; ++c) {
             if (c >= q.col0 && c < q.col0 + q.width) {
                 const uint64_t e = (uint64_t)row * q.width + (uint64_t)(c - q.col0);
-                h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * 0x9E3779B97F4A7C15ull);
+                h[r] += mix64((uint64_t)__double_as_longlong(acc[c]) + e * kGolden);
             }
         }
     }
@@ -774,6 +808,10 @@ int spmv_serve_destroy(spmv_server* sv) {
     if (sv->bucket_rows) cudaFree(sv->bucket_rows);
     delete sv;
     return SPMV_OK;
+}
+
+uint64_t spmv_serve_pm1_bits(uint64_t m) {
+    return pm1_bits_from_u53(m & ((uint64_t(1) << 53) - 1));
 }
 
 int spmv_serve_set_group_max(spmv_server* sv, int max_blocks) {

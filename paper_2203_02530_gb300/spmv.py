@@ -95,6 +95,7 @@ def _load():
         "spmv_serve_single": [vp, i32, i32, ctypes.c_uint64, vp, vp, vp],
         "spmv_serve_launches": [vp, P64],
         "spmv_serve_set_group_max": [vp, i32],
+        "spmv_serve_pm1_bits": [ctypes.c_uint64],
         "spmv_selftest_wait_timeout": [i64, P64],
         "spmv_last_error": [],
     }
@@ -103,6 +104,7 @@ def _load():
         f.argtypes = args
         f.restype = i32
     L.spmv_part_export_len.restype = i64
+    L.spmv_serve_pm1_bits.restype = ctypes.c_uint64
     L.spmv_last_error.restype = ctypes.c_char_p
     return L
 
@@ -424,6 +426,12 @@ def spmv_serve_run(h, matrix, width, seed, arrival_s, mode=SERVE_BATCHED, want_h
 
 def spmv_serve_set_group_max(h, max_blocks):
     _check(lib.spmv_serve_set_group_max(h, int(max_blocks)))
+
+
+def spmv_serve_pm1_bits(m):
+    """Bits of m * 2^-52 - 1 (low 53 bits of m) as the request generator
+    builds them; host only."""
+    return int(lib.spmv_serve_pm1_bits(int(m) & 0xFFFFFFFFFFFFFFFF))
 
 
 def spmv_serve_launches(h):

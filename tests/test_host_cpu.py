@@ -97,6 +97,31 @@ def test_splitmix64_published_first_output():
     assert x.min() >= -1.0 and x.max() < 1.0 and abs(x.mean()) < 0.05
 
 
+def test_request_draw_bits_equal_the_conversion(libpath):
+    """The device generator builds 2u - 1 = m * 2^-52 - 1 from the bits of the
+    53-bit draw m with integer operations; the host copy of that construction
+    must equal converting m to double and subtracting 1, bit for bit, at the
+    ends (m = 0 gives -1, m = 2^52 gives +0), at every exponent on both sides
+    of zero, and on random draws."""
+    import numpy as np
+    from paper_2203_02530_gb300 import spmv
+    ms = {0, 1, 2, 3, 2**52 - 1, 2**52, 2**52 + 1, 2**53 - 1}
+    for b in range(53):
+        for d in (-1, 0, 1):
+            for m in (2**52 + (1 << b) + d, 2**52 - (1 << b) + d):
+                if 0 <= m < 2**53:
+                    ms.add(m)
+    rng = np.random.default_rng(17)
+    ms.update(int(v) for v in rng.integers(0, 2**53, size=2000, dtype=np.uint64))
+    ms = np.array(sorted(ms), dtype=np.uint64)
+    want = (ms.astype(np.float64) * 2.0 ** -53 * 2.0 - 1.0).view(np.uint64)
+    got = np.array([spmv.spmv_serve_pm1_bits(int(m)) for m in ms], dtype=np.uint64)
+    assert np.array_equal(got, want)
+    assert spmv.spmv_serve_pm1_bits(2**52) == 0          # +0, not -0
+    # only the low 53 bits are read
+    assert spmv.spmv_serve_pm1_bits(2**63 + 5) == spmv.spmv_serve_pm1_bits(5)
+
+
 def test_malformed_csr_rejected_before_any_cuda_call(libpath):
     """Host-side fault injection: bad plans are refused with SPMV_EINVAL /
     SPMV_EBOUNDS before the library touches the GPU."""
