@@ -1,8 +1,10 @@
 """Kernel-variant autotuner for the CSR products.
 
 Candidates are the variants compiled into the library: thread-per-row tile
-geometries, vector-per-row widths and the merge-path kernel.  Each is timed
-on the plan's LOCAL operation with CUDA events; the fastest wins.  Results
+geometries, vector-per-row widths, pairs, warp pipelines, the merge-path
+kernel and the sliced layouts.  Each is timed on the plan's LOCAL and REMOTE
+operations with CUDA events (one launch over all ranks for a coarse plan,
+the P per-rank launches in a row otherwise); the fastest wins.  Results
 are cached in a JSON file keyed by a matrix signature (size, entries, row
 length statistics, ranks) and the device name, so a plan of the same shape
 skips the search.
@@ -62,8 +64,13 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
     """Pick the fastest variant for each of part's products (LOCAL, then
     REMOTE) and apply them.  Returns {"local": (variant, param),
     "remote": (variant, param), "times": {(op, variant, param): seconds}}."""
-    if sig:   # a cached choice holds only for the same candidate set
-        sig = "%s cands=%s" % (sig, hashlib.sha256(repr(list(candidates)).encode()).hexdigest()[:12])
+    # a plan whose DAG has one LOCAL and one REMOTE op per rank launches them
+    # rank by rank, and a kernel's tail weighs more in P small launches than
+    # in one: time the P per-rank launches there
+    per_rank = getattr(part, "granularity", spmv.COARSE) != spmv.COARSE
+    if sig:   # a cached choice holds only for the same candidate set and granularity
+        sig = "%s%s cands=%s" % (sig, " per-rank" if per_rank else "",
+                                 hashlib.sha256(repr(list(candidates)).encode()).hexdigest()[:12])
     cache = _load_cache(cache_path) if (use_cache and sig) else {}
     if sig and sig in cache and "local" in cache[sig]:
         e = cache[sig]
@@ -72,8 +79,17 @@ def tune(part, x_dev, y_dev, stream, sig=None, candidates=CANDIDATES, reps=20,
         return {"local": tuple(e["local"]), "remote": tuple(e["remote"]),
                 "times": {tuple(int(c) for c in k.split(",")): t for k, t in e["times"].items()}}
     times = {}
-    ops = [(spmv.OP_LOCAL, lambda: spmv.spmv_local(part.h, -1, x_dev, y_dev, stream)),
-           (spmv.OP_REMOTE, lambda: spmv.spmv_remote(part.h, -1, y_dev, stream))]
+    ranks = list(range(part.P)) if per_rank else [-1]
+
+    def run_local():
+        for p in ranks:
+            spmv.spmv_local(part.h, p, x_dev, y_dev, stream)
+
+    def run_remote():
+        for p in ranks:
+            spmv.spmv_remote(part.h, p, y_dev, stream)
+
+    ops = [(spmv.OP_LOCAL, run_local), (spmv.OP_REMOTE, run_remote)]
     best = {}
     for op, run in ops:
         usable = []

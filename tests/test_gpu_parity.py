@@ -231,15 +231,15 @@ def test_sliced_layout_matches_thread_per_row_bit_for_bit(name):
     s = torch.cuda.Stream()
     x_d = dev(x)
     out = []
-    for v in (("warp", 0), ("sell", 4), ("sell", 9)):
+    for v in (("warp", 0), ("sell", 4), ("sell", 9), ("sell", 104)):
         y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
         with make_part(n, rp, ci, va, P) as part:
             set_variant(part, v)
             run_default(part, x_d, y_d, s)
             s.synchronize()
         out.append(y_d.cpu().numpy())
-    assert np.array_equal(out[0].view(np.uint64), out[1].view(np.uint64))
-    assert np.array_equal(out[0].view(np.uint64), out[2].view(np.uint64))
+    for o in out[1:]:
+        assert np.array_equal(out[0].view(np.uint64), o.view(np.uint64))
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -299,11 +299,13 @@ def _lengths_matrix(lens, seed):
 @pytest.mark.parametrize("lens_kind", ["all_long", "edge_64_65", "long_and_empty", "one_long_in_natural",
                                        "cut_rows"])
 @pytest.mark.parametrize("gran", [0, 1])
-def test_sliced_layout_edge_cases(lens_kind, gran):
+@pytest.mark.parametrize("param", [4, 104])
+def test_sliced_layout_edge_cases(lens_kind, gran, param):
     """Rows at and around the 64-entry long-row threshold, ranks made of long
     rows only, empty rows among long ones, a single long row inside a
     natural-order rank (a hole in its slice), and rows cut into 512-entry
-    pieces, coarse and per rank; twice, so the pieces' counters are reset."""
+    pieces, coarse and per rank, at two launch shapes; twice, so the pieces'
+    counters are reset."""
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
     rng = np.random.default_rng(31)
@@ -328,7 +330,7 @@ def test_sliced_layout_edge_cases(lens_kind, gran):
     y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
     P = 3
     with make_part(n, rp, ci, va, P, gran) as part:
-        set_variant(part, ("sell", 4))
+        set_variant(part, ("sell", param))
         if gran == 0:
             run_default(part, x_d, y_d, s)
         else:
@@ -490,7 +492,8 @@ def test_per_segment_granularity(name, variant):
 
 @pytest.mark.parametrize("name,variant", [("st27_ragged", ("tile", 0)), ("powerlaw", ("merge", 0)),
                                           ("powerlaw", ("tile", 2)), ("band", ("vector", 4)),
-                                          ("powerlaw", ("sell", 4)), ("dense_row", ("sell", 9))])
+                                          ("powerlaw", ("sell", 4)), ("dense_row", ("sell", 9)),
+                                          ("powerlaw", ("sell", 104)), ("dense_row", ("sell", 8))])
 def test_per_partition_schedules_give_identical_y(name, variant):
     from paper_2203_02530_gb300 import spmv
     from paper_2203_02530_gb300 import schedules as E
@@ -690,6 +693,82 @@ def test_full_size_powerlaw_4M_per_partition():
             part.run(order, [0] * 32, [s], x_d, y_d, spmv.RUN_EAGER)
             s.synchronize()
             assert_fp64_close(y_d.cpu().numpy(), want, scale, "powerlaw %s" % (variant,))
+
+
+def test_full_size_powerlaw_4M_sliced_schedules():
+    """The power-law n = 4M, P = 8 per-rank DAG in the form the benchmark
+    times: sliced products (LOCAL and REMOTE at several launch shapes,
+    chosen separately), random 4-stream schedules captured as graphs and
+    replayed twice: y bit-identical across variants, schedules and replays,
+    and equal to the oracle in full."""
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    n, rp, ci, va = W.powerlaw(4_000_000, seed=3)
+    x = W.uniform_x(n, seed=4)
+    want, scale = reference(n, rp, ci, va, x)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    rng = random.Random(11)
+    first = None
+    with make_part(n, rp, ci, va, 8, spmv.PER_PARTITION) as part:
+        del ci, va
+        dag = E.Dag(part.n_ops, part.dag())
+        for lp, rp_ in ((8, 104), (9, 9), (4, 8)):
+            part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, lp)
+            part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_SELL, rp_)
+            order, smap = _random_schedule(dag, 4, rng)
+            g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+            for _ in range(2):
+                y_d.fill_(float("nan"))
+                part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+                torch.cuda.synchronize()
+                y = y_d.cpu().numpy()
+                if first is None:
+                    first = y.copy()
+                    assert_fp64_close(first, want, scale, "powerlaw sliced")
+                assert np.array_equal(y.view(np.uint64), first.view(np.uint64)), (lp, rp_)
+            spmv.spmv_graph_destroy(part.h, g)
+        assert part.query(spmv.Q_ERROR) == 0
+
+
+def test_full_size_27pt_150_benchmark_variants():
+    """The 27-point stencil 150^3, P = 4, with the products the benchmark
+    tunes between: LOCAL in 16-bit-delta or 32-bit sliced form, REMOTE by
+    pairs or sliced; the best schedule's shape
+    (LOCAL on its own stream) captured and replayed: y equal to the oracle
+    in full, and bit-identical across the sliced variants."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va = W.stencil_27pt(150, seed=1)
+    x = W.uniform_x(n, seed=2)
+    want, scale = reference(n, rp, ci, va, x)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    sliced = None
+    with make_part(n, rp, ci, va, 4) as part:
+        del ci, va
+        for (lv, lp), (rv, rpar) in (((spmv.VARIANT_SELL16, 9), (spmv.VARIANT_PAIRS, 1)),
+                                     ((spmv.VARIANT_SELL16, 4), (spmv.VARIANT_SELL, 104)),
+                                     ((spmv.VARIANT_SELL, 8), (spmv.VARIANT_SELL, 4))):
+            part.set_op_variant(spmv.OP_LOCAL, lv, lp)
+            part.set_op_variant(spmv.OP_REMOTE, rv, rpar)
+            order, smap = [0, 2, 1, 3], [0, 1, 0, 0]   # pack, copy, remote on 0; local on 1
+            g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+            y_d.fill_(float("nan"))
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            torch.cuda.synchronize()
+            y = y_d.cpu().numpy()
+            spmv.spmv_graph_destroy(part.h, g)
+            assert_fp64_close(y, want, scale, "27pt 150^3 %s" % ((lv, lp, rv, rpar),))
+            if rv == spmv.VARIANT_SELL:
+                # SELL16 and SELL sum every row in the same order
+                if sliced is None:
+                    sliced = y.copy()
+                assert np.array_equal(y.view(np.uint64), sliced.view(np.uint64)), (lv, lp, rv, rpar)
+        assert part.query(spmv.Q_ERROR) == 0
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
