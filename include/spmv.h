@@ -183,7 +183,12 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *          32-row tiles (bulk copies per warp, no block-wide barrier), one
  *          thread per row, one DFMA per entry
  *   SELL   param = 4, 8, 9 (entries per lane per step) or 104 (4, fewer
- *          registers): a sliced-ELL copy of A_L and A_R that the plan builds
+ *          registers), each + 2000 (2004, 2008, 2009, 2104) for the same
+ *          launch with the work units cut into contiguous ranges of equal
+ *          estimated cost, one per CTA, instead of dealt round-robin to the
+ *          warps (evens out the SMs on skewed rows; y is the same bit for
+ *          bit; the ranges are built when the variant is set, for every
+ *          rank and for all ranks).  A sliced-ELL copy of A_L and A_R that the plan builds
  *          on first use and holds until destroyed.  Per rank, rows longer
  *          than 64 entries are summed by a whole warp each; the others sit
  *          in slices of 32 positions (entry j of position r at slice offset

@@ -26,8 +26,8 @@ CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
               + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8, 102, 104)]
               + [(spmv.VARIANT_WARP, g) for g in range(5)]
               + [(spmv.VARIANT_MERGE, 0)]
-              + [(spmv.VARIANT_SELL, u) for u in (4, 8, 9, 104)]
-              + [(spmv.VARIANT_SELL16, u) for u in (4, 8, 9, 104)])
+              + [(spmv.VARIANT_SELL, u) for u in (4, 8, 9, 104, 2004, 2008, 2009, 2104)]
+              + [(spmv.VARIANT_SELL16, u) for u in (4, 8, 9, 104, 2004, 2008, 2009, 2104)])
 
 
 def signature(n, row_ptr, P, device_name):

@@ -168,11 +168,19 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
     if (var == SPMV_VARIANT_SELL || var == SPMV_VARIANT_SELL16) {
         const spmv_part::SellPart& sp = pt->sell[remote ? 1 : 0];
         spmvk::SellArgs sa{sp.slices, sp.longs, sp.val,  sp.col,         sp.col16,     sp.len, sp.perm,
-                           0,         0,        0,       0,       sp.long_part, sp.long_cnt};
+                           0,         0,        0,       0,       sp.long_part, sp.long_cnt, nullptr};
         sa.slice_begin = (int)(p < 0 ? 0 : sp.slice_off[p]);
         sa.slice_end = (int)(p < 0 ? sp.slice_off[pt->P] : sp.slice_off[p + 1]);
         sa.long_begin = (int)(p < 0 ? 0 : sp.long_off[p]);
         sa.long_end = (int)(p < 0 ? sp.long_off[pt->P] : sp.long_off[p + 1]);
+        if (spmvk::sell_param_balanced(param)) {
+            const int units = (sa.slice_end - sa.slice_begin) + (sa.long_end - sa.long_begin);
+            const int grid = spmvk::sell_grid(param, units, pt->num_sms);
+            if (grid > 0) {
+                sa.cta_off = spmvk::sell_split(pt, remote ? 1 : 0, p < 0 ? pt->P : p, grid);
+                if (!sa.cta_off) fail(SPMV_EINVAL, "balanced sliced ranges not prepared");
+            }
+        }
         check_cuda(spmvk::launch_sell(a, sa, param, var == SPMV_VARIANT_SELL16, pt->num_sms, s), "sliced product");
         return (sa.slice_end > sa.slice_begin || sa.long_end > sa.long_begin) ? 1 : 0;
     }
@@ -613,13 +621,18 @@ static void prepare_variant(spmv_part* pt, int variant, int param, int op_kind) 
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
     } else if (variant == SPMV_VARIANT_SELL || variant == SPMV_VARIANT_SELL16) {
-        if (!spmvk::sell_param_supported(param)) fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104}", param);
+        if (!spmvk::sell_param_supported(param))
+            fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104} (+2000 balanced)", param);
         if (variant == SPMV_VARIANT_SELL16 && op_kind != SPMV_OP_LOCAL)
             fail(SPMV_EINVAL, "16-bit column deltas serve the LOCAL product only");
         check_cuda(cudaDeviceSynchronize(), "synchronize");
         if (!pt->sell_built) spmvk::build_sell(pt);
         if (variant == SPMV_VARIANT_SELL16 && !spmvk::build_sell_delta16(pt))
             fail(SPMV_EINVAL, "a LOCAL column lies more than 32767 rows from its row: no 16-bit deltas");
+        if (spmvk::sell_param_balanced(param)) {
+            if (op_kind != SPMV_OP_REMOTE) spmvk::build_sell_split(pt, 0, param);
+            if (op_kind != SPMV_OP_LOCAL) spmvk::build_sell_split(pt, 1, param);
+        }
     } else {
         fail(SPMV_EINVAL, "unknown variant %d", variant);
     }

@@ -83,6 +83,8 @@ struct SellArgs {
     int slice_begin, slice_end, long_begin, long_end;
     double* long_part;       // partial sums of the pieces of cut rows
     int* long_cnt;           // per cut row: pieces done (zero between launches)
+    const int32_t* cta_off;  // nullptr: units round-robin over the warps; else
+                             // CTA b takes units [cta_off[b], cta_off[b + 1])
 };
 
 // Operands of one CSR product launch.
@@ -131,6 +133,11 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& s, int param, bool del
 cudaError_t launch_sell_delta(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
                               const int32_t* scol, int16_t* scol16, int* bad, int num_sms, cudaStream_t s);
 bool sell_param_supported(int param);
+// Params 2000 + p: the launch of param p with cost-balanced contiguous CTA
+// ranges (SellArgs::cta_off) instead of the round-robin split.
+inline bool sell_param_balanced(int param) { return param >= 2000; }
+// CTAs of a sliced launch of `units` work units.
+int sell_grid(int param, int units, int num_sms);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);
 TileGeom default_tile_geom();

@@ -118,6 +118,11 @@ struct spmv_part {
         int16_t* col16 = nullptr;         // column - row deltas (LOCAL only), once built
         double* long_part = nullptr;      // partial sums of cut long rows
         int* long_cnt = nullptr;          // pieces done per cut long row
+        std::vector<int32_t> h_slice_len; // per slice: its longest row's entries
+        std::vector<int32_t> h_long_len;  // per long-row piece: its entries
+        // balanced CTA ranges per launch site (rank p, or P for all ranks)
+        // and grid: key site << 32 | grid
+        std::map<int64_t, int32_t*> cta_split;
         int delta_state = 0;              // 0 not checked, 1 built, -1 some delta needs > 16 bits
         int64_t entries = 0;              // padded slots
         std::vector<int64_t> slice_off;   // P+1
@@ -165,6 +170,8 @@ void build_merge_tiles(spmv_part* pt);
 void build_warp_tiles(spmv_part* pt, int cap);
 void build_sell(spmv_part* pt);
 bool build_sell_delta16(spmv_part* pt);
+void build_sell_split(spmv_part* pt, int part_idx, int param);
+const int32_t* sell_split(const spmv_part* pt, int part_idx, int site, int grid);
 void* dev_alloc(spmv_part* pt, size_t bytes);
 void free_plan(spmv_part* pt);
 }  // namespace spmvk

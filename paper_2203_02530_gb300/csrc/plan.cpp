@@ -454,6 +454,10 @@ static int64_t build_sell_part(spmv_part* pt, spmv_part::SellPart& sp, const std
     }
     sp.slice_off[P] = (int64_t)slices.size();
     sp.long_off[P] = (int64_t)longs.size();
+    sp.h_slice_len.resize(slices.size());
+    for (size_t i = 0; i < slices.size(); ++i) sp.h_slice_len[i] = slices[i].len;
+    sp.h_long_len.resize(longs.size());
+    for (size_t i = 0; i < longs.size(); ++i) sp.h_long_len[i] = longs[i].k1 - longs[i].k0;
     sp.slices = upload(pt, slices);
     sp.longs = upload(pt, longs);
     sp.long_part = static_cast<double*>(dev_alloc(pt, (size_t)n_slots * sizeof(double)));
@@ -481,6 +485,50 @@ void build_sell(spmv_part* pt) {
     check_cuda(cudaDeviceSynchronize(), "sliced layout");
     pt->sell_entries = pt->sell[0].entries + pt->sell[1].entries;
     pt->sell_built = true;
+}
+
+// Cost-balanced CTA ranges of the sliced launches of part_idx (0 LOCAL, 1
+// REMOTE) at `param`, for every launch site: a site's units (its long-row
+// pieces, then its slices, the order the kernel numbers them) are cut into
+// sell_grid(...) contiguous ranges of about equal estimated cost, so each CTA
+// (and so each SM, which holds several) gets the same work and keeps the
+// neighbouring slices of the round-robin split together.  A unit's cost is
+// its entries per lane (a slice's longest row; a piece's entries over 32,
+// rounded up) plus 3 for its descriptor, row and store.
+void build_sell_split(spmv_part* pt, int part_idx, int param) {
+    spmv_part::SellPart& sp = pt->sell[part_idx];
+    const int P = pt->P;
+    for (int site = 0; site <= P; ++site) {
+        const int64_t lb = site < P ? sp.long_off[site] : 0, le = site < P ? sp.long_off[site + 1] : sp.long_off[P];
+        const int64_t sb = site < P ? sp.slice_off[site] : 0, se = site < P ? sp.slice_off[site + 1] : sp.slice_off[P];
+        const int units = (int)((le - lb) + (se - sb));
+        const int grid = sell_grid(param, units, pt->num_sms);
+        if (grid <= 0) continue;
+        const int64_t key = ((int64_t)site << 32) | grid;
+        if (sp.cta_split.count(key)) continue;
+        std::vector<double> prefix((size_t)units + 1, 0.0);
+        for (int u = 0; u < units; ++u) {
+            const int64_t c = u < le - lb ? 3 + (sp.h_long_len[(size_t)(lb + u)] + 31) / 32
+                                          : 3 + sp.h_slice_len[(size_t)(sb + u - (le - lb))];
+            prefix[(size_t)u + 1] = prefix[(size_t)u] + (double)c;
+        }
+        std::vector<int32_t> off((size_t)grid + 1);
+        const double total = prefix[(size_t)units];
+        for (int b = 0; b <= grid; ++b) {
+            const double target = total * b / grid;
+            off[(size_t)b] = (int32_t)(std::lower_bound(prefix.begin(), prefix.end(), target) - prefix.begin());
+        }
+        off[0] = 0;
+        off[(size_t)grid] = units;
+        for (int b = 1; b <= grid; ++b) off[(size_t)b] = std::max(off[(size_t)b], off[(size_t)b - 1]);
+        sp.cta_split[key] = upload(pt, off);
+    }
+}
+
+const int32_t* sell_split(const spmv_part* pt, int part_idx, int site, int grid) {
+    const spmv_part::SellPart& sp = pt->sell[part_idx];
+    auto it = sp.cta_split.find(((int64_t)site << 32) | grid);
+    return it == sp.cta_split.end() ? nullptr : it->second;
 }
 
 // 16-bit column deltas of the LOCAL sliced layout (built on first use);

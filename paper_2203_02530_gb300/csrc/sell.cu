@@ -79,6 +79,8 @@ __device__ __forceinline__ void sell_store(const CsrArgs& a, int row, double sum
 // per row, U entries per lane per step: U value and U column loads, then U
 // x gathers, then U FMAs, so each lane keeps U gathers in flight).  Long
 // rows come first so that the heaviest units start in the first wave.
+// With sa.cta_off the units are split into contiguous cost-balanced ranges
+// instead, one per CTA, whose 8 warps take the range round-robin.
 // CT = int32_t: slot columns are the CSR's (x index = xoff + column);
 // CT = int16_t: slot columns are deltas to the row (x index = row + delta),
 // half the index bytes where every |column - row| fits in 16 bits.
@@ -91,7 +93,13 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
     const int nwarps = (int)gridDim.x * 8;
     const int n_long = sa.long_end - sa.long_begin;
     const int n_units = n_long + (sa.slice_end - sa.slice_begin);
-    for (int u0 = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); u0 < n_units; u0 += nwarps) {
+    int u0 = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5), u_end = n_units, stride = nwarps;
+    if (sa.cta_off) {
+        u0 = __ldg(sa.cta_off + blockIdx.x) + (int)(threadIdx.x >> 5);
+        u_end = __ldg(sa.cta_off + blockIdx.x + 1);
+        stride = 8;
+    }
+    for (; u0 < u_end; u0 += stride) {
         if (u0 < n_long) {
             const SellLong L = sa.longs[sa.long_begin + u0];
             const int kb = L.k0, ke = L.k1;
@@ -252,27 +260,36 @@ cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const doubl
 }
 
 bool sell_param_supported(int param) {
-    return param == 4 || param == 8 || param == 9 || param == 104;
+    const int base = param >= 2000 ? param - 2000 : param;
+    return base == 4 || base == 8 || base == 9 || base == 104;
+}
+
+int sell_grid(int param, int units, int num_sms) {
+    int blocks_per_sm = 0;
+    switch (param % 1000) {
+        case 4: blocks_per_sm = 8; break;
+        case 8: blocks_per_sm = 4; break;
+        case 9: blocks_per_sm = 4; break;
+        case 104: blocks_per_sm = 6; break;
+        default: return 0;
+    }
+    if (units <= 0) return 0;
+    int grid = num_sms * blocks_per_sm;
+    if (grid > (units + 7) / 8) grid = (units + 7) / 8;
+    return grid;
 }
 
 cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, bool delta16, int num_sms,
                         cudaStream_t st) {
     const int units = (sa.long_end - sa.long_begin) + (sa.slice_end - sa.slice_begin);
     if (units <= 0) return cudaSuccess;
-    int blocks_per_sm = 8;
-    switch (param) {
-        case 4: blocks_per_sm = 8; break;
-        case 8: blocks_per_sm = 4; break;
-        case 9: blocks_per_sm = 4; break;
-        case 104: blocks_per_sm = 6; break;
-        default: return cudaErrorInvalidValue;
-    }
-    int grid = num_sms * blocks_per_sm;
-    if (grid > (units + 7) / 8) grid = (units + 7) / 8;
+    const int grid = sell_grid(param, units, num_sms);
+    if (grid <= 0) return cudaErrorInvalidValue;
+    if (sell_param_balanced(param) != (sa.cta_off != nullptr)) return cudaErrorInvalidValue;
 #define SELL_LAUNCH(u, b)                                                              \
     (delta16 ? (csr_sell_kernel<u, b, int16_t><<<grid, 256, 0, st>>>(a, sa), 0)        \
              : (csr_sell_kernel<u, b, int32_t><<<grid, 256, 0, st>>>(a, sa), 0))
-    switch (param) {
+    switch (param % 1000) {
         case 4: SELL_LAUNCH(4, 8); break;
         case 8: SELL_LAUNCH(8, 4); break;
         case 9: SELL_LAUNCH(9, 4); break;

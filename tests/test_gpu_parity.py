@@ -68,7 +68,7 @@ def case(name):
 
 VARIANTS = ([("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)]
             + [("pairs", v) for v in (1, 2, 4, 8, 102, 104)] + [("warp", g) for g in range(5)]
-            + [("merge", 0)] + [("sell", u) for u in (4, 8, 9, 104)])
+            + [("merge", 0)] + [("sell", u) for u in (4, 8, 9, 104, 2004, 2009, 2104)])
 
 SELL_LONG = 64
 
@@ -231,7 +231,7 @@ def test_sliced_layout_matches_thread_per_row_bit_for_bit(name):
     s = torch.cuda.Stream()
     x_d = dev(x)
     out = []
-    for v in (("warp", 0), ("sell", 4), ("sell", 9), ("sell", 104)):
+    for v in (("warp", 0), ("sell", 4), ("sell", 9), ("sell", 104), ("sell", 2008), ("sell", 2104)):
         y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
         with make_part(n, rp, ci, va, P) as part:
             set_variant(part, v)
@@ -299,13 +299,13 @@ def _lengths_matrix(lens, seed):
 @pytest.mark.parametrize("lens_kind", ["all_long", "edge_64_65", "long_and_empty", "one_long_in_natural",
                                        "cut_rows"])
 @pytest.mark.parametrize("gran", [0, 1])
-@pytest.mark.parametrize("param", [4, 104])
+@pytest.mark.parametrize("param", [4, 2104])
 def test_sliced_layout_edge_cases(lens_kind, gran, param):
     """Rows at and around the 64-entry long-row threshold, ranks made of long
     rows only, empty rows among long ones, a single long row inside a
     natural-order rank (a hole in its slice), and rows cut into 512-entry
-    pieces, coarse and per rank, at two launch shapes; twice, so the pieces'
-    counters are reset."""
+    pieces, coarse and per rank, with round-robin and cost-balanced CTA
+    ranges; twice, so the pieces' counters are reset."""
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
     rng = np.random.default_rng(31)
@@ -493,7 +493,7 @@ def test_per_segment_granularity(name, variant):
 @pytest.mark.parametrize("name,variant", [("st27_ragged", ("tile", 0)), ("powerlaw", ("merge", 0)),
                                           ("powerlaw", ("tile", 2)), ("band", ("vector", 4)),
                                           ("powerlaw", ("sell", 4)), ("dense_row", ("sell", 9)),
-                                          ("powerlaw", ("sell", 104)), ("dense_row", ("sell", 8))])
+                                          ("powerlaw", ("sell", 2104)), ("dense_row", ("sell", 2008))])
 def test_per_partition_schedules_give_identical_y(name, variant):
     from paper_2203_02530_gb300 import spmv
     from paper_2203_02530_gb300 import schedules as E
@@ -697,8 +697,9 @@ def test_full_size_powerlaw_4M_per_partition():
 
 def test_full_size_powerlaw_4M_sliced_schedules():
     """The power-law n = 4M, P = 8 per-rank DAG in the form the benchmark
-    times: sliced products (LOCAL and REMOTE at several launch shapes,
-    chosen separately), random 4-stream schedules captured as graphs and
+    times: sliced products (LOCAL and REMOTE at several launch shapes, with
+    round-robin and cost-balanced CTA ranges, chosen separately), random
+    4-stream schedules captured as graphs and
     replayed twice: y bit-identical across variants, schedules and replays,
     and equal to the oracle in full."""
     from paper_2203_02530_gb300 import spmv
@@ -715,7 +716,7 @@ def test_full_size_powerlaw_4M_sliced_schedules():
     with make_part(n, rp, ci, va, 8, spmv.PER_PARTITION) as part:
         del ci, va
         dag = E.Dag(part.n_ops, part.dag())
-        for lp, rp_ in ((8, 104), (9, 9), (4, 8)):
+        for lp, rp_ in ((8, 104), (2008, 2104), (2004, 9)):
             part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, lp)
             part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_SELL, rp_)
             order, smap = _random_schedule(dag, 4, rng)
@@ -736,7 +737,8 @@ def test_full_size_powerlaw_4M_sliced_schedules():
 def test_full_size_27pt_150_benchmark_variants():
     """The 27-point stencil 150^3, P = 4, with the products the benchmark
     tunes between: LOCAL in 16-bit-delta or 32-bit sliced form, REMOTE by
-    pairs or sliced; the best schedule's shape
+    pairs or sliced, round-robin or with balanced CTA ranges; the best
+    schedule's shape
     (LOCAL on its own stream) captured and replayed: y equal to the oracle
     in full, and bit-identical across the sliced variants."""
     from paper_2203_02530_gb300 import spmv
@@ -751,8 +753,8 @@ def test_full_size_27pt_150_benchmark_variants():
     with make_part(n, rp, ci, va, 4) as part:
         del ci, va
         for (lv, lp), (rv, rpar) in (((spmv.VARIANT_SELL16, 9), (spmv.VARIANT_PAIRS, 1)),
-                                     ((spmv.VARIANT_SELL16, 4), (spmv.VARIANT_SELL, 104)),
-                                     ((spmv.VARIANT_SELL, 8), (spmv.VARIANT_SELL, 4))):
+                                     ((spmv.VARIANT_SELL16, 2009), (spmv.VARIANT_SELL, 104)),
+                                     ((spmv.VARIANT_SELL, 8), (spmv.VARIANT_SELL, 2004))):
             part.set_op_variant(spmv.OP_LOCAL, lv, lp)
             part.set_op_variant(spmv.OP_REMOTE, rv, rpar)
             order, smap = [0, 2, 1, 3], [0, 1, 0, 0]   # pack, copy, remote on 0; local on 1
