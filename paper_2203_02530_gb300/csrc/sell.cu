@@ -71,14 +71,38 @@ __device__ __forceinline__ void sell_store(const CsrArgs& a, int row, double sum
     }
 }
 
+// K consecutive slots j .. j + K - 1 of a slice lane: K value and K column
+// loads, then K x gathers, then K FMAs in slot order (slots at or past the
+// lane's row length discarded by a select).
+template <int K, typename CT>
+__device__ __forceinline__ void sell_round(const CT* cp, const double* vp, const double* xb, int j, int len,
+                                           double& sum, uint64_t pol_stream, uint64_t pol_keep) {
+    int32_t c[K];
+    double v[K], xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        c[u] = ld_stream(cp + 32 * (j + u), pol_stream);
+        v[u] = ld_stream(vp + 32 * (j + u), pol_stream);
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) xv[u] = ld_keep(xb + c[u], pol_keep);
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const double t = fma(v[u], xv[u], sum);
+        sum = (j + u < len) ? t : sum;
+    }
+}
+
 }  // namespace
 
 // One warp per work unit, grid-stride: units [0, n_long) are the launch's
 // long rows (each summed by the whole warp: lane l takes entries l, l+32,
 // ... in order, then a fixed xor-butterfly), the rest its slices (one lane
 // per row, U entries per lane per step: U value and U column loads, then U
-// x gathers, then U FMAs, so each lane keeps U gathers in flight).  Long
-// rows come first so that the heaviest units start in the first wave.
+// x gathers, then U FMAs, so each lane keeps U gathers in flight; the slots
+// past the last full step go in rounds of 4, 2 and 1, the long rows' last
+// entries in a round of 2 and 1).  Long rows come first so that the
+// heaviest units start in the first wave.
 // With sa.cta_off the units are split into contiguous cost-balanced ranges
 // instead, one per CTA, whose 8 warps take the range round-robin.
 // CT = int32_t: slot columns are the CSR's (x index = xoff + column);
@@ -116,7 +140,15 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
 #pragma unroll
                 for (int u = 0; u < 4; ++u) part = fma(v[u], xv[u], part);
             }
-            for (; k < ke; k += 32)
+            if (k + 32 < ke) {   // at most 3 entries of this lane left: two, then one
+                const double v0 = ld_stream(a.val + k, pol_stream), v1 = ld_stream(a.val + k + 32, pol_stream);
+                const int c0 = ld_stream(a.col + k, pol_stream), c1 = ld_stream(a.col + k + 32, pol_stream);
+                const double x0 = ld_keep(xb + c0, pol_keep), x1 = ld_keep(xb + c1, pol_keep);
+                part = fma(v0, x0, part);
+                part = fma(v1, x1, part);
+                k += 64;
+            }
+            if (k < ke)
                 part = fma(ld_stream(a.val + k, pol_stream), ld_keep(xb + ld_stream(a.col + k, pol_stream), pol_keep),
                            part);
 #pragma unroll
@@ -157,28 +189,17 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
         const double* xb = kDelta ? a.x + row : a.x + d.xoff;
         double sum = 0.0;
         int j = 0;
-        for (; j + U <= d.len; j += U) {
-            int32_t c[U];
-            double v[U], xv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                c[u] = ld_stream(cp + 32 * (j + u), pol_stream);
-                v[u] = ld_stream(vp + 32 * (j + u), pol_stream);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = ld_keep(xb + c[u], pol_keep);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const double t = fma(v[u], xv[u], sum);
-                sum = (j + u < len) ? t : sum;
-            }
+        for (; j + U <= d.len; j += U) sell_round<U>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
+        // the last d.len mod U slots in rounds of 4, 2 and 1 (each round one
+        // load-then-gather latency), not one slot at a time: short slices,
+        // the common case on skewed rows, keep several gathers in flight
+        if (U > 4)
+            for (; j + 4 <= d.len; j += 4) sell_round<4>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
+        if (U > 2 && j + 2 <= d.len) {   // at most 3 slots left here
+            sell_round<2>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
+            j += 2;
         }
-        for (; j < d.len; ++j) {
-            const int32_t c = ld_stream(cp + 32 * j, pol_stream);
-            const double v = ld_stream(vp + 32 * j, pol_stream);
-            const double t = fma(v, ld_keep(xb + c, pol_keep), sum);
-            sum = (j < len) ? t : sum;
-        }
+        for (; j < d.len; ++j) sell_round<1>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
         if (store) sell_store(a, row, sum);
     }
 }
