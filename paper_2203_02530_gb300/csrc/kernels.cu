@@ -112,23 +112,40 @@ __device__ __forceinline__ void store_row(const CsrArgs& a, int row, double sum)
 
 // ------------------------------------------------------------------------
 // Pack: dst[k] = x[idx[k]] for every slot k (pos == nullptr) or for the
-// slots listed in pos[0..count).
+// slots listed in pos[0..count).  A thread takes kPackIlp slots a grid
+// stride apart per step: their index loads, then their gathers, then their
+// stores, so kPackIlp index-then-gather chains are in flight at once.
 // ------------------------------------------------------------------------
+constexpr int kPackIlp = 4;
+
 __global__ void __launch_bounds__(256) gather_kernel(const double* __restrict__ x,
                                                      const int32_t* __restrict__ idx,
                                                      const int32_t* __restrict__ pos,
                                                      double* __restrict__ dst, int64_t count) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const int64_t k = pos ? (int64_t)__ldg(pos + i) : i;
-        dst[k] = __ldg(x + __ldg(idx + k));
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += kPackIlp * stride) {
+        int64_t k[kPackIlp];
+        int32_t c[kPackIlp];
+        double v[kPackIlp];
+#pragma unroll
+        for (int u = 0; u < kPackIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            k[u] = i < count ? (pos ? (int64_t)__ldg(pos + i) : i) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kPackIlp; ++u) c[u] = k[u] >= 0 ? __ldg(idx + k[u]) : 0;
+#pragma unroll
+        for (int u = 0; u < kPackIlp; ++u) v[u] = k[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPackIlp; ++u)
+            if (k[u] >= 0) dst[k[u]] = v[u];
     }
 }
 
 cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* pos,
                           double* dst, int64_t count, int num_sms, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    int64_t blocks = (count + 255) / 256;
+    int64_t blocks = (count + 256 * kPackIlp - 1) / (256 * kPackIlp);
     const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     gather_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, idx, pos, dst, count);
@@ -136,7 +153,8 @@ cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* po
 }
 
 // ------------------------------------------------------------------------
-// Halo exchange: dst[0..count) = src[0..count)
+// Halo exchange: dst[0..count) = src[0..count).  Aligned: 16-byte pairs,
+// kPackIlp loads in flight per thread before their stores.
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ src,
                                                    double* __restrict__ dst, int64_t count) {
@@ -146,8 +164,15 @@ __global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ sr
         const int64_t pairs = count >> 1;
         const double2* s2 = reinterpret_cast<const double2*>(src);
         double2* d2 = reinterpret_cast<double2*>(dst);
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += stride)
-            d2[i] = __ldg(s2 + i);
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < pairs; i0 += kPackIlp * stride) {
+            double2 t[kPackIlp];
+#pragma unroll
+            for (int u = 0; u < kPackIlp; ++u)
+                if (i0 + u * stride < pairs) t[u] = __ldg(s2 + i0 + u * stride);
+#pragma unroll
+            for (int u = 0; u < kPackIlp; ++u)
+                if (i0 + u * stride < pairs) d2[i0 + u * stride] = t[u];
+        }
         if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) dst[count - 1] = src[count - 1];
     } else {
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
@@ -158,7 +183,7 @@ __global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ sr
 cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_sms,
                         cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    int64_t blocks = (count / 2 + 255) / 256;
+    int64_t blocks = (count / 2 + 256 * kPackIlp - 1) / (256 * kPackIlp);
     if (blocks < 1) blocks = 1;
     const int64_t cap = (int64_t)num_sms * 4;
     if (blocks > cap) blocks = cap;
