@@ -524,14 +524,21 @@ def run_batched(args, world, rank, local):
 
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def e2e():   # through the library: chunked x in, products, y out, overlapped
-        spmv.spmv_batch_run_host(b.h, xh, yh, 8, s_in, s, s_out)
+    def e2e(chunks):   # through the library: chunked x in, products, y out, overlapped
+        spmv.spmv_batch_run_host(b.h, xh, yh, chunks, s_in, s, s_out)
 
-    e2e()
+    chunk_t = {}
+    for c in (8, 16, 32):   # the chunk count: finer chunks shorten the pipeline's fill and drain
+        e2e(c)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            e2e(c)
+        chunk_t[c] = (time.perf_counter() - t0) / 3
+    n_chunks = min(chunk_t, key=chunk_t.get)
     k_e2e = max(5, min(args.steps, 50))
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        e2e()
+        e2e(n_chunks)
     t_e2e = (time.perf_counter() - t0) / k_e2e
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -579,7 +586,8 @@ def run_batched(args, world, rank, local):
                        "measurements": len(meas), "protocol": "0.01 s of samples each"},
         "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
-                "ms_per_step": round(t_e2e * 1e3, 4), "path": "spmv_batch_run_host, 8 chunks"},
+                "ms_per_step": round(t_e2e * 1e3, 4), "path": "spmv_batch_run_host, %d chunks" % n_chunks,
+                "chunk_sweep_ms": {str(c): round(t * 1e3, 4) for c, t in sorted(chunk_t.items())}},
         "cpu_baseline": cpu, "clocks": clocks,
         "autotune_us": {k: round(t * 1e6, 1) for k, t in tune_log},
         "gpu_launches": args.steps * launches,

@@ -277,14 +277,17 @@ int spmv_apply_host(spmv_part* part, int64_t graph_handle, const double* x_host,
 /*
  * The same end-to-end product with the transfers overlapped: x_host's row
  * blocks are copied in one by one on copy_stream, rank p's LOCAL product
- * starts on compute_stream as soon as block p has arrived (it reads no other
- * x), then PACK, COPY and REMOTE for every rank follow on compute_stream.
- * y comes back on copy_stream in two parts: each rank's longest run of rows
- * without remote entries as soon as its LOCAL product is done (those rows
- * are final then), the remaining rows after REMOTE.  Returns after y has
- * arrived.  The two streams must differ.  Same y as the graph path, bit for
- * bit (the same kernels on the same rows).  Plan-owned device vectors as
- * above.
+ * starts as soon as block p has arrived (it reads no other x), on
+ * compute_stream for even p and on a plan-owned second stream for odd p (so
+ * consecutive ranks' launches overlap), then PACK, COPY and REMOTE for every
+ * rank follow on compute_stream.
+ * y comes back in two parts on a plan-owned stream of its own (so the copies
+ * out overlap the copies in, the link's two directions): each rank's longest
+ * run of rows without remote entries as soon as its LOCAL product is done
+ * (those rows are final then), the remaining rows after REMOTE.  Returns
+ * after y has arrived.  The two streams must differ.  Same y as the graph
+ * path, bit for bit (the same kernels on the same rows).  Plan-owned device
+ * vectors as above.
  */
 int spmv_apply_host_pipelined(spmv_part* part, const double* x_host, double* y_host,
                               cudaStream_t copy_stream, cudaStream_t compute_stream);

@@ -791,6 +791,9 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
         check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         pt->io_ev.push_back(e);
     }
+    if (!pt->io_out) check_cuda(cudaStreamCreateWithFlags(&pt->io_out, cudaStreamNonBlocking), "stream");
+    if (!pt->io_alt) check_cuda(cudaStreamCreateWithFlags(&pt->io_alt, cudaStreamNonBlocking), "stream");
+    cudaStream_t out_stream = pt->io_out;
     if (pt->io_free.empty()) {   // once per plan: the remote-free run of every rank
         std::vector<int32_t> rr((size_t)pt->n_rr);
         if (pt->n_rr)
@@ -821,35 +824,44 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
                        "copy x in");
         check_cuda(cudaEventRecord(pt->io_ev[p], copy_stream), "event");
     }
+    // The LOCAL products alternate between compute_stream and a second
+    // stream, so that one rank's launch fills the SMs the previous one leaves
+    // idle at its tail.
     for (int p = 0; p < P; ++p) {
-        check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[p], 0), "wait");
-        launches += op_local(pt, p, pt->io_x, pt->io_y, compute_stream);
-        check_cuda(cudaEventRecord(pt->io_ev[P + p], compute_stream), "event");
+        cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
+        check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[p], 0), "wait");
+        launches += op_local(pt, p, pt->io_x, pt->io_y, cs);
+        check_cuda(cudaEventRecord(pt->io_ev[P + p], cs), "event");
     }
-    // the rest of the DAG needs all of x: pack, exchange, remote products
+    // the rest of the DAG needs all of x (pack, exchange) and every LOCAL
+    // product (the remote products accumulate into y)
+    check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[P - 1], 0), "wait");
     launches += op_pack(pt, -1, pt->io_x, compute_stream);
     launches += op_copy(pt, -1, compute_stream);
+    for (int p = 1; p < P; p += 2) check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[P + p], 0), "wait");
     launches += op_remote(pt, -1, pt->io_y, compute_stream);
     check_cuda(cudaEventRecord(pt->io_ev[2 * P], compute_stream), "event");
-    // y: each rank's remote-free run as soon as its LOCAL product is done
+    // y on a stream of its own, so that it overlaps the copies in: each
+    // rank's remote-free run as soon as its LOCAL product is done
     // (overlapping the other ranks' products), the rest after REMOTE
     auto copy_out = [&](int64_t a, int64_t b) {
         if (b > a)
             check_cuda(cudaMemcpyAsync(y_host + a, pt->io_y + a, (size_t)(b - a) * sizeof(double),
-                                       cudaMemcpyDeviceToHost, copy_stream),
+                                       cudaMemcpyDeviceToHost, out_stream),
                        "copy y out");
     };
     for (int p = 0; p < P; ++p) {
-        check_cuda(cudaStreamWaitEvent(copy_stream, pt->io_ev[P + p], 0), "wait");
+        check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[P + p], 0), "wait");
         copy_out(pt->io_free[p].first, pt->io_free[p].second);
     }
-    check_cuda(cudaStreamWaitEvent(copy_stream, pt->io_ev[2 * P], 0), "wait");
+    check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[2 * P], 0), "wait");
     int64_t from = 0;
     for (int p = 0; p < P; ++p) {
         copy_out(from, pt->io_free[p].first);
         from = std::max(from, pt->io_free[p].second);
     }
     copy_out(from, pt->n);
+    check_cuda(cudaStreamSynchronize(out_stream), "synchronize");
     check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
     pt->last_launches = launches;
     API_CATCH

@@ -76,6 +76,8 @@ struct spmv_part {
     double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
     double* io_y = nullptr;
     std::vector<cudaEvent_t> io_ev;   // 2P+1: x block p arrived; LOCAL p done; products done
+    cudaStream_t io_out = nullptr;    // the host path's copies of y out
+    cudaStream_t io_alt = nullptr;    // the host path's second stream for LOCAL products
     // per rank: the longest run [a, b) of rows without remote entries (final
     // after the rank's LOCAL product; the host path copies it out early)
     std::vector<std::pair<int64_t, int64_t>> io_free;

@@ -81,6 +81,10 @@ void free_plan(spmv_part* pt) {
     for (cudaEvent_t e : pt->io_ev)
         if (e) cudaEventDestroy(e);
     pt->io_ev.clear();
+    if (pt->io_out) cudaStreamDestroy(pt->io_out);
+    if (pt->io_alt) cudaStreamDestroy(pt->io_alt);
+    pt->io_out = nullptr;
+    pt->io_alt = nullptr;
     pt->op_ev.clear();
     pt->join_ev.clear();
     pt->fork_ev = nullptr;
