@@ -11,6 +11,7 @@
 // shuffle reductions.  Every row is summed by one thread in storage order,
 // so results do not depend on the grid, the stream or the schedule.
 #include "internal.h"
+#include "pdl.cuh"
 
 #include <cuda_runtime.h>
 
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const double* __restrict__ 
                                                      const int32_t* __restrict__ idx,
                                                      const int32_t* __restrict__ pos,
                                                      double* __restrict__ dst, int64_t count) {
+    pdl_wait();      // the previous kernel of this stream is done
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += kPackIlp * stride) {
         int64_t k[kPackIlp];
@@ -148,8 +150,7 @@ cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* po
     int64_t blocks = (count + 256 * kPackIlp - 1) / (256 * kPackIlp);
     const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
-    gather_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, idx, pos, dst, count);
-    return cudaGetLastError();
+    return launch_pdl(gather_kernel, dim3((unsigned)blocks), dim3(256), 0, s, x, idx, pos, dst, count);
 }
 
 // ------------------------------------------------------------------------
@@ -158,6 +159,7 @@ cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* po
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ src,
                                                    double* __restrict__ dst, int64_t count) {
+    pdl_wait();      // the previous kernel of this stream is done
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     if (vec) {
@@ -187,8 +189,7 @@ cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_s
     if (blocks < 1) blocks = 1;
     const int64_t cap = (int64_t)num_sms * 4;
     if (blocks > cap) blocks = cap;
-    copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, count);
-    return cudaGetLastError();
+    return launch_pdl(copy_kernel, dim3((unsigned)blocks), dim3(256), 0, s, src, dst, count);
 }
 
 // ------------------------------------------------------------------------
@@ -217,6 +218,7 @@ struct TileLayout {
 template <int NT, int CAP, int ST, int CH, int LANES>
 __global__ void __launch_bounds__(NT, 1) csr_tile_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                       int tile_begin, int tile_end) {
+    pdl_wait();      // the previous kernel of this stream is done
     static_assert(LANES == 1 || LANES == 2 || LANES == 4, "lanes per row");
     using L = TileLayout<NT / LANES, CAP>;
     const uint64_t pol_stream = policy_evict_first();
@@ -381,8 +383,7 @@ static cudaError_t run_tile(const CsrArgs& a, const Tile* tiles, int tb, int te,
     const int n_tiles = te - tb;
     int grid = num_sms * occ;
     if (grid > n_tiles) grid = n_tiles;
-    csr_tile_kernel<NT, CAP, ST, CH, LANES><<<grid, NT, smem, s>>>(a, tiles, tb, te);
-    return cudaGetLastError();
+    return launch_pdl(csr_tile_kernel<NT, CAP, ST, CH, LANES>, dim3(grid), dim3(NT), smem, s, a, tiles, tb, te);
 }
 
 template <int NT, int CAP, int ST, int CH, int LANES>
@@ -450,6 +451,7 @@ cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin, int
 template <int V>
 __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                          int tile_begin, int tile_end) {
+    pdl_wait();      // the previous kernel of this stream is done
     constexpr int GROUPS = 256 / V;
     const uint64_t pol_keep = policy_evict_last();
     const int lane = threadIdx.x % V;
@@ -501,6 +503,7 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* 
 template <int WARPS, int CAP, int ST, int CH>
 __global__ void __launch_bounds__(WARPS * 32, 1) csr_warp_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                                 int tile_begin, int tile_end) {
+    pdl_wait();      // the previous kernel of this stream is done
     using L = TileLayout<32, CAP>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[WARPS][ST];
@@ -632,8 +635,7 @@ static cudaError_t run_warp(const CsrArgs& a, const Tile* tiles, int tb, int te,
     int grid = num_sms * occ;
     const int need = (te - tb + WARPS - 1) / WARPS;
     if (grid > need) grid = need;
-    csr_warp_kernel<WARPS, CAP, ST, CH><<<grid, WARPS * 32, smem, s>>>(a, tiles, tb, te);
-    return cudaGetLastError();
+    return launch_pdl(csr_warp_kernel<WARPS, CAP, ST, CH>, dim3(grid), dim3(WARPS * 32), smem, s, a, tiles, tb, te);
 }
 
 // Warp-tile geometries: (warps per CTA, entries per stage, stages, gathers per chunk).
@@ -674,6 +676,7 @@ cudaError_t launch_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int
 template <int V, int U, int MINB>
 __global__ void __launch_bounds__(256, MINB) csr_pair_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                           int tile_begin, int tile_end) {
+    pdl_wait();      // the previous kernel of this stream is done
     constexpr int GROUPS = 256 / V;
     const uint64_t pol_keep = policy_evict_last();
     const int lane = threadIdx.x % V;
@@ -733,16 +736,17 @@ cudaError_t launch_pairs(const CsrArgs& a, const Tile* tiles, int tile_begin, in
     // lanes 1/2/4/8: 4 pairs in flight per lane (up to 64 registers);
     // 102/104: 2 or 4 lanes with 2 pairs in flight in 32 registers, so 8
     // CTAs (64 warps) fit on an SM
+    cudaError_t e = cudaSuccess;
     switch (lanes) {
-        case 1: csr_pair_kernel<1, 4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 2: csr_pair_kernel<2, 4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 4: csr_pair_kernel<4, 4, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 8: csr_pair_kernel<8, 2, 4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 102: csr_pair_kernel<2, 2, 8><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 104: csr_pair_kernel<4, 2, 8><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 1: e = launch_pdl(csr_pair_kernel<1, 4, 4>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 2: e = launch_pdl(csr_pair_kernel<2, 4, 4>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 4: e = launch_pdl(csr_pair_kernel<4, 4, 4>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 8: e = launch_pdl(csr_pair_kernel<8, 2, 4>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 102: e = launch_pdl(csr_pair_kernel<2, 2, 8>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 104: e = launch_pdl(csr_pair_kernel<4, 2, 8>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
@@ -750,15 +754,16 @@ cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, i
     if (tile_end <= tile_begin) return cudaSuccess;
     int grid = num_sms * 8;
     if (grid > tile_end - tile_begin) grid = tile_end - tile_begin;
+    cudaError_t e = cudaSuccess;
     switch (lanes) {
-        case 2: csr_vector_kernel<2><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 4: csr_vector_kernel<4><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 8: csr_vector_kernel<8><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 16: csr_vector_kernel<16><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
-        case 32: csr_vector_kernel<32><<<grid, 256, 0, s>>>(a, tiles, tile_begin, tile_end); break;
+        case 2: e = launch_pdl(csr_vector_kernel<2>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 4: e = launch_pdl(csr_vector_kernel<4>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 8: e = launch_pdl(csr_vector_kernel<8>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 16: e = launch_pdl(csr_vector_kernel<16>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
+        case 32: e = launch_pdl(csr_vector_kernel<32>, dim3(grid), dim3(256), 0, s, a, tiles, tile_begin, tile_end); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 // ------------------------------------------------------------------------

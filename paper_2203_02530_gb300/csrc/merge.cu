@@ -11,6 +11,7 @@
 // per-tile carry that a second kernel adds in tile order.  No atomics and no
 // data-dependent order: results depend only on the matrix.
 #include "internal.h"
+#include "pdl.cuh"
 
 #include <cuda_runtime.h>
 
@@ -114,6 +115,7 @@ template <bool GUARD>
 __global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const MergeTile* __restrict__ tiles,
                                                          int tile_begin, int tile_end,
                                                          Carry* __restrict__ carries) {
+    pdl_wait();      // the previous kernel of this stream is done
     using L = MergeLayout;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[MERGE_ST];
@@ -319,6 +321,7 @@ __global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const Mer
 // carrying the same row sums the run in tile order and adds it once.
 __global__ void __launch_bounds__(256) merge_fixup_kernel(CsrArgs a, const Carry* __restrict__ carries,
                                                           int tile_begin, int tile_end) {
+    pdl_wait();      // the previous kernel of this stream is done
     const int t = tile_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (t >= tile_end) return;
     const Carry c = carries[t];
@@ -377,8 +380,8 @@ static cudaError_t run_merge(const CsrArgs& a, const MergeTile* tiles, int tile_
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int grid = num_sms * occ;
     if (grid > tile_end - tile_begin) grid = tile_end - tile_begin;
-    merge_kernel<GUARD><<<grid, MERGE_NT, smem, s>>>(a, tiles, tile_begin, tile_end, carries);
-    return cudaGetLastError();
+    return launch_pdl(merge_kernel<GUARD>, dim3(grid), dim3(MERGE_NT), smem, s, a, tiles, tile_begin, tile_end,
+                      carries);
 }
 
 cudaError_t launch_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begin, int tile_end,
@@ -388,8 +391,7 @@ cudaError_t launch_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begi
                               : run_merge<false>(a, tiles, tile_begin, tile_end, carries, num_sms, s);
     if (e != cudaSuccess) return e;
     const int n = tile_end - tile_begin;
-    merge_fixup_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, carries, tile_begin, tile_end);
-    return cudaGetLastError();
+    return launch_pdl(merge_fixup_kernel, dim3((n + 255) / 256), dim3(256), 0, s, a, carries, tile_begin, tile_end);
 }
 
 cudaError_t launch_merge_partition(const int32_t* ptr, int row_begin, int row_end, int32_t xoff,

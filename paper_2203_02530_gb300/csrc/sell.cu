@@ -22,6 +22,7 @@
 // per entry from 0.0; padded slots are discarded by a select, so y equals
 // that of the other one-thread-per-row kernels bit for bit.
 #include "internal.h"
+#include "pdl.cuh"
 
 #include <cuda_runtime.h>
 
@@ -110,6 +111,7 @@ __device__ __forceinline__ void sell_round(const CT* cp, const double* vp, const
 // half the index bytes where every |column - row| fits in 16 bits.
 template <int U, int MINB, typename CT>
 __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs sa) {
+    pdl_wait();      // the previous kernel of this stream is done
     constexpr bool kDelta = sizeof(CT) == 2;
     const uint64_t pol_stream = sell_policy_evict_first();
     const uint64_t pol_keep = sell_policy_evict_last();
@@ -307,17 +309,19 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, bool de
     const int grid = sell_grid(param, units, num_sms);
     if (grid <= 0) return cudaErrorInvalidValue;
     if (sell_param_balanced(param) != (sa.cta_off != nullptr)) return cudaErrorInvalidValue;
-#define SELL_LAUNCH(u, b)                                                              \
-    (delta16 ? (csr_sell_kernel<u, b, int16_t><<<grid, 256, 0, st>>>(a, sa), 0)        \
-             : (csr_sell_kernel<u, b, int32_t><<<grid, 256, 0, st>>>(a, sa), 0))
+#define SELL_LAUNCH(u, b)                                                                   \
+    e = delta16 ? launch_pdl(csr_sell_kernel<u, b, int16_t>, dim3(grid), dim3(256), 0, st, a, sa) \
+                : launch_pdl(csr_sell_kernel<u, b, int32_t>, dim3(grid), dim3(256), 0, st, a, sa)
+    cudaError_t e = cudaSuccess;
     switch (param % 1000) {
         case 4: SELL_LAUNCH(4, 8); break;
         case 8: SELL_LAUNCH(8, 4); break;
         case 9: SELL_LAUNCH(9, 4); break;
         case 104: SELL_LAUNCH(4, 6); break;
+        default: return cudaErrorInvalidValue;
     }
 #undef SELL_LAUNCH
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace spmvk
