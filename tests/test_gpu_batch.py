@@ -146,3 +146,37 @@ def test_batch_run_host_matches_device_run(chunks):
             spmv.spmv_batch_run_host(b.h, xh, yh, chunks, s_c, s_c, s_out)
         with pytest.raises(spmv.SpmvError):
             spmv.spmv_batch_run_host(b.h, xh, yh, 0, s_in, s_c, s_out)
+
+
+def test_full_size_batch_mix_256_sliced():
+    """The benchmark's batch (256 matrices, n log-uniform in [1e3, 1e6],
+    5-point / 7-point / Zipf rows, 4.19 GB) in the sliced layout the tuner
+    picks: the persistent launch gives the oracle's y in full, bit-identical
+    to one launch per matrix and to the chunked host-buffer path, twice."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = [m for _, m in W.batch_mix(256, seed=5)]
+    with spmv.Batch(mats) as b:
+        offs = b.offsets()
+        spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        x = W.uniform_x(offs[-1], seed=6)
+        want, scale = _oracle(mats, x, offs)
+        del mats
+        s, s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        x_d = dev(x)
+        y1 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
+        y2 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
+        spmv.spmv_batch_run(b.h, x_d, y1, s)
+        spmv.spmv_batch_run_separate(b.h, -1, x_d, y2, s)
+        s.synchronize()
+        a1 = y1.cpu().numpy()
+        assert np.array_equal(a1, y2.cpu().numpy()), "batched and separate launches differ"
+        assert_fp64_close(a1, want, scale, "batch mix 256 sliced")
+        y1.fill_(float("nan"))
+        spmv.spmv_batch_run(b.h, x_d, y1, s)
+        s.synchronize()
+        assert np.array_equal(y1.cpu().numpy(), a1)
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.full((offs[-1],), float("nan"), dtype=torch.float64).pin_memory()
+        spmv.spmv_batch_run_host(b.h, xh, yh, 16, s_in, s, s_out)
+        assert np.array_equal(yh.numpy(), a1)

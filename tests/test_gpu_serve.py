@@ -182,3 +182,42 @@ def test_serving_empty_and_one_row_matrices(layout):
                     want = oracle.csr_spmv(n, rp, ci, va, X[:, j])
                     scale = oracle.csr_absdot(n, rp, ci, va, X[:, j])
                     assert_fp64_close(Y[:, j], want, scale, "request %d column %d" % (r, j))
+
+
+def test_full_size_serving_mix_sampled():
+    """The benchmark's serving mix (64 resident matrices, 1.3 GB, sliced
+    layout, 32 stream slots, 40 GB budget) under a burst of 3000 requests:
+    grouped and plain serving give the same hash for every request, and
+    sampled requests run alone match their hash and the oracle column by
+    column."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = [m for _, m in W.serve_mix(64, seed=6)]
+    rng = np.random.default_rng(8)
+    count = 3000
+    mat = rng.integers(0, len(mats), size=count).astype(np.int32)
+    wid = rng.integers(1, 9, size=count).astype(np.int32)
+    sd = rng.integers(0, 2**63, size=count, dtype=np.uint64)
+    with spmv.Batch(mats) as b:
+        spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        with spmv.Server(b, n_streams=32, budget_bytes=40 << 30) as sv:
+            _, h_b, st_b = sv.run(mat, wid, sd, np.zeros(count), spmv.SERVE_BATCHED)
+            _, h_p, _ = sv.run(mat, wid, sd, np.zeros(count), spmv.SERVE_PLAIN)
+            assert np.array_equal(h_b, h_p)
+            assert st_b["blocks"] < count
+            s = torch.cuda.Stream()
+            for r in (0, 1, 777, 2999):
+                m, k = int(mat[r]), int(wid[r])
+                n, rp, ci, va = mats[m]
+                x = torch.empty((n, k), dtype=torch.float64, device="cuda")
+                y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+                spmv.spmv_serve_single(sv.h, m, k, int(sd[r]), y, x, s)
+                s.synchronize()
+                Y = y.cpu().numpy()
+                assert host_hash(Y, k) == h_b[r], "request %d differs alone and in the mix" % r
+                X = W.request_x(int(sd[r]), n, k)
+                assert np.array_equal(x.cpu().numpy(), X)
+                for j in range(k):
+                    want = oracle.csr_spmv(n, rp, ci, va, X[:, j])
+                    scale = oracle.csr_absdot(n, rp, ci, va, X[:, j])
+                    assert_fp64_close(Y[:, j], want, scale, "request %d column %d" % (r, j))
