@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_persistent_kernel(BatchArgs
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 5) batch_sliced_persistent_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 6) batch_sliced_persistent_kernel(BatchArgs a) {
     const uint64_t pol = policy_evict_last();
     for (;;) {
         int t = 0;
