@@ -182,8 +182,9 @@ int spmv_part_dag(const spmv_part* part, int32_t* edges_host, int64_t cap_pairs,
  *   WARP   param = geometry 0..4: warp-private shared-memory pipelines of
  *          32-row tiles (bulk copies per warp, no block-wide barrier), one
  *          thread per row, one DFMA per entry
- *   SELL   param = 4, 8, 9 (entries per lane per step) or 104 (4, fewer
- *          registers), each + 2000 (2004, 2008, 2009, 2104) for the same
+ *   SELL   param = 4, 8, 9 (entries per lane per step; 8, 4 and 4 CTAs per
+ *          SM) or 104 / 105 / 106 / 107 (4 at 6, 8 at 5, 8 at 6, 9 at 5 CTAs
+ *          per SM, in fewer registers), each + 2000 (2004, ..., 2107) for the same
  *          launch with the work units cut into contiguous ranges of equal
  *          estimated cost, one per CTA, instead of dealt round-robin to the
  *          warps (evens out the SMs on skewed rows; y is the same bit for

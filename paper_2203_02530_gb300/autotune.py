@@ -21,13 +21,15 @@ from .benchmark import time_loop
 CACHE = os.environ.get("SPMV_TUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "spmv_gb300_tune.json"))
 
+SELL_PARAMS = (4, 8, 9, 104, 105, 106, 107) + tuple(2000 + p for p in (4, 8, 9, 104, 105, 106, 107))
+
 CANDIDATES = ([(spmv.VARIANT_TILE, g) for g in range(5)]
               + [(spmv.VARIANT_VECTOR, w) for w in (2, 4, 8)]
               + [(spmv.VARIANT_PAIRS, w) for w in (1, 2, 4, 8, 102, 104)]
               + [(spmv.VARIANT_WARP, g) for g in range(5)]
               + [(spmv.VARIANT_MERGE, 0)]
-              + [(spmv.VARIANT_SELL, u) for u in (4, 8, 9, 104, 2004, 2008, 2009, 2104)]
-              + [(spmv.VARIANT_SELL16, u) for u in (4, 8, 9, 104, 2004, 2008, 2009, 2104)])
+              + [(spmv.VARIANT_SELL, u) for u in SELL_PARAMS]
+              + [(spmv.VARIANT_SELL16, u) for u in SELL_PARAMS])
 
 
 def signature(n, row_ptr, P, device_name):

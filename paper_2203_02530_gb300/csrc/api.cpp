@@ -622,7 +622,7 @@ static void prepare_variant(spmv_part* pt, int variant, int param, int op_kind) 
         if (!pt->lmtiles) spmvk::build_merge_tiles(pt);
     } else if (variant == SPMV_VARIANT_SELL || variant == SPMV_VARIANT_SELL16) {
         if (!spmvk::sell_param_supported(param))
-            fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104} (+2000 balanced)", param);
+            fail(SPMV_EINVAL, "sliced variant %d not in {4,8,9,104..107} (+2000 balanced)", param);
         if (variant == SPMV_VARIANT_SELL16 && op_kind != SPMV_OP_LOCAL)
             fail(SPMV_EINVAL, "16-bit column deltas serve the LOCAL product only");
         check_cuda(cudaDeviceSynchronize(), "synchronize");

@@ -284,7 +284,7 @@ cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const doubl
 
 bool sell_param_supported(int param) {
     const int base = param >= 2000 ? param - 2000 : param;
-    return base == 4 || base == 8 || base == 9 || base == 104;
+    return base == 4 || base == 8 || base == 9 || (base >= 104 && base <= 107);
 }
 
 int sell_grid(int param, int units, int num_sms) {
@@ -294,6 +294,9 @@ int sell_grid(int param, int units, int num_sms) {
         case 8: blocks_per_sm = 4; break;
         case 9: blocks_per_sm = 4; break;
         case 104: blocks_per_sm = 6; break;
+        case 105: blocks_per_sm = 5; break;
+        case 106: blocks_per_sm = 6; break;
+        case 107: blocks_per_sm = 5; break;
         default: return 0;
     }
     if (units <= 0) return 0;
@@ -318,6 +321,9 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, bool de
         case 8: SELL_LAUNCH(8, 4); break;
         case 9: SELL_LAUNCH(9, 4); break;
         case 104: SELL_LAUNCH(4, 6); break;
+        case 105: SELL_LAUNCH(8, 5); break;
+        case 106: SELL_LAUNCH(8, 6); break;
+        case 107: SELL_LAUNCH(9, 5); break;
         default: return cudaErrorInvalidValue;
     }
 #undef SELL_LAUNCH

@@ -68,7 +68,7 @@ def case(name):
 
 VARIANTS = ([("tile", g) for g in range(5)] + [("vector", v) for v in (2, 4, 8, 16, 32)]
             + [("pairs", v) for v in (1, 2, 4, 8, 102, 104)] + [("warp", g) for g in range(5)]
-            + [("merge", 0)] + [("sell", u) for u in (4, 8, 9, 104, 2004, 2009, 2104)])
+            + [("merge", 0)] + [("sell", u) for u in (4, 8, 9, 104, 105, 106, 107, 2004, 2009, 2104, 2106)])
 
 SELL_LONG = 64
 
