@@ -786,7 +786,7 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
         pt->io_y = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
     }
     const int P = pt->P;
-    while ((int)pt->io_ev.size() < 2 * P + 1) {
+    while ((int)pt->io_ev.size() < 3 * P + 1) {
         cudaEvent_t e;
         check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         pt->io_ev.push_back(e);
@@ -839,11 +839,16 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
     launches += op_pack(pt, -1, pt->io_x, compute_stream);
     launches += op_copy(pt, -1, compute_stream);
     for (int p = 1; p < P; p += 2) check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[P + p], 0), "wait");
-    launches += op_remote(pt, -1, pt->io_y, compute_stream);
-    check_cuda(cudaEventRecord(pt->io_ev[2 * P], compute_stream), "event");
+    // the remote products rank by rank, so that a rank's remaining rows go
+    // out while the later ranks' products run
+    for (int p = 0; p < P; ++p) {
+        launches += op_remote(pt, p, pt->io_y, compute_stream);
+        check_cuda(cudaEventRecord(pt->io_ev[2 * P + p], compute_stream), "event");
+    }
     // y on a stream of its own, so that it overlaps the copies in: each
     // rank's remote-free run as soon as its LOCAL product is done
-    // (overlapping the other ranks' products), the rest after REMOTE
+    // (overlapping the other ranks' products), its other rows after its
+    // REMOTE product
     auto copy_out = [&](int64_t a, int64_t b) {
         if (b > a)
             check_cuda(cudaMemcpyAsync(y_host + a, pt->io_y + a, (size_t)(b - a) * sizeof(double),
@@ -854,13 +859,11 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
         check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[P + p], 0), "wait");
         copy_out(pt->io_free[p].first, pt->io_free[p].second);
     }
-    check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[2 * P], 0), "wait");
-    int64_t from = 0;
     for (int p = 0; p < P; ++p) {
-        copy_out(from, pt->io_free[p].first);
-        from = std::max(from, pt->io_free[p].second);
+        check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[2 * P + p], 0), "wait");
+        copy_out(pt->bounds[p], pt->io_free[p].first);
+        copy_out(pt->io_free[p].second, pt->bounds[p + 1]);
     }
-    copy_out(from, pt->n);
     check_cuda(cudaStreamSynchronize(out_stream), "synchronize");
     check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
     pt->last_launches = launches;

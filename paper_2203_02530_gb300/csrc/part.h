@@ -75,7 +75,7 @@ struct spmv_part {
     int* err = nullptr;               // device error word
     double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
     double* io_y = nullptr;
-    std::vector<cudaEvent_t> io_ev;   // 2P+1: x block p arrived; LOCAL p done; products done
+    std::vector<cudaEvent_t> io_ev;   // 3P+1: x block p arrived; LOCAL p done; REMOTE p done
     cudaStream_t io_out = nullptr;    // the host path's copies of y out
     cudaStream_t io_alt = nullptr;    // the host path's second stream for LOCAL products
     // per rank: the longest run [a, b) of rows without remote entries (final
