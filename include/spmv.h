@@ -280,8 +280,9 @@ int spmv_apply_host(spmv_part* part, int64_t graph_handle, const double* x_host,
  * blocks are copied in one by one on copy_stream, rank p's LOCAL product
  * starts as soon as block p has arrived (it reads no other x), on
  * compute_stream for even p and on a plan-owned second stream for odd p (so
- * consecutive ranks' launches overlap), then PACK and COPY for every rank
- * and the REMOTE products rank by rank follow on compute_stream.
+ * consecutive ranks' launches overlap); PACK and COPY for every rank run on
+ * a third plan-owned stream once all of x has arrived; each rank's REMOTE
+ * product follows its LOCAL product (same stream) once COPY is done.
  * y comes back in two parts on a plan-owned stream of its own (so the copies
  * out overlap the copies in, the link's two directions): each rank's longest
  * run of rows without remote entries as soon as its LOCAL product is done

@@ -793,6 +793,7 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
     }
     if (!pt->io_out) check_cuda(cudaStreamCreateWithFlags(&pt->io_out, cudaStreamNonBlocking), "stream");
     if (!pt->io_alt) check_cuda(cudaStreamCreateWithFlags(&pt->io_alt, cudaStreamNonBlocking), "stream");
+    if (!pt->io_aux) check_cuda(cudaStreamCreateWithFlags(&pt->io_aux, cudaStreamNonBlocking), "stream");
     cudaStream_t out_stream = pt->io_out;
     if (pt->io_free.empty()) {   // once per plan: the remote-free run of every rank
         std::vector<int32_t> rr((size_t)pt->n_rr);
@@ -824,26 +825,29 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
                        "copy x in");
         check_cuda(cudaEventRecord(pt->io_ev[p], copy_stream), "event");
     }
-    // The LOCAL products alternate between compute_stream and a second
-    // stream, so that one rank's launch fills the SMs the previous one leaves
-    // idle at its tail.
+    // The LOCAL products (and later the REMOTE products) alternate between
+    // compute_stream and a second stream, so that one rank's launch fills the
+    // SMs the previous one leaves idle at its tail.
     for (int p = 0; p < P; ++p) {
         cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
         check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[p], 0), "wait");
         launches += op_local(pt, p, pt->io_x, pt->io_y, cs);
         check_cuda(cudaEventRecord(pt->io_ev[P + p], cs), "event");
     }
-    // the rest of the DAG needs all of x (pack, exchange) and every LOCAL
-    // product (the remote products accumulate into y)
-    check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[P - 1], 0), "wait");
-    launches += op_pack(pt, -1, pt->io_x, compute_stream);
-    launches += op_copy(pt, -1, compute_stream);
-    for (int p = 1; p < P; p += 2) check_cuda(cudaStreamWaitEvent(compute_stream, pt->io_ev[P + p], 0), "wait");
-    // the remote products rank by rank, so that a rank's remaining rows go
+    // pack and exchange need all of x: on a third stream as soon as the last
+    // block has arrived, beside the LOCAL products
+    check_cuda(cudaStreamWaitEvent(pt->io_aux, pt->io_ev[P - 1], 0), "wait");
+    launches += op_pack(pt, -1, pt->io_x, pt->io_aux);
+    launches += op_copy(pt, -1, pt->io_aux);
+    check_cuda(cudaEventRecord(pt->io_ev[3 * P], pt->io_aux), "event");
+    // the remote products rank by rank, each after its own LOCAL product (on
+    // the same stream) and the exchange, so that a rank's remaining rows go
     // out while the later ranks' products run
     for (int p = 0; p < P; ++p) {
-        launches += op_remote(pt, p, pt->io_y, compute_stream);
-        check_cuda(cudaEventRecord(pt->io_ev[2 * P + p], compute_stream), "event");
+        cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
+        check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[3 * P], 0), "wait");
+        launches += op_remote(pt, p, pt->io_y, cs);
+        check_cuda(cudaEventRecord(pt->io_ev[2 * P + p], cs), "event");
     }
     // y on a stream of its own, so that it overlaps the copies in: each
     // rank's remote-free run as soon as its LOCAL product is done
@@ -864,7 +868,7 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
         copy_out(pt->bounds[p], pt->io_free[p].first);
         copy_out(pt->io_free[p].second, pt->bounds[p + 1]);
     }
-    check_cuda(cudaStreamSynchronize(out_stream), "synchronize");
+    check_cuda(cudaStreamSynchronize(out_stream), "synchronize");   // after every REMOTE, so after all work
     check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
     pt->last_launches = launches;
     API_CATCH

@@ -75,9 +75,10 @@ struct spmv_part {
     int* err = nullptr;               // device error word
     double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
     double* io_y = nullptr;
-    std::vector<cudaEvent_t> io_ev;   // 3P+1: x block p arrived; LOCAL p done; REMOTE p done
+    std::vector<cudaEvent_t> io_ev;   // 3P+1: x block p arrived; LOCAL p done; REMOTE p done; exchange done
     cudaStream_t io_out = nullptr;    // the host path's copies of y out
-    cudaStream_t io_alt = nullptr;    // the host path's second stream for LOCAL products
+    cudaStream_t io_alt = nullptr;    // the host path's second stream for LOCAL / REMOTE products
+    cudaStream_t io_aux = nullptr;    // the host path's stream for pack and exchange
     // per rank: the longest run [a, b) of rows without remote entries (final
     // after the rank's LOCAL product; the host path copies it out early)
     std::vector<std::pair<int64_t, int64_t>> io_free;

@@ -83,8 +83,10 @@ void free_plan(spmv_part* pt) {
     pt->io_ev.clear();
     if (pt->io_out) cudaStreamDestroy(pt->io_out);
     if (pt->io_alt) cudaStreamDestroy(pt->io_alt);
+    if (pt->io_aux) cudaStreamDestroy(pt->io_aux);
     pt->io_out = nullptr;
     pt->io_alt = nullptr;
+    pt->io_aux = nullptr;
     pt->op_ev.clear();
     pt->join_ev.clear();
     pt->fork_ev = nullptr;
