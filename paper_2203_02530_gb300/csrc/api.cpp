@@ -825,14 +825,26 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
                        "copy x in");
         check_cuda(cudaEventRecord(pt->io_ev[p], copy_stream), "event");
     }
+    // y goes out on a stream of its own, so that it overlaps the copies in.
+    // Each copy out is issued right after the product that finishes its rows,
+    // so that it is queued before the host is through issuing the rest.
+    auto copy_out = [&](int64_t a, int64_t b) {
+        if (b > a)
+            check_cuda(cudaMemcpyAsync(y_host + a, pt->io_y + a, (size_t)(b - a) * sizeof(double),
+                                       cudaMemcpyDeviceToHost, out_stream),
+                       "copy y out");
+    };
     // The LOCAL products (and later the REMOTE products) alternate between
     // compute_stream and a second stream, so that one rank's launch fills the
-    // SMs the previous one leaves idle at its tail.
+    // SMs the previous one leaves idle at its tail.  A rank's remote-free run
+    // is final after its LOCAL product.
     for (int p = 0; p < P; ++p) {
         cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
         check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[p], 0), "wait");
         launches += op_local(pt, p, pt->io_x, pt->io_y, cs);
         check_cuda(cudaEventRecord(pt->io_ev[P + p], cs), "event");
+        check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[P + p], 0), "wait");
+        copy_out(pt->io_free[p].first, pt->io_free[p].second);
     }
     // pack and exchange need all of x: on a third stream as soon as the last
     // block has arrived, beside the LOCAL products
@@ -841,29 +853,13 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
     launches += op_copy(pt, -1, pt->io_aux);
     check_cuda(cudaEventRecord(pt->io_ev[3 * P], pt->io_aux), "event");
     // the remote products rank by rank, each after its own LOCAL product (on
-    // the same stream) and the exchange, so that a rank's remaining rows go
-    // out while the later ranks' products run
+    // the same stream) and the exchange; a rank's other rows go out after its
+    // REMOTE product, while the later ranks' products run
     for (int p = 0; p < P; ++p) {
         cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
         check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[3 * P], 0), "wait");
         launches += op_remote(pt, p, pt->io_y, cs);
         check_cuda(cudaEventRecord(pt->io_ev[2 * P + p], cs), "event");
-    }
-    // y on a stream of its own, so that it overlaps the copies in: each
-    // rank's remote-free run as soon as its LOCAL product is done
-    // (overlapping the other ranks' products), its other rows after its
-    // REMOTE product
-    auto copy_out = [&](int64_t a, int64_t b) {
-        if (b > a)
-            check_cuda(cudaMemcpyAsync(y_host + a, pt->io_y + a, (size_t)(b - a) * sizeof(double),
-                                       cudaMemcpyDeviceToHost, out_stream),
-                       "copy y out");
-    };
-    for (int p = 0; p < P; ++p) {
-        check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[P + p], 0), "wait");
-        copy_out(pt->io_free[p].first, pt->io_free[p].second);
-    }
-    for (int p = 0; p < P; ++p) {
         check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[2 * P + p], 0), "wait");
         copy_out(pt->bounds[p], pt->io_free[p].first);
         copy_out(pt->io_free[p].second, pt->bounds[p + 1]);
