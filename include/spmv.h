@@ -37,6 +37,11 @@
  *   - Indices: column indices are int32 and n < 2^31; the number of nonzeros
  *     must also be below 2^31.
  *   - All FP values and accumulations are IEEE binary64.
+ *   - Consecutive kernels of the operations on one stream are launched with
+ *     programmatic dependent launch: a kernel may be scheduled as the
+ *     previous one's CTAs exit and waits for its completion before touching
+ *     memory, so ordering is unchanged.  SPMV_NO_PDL=1 in the environment
+ *     (read once per process) launches them plainly.
  */
 #ifndef SPMV_H
 #define SPMV_H
