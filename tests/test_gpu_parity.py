@@ -788,3 +788,56 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         s.synchronize()
         assert_fp64_close(y_d.cpu().numpy(), want, scale, "after the timeout self-test")
         assert part.query(spmv.Q_ERROR) == 0
+
+
+_PLAIN_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2203_02530_gb300 import spmv, workloads as W
+n, rp, ci, va = W.powerlaw(3000, seed=3, cap=500)
+x = W.uniform_x(n, seed=99)
+s = [torch.cuda.Stream() for _ in range(2)]
+x_d = torch.from_numpy(x).cuda()
+y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+with spmv.Part(n, rp, ci, va, 3, spmv.PER_PARTITION) as part:
+    part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, 2008)
+    part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_MERGE, 0)
+    order = [4 * p + k for k in (0, 1, 2, 3) for p in range(3)]
+    g = part.run(order, [0, 1] * 6, s, x_d, y_d, spmv.RUN_CAPTURE)
+    part.run(order, [0, 1] * 6, s, x_d, y_d, spmv.RUN_REPLAY, g)
+    torch.cuda.synchronize()
+np.save(sys.argv[2], y_d.cpu().numpy())
+"""
+
+
+@pytest.mark.parametrize("no_pdl", ["1", "0"])
+def test_programmatic_launch_off_and_on_give_the_same_y(tmp_path, no_pdl):
+    """The same captured per-rank schedule (sliced and merge-path products,
+    two streams) in a child process with programmatic dependent launch
+    switched off (SPMV_NO_PDL=1) or left on gives this process's y bit for
+    bit."""
+    import os
+    import subprocess
+    import sys
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "y.npy")
+    env = dict(os.environ, SPMV_NO_PDL=no_pdl)
+    subprocess.run([sys.executable, "-c", _PLAIN_CHILD, root, out], env=env, check=True, timeout=600)
+    n, rp, ci, va = W.powerlaw(3000, seed=3, cap=500)
+    x = W.uniform_x(n, seed=99)
+    want, scale = reference(n, rp, ci, va, x)
+    s = [torch.cuda.Stream() for _ in range(2)]
+    x_d = dev(x)
+    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    with make_part(n, rp, ci, va, 3, spmv.PER_PARTITION) as part:
+        part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, 2008)
+        part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_MERGE, 0)
+        order = [4 * p + k for k in (0, 1, 2, 3) for p in range(3)]
+        g = part.run(order, [0, 1] * 6, s, x_d, y_d, spmv.RUN_CAPTURE)
+        part.run(order, [0, 1] * 6, s, x_d, y_d, spmv.RUN_REPLAY, g)
+        torch.cuda.synchronize()
+    y = y_d.cpu().numpy()
+    assert_fp64_close(y, want, scale, "programmatic launch")
+    assert np.array_equal(np.load(out).view(np.uint64), y.view(np.uint64))
