@@ -366,8 +366,10 @@ __device__ __forceinline__ void long_unit(const int32_t* __restrict__ ptr, const
 }
 
 // One block over the sliced layout: one warp per slice (grid-stride).
+// Registers capped so that 4 CTAs (widths 1-3) or 3 CTAs (widths 4-8) fit an
+// SM without spills; uncapped, width 4 took 128 registers (2 CTAs).
 template <int W>
-__global__ void __launch_bounds__(kThreads) spmm_sliced_kernel(BatchMat m, const double* __restrict__ X,
+__global__ void __launch_bounds__(kThreads, (W <= 3 ? 4 : 3)) spmm_sliced_kernel(BatchMat m, const double* __restrict__ X,
                                                                double* __restrict__ Y, BlockDesc b,
                                                                unsigned long long* __restrict__ hashes) {
     unsigned long long h[kMaxW];
