@@ -2,6 +2,7 @@
 exports every function include/spmv.h declares, and the schedule enumerator
 of the package agrees with the oracle's brute force (Sec. III-B/III-C)."""
 import ctypes
+import json
 import os
 import random
 
@@ -163,3 +164,54 @@ def test_record_log_resumes_without_remeasuring(tmp_path):
     ev = search.graph_evaluator(FakePart(), [None], None, None, recorder=again)
     assert ev([0, 1, 2, 3], [0, 0, 0, 0]) == 1.5e-4
     assert not calls
+
+
+def test_tuner_times_per_rank_plans_rank_by_rank(libpath, monkeypatch, tmp_path):
+    """The variant tuner times a coarse plan's products as one launch over
+    all ranks and a per-rank plan's as its P per-rank launches, skips the
+    candidates a plan refuses (EINVAL), keeps the fastest, and keys its cache
+    by granularity as well as by matrix and candidate set."""
+    from paper_2203_02530_gb300 import autotune, spmv
+
+    class FakePart:
+        def __init__(self, P, gran):
+            self.P, self.granularity, self.h = P, gran, object()
+            self.set = []
+
+        def set_op_variant(self, op, v, p):
+            if v == spmv.VARIANT_MERGE:
+                raise spmv.SpmvError(spmv.EINVAL, "refused")
+            self.set.append((op, v, p))
+
+    calls = []
+    monkeypatch.setattr(spmv, "spmv_local", lambda h, p, x, y, s: calls.append(("L", p)))
+    monkeypatch.setattr(spmv, "spmv_remote", lambda h, p, y, s: calls.append(("R", p)))
+    cost = {(spmv.VARIANT_SELL, 8): 2.0, (spmv.VARIANT_SELL, 2008): 1.0, (spmv.VARIANT_PAIRS, 1): 3.0}
+    current = {}
+
+    def fake_time(run, stream, reps):
+        before = len(calls)
+        run()
+        current["launches"] = calls[before:]
+        return cost[current["vp"]]
+
+    monkeypatch.setattr(autotune, "time_loop", fake_time)
+    cands = [(spmv.VARIANT_SELL, 8), (spmv.VARIANT_MERGE, 0), (spmv.VARIANT_SELL, 2008), (spmv.VARIANT_PAIRS, 1)]
+    orig_set = FakePart.set_op_variant
+
+    def tracking_set(self, op, v, p):
+        orig_set(self, op, v, p)
+        current["vp"] = (v, p)
+
+    monkeypatch.setattr(FakePart, "set_op_variant", tracking_set)
+    cache = str(tmp_path / "tune.json")
+    for gran, ranks in ((spmv.COARSE, [-1]), (spmv.PER_PARTITION, [0, 1, 2])):
+        part = FakePart(3, gran)
+        calls.clear()
+        r = autotune.tune(part, None, None, None, sig="sig", candidates=cands, cache_path=cache)
+        assert r["local"] == (spmv.VARIANT_SELL, 2008) and r["remote"] == (spmv.VARIANT_SELL, 2008)
+        assert all((op, spmv.VARIANT_MERGE, 0) not in r["times"] for op in (spmv.OP_LOCAL, spmv.OP_REMOTE))
+        assert [p for k, p in current["launches"]] == ranks
+        assert {k for k, p in calls} == {"L", "R"}
+    keys = list(json.load(open(cache)).keys())
+    assert len(keys) == 2 and sum("per-rank" in k for k in keys) == 1
