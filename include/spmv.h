@@ -474,6 +474,22 @@ int spmv_serve_launches(const spmv_server* server, int64_t* out);
 int spmv_serve_single(spmv_server* server, int matrix, int width, uint64_t seed,
                       double* y_dev, double* x_dev, cudaStream_t s);
 
+/* Index check of a plan (a memory checker's job, done by the library): reads
+ * every index array and counts into *bad_out the indices outside the range
+ * the plan's definition allows (Sec. III-A): A_L's columns inside their
+ * rank's block, A_R's receive-buffer positions inside their rank's halo, the
+ * remote rows inside their rank's rows, every send slot of segment (p, q)
+ * naming a row of q, the per-rank pack positions inside the send buffer,
+ * row pointers ascending from 0 to the entry count, and, once built, every
+ * live slot of the sliced layouts (and of the 16-bit deltas) inside x or the
+ * receive buffer, with each long-row piece inside its row.  No index is used
+ * to address memory, so a damaged plan is reported, not dereferenced.  0 for
+ * every plan this library builds.  Synchronises. */
+int spmv_part_check(spmv_part* part, int64_t* bad_out);
+/* Self-test of those checks on a planted 3-row CSR and index list with one
+ * out-of-range index each: *found_out receives 2.  Synchronises. */
+int spmv_selftest_check(int64_t* found_out);
+
 /* Self-test of the bounded device waits: one thread waits on an mbarrier
  * that nothing ever completes; the wait gives up after limit_ns (1e3..2e9)
  * and *status_out receives 6 (the magnitude of SPMV_ETIMEOUT) -- the status

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libspmv.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["kernels.cu", "merge.cu", "sell.cu", "batch.cu", "serve.cu", "plan.cpp", "api.cpp"]
+SOURCES = ["kernels.cu", "merge.cu", "sell.cu", "check.cu", "batch.cu", "serve.cu", "plan.cpp", "api.cpp"]
 
 
 def _nvcc():

@@ -975,6 +975,128 @@ int spmv_csr_error(int64_t* out) {
     return SPMV_OK;
 }
 
+int spmv_part_check(spmv_part* pt, int64_t* bad_out) {
+    API_TRY
+    check_part(pt);
+    need(bad_out != nullptr, SPMV_EINVAL, "bad_out is NULL");
+    const int P = pt->P;
+    // host tables of group offsets and ranges, one device copy
+    std::vector<int64_t> tab;
+    auto put = [&](const std::vector<int64_t>& v) {
+        const size_t at = tab.size();
+        tab.insert(tab.end(), v.begin(), v.end());
+        return at;
+    };
+    std::vector<int64_t> zeros(P, 0), bsize(P), blo(P), bhi(P), hlo(P), hhi(P);
+    for (int p = 0; p < P; ++p) {
+        bsize[p] = pt->bounds[p + 1] - pt->bounds[p];
+        blo[p] = pt->bounds[p];
+        bhi[p] = pt->bounds[p + 1];
+        hlo[p] = pt->halo_off[p];
+        hhi[p] = pt->halo_off[p + 1];
+    }
+    std::vector<int64_t> slo((size_t)P * P), shi((size_t)P * P);
+    for (int p = 0; p < P; ++p)
+        for (int q = 0; q < P; ++q) {
+            slo[(size_t)p * P + q] = pt->bounds[q];
+            shi[(size_t)p * P + q] = pt->bounds[q + 1];
+        }
+    const size_t t_bounds = put(pt->bounds), t_zero = put(zeros), t_bsize = put(bsize), t_blo = put(blo),
+                 t_bhi = put(bhi), t_rr = put(pt->rr_off), t_hlo = put(hlo), t_hhi = put(hhi),
+                 t_seg = put(pt->seg_off), t_slo = put(slo), t_shi = put(shi),
+                 t_one = put(std::vector<int64_t>{0, pt->n_send});
+    int64_t* d_tab = nullptr;
+    unsigned long long* d_bad = nullptr;
+    check_cuda(cudaMalloc(&d_tab, tab.size() * sizeof(int64_t) + 64), "check tables");
+    cudaError_t e = cudaMalloc(&d_bad, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(d_tab);
+        check_cuda(e, "check counter");
+    }
+    auto run = [&]() -> cudaError_t {
+        cudaError_t r = cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (r == cudaSuccess) r = cudaMemset(d_bad, 0, sizeof(unsigned long long));
+        const int sms = pt->num_sms;
+        // A_L: row i of rank p has columns in [0, r_{p+1} - r_p)
+        if (r == cudaSuccess)
+            r = spmvk::launch_check_csr(pt->l_ptr, pt->l_col, pt->n, pt->nnz_l, d_tab + t_bounds, P,
+                                        d_tab + t_zero, d_tab + t_bsize, d_bad, sms, 0);
+        // A_R: remote row k of rank p has receive-buffer positions in p's halo
+        if (r == cudaSuccess)
+            r = spmvk::launch_check_csr(pt->rr_ptr, pt->r_col, pt->n_rr, pt->nnz_r, d_tab + t_rr, P,
+                                        d_tab + t_hlo, d_tab + t_hhi, d_bad, sms, 0);
+        // remote rows of rank p are p's rows
+        if (r == cudaSuccess)
+            r = spmvk::launch_check_list(pt->rr_row, pt->n_rr, d_tab + t_rr, P, d_tab + t_blo, d_tab + t_bhi,
+                                         d_bad, sms, 0);
+        // send slot of segment (dst p, src q) names a row of q
+        if (r == cudaSuccess)
+            r = spmvk::launch_check_list(pt->send_idx, pt->n_send, d_tab + t_seg, P * P, d_tab + t_slo,
+                                         d_tab + t_shi, d_bad, sms, 0);
+        if (r == cudaSuccess)
+            r = spmvk::launch_check_list(pt->pack_pos, pt->n_send, d_tab + t_one, 1, d_tab + t_one,
+                                         d_tab + t_one + 1, d_bad, sms, 0);
+        if (r == cudaSuccess && pt->sell_built) {
+            for (int part = 0; part < 2 && r == cudaSuccess; ++part) {
+                const spmv_part::SellPart& sp = pt->sell[part];
+                const int64_t npos = part ? pt->n_rr : pt->n;
+                const int64_t xhi = part ? pt->n_send : pt->n;
+                const int32_t* cptr = part ? pt->rr_ptr : pt->l_ptr;
+                r = spmvk::launch_check_sell(sp.slices, (int)sp.slice_off[P], sp.len, sp.perm, sp.col, nullptr,
+                                             sp.entries, npos, 0, xhi, sp.longs, (int)sp.long_off[P], cptr, d_bad,
+                                             sms, 0);
+                if (r == cudaSuccess && sp.col16)
+                    r = spmvk::launch_check_sell(sp.slices, (int)sp.slice_off[P], sp.len, sp.perm, nullptr,
+                                                 sp.col16, sp.entries, npos, 0, xhi, sp.longs, 0, cptr, d_bad,
+                                                 sms, 0);
+            }
+        }
+        unsigned long long h = 0;
+        if (r == cudaSuccess) r = cudaDeviceSynchronize();
+        if (r == cudaSuccess) r = cudaMemcpy(&h, d_bad, sizeof h, cudaMemcpyDeviceToHost);
+        *bad_out = (int64_t)h;
+        return r;
+    };
+    e = run();
+    cudaFree(d_tab);
+    cudaFree(d_bad);
+    check_cuda(e, "index check");
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_selftest_check(int64_t* found_out) {
+    API_TRY
+    need(found_out != nullptr, SPMV_EINVAL, "found_out is NULL");
+    // a 3-row CSR whose column 5 lies outside [0, 4), and an index list
+    // whose 7 lies outside [0, 3): the checks must find exactly these two
+    const int32_t h_ptr[4] = {0, 2, 3, 3}, h_col[3] = {0, 5, 1}, h_idx[3] = {0, 7, 2};
+    const int64_t h_tab[4] = {0, 0, 4, 3};   // offsets {0}, lo {0}, hi {4}; list hi {3}
+    int32_t* d_i = nullptr;
+    int64_t* d_t = nullptr;
+    unsigned long long* d_bad = nullptr;
+    check_cuda(cudaMalloc(&d_i, 16 * sizeof(int32_t)), "self-test");
+    cudaError_t e = cudaMalloc(&d_t, 4 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(d_i, h_ptr, sizeof h_ptr, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_i + 4, h_col, sizeof h_col, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_i + 8, h_idx, sizeof h_idx, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_t, h_tab, sizeof h_tab, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = spmvk::launch_check_csr(d_i, d_i + 4, 3, 3, d_t, 1, d_t + 1, d_t + 2, d_bad, 1, 0);
+    if (e == cudaSuccess) e = spmvk::launch_check_list(d_i + 8, 3, d_t, 1, d_t + 1, d_t + 3, d_bad, 1, 0);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_bad, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d_i);
+    cudaFree(d_t);
+    cudaFree(d_bad);
+    check_cuda(e, "self-test");
+    *found_out = (int64_t)h;
+    API_CATCH
+    return SPMV_OK;
+}
+
 int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out) {
     API_TRY
     need(status_out != nullptr, SPMV_EINVAL, "status_out is NULL");

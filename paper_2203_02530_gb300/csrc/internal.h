@@ -133,6 +133,18 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& s, int param, bool del
 cudaError_t launch_sell_delta(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
                               const int32_t* scol, int16_t* scol16, int* bad, int num_sms, cudaStream_t s);
 bool sell_param_supported(int param);
+
+// Index checks (check.cu): count into *bad the indices outside their ranges;
+// read-only, no index is used as an address.
+cudaError_t launch_check_csr(const int32_t* ptr, const int32_t* col, int64_t nrows, int64_t nnz,
+                             const int64_t* row_off, int G, const int64_t* lo, const int64_t* hi,
+                             unsigned long long* bad, int num_sms, cudaStream_t s);
+cudaError_t launch_check_list(const int32_t* idx, int64_t count, const int64_t* seg, int S, const int64_t* lo,
+                              const int64_t* hi, unsigned long long* bad, int num_sms, cudaStream_t s);
+cudaError_t launch_check_sell(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
+                              const int32_t* col, const int16_t* col16, int64_t entries, int64_t npos, int64_t x_lo,
+                              int64_t x_hi, const SellLong* longs, int n_longs, const int32_t* csr_ptr,
+                              unsigned long long* bad, int num_sms, cudaStream_t s);
 // Params 2000 + p: the launch of param p with cost-balanced contiguous CTA
 // ranges (SellArgs::cta_off) instead of the round-robin split.
 inline bool sell_param_balanced(int param) { return param >= 2000; }

@@ -97,6 +97,8 @@ def _load():
         "spmv_serve_set_group_max": [vp, i32],
         "spmv_serve_pm1_bits": [ctypes.c_uint64],
         "spmv_selftest_wait_timeout": [i64, P64],
+        "spmv_part_check": [vp, P64],
+        "spmv_selftest_check": [P64],
         "spmv_last_error": [],
     }
     for name, args in sig.items():
@@ -249,6 +251,19 @@ def spmv_csr_merge_noalloc(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_
     (no allocation during the call; see include/spmv.h for the limit)."""
     _check(lib.spmv_csr_merge_noalloc(int(n), int(nnz), _ptr(row_ptr_dev), _ptr(col_idx_dev),
                                       _ptr(vals_dev), _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def spmv_part_check(h):
+    """Indices of the plan outside their ranges (0 for a sound plan)."""
+    out = ctypes.c_int64()
+    _check(lib.spmv_part_check(h, ctypes.byref(out)))
+    return out.value
+
+
+def spmv_selftest_check():
+    out = ctypes.c_int64()
+    _check(lib.spmv_selftest_check(ctypes.byref(out)))
+    return out.value
 
 
 def spmv_selftest_wait_timeout(limit_ns):

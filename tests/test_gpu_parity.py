@@ -732,6 +732,7 @@ def test_full_size_powerlaw_4M_sliced_schedules():
                 assert np.array_equal(y.view(np.uint64), first.view(np.uint64)), (lp, rp_)
             spmv.spmv_graph_destroy(part.h, g)
         assert part.query(spmv.Q_ERROR) == 0
+        assert spmv.spmv_part_check(part.h) == 0
 
 
 def test_full_size_27pt_150_benchmark_variants():
@@ -771,6 +772,7 @@ def test_full_size_27pt_150_benchmark_variants():
                     sliced = y.copy()
                 assert np.array_equal(y.view(np.uint64), sliced.view(np.uint64)), (lv, lp, rv, rpar)
         assert part.query(spmv.Q_ERROR) == 0
+        assert spmv.spmv_part_check(part.h) == 0
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
@@ -841,3 +843,31 @@ def test_programmatic_launch_off_and_on_give_the_same_y(tmp_path, no_pdl):
     y = y_d.cpu().numpy()
     assert_fp64_close(y, want, scale, "programmatic launch")
     assert np.array_equal(np.load(out).view(np.uint64), y.view(np.uint64))
+
+
+def test_index_check_finds_the_planted_indices():
+    """The plan checks' kernels count exactly the two planted out-of-range
+    indices of their self-test (nothing is dereferenced)."""
+    from paper_2203_02530_gb300 import spmv
+    torch_cuda()
+    assert spmv.spmv_selftest_check() == 2
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("gran", [0, 1])
+def test_every_plan_index_in_range(name, gran):
+    """Every index array of every plan (CSR blocks, halo maps, send lists,
+    pack positions, and the sliced layouts with their 16-bit deltas once
+    built) lies inside the range its definition allows."""
+    from paper_2203_02530_gb300 import spmv
+    torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    with make_part(n, rp, ci, va, P, gran) as part:
+        assert spmv.spmv_part_check(part.h) == 0
+        part.set_variant(spmv.VARIANT_SELL, 4)
+        assert spmv.spmv_part_check(part.h) == 0
+        try:
+            part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL16, 2009)
+        except spmv.SpmvError as e:
+            assert e.code == spmv.EINVAL    # some |column - row| needs more than 16 bits
+        assert spmv.spmv_part_check(part.h) == 0
