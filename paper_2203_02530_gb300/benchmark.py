@@ -9,7 +9,9 @@ per measurement is found by doubling batches.
 """
 import time
 
-T_MEASURE = 0.01   # seconds (Sec. III-C.3)
+from .constants import PAPER
+
+T_MEASURE = PAPER.t_measure   # seconds (Sec. III-C.3)
 
 
 def _events(torch):

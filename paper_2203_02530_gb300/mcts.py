@@ -26,9 +26,10 @@ ties in selection go to the first child in decision order.
 import math
 import random
 
+from .constants import PAPER
 from .schedules import children
 
-C_EXPLORE = math.sqrt(2.0)
+C_EXPLORE = PAPER.c_explore
 
 
 class Node:

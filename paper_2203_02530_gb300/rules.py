@@ -31,6 +31,8 @@ import math
 
 import numpy as np
 
+from .constants import PAPER
+
 
 # ---------------------------------------------------------------- labels
 def step_convolution(a, r):
@@ -47,7 +49,7 @@ def step_convolution(a, r):
     return after - upto, r - 1
 
 
-def class_labels(times, radius_frac=0.005, percentile=98.0):
+def class_labels(times, radius_frac=PAPER.label_radius_frac, percentile=PAPER.prominence_percentile):
     """Class of every time (0 = fastest), in the input order, and the sorted
     positions after which a new class starts."""
     from scipy.signal import find_peaks
@@ -131,9 +133,9 @@ def column_text(col, value):
 def train(X, y, max_leaf_nodes, seed=0):
     """(training error, classifier) with the parameters of Table IV."""
     from sklearn.tree import DecisionTreeClassifier
-    clf = DecisionTreeClassifier(criterion="gini", max_leaf_nodes=max_leaf_nodes,
+    clf = DecisionTreeClassifier(criterion=PAPER.tree_criterion, max_leaf_nodes=max_leaf_nodes,
                                  max_depth=max(1, max_leaf_nodes - 1),
-                                 class_weight="balanced", random_state=seed)
+                                 class_weight=PAPER.tree_class_weight, random_state=seed)
     clf.fit(X, y)
     return 1.0 - clf.score(X, y), clf
 
@@ -141,13 +143,13 @@ def train(X, y, max_leaf_nodes, seed=0):
 def search_tree(X, y, seed=0):
     """Alg. 1: grow max_leaf_nodes from 2 while the training error falls,
     trying up to 5 more leaves each time.  Returns (clf, mln, history)."""
-    mln = 2
+    mln = PAPER.tree_first_leaves
     err = math.inf
     cur, clf = train(X, y, mln, seed)
     history = [(mln, cur, clf.get_depth())]
     while cur < err:
         err = cur
-        for i in range(1, 6):
+        for i in range(1, PAPER.tree_more_leaves + 1):
             cur, nclf = train(X, y, mln + i, seed)
             history.append((mln + i, cur, nclf.get_depth()))
             if cur < err:

@@ -95,3 +95,25 @@ def test_report_renders():
     recs, edges, names = _planted_records()
     text = R.report(recs, edges, names, "planted")
     assert "Class 0" in text and "class accuracy" in text
+
+
+def test_method_constants_come_from_one_place():
+    """The search, the measurement protocol and the rule stage read the
+    paper's constants from one frozen dataclass: c = sqrt(2) (Sec. III-C.1),
+    0.01 s per measurement (Sec. III-C.3), radius 0.5 % and the 98th
+    percentile (Sec. IV-A), gini with balanced weights (Table IV), Alg. 1
+    starting at 2 leaves and trying 5 more."""
+    import dataclasses
+    import inspect
+    import math
+    from paper_2203_02530_gb300 import benchmark, mcts, rules
+    from paper_2203_02530_gb300.constants import PAPER
+    assert PAPER.c_explore == math.sqrt(2.0) and mcts.C_EXPLORE == PAPER.c_explore
+    assert PAPER.t_measure == 0.01 and benchmark.T_MEASURE == PAPER.t_measure
+    sig = inspect.signature(rules.class_labels)
+    assert sig.parameters["radius_frac"].default == PAPER.label_radius_frac == 0.005
+    assert sig.parameters["percentile"].default == PAPER.prominence_percentile == 98.0
+    assert (PAPER.tree_criterion, PAPER.tree_class_weight) == ("gini", "balanced")
+    assert (PAPER.tree_first_leaves, PAPER.tree_more_leaves) == (2, 5)
+    with pytest.raises(dataclasses.FrozenInstanceError):
+        PAPER.t_measure = 1.0
