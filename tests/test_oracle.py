@@ -210,3 +210,31 @@ def test_pins_catch_planted_mistakes():
     H = pl.export(oracle.HALO, 1)
     if len(H) > 1:
         assert not np.all(np.diff(np.roll(H, 1)) > 0)
+
+
+def test_plan_and_product_properties_on_random_matrices():
+    """Property check over random small matrices (sizes 0-48, 1-9 ranks so
+    P > n occurs, densities up to 0.6, duplicate and unsorted columns): the
+    plan keeps every invariant above, the partitioned product equals the
+    dense brute force within the dot-product error bound, and on integer
+    data the partitioned and plain products are equal bit for bit."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+
+    @settings(max_examples=80, deadline=None, derandomize=True)
+    @given(n=st.integers(0, 48), P=st.integers(1, 9), density=st.floats(0.0, 0.6),
+           seed=st.integers(0, 2**31 - 1), dup=st.booleans(), shuf=st.booleans())
+    def prop(n, P, density, seed, dup, shuf):
+        n, rp, ci, va = W.random_csr(n, density=density, seed=seed, duplicates=dup, shuffle_cols=shuf)
+        pl = check_plan(n, rp, ci, va, P)
+        x = W.uniform_x(n, seed=seed % 1000)
+        y = pl.spmv(x)
+        want = dense(n, rp, ci, va) @ x
+        scale = csr_absdot(n, rp, ci, va, x)
+        assert np.all(np.abs(y - want) <= 1e-12 * scale + 1e-300)
+        n, rp, ci, va = W.random_csr(n, density=density, seed=seed, integer=True, duplicates=dup,
+                                     shuffle_cols=shuf)
+        xi = W.uniform_x(n, seed=seed % 1000, integer=True)
+        assert np.array_equal(OraclePlan(n, rp, ci, va, P).spmv(xi), csr_spmv(n, rp, ci, va, xi))
+
+    prop()
