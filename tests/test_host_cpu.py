@@ -215,3 +215,26 @@ def test_tuner_times_per_rank_plans_rank_by_rank(libpath, monkeypatch, tmp_path)
         assert {k for k, p in calls} == {"L", "R"}
     keys = list(json.load(open(cache)).keys())
     assert len(keys) == 2 and sum("per-rank" in k for k in keys) == 1
+
+
+def test_enumerator_matches_brute_force_on_random_dags():
+    """Property check: on random DAGs of up to 6 operations and 1-3 streams
+    the package's enumerator yields exactly the oracle's brute-force set of
+    canonical schedules (all orders x all stream maps, filtered for
+    topological order and canonical stream numbering), and counts it."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+
+    @settings(max_examples=60, deadline=None, derandomize=True)
+    @given(m=st.integers(1, 6), streams=st.integers(1, 3), bits=st.integers(0, 2**15 - 1))
+    def prop(m, streams, bits):
+        pairs = [(u, v) for u in range(m) for v in range(u + 1, m)]
+        edges = [e for k, e in enumerate(pairs) if bits >> k & 1]
+        ops = list(range(m))
+        want = set(S.brute_force_schedules(ops, edges, streams))
+        dag = E.Dag(m, edges)
+        got = {(tuple(o), tuple(s)) for o, s in E.enumerate_schedules(dag, streams)}
+        assert got == want
+        assert E.count_schedules(dag, streams) == len(want)
+
+    prop()
