@@ -497,6 +497,17 @@ int spmv_selftest_check(int64_t* found_out);
  * runs out.  Synchronises; leaves the context usable. */
 int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out);
 
+/* Test hook of the merge-path kernel's give-up path (the path a bounded wait
+ * that runs out takes), for the plan-free entry points spmv_csr_merge and
+ * spmv_csr_merge_noalloc: while set (tile >= 0), their launches treat merge
+ * tile `tile` and every later tile as if the wait for its staged copy had run
+ * out, once that copy has landed (so no copy is left in flight).  Such a
+ * launch sets the error word (spmv_csr_error reports 6), leaves the rows of
+ * the abandoned tiles unfinished, marks their carries empty and writes nothing
+ * outside y[0, n).  tile = -1 turns the hook off (the default).  Process-wide;
+ * plans are not affected.  SPMV_EINVAL outside [-1, 2^30). */
+int spmv_selftest_merge_abort(int64_t tile);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* spmv_last_error(void);
 

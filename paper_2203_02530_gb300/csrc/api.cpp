@@ -4,6 +4,7 @@
 #include "part.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -13,6 +14,10 @@ using spmvk::check_cuda;
 namespace {
 
 thread_local std::string g_err;
+
+// Test hook of the plan-free merge entry points (spmv_selftest_merge_abort):
+// tile + 1 from which their merge kernel takes the give-up path, 0 = never.
+std::atomic<int> g_merge_abort_tile{0};
 
 int fail_status(int code, const std::string& msg) {
     g_err = msg;
@@ -921,6 +926,7 @@ int spmv_csr_merge(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t
     a.nnz_total = (int)nnz;
     a.guarded = 1;
     a.err = nullptr;
+    a.abort_tile = g_merge_abort_tile.load();
     cudaError_t e = spmvk::launch_merge_partition(row_ptr, 0, (int)n, 0, tiles, n_tiles, s);
     if (e == cudaSuccess) e = spmvk::launch_merge(a, tiles, 0, n_tiles, carries, sms, s);
     cudaError_t ef = cudaFreeAsync(scratch, s);
@@ -959,6 +965,7 @@ int spmv_csr_merge_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr, const
     a.nnz_total = (int)nnz;
     a.guarded = 1;
     a.err = nullptr;
+    a.abort_tile = g_merge_abort_tile.load();
     check_cuda(spmvk::launch_merge_noalloc(a, sms, s), "no-allocation merge product");
     API_CATCH
     return SPMV_OK;
@@ -1104,6 +1111,14 @@ int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out) {
     int st = 0;
     check_cuda(spmvk::selftest_wait_timeout((uint64_t)limit_ns, &st), "self-test");
     *status_out = st;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_selftest_merge_abort(int64_t tile) {
+    API_TRY
+    if (tile < -1 || tile >= (int64_t(1) << 30)) fail(SPMV_EINVAL, "tile %lld not in [-1, 2^30)", (long long)tile);
+    g_merge_abort_tile.store((int)(tile + 1));
     API_CATCH
     return SPMV_OK;
 }

@@ -100,6 +100,9 @@ struct CsrArgs {
     int nnz_total;          // entries of the CSR (bounds the guarded reads)
     int guarded;            // 1: arrays are not padded past their ends
     int* err;               // device error word
+    int abort_tile;         // test hook of the merge-path kernel: k > 0 makes
+                            // tiles k-1 and later take the path of a wait that
+                            // ran out (after their copies landed); 0 = never
 };
 
 // Launchers (kernels.cu).  All return cudaGetLastError() after the launch.

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 namespace spmvk {
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const Mer
             issue(j + MERGE_ST - 1);
         }
         const int s = j % MERGE_ST;
-        const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / MERGE_ST) & 1), kWaitLimitNs);
+        bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / MERGE_ST) & 1), kWaitLimitNs);
+        if (a.abort_tile > 0 && t >= a.abort_tile - 1) ok = false;   // test hook: the stage has landed
         if (__syncthreads_or(!ok)) {
             aborted = true;
             break;
@@ -310,6 +312,9 @@ __global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const Mer
     }
     if (aborted && tid == 0) {
         atomicExch(a.err ? a.err : &g_csr_err, kErrTimeout);
+        // the tiles this CTA will not finish carry nothing, so the fixup
+        // kernel never reads a carry left by an earlier launch
+        for (int jj = j; first + jj * stride < tile_end; ++jj) carries[first + jj * stride] = Carry{-1, 0, 0.0};
         for (int jj = j + 1; jj < j + MERGE_ST; ++jj) {
             if (first + jj * stride >= tile_end) break;
             mbar_wait_bounded(smem_u32(&bars[jj % MERGE_ST]), (uint32_t)((jj / MERGE_ST) & 1), kDrainLimitNs);
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(256) merge_fixup_kernel(CsrArgs a, const Carry
     const int t = tile_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (t >= tile_end) return;
     const Carry c = carries[t];
-    if (c.row < 0) return;
+    if (c.row < 0 || c.row >= a.n_rows) return;   // none, or not a row of this product
     if (t > tile_begin && carries[t - 1].row == c.row) return;
     double tot = c.val;
     for (int u = t + 1; u < tile_end && carries[u].row == c.row; ++u) tot += carries[u].val;
@@ -365,14 +370,14 @@ template <bool GUARD>
 static cudaError_t run_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begin, int tile_end,
                              Carry* carries, int num_sms, cudaStream_t s) {
     const size_t smem = (size_t)MERGE_ST * MergeLayout::BYTES;
-    static unsigned long long configured = 0;
+    static std::atomic<unsigned long long> configured{0};   // one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(configured >> dev & 1ull)) {
+    if (dev >= 64 || !(configured.load(std::memory_order_acquire) >> dev & 1ull)) {
         e = cudaFuncSetAttribute(merge_kernel<GUARD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) configured |= 1ull << dev;
+        if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_acq_rel);
     }
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, merge_kernel<GUARD>, MERGE_NT, smem);

@@ -97,6 +97,7 @@ def _load():
         "spmv_serve_set_group_max": [vp, i32],
         "spmv_serve_pm1_bits": [ctypes.c_uint64],
         "spmv_selftest_wait_timeout": [i64, P64],
+        "spmv_selftest_merge_abort": [i64],
         "spmv_part_check": [vp, P64],
         "spmv_selftest_check": [P64],
         "spmv_last_error": [],
@@ -270,6 +271,12 @@ def spmv_selftest_wait_timeout(limit_ns):
     out = ctypes.c_int64()
     _check(lib.spmv_selftest_wait_timeout(int(limit_ns), ctypes.byref(out)))
     return out.value
+
+
+def spmv_selftest_merge_abort(tile):
+    """Make the plan-free merge launches give up from merge tile `tile` on
+    (-1: off); a test hook of the bounded-wait give-up path."""
+    _check(lib.spmv_selftest_merge_abort(int(tile)))
 
 
 def spmv_csr_error():

@@ -792,6 +792,53 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         assert part.query(spmv.Q_ERROR) == 0
 
 
+@pytest.mark.parametrize("entry", ["spmv_csr_merge", "spmv_csr_merge_noalloc"])
+def test_merge_give_up_path_writes_nothing_outside_y(entry):
+    """The merge-path kernel's give-up path (taken when a bounded wait runs
+    out), planted from the host: a large product first leaves carries of its
+    own rows in the scratch, then a small product gives up from tile 10 on.
+    Its error word reads 6, nothing is written past y[n) (where the large
+    product's rows would land if a stale carry were used), and the next
+    product without the hook is right."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    s = torch.cuda.Stream()
+    run = getattr(spmv, entry)
+    n0, rp0, ci0, va0 = W.powerlaw(300_000, seed=13)
+    big = torch.empty(n0, dtype=torch.float64, device="cuda")
+    run(n0, int(rp0[-1]), dev(rp0.astype(np.int32)), dev(ci0), dev(va0), dev(W.uniform_x(n0, seed=1)), big, s)
+    s.synchronize()
+    assert spmv.spmv_csr_error() == 0
+    n, rp, ci, va = W.stencil_27pt(0, seed=14, dims=(20, 20, 20))
+    x = W.uniform_x(n, seed=15)
+    want, scale = reference(n, rp, ci, va, x)
+    tiles = (n + int(rp[-1]) + 2047) // 2048
+    assert tiles > 40
+    guard = torch.full((n0,), 7.0, dtype=torch.float64, device="cuda")   # y is guard[:n]
+    args = (n, int(rp[-1]), dev(rp.astype(np.int32)), dev(ci), dev(va), dev(x), guard)
+    spmv.spmv_selftest_merge_abort(10)
+    try:
+        run(*args, s)
+        s.synchronize()
+    finally:
+        spmv.spmv_selftest_merge_abort(-1)
+    assert spmv.spmv_csr_error() == 6
+    g = guard.cpu().numpy()
+    assert np.all(g[n:] == 7.0), "a write landed past y[n)"
+    run(*args, s)
+    s.synchronize()
+    assert spmv.spmv_csr_error() == 0
+    assert_fp64_close(guard.cpu().numpy()[:n], want, scale, "after the give-up self-test")
+    assert np.all(guard.cpu().numpy()[n:] == 7.0)
+
+
+def test_merge_abort_hook_rejects_bad_tiles():
+    from paper_2203_02530_gb300 import spmv
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_selftest_merge_abort(-2)
+    assert e.value.code == spmv.EINVAL
+
+
 _PLAIN_CHILD = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, sys.argv[1])
