@@ -102,3 +102,138 @@ def canonicalize(order, stream_of_op):
 
 def stirling2(m, k):
     return sum((-1) ** j * math.comb(k, j) * (k - j) ** m for j in range(k + 1)) // math.factorial(k)
+
+
+def stream_map_counts(n_ops, n_streams):
+    """g[r][k]: canonical stream bindings of r more operations when k streams
+    are already in use.  Each operation takes one of the k streams in use or,
+    while k < n_streams, opens the next one; the count does not depend on
+    which operations these are or in what order they come:
+    g[0][k] = 1, g[r][k] = k g[r-1][k] + [k < S] g[r-1][k+1]."""
+    S = int(n_streams)
+    g = [[1] * (S + 1)]
+    for r in range(1, n_ops + 1):
+        prev = g[-1]
+        g.append([k * prev[k] + (prev[k + 1] if k < S else 0) for k in range(S + 1)])
+    return g
+
+
+class UniformSampler:
+    """Draws canonical implementations uniformly over all of them (the
+    random-sampling baseline of Sec. VI, against which MCTS is compared).
+
+    The implementations reachable from a prefix number e(done) * g[r][k]:
+    e(done) is the count of topological orders of the operations not yet
+    issued (a dynamic program over the DAG's downsets, memoised), g the
+    stream bindings above (r operations left, k streams in use).  Each step
+    takes ready operation v with probability e(done | v) / e(done) and then
+    a stream in use with probability g[r-1][k] / g[r][k] each, or the next
+    stream with probability g[r-1][k+1] / g[r][k]; the product of the
+    step probabilities is 1 / (e(0) g[n][0]) for every implementation."""
+
+    def __init__(self, dag, n_streams, max_states=5_000_000):
+        self.dag = dag
+        self.S = int(n_streams)
+        self.full = (1 << dag.n_ops) - 1
+        self.g = stream_map_counts(dag.n_ops, self.S)
+        self.max_states = max_states
+        self._e = {self.full: 1}
+        self._count_orders()
+
+    def _count_orders(self):
+        # downsets reached from the empty prefix, then e() from the full
+        # set back (iterative: no recursion limit, one pass per downset)
+        dag, seen, stack, topo = self.dag, {0}, [0], []
+        while stack:
+            d = stack.pop()
+            topo.append(d)
+            for v in dag.ready(d):
+                nd = d | 1 << v
+                if nd not in seen:
+                    if len(seen) >= self.max_states:
+                        raise ValueError("more than %d downsets: the DAG is too wide to count" % self.max_states)
+                    seen.add(nd)
+                    stack.append(nd)
+        for d in sorted(topo, key=lambda m: -bin(m).count("1")):
+            if d != self.full:
+                self._e[d] = sum(self._e[d | 1 << v] for v in dag.ready(d))
+        self.n_downsets = len(seen)
+
+    def orders(self, done=0):
+        """Topological orders of the operations outside `done` (a downset)."""
+        return self._e[done]
+
+    def total(self):
+        """Canonical implementations: orders x stream bindings."""
+        return self._e[0] * self.g[self.dag.n_ops][0]
+
+    def draw(self, rng):
+        """One implementation (order, stream_of_op); rng: random.Random."""
+        dag, g = self.dag, self.g
+        done, used, order, smap = 0, 0, [], [0] * dag.n_ops
+        left = dag.n_ops
+        while done != self.full:
+            ready = dag.ready(done)
+            u = rng.randrange(self._e[done])
+            for v in ready:
+                u -= self._e[done | 1 << v]
+                if u < 0:
+                    break
+            w = rng.randrange(g[left][used])
+            s = w // g[left - 1][used] if w < used * g[left - 1][used] else used
+            order.append(v)
+            smap[v] = s
+            used = max(used, s + 1)
+            done |= 1 << v
+            left -= 1
+        return order, smap
+
+
+def draw_per_decision(dag, n_streams, rng):
+    """One implementation completed by uniformly random legal decisions from
+    the empty prefix (the rollout of Sec. III-C without a tree).  Not uniform
+    over implementations: a decision leading to fewer completions is taken
+    as often as one leading to many."""
+    full = (1 << dag.n_ops) - 1
+    done, used, order, smap = 0, 0, [], [0] * dag.n_ops
+    while done != full:
+        opts = children(dag, done, used, n_streams)
+        v, s = opts[rng.randrange(len(opts))]
+        order.append(v)
+        smap[v] = s
+        used = max(used, s + 1)
+        done |= 1 << v
+    return order, smap
+
+
+def sample_programs(dag, n_streams, count, seed=0, mode="uniform", max_draws=None):
+    """`count` distinct implementations drawn at random (all of them, in a
+    random order, when the space holds no more than `count`).
+    mode "uniform": every implementation equally likely (UniformSampler);
+    "per_decision": uniformly random legal decisions (draw_per_decision)."""
+    import random
+    rng = random.Random(seed)
+    if mode == "uniform":
+        sampler = UniformSampler(dag, n_streams)
+        total = sampler.total()
+        draw = lambda: sampler.draw(rng)
+    elif mode == "per_decision":
+        total = count_schedules(dag, n_streams) if dag.n_ops <= 16 else None
+        draw = lambda: draw_per_decision(dag, n_streams, rng)
+    else:
+        raise ValueError("mode %r" % (mode,))
+    if total is not None and total <= count:
+        out = [(o, m) for o, m in enumerate_schedules(dag, n_streams)]
+        rng.shuffle(out)
+        return out
+    seen, out, draws = set(), [], 0
+    limit = max_draws if max_draws is not None else 50 * count + 10_000
+    while len(out) < count and draws < limit:
+        draws += 1
+        o, m = draw()
+        key = (tuple(o), tuple(m))
+        if key in seen:
+            continue
+        seen.add(key)
+        out.append((o, m))
+    return out

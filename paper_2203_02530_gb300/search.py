@@ -82,30 +82,15 @@ def mcts(part, streams, evaluate, iterations, seed=0):
     return tree.run(iterations), tree
 
 
-def random_sampling(part, streams, evaluate, count, seed=0):
-    """Baseline search: `count` distinct programs, each completed by
-    uniformly random legal decisions from the empty prefix (the rollout of
-    Sec. III-C without a tree).  Returns [(order, smap, seconds)]."""
-    import random
-    from .schedules import children
+def random_sampling(part, streams, evaluate, count, seed=0, mode="uniform"):
+    """Baseline search (Sec. VI: random sampling against MCTS at an equal
+    number of measured programs): `count` distinct programs drawn at random
+    and measured.  mode "uniform" draws every program with equal probability;
+    "per_decision" completes each program by uniformly random legal decisions
+    from the empty prefix (the rollout of Sec. III-C without a tree, which
+    favours programs whose prefixes have few completions).  Returns
+    [(order, smap, seconds)]."""
+    from .schedules import sample_programs
     dag = Dag(part.n_ops, part.dag())
-    rng = random.Random(seed)
-    full = (1 << dag.n_ops) - 1
-    seen, out = set(), []
-    tries = 0
-    while len(out) < count and tries < 50 * count:
-        tries += 1
-        done, used, order, smap = 0, 0, [], [0] * dag.n_ops
-        while done != full:
-            opts = children(dag, done, used, len(streams))
-            v, s_ = opts[rng.randrange(len(opts))]
-            order.append(v)
-            smap[v] = s_
-            used = max(used, s_ + 1)
-            done |= 1 << v
-        key = (tuple(order), tuple(smap))
-        if key in seen:
-            continue
-        seen.add(key)
-        out.append((order, smap, evaluate(order, smap)))
-    return out
+    progs = sample_programs(dag, len(streams), count, seed=seed, mode=mode)
+    return [(o, m, evaluate(o, m)) for o, m in progs]
