@@ -10,8 +10,15 @@ is the one timed.  A step is one replay of that graph: one whole SpMV.
 
 Output: one JSON line (rank 0).  ``value`` is effective GB/s = algorithmic
 bytes per SpMV x steps / time, summed over ranks (each rank runs its own
-replica: weak scaling, no data-path collective).  ``--impl reference`` times
-the CPU oracle on the host cores instead.
+replica: weak scaling, no data-path collective).  On one GPU the line also
+carries the metric's other configurations as sub-objects, each measured in
+the same run with its own value, roofline, latency, end-to-end figure, CPU
+baseline and clocks: ``powerlaw`` (n = 4M power-law rows, P = 8 per-rank
+DAG, a bounded MCTS search), ``batched`` (256 matrices in one persistent
+launch against each matrix through the tuned single-matrix product) and
+``serving`` (Poisson arrivals served with continuous batching against one
+plain launch per request).  ``--impl reference`` times the CPU oracle on the
+host cores instead.
 """
 import argparse
 import hashlib
@@ -143,12 +150,19 @@ def hbm_peak():
         return FALLBACK_HBM, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the product kernels' code (comments and blank lines left out,
-    so that a comment edit does not invalidate a profile)."""
+# the files each profiled kernel is built from (besides the shared headers)
+KERNEL_FILES = {"csr_sell_kernel": ["sell.cu"], "merge_kernel": ["merge.cu"],
+                "batch_sliced_persistent_kernel": ["batch.cu", "batch.h"],
+                "batch_persistent_kernel": ["batch.cu", "batch.h"]}
+SHARED_HEADERS = ["internal.h", "pdl.cuh"]
+
+
+def kernel_source_hash(kernel):
+    """Hash of the code a kernel is built from (comments and blank lines
+    left out, so that a comment edit does not invalidate a profile)."""
     import re
     h = hashlib.sha256()
-    for f in ("kernels.cu", "merge.cu", "sell.cu"):
+    for f in KERNEL_FILES.get(kernel, ["kernels.cu"]) + SHARED_HEADERS:
         with open(os.path.join(ROOT, "paper_2203_02530_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = re.sub(r"//.*", "", line).rstrip()
@@ -157,19 +171,57 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel sources."""
+def profiled_traffic(workload, key):
+    """DRAM bytes per launch (or per launch group) of `key` (kernel/variant/
+    param) on `workload` from the committed ncu summary, if it was taken on
+    the kernel's current sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("source_hash") != kernel_source_hash():
+    k = d.get("workloads", {}).get(workload, {}).get(key)
+    if k is None or k.get("source_hash") != kernel_source_hash(key.split("/")[0]):
         return None
-    k = d.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_full_launch")
+    return k.get("dram_bytes_per_full_launch")
+
+
+def fp64_probe(dev, props, seconds=0.25):
+    """Measured FP64 FMA throughput of this GPU (the library's DFMA probe,
+    timed with CUDA events, SM clock sampled meanwhile): G DFMA/s with 32 and
+    with 1 active lane per warp."""
+    import torch
+    from paper_2203_02530_gb300 import benchmark, spmv
+    s = torch.cuda.Stream(device=dev)
+    cps = 4
+    cap = props.multi_processor_count * cps * 256
+    out = torch.empty(cap, dtype=torch.float64, device=dev)
+    res = {}
+    sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+    sampler.start()
+    for lanes in (32, 1):
+        iters = 1 << 12
+        while True:   # size one launch to about 20 ms
+            t = benchmark.time_loop(lambda: spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s), s, 1, warmup=1)
+            if t > 0.02 or iters >= 1 << 30:
+                break
+            iters *= 2
+        reps = max(2, int(seconds / 2 / t))
+        dfma = spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s)
+        t = benchmark.time_loop(lambda: spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s), s, reps, warmup=1)
+        res[lanes] = (dfma / t, t, iters)
+    clocks = sampler.stop()
+    mhz = clocks.get("sm_mhz") or props.clock_rate / 1e3
+    rate = res[32][0]
+    return {"dfma_per_s": rate, "unit": "G DFMA/s", "g_dfma_per_s": round(rate / 1e9, 1),
+            "per_clk_per_sm": round(rate / (mhz * 1e6) / props.multi_processor_count, 3),
+            "sm_mhz": mhz, "one_lane_g_dfma_per_s": round(res[1][0] / 1e9, 2),
+            "one_lane_g_warp_instr_per_s": round(res[1][0] / 1e9, 2),
+            "full_warp_g_warp_instr_per_s": round(rate / 32 / 1e9, 2),
+            "how": "spmv_probe_dfma: %d CTAs x 256 threads, 8 chains of %d DFMAs per lane, CUDA events, "
+                   "%d launches; the one-lane run keeps 1 lane of each warp busy" % (
+                       props.multi_processor_count * cps, res[32][2], max(2, int(seconds / 2 / res[32][1])))}
 
 
 # ---------------------------------------------------------------- workload
@@ -272,11 +324,44 @@ def powerlaw():
     return n, rp, ci, va, W.uniform_x(n, seed=4)
 
 
-def run_ours(args, world, rank, local):
+_DIST = {}
+
+
+def dist_once(world):
+    if "d" not in _DIST:
+        _DIST["d"] = dist_init(world, "nccl")
+    return _DIST["d"]
+
+
+def per_sample_latency(step, stream, count):
+    """Per-sample times (s) of `count` back-to-back samples, each bracketed
+    by its own pair of CUDA events on `stream`."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(count + 1)]
+    ev[0].record(stream)
+    for i in range(count):
+        step()
+        ev[i + 1].record(stream)
+    ev[-1].synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) * 1e-3 for i in range(count)]
+
+
+def latency_block(per_sample, meas):
+    from paper_2203_02530_gb300 import benchmark
+    return {"p50": round(benchmark.percentile(per_sample, 50) * 1e6, 2),
+            "p99": round(benchmark.percentile(per_sample, 99) * 1e6, 2),
+            "samples": len(per_sample), "protocol": "per sample: CUDA events around each of back-to-back "
+                                                    "replays",
+            "measurements": {"p50": round(benchmark.percentile(meas, 50) * 1e6, 2),
+                             "p99": round(benchmark.percentile(meas, 99) * 1e6, 2),
+                             "count": len(meas), "protocol": "Sec. III-C.3: mean over 0.01 s of samples each"}}
+
+
+def run_ours(args, world, rank, local, fp64=None):
     import numpy as np
     import torch
     torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
+    dist = dist_once(world)
     from paper_2203_02530_gb300 import autotune, benchmark, search, spmv
 
     desc, gen, P, S, gran, mode = WORKLOADS[args.workload]
@@ -304,20 +389,25 @@ def run_ours(args, world, rank, local):
     # hiccup during one measurement does not masquerade as a slow program
     evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec, measurements=3
                                       if mode == "exhaustive" else 2)
+    t_search = time.perf_counter()
     if mode == "exhaustive":
         sched = search.exhaustive(part, streams, evaluate)
     elif mode == "mcts":
         sched, _ = search.mcts(part, streams, evaluate, args.mcts_iters, seed=0)
         if args.random_baseline:
-            rand = search.random_sampling(part, streams, evaluate, args.random_baseline, seed=1)
-            rt = [r[2] for r in rand]
+            cmp = {"samples": args.random_baseline}
             mt = [r[2] for r in sched[:args.random_baseline]]
-            search_cmp = {"samples": len(rand),
-                          "random": {"best_us": round(min(rt) * 1e6, 2), "worst_us": round(max(rt) * 1e6, 2)},
-                          "mcts": {"best_us": round(min(mt) * 1e6, 2), "worst_us": round(max(mt) * 1e6, 2)}}
+            cmp["mcts"] = {"best_us": round(min(mt) * 1e6, 2), "worst_us": round(max(mt) * 1e6, 2)}
+            for rmode in ("uniform", "per_decision"):
+                rand = search.random_sampling(part, streams, evaluate, args.random_baseline, seed=1, mode=rmode)
+                rt = [r[2] for r in rand]
+                cmp["random_" + rmode] = {"best_us": round(min(rt) * 1e6, 2), "worst_us": round(max(rt) * 1e6, 2),
+                                          "samples": len(rand)}
+            search_cmp = cmp
     else:
         order = list(range(part.n_ops))
         sched = [(order, [0] * part.n_ops, evaluate(order, [0] * part.n_ops))]
+    t_search = time.perf_counter() - t_search
     sched = sorted(sched, key=lambda r: r[2])
     order, smap, t_best = sched[0]
     spread = sched[-1][2] / sched[0][2]
@@ -360,22 +450,27 @@ def run_ours(args, world, rank, local):
     elapsed = max_over_ranks(dist, elapsed, dev)
     value = world * alg * args.steps / elapsed / 1e9
 
-    # the dominant kernel (LOCAL product, coarse launch), timed alone on the
-    # stream the schedule launches it on, with CUDA events
-    s_local = streams[smap[spmv.OP_LOCAL]]
-    t_local = benchmark.time_loop(lambda: spmv.spmv_local(part.h, -1, x_d, y_d, s_local),
-                                  s_local, max(50, min(args.steps, 1000)))
+    # the dominant kernel (the LOCAL product) timed alone on the stream the
+    # schedule launches it on, with CUDA events: one launch over all ranks
+    # for a coarse plan, the P per-rank launches in a row for a per-rank plan
+    # (the launches its schedules run)
+    per_rank = gran != spmv.COARSE
+    s_local = streams[smap[spmv.OP_LOCAL]] if not per_rank else streams[0]
+    if per_rank:
+        local_unit = lambda: [spmv.spmv_local(part.h, p, x_d, y_d, s_local) for p in range(P)]
+    else:
+        local_unit = lambda: spmv.spmv_local(part.h, -1, x_d, y_d, s_local)
+    t_local = benchmark.time_loop(local_unit, s_local, max(50, min(args.steps, 1000)))
     peak, peak_kind = hbm_peak()
     achieved = alg_local / t_local / 1e9
     kname = {spmv.VARIANT_TILE: "csr_tile_kernel", spmv.VARIANT_VECTOR: "csr_vector_kernel",
              spmv.VARIANT_MERGE: "merge_kernel", spmv.VARIANT_PAIRS: "csr_pair_kernel",
              spmv.VARIANT_WARP: "csr_warp_kernel", spmv.VARIANT_SELL: "csr_sell_kernel",
              spmv.VARIANT_SELL16: "csr_sell_kernel"}[variant]
-    traffic = profiled_traffic("%s/%d/%d" % (kname, variant, vparam))
-    if traffic is None:   # the layout's bytes, measured with another param of the variant
-        traffic = profiled_traffic("%s/%d" % (kname, variant))
+    traffic = profiled_traffic(args.workload, "%s/%d/%d" % (kname, variant, vparam))
 
-    # paper protocol: per-measurement latency percentiles of the best schedule
+    # latency of the best schedule: per sample, and per 0.01 s measurement
+    per_sample = per_sample_latency(step, streams[0], max(args.latency_samples, args.steps))
     meas = benchmark.measurements(step, streams[0], args.measurements)
 
     # end to end through the C ABI with host buffers
@@ -400,6 +495,7 @@ def run_ours(args, world, rank, local):
         spmv.spmv_apply_host_pipelined(part.h, xh, yh, cs, streams[0])
     t_e2e = max_over_ranks(dist, (time.perf_counter() - t0) / k_e2e, dev)
     err = part.query(spmv.Q_ERROR)
+    dev_bytes = part.query(spmv.Q_DEVICE_BYTES)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -412,8 +508,9 @@ def run_ours(args, world, rank, local):
     part.close()
     if rank != 0:
         return None
-    sm_mhz = clocks.get("sm_mhz") or 0.0
-    fp64_peak = 2.0 * props.multi_processor_count * (sm_mhz or 2070.0) * 1e6   # DFMA/s
+    if fp64 is None:
+        fp64 = fp64_probe(dev, props)
+    dfma_rate = nnz_l / t_local
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -423,28 +520,30 @@ def run_ours(args, world, rank, local):
         "config": {"workload": desc, "n": n, "nnz": int(rp[-1]), "P": P, "streams": S,
                    "granularity": ("coarse", "per-rank", "per-segment")[gran],
                    "search": mode, "schedules_measured": len(sched),
+                   "search_seconds": round(t_search, 1),
                    "best_order": order, "best_streams": smap,
                    "variant": {"local": list(tuned["local"]), "remote": list(tuned["remote"])},
                    "l2": "inputs larger than L2" if 12 * int(rp[-1]) > 129e6
                          else "L2-resident (replay latency)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "alg_bytes_per_step": alg},
+                   "alg_bytes_per_step": alg, "plan_device_bytes": dev_bytes},
         "percent_hbm": round(100.0 * value / world / peak, 2),
         "roofline": dict({"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                           "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                           "traffic": traffic, "peak_kind": peak_kind,
-                          "alg_bytes_per_launch": alg_local, "launch_us": round(t_local * 1e6, 2)},
+                          "alg_bytes_per_launch": alg_local, "launch_us": round(t_local * 1e6, 2),
+                          "launches": P if per_rank else 1},
                          **({} if traffic is None else {
                              "dram_gbs": round(traffic / t_local / 1e9, 1),
                              "dram_frac": round(traffic / t_local / 1e9 / peak, 4),
                              "note": "achieved counts the CSR algorithmic bytes; the DRAM traffic of "
                                      "the launch (ncu) is `traffic`"})),
-        "fp64": {"dfma_per_s": round(nnz_l / t_local / 1e9, 1), "unit": "G DFMA/s",
-                 "peak": round(fp64_peak / 1e9, 1), "frac": round(nnz_l / t_local / fp64_peak, 4),
-                 "note": "2 DFMA/clk/SM at the sampled SM clock"},
-        "latency_us": {"p50": round(benchmark.percentile(meas, 50) * 1e6, 2),
-                       "p99": round(benchmark.percentile(meas, 99) * 1e6, 2),
-                       "measurements": len(meas), "protocol": "0.01 s of samples each"},
+        "fp64": {"dfma_per_s": round(dfma_rate / 1e9, 1), "unit": "G DFMA/s",
+                 "peak": fp64["g_dfma_per_s"], "frac": round(dfma_rate / fp64["dfma_per_s"], 4),
+                 "peak_kind": "measured by spmv_probe_dfma in this run (%.3f DFMA/clk/SM at %.0f MHz)" % (
+                     fp64["per_clk_per_sm"], fp64["sm_mhz"]),
+                 "note": "one DFMA per stored local entry over the LOCAL launch time"},
+        "latency_us": latency_block(per_sample, meas),
         "schedule_spread": round(spread, 4),
         "search_vs_random": search_cmp,
         "e2e": {"value": round(alg / min(t_e2e, t_e2e_graph) / 1e9, 2), "unit": "GB/s",
@@ -466,14 +565,58 @@ def run_ours(args, world, rank, local):
 
 
 # ---------------------------------------------------------------- batched
+# variants the plain per-matrix form picks from, per matrix (the families the
+# single-matrix tuner chooses on stencils, Zipf rows and skewed rows)
+def plain_candidates():
+    from paper_2203_02530_gb300 import spmv
+    return [(spmv.VARIANT_SELL16, 107), (spmv.VARIANT_SELL16, 9), (spmv.VARIANT_SELL, 105),
+            (spmv.VARIANT_SELL, 8), (spmv.VARIANT_SELL, 2105), (spmv.VARIANT_SELL, 4),
+            (spmv.VARIANT_VECTOR, 2), (spmv.VARIANT_MERGE, 0)]
+
+
+def plain_per_matrix(mats, offs, x_d, s, reps=10):
+    """The plain form of many products: every matrix through the library's
+    single-matrix product (a plan with P = 1, whose LOCAL product is the
+    whole product), each with the fastest of plain_candidates() on that
+    matrix, launched one after another.  Returns (parts, run(y), variants)."""
+    import torch
+    from paper_2203_02530_gb300 import benchmark, spmv
+    parts, chosen = [], []
+    y_tmp = torch.empty(offs[-1], dtype=torch.float64, device=x_d.device)
+    for m, (n, rp, ci, va) in enumerate(mats):
+        part = spmv.Part(n, rp, ci, va, 1)
+        xm, ym = x_d[offs[m]:offs[m] + n], y_tmp[offs[m]:offs[m] + n]
+        best = None
+        for v, p in plain_candidates():
+            try:
+                part.set_op_variant(spmv.OP_LOCAL, v, p)
+            except spmv.SpmvError as e:
+                if e.code != spmv.EINVAL:
+                    raise
+                continue
+            t = benchmark.time_loop(lambda: spmv.spmv_local(part.h, -1, xm, ym, s), s, reps, warmup=2)
+            if best is None or t < best[0]:
+                best = (t, v, p)
+        part.set_op_variant(spmv.OP_LOCAL, best[1], best[2])
+        parts.append(part)
+        chosen.append((best[1], best[2]))
+
+    def run(y_d):
+        for m, part in enumerate(parts):
+            n = mats[m][0]
+            spmv.spmv_local(part.h, -1, x_d[offs[m]:offs[m] + n], y_d[offs[m]:offs[m] + n], s)
+    return parts, run, chosen
+
+
 def run_batched(args, world, rank, local):
     """256 independent SpMVs (n log-uniform in [1e3, 1e6]; 5-point, 7-point
-    and Zipf-row matrices) in one persistent launch, against the same
-    products as 256 launches (eager and captured in a CUDA graph)."""
+    and Zipf-row matrices) in one persistent launch, against the plain form
+    (each matrix through the library's tuned single-matrix product, the 256
+    launches captured in one CUDA graph)."""
     import numpy as np
     import torch
     torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
+    dist = dist_once(world)
     from paper_2203_02530_gb300 import autotune, benchmark, spmv
     from paper_2203_02530_gb300 import workloads as W
     dev = torch.device("cuda", local)
@@ -487,6 +630,7 @@ def run_batched(args, world, rank, local):
     x_d = torch.from_numpy(x).to(dev)
     y_b = torch.empty(total, dtype=torch.float64, device=dev)
     y_s = torch.empty(total, dtype=torch.float64, device=dev)
+    y_p = torch.empty(total, dtype=torch.float64, device=dev)
     s = torch.cuda.Stream(device=dev)
     mrl = [(int(m[1][-1]) / m[0]) if m[0] else 0.0 for m in mats]
     tune_log = []
@@ -498,13 +642,11 @@ def run_batched(args, world, rank, local):
     separate()
     s.synchronize()
     identical = bool(torch.equal(y_b, y_s))
-    # the 256 launches captured once as a graph (the fairest plain form)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        separate()
     for _ in range(args.warmup):
         batched()
     s.synchronize()
+    if dist:
+        dist.barrier()
     sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
     sampler.start()
     torch.cuda.nvtx.range_push("timed_region")
@@ -512,16 +654,34 @@ def run_batched(args, world, rank, local):
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     t_b = max_over_ranks(dist, t_b, dev)
-    t_sep = benchmark.time_loop(separate, s, max(3, args.steps // 10), warmup=args.warmup)
+    per_sample = per_sample_latency(batched, s, max(args.latency_samples, args.steps))
+    meas = benchmark.measurements(batched, s, max(3, args.measurements // 4))
+    # the plain form: every matrix through the tuned single-matrix product
+    t0 = time.perf_counter()
+    parts, plain_run, chosen = plain_per_matrix(mats, offs, x_d, s)
+    t_plain_tune = time.perf_counter() - t0
+    plain_run(y_p)
+    s.synchronize()
+    d = (y_p - y_b).abs().max().item()
+    rel_plain = d / max(y_b.abs().max().item(), 1e-300)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plain_run(y_p)
+
     def replay():
         with torch.cuda.stream(s):
             g.replay()
-    t_graph = benchmark.time_loop(replay, s, max(3, args.steps // 4), warmup=args.warmup)
-    meas = benchmark.measurements(batched, s, args.measurements)
+    t_plain_graph = benchmark.time_loop(replay, s, max(5, args.steps), warmup=args.warmup)
+    t_plain_eager = benchmark.time_loop(lambda: plain_run(y_p), s, max(3, args.steps // 4), warmup=2)
+    plain_sample = per_sample_latency(replay, s, max(20, args.steps))
+    del g
+    for part in parts:
+        part.close()
+    # ablation: the batch's own work items launched once per matrix
+    t_sep = benchmark.time_loop(separate, s, max(3, args.steps // 4), warmup=2)
     # end to end: x from pinned host memory, the product, y back to the host
     xh = torch.from_numpy(x).pin_memory()
     yh = torch.empty(total, dtype=torch.float64).pin_memory()
-
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
     def e2e(chunks):   # through the library: chunked x in, products, y out, overlapped
@@ -544,21 +704,35 @@ def run_batched(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         reps, t0 = 0, time.perf_counter()
+        byts = 0
         while time.perf_counter() - t0 < args.cpu_seconds or reps == 0:
             for m, (n, rp, ci, va) in enumerate(mats):
                 oracle.csr_spmv(n, rp, ci, va, x[offs[m]:offs[m] + n])
+                byts += 12 * int(rp[-1]) + 4 * (n + 1) + 16 * n
+                if time.perf_counter() - t0 >= args.cpu_seconds:
+                    break
             reps += 1
         secs = time.perf_counter() - t0
-        cpu = {"value": round(alg * reps / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "%d passes over all 256 matrices (plain CSR products), single-threaded C "
-                         "oracle, %.1f s (nproc=%d)" % (reps, secs, os.cpu_count() or 0)}
+        cpu = {"value": round(byts / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "plain CSR products of the batch's matrices in order (%.2f passes over all 256), "
+                         "single-threaded C oracle, %.1f s (nproc=%d)" % (byts / alg, secs, os.cpu_count() or 0)}
     launches = spmv.spmv_batch_query(b.h, spmv.BQ_LAUNCHES, -1)
+    dev_bytes = b.query(spmv.BQ_DEVICE_BYTES)
     b.close()
     if rank != 0:
         return None
     peak, peak_kind = hbm_peak()
     value = world * alg / t_b / 1e9
     nnz = int(sum(int(m[1][-1]) for m in mats))
+    kname = ("batch_sliced_persistent_kernel" if all(l == spmv.BATCH_SLICED for l in lanes)
+             else "batch_persistent_kernel")
+    traffic = profiled_traffic("batched", kname)
+    vname = {spmv.VARIANT_SELL16: "SELL16", spmv.VARIANT_SELL: "SELL", spmv.VARIANT_VECTOR: "VECTOR",
+             spmv.VARIANT_MERGE: "MERGE"}
+    hist = {}
+    for v, p in chosen:
+        k = "%s/%d" % (vname.get(v, str(v)), p)
+        hist[k] = hist.get(k, 0) + 1
     return {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_b * 1e3, 5),
@@ -568,22 +742,26 @@ def run_batched(args, world, rank, local):
                                "5-point / 7-point / Zipf-row (mean ~10) matrices, one persistent launch",
                    "matrices": len(mats), "total_rows": total, "nnz": nnz,
                    "lanes_histogram": {str(v): lanes.count(v) for v in sorted(set(lanes))},
-                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg},
+                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg, "batch_device_bytes": dev_bytes},
         "percent_hbm": round(100.0 * value / world / peak, 2),
-        "separate_launches": {"eager_gbs": round(alg / t_sep / 1e9, 2),
-                              "graph_gbs": round(alg / t_graph / 1e9, 2),
-                              "eager_ms": round(t_sep * 1e3, 4), "graph_ms": round(t_graph * 1e3, 4),
-                              "bit_identical_to_batched": identical},
-        "speedup_vs_separate_graph": round(t_graph / t_b, 3),
-        "speedup_vs_separate_eager": round(t_sep / t_b, 3),
-        "roofline": {"bound": "hbm",
-                     "kernel": ("batch_sliced_persistent_kernel" if all(l == spmv.BATCH_SLICED for l in lanes)
-                                else "batch_persistent_kernel"),
+        "plain": {"form": "each matrix through the library's single-matrix product (P=1 plan, LOCAL "
+                          "variant tuned per matrix), 256 launches captured in one CUDA graph",
+                  "graph_ms": round(t_plain_graph * 1e3, 4), "gbs": round(alg / t_plain_graph / 1e9, 2),
+                  "eager_ms": round(t_plain_eager * 1e3, 4),
+                  "p50_us": round(benchmark.percentile(plain_sample, 50) * 1e6, 2),
+                  "p99_us": round(benchmark.percentile(plain_sample, 99) * 1e6, 2),
+                  "variants": hist, "tune_seconds": round(t_plain_tune, 1),
+                  "max_abs_diff_over_max_abs_y": rel_plain},
+        "speedup_vs_plain": round(t_plain_graph / t_b, 3),
+        "ablation_batch_items_per_matrix": {
+            "form": "the persistent kernel's work items launched once per matrix (spmv_batch_run_separate)",
+            "eager_ms": round(t_sep * 1e3, 4), "gbs": round(alg / t_sep / 1e9, 2),
+            "bit_identical_to_batched": identical},
+        "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": round(alg / t_b / 1e9, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(alg / t_b / 1e9 / peak, 4), "traffic": None, "peak_kind": peak_kind},
-        "latency_us": {"p50": round(benchmark.percentile(meas, 50) * 1e6, 2),
-                       "p99": round(benchmark.percentile(meas, 99) * 1e6, 2),
-                       "measurements": len(meas), "protocol": "0.01 s of samples each"},
+                     "frac": round(alg / t_b / 1e9 / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg, "launch_us": round(t_b * 1e6, 2)},
+        "latency_us": latency_block(per_sample, meas),
         "e2e": {"value": round(alg / t_e2e / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
                 "ms_per_step": round(t_e2e * 1e3, 4), "path": "spmv_batch_run_host, %d chunks" % n_chunks,
@@ -595,7 +773,7 @@ def run_batched(args, world, rank, local):
 
 
 # ---------------------------------------------------------------- serving
-def run_serving(args, world, rank, local):
+def run_serving(args, world, rank, local, fp64=None):
     """Poisson arrivals of SpMV requests over 64 resident matrices, each a
     block of 1..8 right-hand sides with device-drawn inputs, served with
     continuous batching against one plain launch per request."""
@@ -604,6 +782,8 @@ def run_serving(args, world, rank, local):
     torch.cuda.set_device(local)
     from paper_2203_02530_gb300 import spmv
     from paper_2203_02530_gb300 import workloads as W
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
     mix = W.serve_mix(64, seed=6)
     mats = [m for _, m in mix]
     b = spmv.Batch(mats)
@@ -623,15 +803,23 @@ def run_serving(args, world, rank, local):
     req_bytes = 12 * zz[mat] + 4 * (nn[mat] + 1) + 16 * nn[mat] * wid
     warm = min(2000, count)
     sv.run(mat[:warm], wid[:warm], sd[:warm], np.zeros(warm), spmv.SERVE_BATCHED, want_hash=False)
+    sv.run(mat[:warm], wid[:warm], sd[:warm], np.zeros(warm), spmv.SERVE_PLAIN, want_hash=False)
     out = {}
+    clocks = None
     for name, mode in (("served", spmv.SERVE_BATCHED), ("plain", spmv.SERVE_PLAIN)):
+        sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+        sampler.start()
         lat, hs, st = sv.run(mat, wid, sd, arr, mode, want_hash=True)
+        c = sampler.stop()
+        clocks = clocks or c
         el = st["elapsed_ns"] * 1e-9
         out[name] = {"p50_us": round(float(np.percentile(lat, 50)) * 1e6, 2),
                      "p99_us": round(float(np.percentile(lat, 99)) * 1e6, 2),
+                     "p999_us": round(float(np.percentile(lat, 99.9)) * 1e6, 2),
                      "throughput_req_s": round(count / el, 1), "gbs": round(req_bytes.sum() / el / 1e9, 2),
                      "blocks": st["blocks"], "max_inflight": st["max_inflight"],
                      "admitted_while_busy": st["admitted_while_busy"],
+                     "launches": spmv.spmv_serve_launches(sv.h),
                      "peak_pool_mb": round(st["peak_pool_bytes"] / 1e6, 1), "hash": hs}
     same = bool(np.array_equal(out["served"].pop("hash"), out["plain"].pop("hash")))
     # saturation: every request present at t = 0 (the most either form can do)
@@ -667,7 +855,9 @@ def run_serving(args, world, rank, local):
     total = int(sum(zz) * 12 + sum(nn) * 4)
     b.close()
     peak, peak_kind = hbm_peak()
-    fp64_peak = 2.0 * torch.cuda.get_device_properties(local).multi_processor_count * 2070.0e6   # DFMA/s
+    if fp64 is None:
+        fp64 = fp64_probe(dev, props)
+    fpeak = 2.0 * fp64["dfma_per_s"]   # flop/s
     value = sat["served"]["gbs"]
     return {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
@@ -679,25 +869,29 @@ def run_serving(args, world, rank, local):
                                "budget 40 GB, %d stream slots, %s layout" % (
                                    rate, args.serve_seconds, count, total / 1e9, args.serve_streams,
                                    args.serve_layout),
-                   "value": "saturation throughput of the served form (all requests present at t=0)"},
+                   "value": "saturation throughput of the served form (all requests present at t=0; a "
+                            "step is one request), per-request algorithmic bytes"},
         "open_loop": out, "saturation": sat,
         "served_vs_plain_saturation": round(sat["served"]["gbs"] / sat["plain"]["gbs"], 3),
         "results_identical_served_vs_plain": same,
         "latency_us": {"p50": out["served"]["p50_us"], "p99": out["served"]["p99_us"],
-                       "protocol": "arrival to observed completion, open loop"},
+                       "plain_p50": out["plain"]["p50_us"], "plain_p99": out["plain"]["p99_us"],
+                       "protocol": "arrival to observed completion, open loop, %d requests" % count},
         "roofline": {"bound": "alu",
                      "kernel": "spmm_group_kernel" if args.serve_layout == "sliced" else "spmm_kernel",
-                     "achieved": round(sat_flops / 1e12, 4), "peak": round(fp64_peak * 2 / 1e12, 4),
-                     "unit": "TFLOP/s", "frac": round(sat_flops / (fp64_peak * 2), 4), "traffic": None,
-                     "peak_kind": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs at the maximum SM clock",
+                     "achieved": round(sat_flops / 1e12, 4), "peak": round(fpeak / 1e12, 4),
+                     "unit": "TFLOP/s", "frac": round(sat_flops / fpeak, 4), "traffic": None,
+                     "peak_kind": "FP64 FMA pipe measured by spmv_probe_dfma in this run (2 flops per DFMA)",
                      "note": "2 flops per entry per right-hand side, over the saturation run's elapsed time "
                              "(all launches and the gaps between them)"},
-        "hbm_fraction": {"achieved": value, "peak": peak, "unit": "GB/s", "frac": round(value / peak, 4),
+        "hbm_fraction": {"achieved": sat["served"]["gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": round(sat["served"]["gbs"] / peak, 4),
                          "peak_kind": peak_kind, "note": "per-request algorithmic bytes at saturation"},
-        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
-                "note": "inputs are drawn on the device from each request's seed; the host reads "
-                        "one 8-byte hash per request"},
-        "cpu_baseline": cpu, "gpu_launches": sat["served"]["launches"],
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 16, "d2h_bytes_per_step": 8,
+                "note": "the saturation run is already end to end: host-timed through spmv_serve_run, the "
+                        "public entry point, which takes each request's descriptor (matrix, width, seed) "
+                        "from the host and returns an 8-byte hash of its Y; X is drawn on the device"},
+        "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": out["served"]["launches"],
     }
 
 
@@ -748,13 +942,58 @@ def run_reference(args, world, rank):
     }
 
 
+SUB_DROP = ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data")
+
+
+def sub_line(line):
+    """A workload's line as a sub-object of the headline line."""
+    return {k: v for k, v in line.items() if k not in SUB_DROP}
+
+
+def run_subs(args, world, rank, local, fp64):
+    """Configs 3-5 of the metric, each measured and reported as a
+    sub-object: the power-law matrix with a bounded MCTS search, the batch of
+    256 matrices against its plain per-matrix form, and serving against
+    plain per-request launches."""
+    import copy
+    out = {}
+    for name in args.subs.split(","):
+        a = copy.copy(args)
+        a.cpu_seconds = args.sub_cpu_seconds
+        a.records = None
+        a.random_baseline = 0
+        a.measurements = args.sub_measurements
+        t0 = time.perf_counter()
+        if name == "powerlaw":
+            a.workload = "powerlaw"
+            a.mcts_iters = args.sub_mcts_iters
+            line = run_ours(a, world, rank, local, fp64=fp64)
+        elif name == "batched":
+            line = run_batched(a, world, rank, local)
+        elif name == "serving":
+            a.serve_seconds = args.sub_serve_seconds
+            line = run_serving(a, world, rank, local, fp64=fp64)
+        else:
+            raise SystemExit("unknown sub-workload %r" % name)
+        if line is not None:
+            sub = sub_line(line)
+            sub["wall_seconds"] = round(time.perf_counter() - t0, 1)
+            out[name] = sub
+        import torch
+        torch.cuda.empty_cache()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--measurements", type=int, default=40)
+    ap.add_argument("--measurements", type=int, default=200,
+                    help="0.01 s measurements of the best schedule (Sec. III-C.3) for its percentiles")
+    ap.add_argument("--latency-samples", type=int, default=2000,
+                    help="back-to-back samples timed one by one for the per-sample percentiles")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--retune", action="store_true")
@@ -764,9 +1003,17 @@ def main(argv=None):
                     default="stencil27",
                     help="stencil27 (default): 27-point 150^3; laplacian: 5-point 64x64; "
                          "powerlaw: n=4M with MCTS over the per-rank DAG")
+    ap.add_argument("--subs", default="powerlaw,batched,serving",
+                    help="with the default workload on one GPU: the other configs of the metric "
+                         "measured after it and reported as sub-objects ('' for none)")
+    ap.add_argument("--sub-mcts-iters", type=int, default=200)
+    ap.add_argument("--sub-serve-seconds", type=float, default=3.0)
+    ap.add_argument("--sub-cpu-seconds", type=float, default=6.0)
+    ap.add_argument("--sub-measurements", type=int, default=50)
     ap.add_argument("--mcts-iters", type=int, default=2000)
     ap.add_argument("--random-baseline", type=int, default=0,
-                    help="also measure this many random-rollout programs (search baseline)")
+                    help="also measure this many random programs (uniform over programs, and by "
+                         "random decisions) as the search baseline")
     ap.add_argument("--records", default=None, help="JSONL log of every measured schedule")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -782,12 +1029,21 @@ def main(argv=None):
     else:
         import __graft_entry__
         __graft_entry__.build()
+        import torch
+        torch.cuda.set_device(local)
+        fp64 = fp64_probe(torch.device("cuda", local), torch.cuda.get_device_properties(local))
         if args.workload == "batched":
             line = run_batched(args, world, rank, local)
         elif args.workload == "serving":
-            line = run_serving(args, world, rank, local)
+            line = run_serving(args, world, rank, local, fp64=fp64)
         else:
-            line = run_ours(args, world, rank, local)
+            line = run_ours(args, world, rank, local, fp64=fp64)
+            if args.workload == "stencil27" and args.subs and world == 1:
+                subs = run_subs(args, world, rank, local, fp64)
+                if line is not None:
+                    line.update(subs)
+        if line is not None:
+            line["fp64_probe"] = {k: v for k, v in fp64.items() if k != "dfma_per_s"}
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -497,6 +497,20 @@ int spmv_selftest_check(int64_t* found_out);
  * runs out.  Synchronises; leaves the context usable. */
 int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out);
 
+/* FP64 fused multiply-add throughput probe (a measurement helper, not part
+ * of the paper's method): the second roofline of the product, whose cost on
+ * this part is one DFMA per stored entry.  Launches SM count x ctas_per_sm
+ * (1..8) CTAs of 256 threads on stream s; in every warp the first `lanes`
+ * (1..32) lanes run 8 independent chains of `iters` DFMAs each; every thread
+ * then writes one double to out_dev (caller-owned device memory of at least
+ * out_cap >= SM count x ctas_per_sm x 256 doubles, 8-byte aligned).
+ * *dfma_out receives the DFMAs the launch executes (lane operations; with
+ * lanes < 32 the warp instructions number 32 / lanes times fewer per lane
+ * operation).  Time it with events on s; asynchronous, no allocation.
+ * Errors: SPMV_EINVAL for arguments out of range. */
+int spmv_probe_dfma(int64_t iters, int ctas_per_sm, int lanes, double* out_dev, int64_t out_cap,
+                    int64_t* dfma_out, cudaStream_t s);
+
 /* Test hook of the merge-path kernel's give-up path (the path a bounded wait
  * that runs out takes), for the plan-free entry points spmv_csr_merge and
  * spmv_csr_merge_noalloc: while set (tile >= 0), their launches treat merge

@@ -1115,6 +1115,26 @@ int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out) {
     return SPMV_OK;
 }
 
+int spmv_probe_dfma(int64_t iters, int ctas_per_sm, int lanes, double* out_dev, int64_t out_cap,
+                    int64_t* dfma_out, cudaStream_t s) {
+    API_TRY
+    need(out_dev != nullptr && dfma_out != nullptr, SPMV_EINVAL, "NULL pointer");
+    if (iters < 1 || iters > (int64_t(1) << 40)) fail(SPMV_EINVAL, "iters = %lld", (long long)iters);
+    if (ctas_per_sm < 1 || ctas_per_sm > 8) fail(SPMV_EINVAL, "ctas_per_sm = %d not in [1, 8]", ctas_per_sm);
+    if (lanes < 1 || lanes > 32) fail(SPMV_EINVAL, "lanes = %d not in [1, 32]", lanes);
+    if (reinterpret_cast<uintptr_t>(out_dev) & 7) fail(SPMV_EINVAL, "out_dev must be 8-byte aligned");
+    int dev = 0, sms = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int grid = sms * ctas_per_sm;
+    if (out_cap < (int64_t)grid * spmvk::probe_threads())
+        fail(SPMV_EINVAL, "out_cap %lld below the %lld threads of the launch", (long long)out_cap,
+             (long long)grid * spmvk::probe_threads());
+    check_cuda(spmvk::launch_dfma_probe(iters, grid, lanes, out_dev, dfma_out, s), "FP64 probe");
+    API_CATCH
+    return SPMV_OK;
+}
+
 int spmv_selftest_merge_abort(int64_t tile) {
     API_TRY
     if (tile < -1 || tile >= (int64_t(1) << 30)) fail(SPMV_EINVAL, "tile %lld not in [-1, 2^30)", (long long)tile);

@@ -795,4 +795,40 @@ cudaError_t selftest_wait_timeout(uint64_t limit_ns, int* status_host) {
     return e;
 }
 
+// ------------------------------------------------------------------------
+// FP64 FMA throughput probe: the first `lanes` lanes of every warp run 8
+// independent chains of `iters` fused multiply-adds each (enough chains to
+// cover the pipe's latency), then store their sum, so no chain is dead code.
+// The multiplier and addend keep every value near 1 (no overflow, no
+// subnormals).
+// ------------------------------------------------------------------------
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+__global__ void __launch_bounds__(kProbeThreads) dfma_probe_kernel(int64_t iters, int lanes, double* out) {
+    const int64_t gid = (int64_t)blockIdx.x * kProbeThreads + threadIdx.x;
+    double a[kProbeChains];
+#pragma unroll
+    for (int u = 0; u < kProbeChains; ++u) a[u] = 1.0 + 1e-3 * u + 1e-9 * (double)(gid & 1023);
+    if ((int)(threadIdx.x & 31) < lanes) {
+        const double m = 0.9999999999, c = 1e-10;
+        for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kProbeChains; ++u) a[u] = fma(a[u], m, c);
+        }
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int u = 0; u < kProbeChains; ++u) sum += a[u];
+    out[gid] = sum;
+}
+
+int probe_threads() { return kProbeThreads; }
+
+cudaError_t launch_dfma_probe(int64_t iters, int grid, int lanes, double* out, int64_t* dfma, cudaStream_t s) {
+    dfma_probe_kernel<<<grid, kProbeThreads, 0, s>>>(iters, lanes, out);
+    *dfma = (int64_t)grid * (kProbeThreads / 32) * lanes * kProbeChains * iters;
+    return cudaGetLastError();
+}
+
 }  // namespace spmvk

@@ -32,6 +32,7 @@ def load(workload, cache_dir):
         n, rp, ci, va = int(z["n"]), z["rp"], z["ci"], z["va"]
     else:
         n, rp, ci, va = W.powerlaw(4_000_000, seed=3)
+        os.makedirs(cache_dir, exist_ok=True)
         np.savez(path, n=n, rp=rp, ci=ci, va=va)
     return n, rp, ci, va, W.uniform_x(n, seed=4), 8, 1
 
@@ -87,7 +88,9 @@ def main(argv=None):
     ap.add_argument("--variant", type=int, nargs=2, default=[1, 2], metavar=("VARIANT", "PARAM"))
     ap.add_argument("--op", choices=["local", "remote"], default="local")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--cache-dir", default="/tmp")
+    ap.add_argument("--cache-dir", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build"),
+                    help="where the generated power-law matrix is cached (default: the package's "
+                         "ignored build folder)")
     args = ap.parse_args(argv)
     import torch
     from . import spmv

@@ -98,6 +98,7 @@ def _load():
         "spmv_serve_pm1_bits": [ctypes.c_uint64],
         "spmv_selftest_wait_timeout": [i64, P64],
         "spmv_selftest_merge_abort": [i64],
+        "spmv_probe_dfma": [i64, i32, i32, vp, i64, P64, vp],
         "spmv_part_check": [vp, P64],
         "spmv_selftest_check": [P64],
         "spmv_last_error": [],
@@ -270,6 +271,14 @@ def spmv_selftest_check():
 def spmv_selftest_wait_timeout(limit_ns):
     out = ctypes.c_int64()
     _check(lib.spmv_selftest_wait_timeout(int(limit_ns), ctypes.byref(out)))
+    return out.value
+
+
+def spmv_probe_dfma(iters, ctas_per_sm, lanes, out_dev, out_cap, stream):
+    """Launch the FP64 FMA throughput probe; returns the DFMAs it executes."""
+    out = ctypes.c_int64()
+    _check(lib.spmv_probe_dfma(int(iters), int(ctas_per_sm), int(lanes), _ptr(out_dev), int(out_cap),
+                               ctypes.byref(out), _stream(stream)))
     return out.value
 
 

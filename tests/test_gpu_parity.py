@@ -832,6 +832,32 @@ def test_merge_give_up_path_writes_nothing_outside_y(entry):
     assert np.all(guard.cpu().numpy()[n:] == 7.0)
 
 
+def test_fp64_probe_does_the_work_it_counts():
+    """Every chain of the FP64 probe follows a_{i+1} = a_i m + c, so after k
+    steps a_k = a_0 m^k + c (1 - m^k) / (1 - m); the stored sums match that
+    closed form (up to rounding), and the returned count is grid x warps x
+    lanes x 8 chains x k."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    k = 1000
+    for lanes in (32, 1):
+        out = torch.zeros(sms * 2 * 256, dtype=torch.float64, device="cuda")
+        dfma = spmv.spmv_probe_dfma(k, 2, lanes, out, out.numel(), None)
+        torch.cuda.synchronize()
+        assert dfma == sms * 2 * 8 * lanes * 8 * k
+        o = out.cpu().numpy().reshape(-1, 32)
+        gid = np.arange(o.size).reshape(-1, 32)
+        m, c = 0.9999999999, 1e-10
+        a0 = 1.0 + 1e-3 * np.arange(8)[None, None, :] + 1e-9 * (gid & 1023)[:, :, None]
+        run = a0 * m ** k + c * (1 - m ** k) / (1 - m)
+        want = np.where((np.arange(32) < lanes)[None, :, None], run, a0).sum(axis=2)
+        assert np.allclose(o, want, rtol=1e-12, atol=0)
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_probe_dfma(10, 2, 32, out, 10, None)
+    assert e.value.code == spmv.EINVAL
+
+
 def test_merge_abort_hook_rejects_bad_tiles():
     from paper_2203_02530_gb300 import spmv
     with pytest.raises(spmv.SpmvError) as e:

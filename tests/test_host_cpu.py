@@ -47,6 +47,12 @@ def test_invalid_arguments_fail_without_a_gpu(libpath):
     with pytest.raises(spmv.SpmvError) as e:
         spmv.spmv_csr_merge(2**30, 2**30, 0, 0, 0, 0, 0, None)
     assert e.value.code == spmv.EBOUNDS
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_probe_dfma(10, 2, 32, None, 0, None)
+    assert e.value.code == spmv.EINVAL
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_selftest_merge_abort(-5)
+    assert e.value.code == spmv.EINVAL
 
 
 @pytest.mark.parametrize("streams", [1, 2, 3, 4])
