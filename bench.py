@@ -189,39 +189,73 @@ def profiled_traffic(workload, key):
 
 def fp64_probe(dev, props, seconds=0.25):
     """Measured FP64 FMA throughput of this GPU (the library's DFMA probe,
-    timed with CUDA events, SM clock sampled meanwhile): G DFMA/s with 32 and
-    with 1 active lane per warp."""
+    timed with CUDA events, SM clock sampled meanwhile): the best G DFMA/s
+    over 1, 2, 4 and 8 CTAs of 256 threads per SM with 32 active lanes per
+    warp, and the same launch with 1 active lane per warp."""
     import torch
     from paper_2203_02530_gb300 import benchmark, spmv
     s = torch.cuda.Stream(device=dev)
+    cap = props.multi_processor_count * 8 * 256
+    out = torch.empty(cap, dtype=torch.float64, device=dev)
+
+    def rate(cps, lanes, budget):
+        iters = 1 << 10
+        while True:   # size one launch to about 10 ms
+            t = benchmark.time_loop(lambda: spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s), s, 1, warmup=1)
+            if t > 0.01 or iters >= 1 << 30:
+                break
+            iters *= 2
+        reps = max(2, int(budget / t))
+        dfma = spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s)
+        t = benchmark.time_loop(lambda: spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s), s, reps, warmup=1)
+        return dfma / t, iters, reps
+
+    sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+    sampler.start()
+    sweep = {cps: rate(cps, 32, seconds / 5) for cps in (1, 2, 4, 8)}
+    best = max(sweep, key=lambda c: sweep[c][0])
+    one = rate(best, 1, seconds / 5)
+    clocks = sampler.stop()
+    mhz = clocks.get("sm_mhz") or props.clock_rate / 1e3
+    r = sweep[best][0]
+    return {"dfma_per_s": r, "unit": "G DFMA/s", "g_dfma_per_s": round(r / 1e9, 1),
+            "per_clk_per_sm": round(r / (mhz * 1e6) / props.multi_processor_count, 3),
+            "sm_mhz": mhz, "ctas_per_sm": best,
+            "sweep_g_dfma_per_s": {str(c): round(v[0] / 1e9, 1) for c, v in sorted(sweep.items())},
+            "one_lane_g_warp_instr_per_s": round(one[0] / 1e9, 2),
+            "full_warp_g_warp_instr_per_s": round(r / 32 / 1e9, 2),
+            "how": "spmv_probe_dfma: 1, 2, 4 and 8 CTAs x 256 threads per SM, 8 chains of DFMAs per lane, "
+                   "each launch about 10 ms, CUDA events; the best is the peak; the one-lane run keeps 1 lane "
+                   "of each warp busy at the best CTA count"}
+
+
+def gather_probe(dev, props, table_len=4_000_000, count=1 << 26, seconds=0.2):
+    """Measured rate of scattered 8-byte reads (the library's gather probe,
+    CUDA events): `count` uniformly random positions into a table of
+    `table_len` doubles (32 MB: L2-resident, the size of the power-law x),
+    read through a coalesced int32 index stream as a product reads its
+    columns.  Returns G gathers/s."""
+    import torch
+    from paper_2203_02530_gb300 import benchmark, spmv
+    s = torch.cuda.Stream(device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(31)
+    table = torch.rand(table_len, dtype=torch.float64, device=dev, generator=gen)
+    idx = torch.randint(0, table_len, (count,), dtype=torch.int32, device=dev, generator=gen)
+    # the table and indices come from the current stream; the probe runs on s
+    torch.cuda.synchronize(dev)
     cps = 4
     cap = props.multi_processor_count * cps * 256
     out = torch.empty(cap, dtype=torch.float64, device=dev)
-    res = {}
-    sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
-    sampler.start()
-    for lanes in (32, 1):
-        iters = 1 << 12
-        while True:   # size one launch to about 20 ms
-            t = benchmark.time_loop(lambda: spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s), s, 1, warmup=1)
-            if t > 0.02 or iters >= 1 << 30:
-                break
-            iters *= 2
-        reps = max(2, int(seconds / 2 / t))
-        dfma = spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s)
-        t = benchmark.time_loop(lambda: spmv.spmv_probe_dfma(iters, cps, lanes, out, cap, s), s, reps, warmup=1)
-        res[lanes] = (dfma / t, t, iters)
-    clocks = sampler.stop()
-    mhz = clocks.get("sm_mhz") or props.clock_rate / 1e3
-    rate = res[32][0]
-    return {"dfma_per_s": rate, "unit": "G DFMA/s", "g_dfma_per_s": round(rate / 1e9, 1),
-            "per_clk_per_sm": round(rate / (mhz * 1e6) / props.multi_processor_count, 3),
-            "sm_mhz": mhz, "one_lane_g_dfma_per_s": round(res[1][0] / 1e9, 2),
-            "one_lane_g_warp_instr_per_s": round(res[1][0] / 1e9, 2),
-            "full_warp_g_warp_instr_per_s": round(rate / 32 / 1e9, 2),
-            "how": "spmv_probe_dfma: %d CTAs x 256 threads, 8 chains of %d DFMAs per lane, CUDA events, "
-                   "%d launches; the one-lane run keeps 1 lane of each warp busy" % (
-                       props.multi_processor_count * cps, res[32][2], max(2, int(seconds / 2 / res[32][1])))}
+    run = lambda: spmv.spmv_probe_gather(table, idx, count, cps, out, cap, s)
+    t = benchmark.time_loop(run, s, 1, warmup=2)
+    reps = max(3, int(seconds / t))
+    t = benchmark.time_loop(run, s, reps, warmup=1)
+    del table, idx, out
+    return {"g_gathers_per_s": round(count / t / 1e9, 2), "table_mb": round(table_len * 8 / 1e6, 1),
+            "how": "spmv_probe_gather: %d uniformly random 8-byte reads from a %d-entry table through a "
+                   "coalesced int32 index stream, %d CTAs x 256 threads, 4 in flight per thread, CUDA events "
+                   "over %d launches" % (count, table_len, props.multi_processor_count * cps, reps)}
 
 
 # ---------------------------------------------------------------- workload
@@ -543,6 +577,12 @@ def run_ours(args, world, rank, local, fp64=None):
                  "peak_kind": "measured by spmv_probe_dfma in this run (%.3f DFMA/clk/SM at %.0f MHz)" % (
                      fp64["per_clk_per_sm"], fp64["sm_mhz"]),
                  "note": "one DFMA per stored local entry over the LOCAL launch time"},
+        "gather": None if "gather" not in fp64 else {
+            "achieved": round(nnz_l / t_local / 1e9, 2), "unit": "G gathers/s",
+            "peak": fp64["gather"]["g_gathers_per_s"],
+            "frac": round(nnz_l / t_local / 1e9 / fp64["gather"]["g_gathers_per_s"], 4),
+            "note": "one x gather per stored local entry over the LOCAL launch time, against the gather "
+                    "probe's rate for random reads from an L2-resident table"},
         "latency_us": latency_block(per_sample, meas),
         "schedule_spread": round(spread, 4),
         "search_vs_random": search_cmp,
@@ -1032,6 +1072,7 @@ def main(argv=None):
         import torch
         torch.cuda.set_device(local)
         fp64 = fp64_probe(torch.device("cuda", local), torch.cuda.get_device_properties(local))
+        fp64["gather"] = gather_probe(torch.device("cuda", local), torch.cuda.get_device_properties(local))
         if args.workload == "batched":
             line = run_batched(args, world, rank, local)
         elif args.workload == "serving":
@@ -1043,7 +1084,8 @@ def main(argv=None):
                 if line is not None:
                     line.update(subs)
         if line is not None:
-            line["fp64_probe"] = {k: v for k, v in fp64.items() if k != "dfma_per_s"}
+            line["probes"] = {"fp64": {k: v for k, v in fp64.items() if k not in ("dfma_per_s", "gather")},
+                              "gather": fp64["gather"]}
     if line is not None:
         print(json.dumps(line), flush=True)
 

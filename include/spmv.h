@@ -426,12 +426,17 @@ int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, doubl
  *   resident matrices, SPMV_EBOUNDS for a matrix with n >= 2^28.
  * spmv_serve_run: runs n_req requests open loop against their arrival times
  *   (seconds from the call, non-decreasing), on the host thread, until all
- *   completed.  BATCHED merges the oldest requests of one matrix into one
- *   block of total width <= 8 whenever a slot and pool memory are free;
- *   requests arriving while blocks run join at the next turn of the loop.
- *   When every matrix is in the sliced layout, BATCHED goes further: a free
- *   slot takes up to 64 such blocks, across matrices, as one group run by
- *   one launch per kernel kind (X generation, slices, long rows).
+ *   completed.  Queues are served oldest first (the matrix whose oldest
+ *   waiting request arrived first; ties by request index).  BATCHED merges
+ *   the oldest requests of one matrix into one block of total width <= 8
+ *   whenever a slot and pool memory are free; requests arriving while blocks
+ *   run join at the next turn of the loop.  When every matrix is in the
+ *   sliced layout, BATCHED goes further: the blocks the queues would form
+ *   are spread over the free slots, ceil(blocks / free slots) per slot (at
+ *   most the group size, spmv_serve_set_group_max), and a slot given more
+ *   than one block runs them, across matrices, as one group with one launch
+ *   per kernel kind (X generation, slices, long rows); under light load every
+ *   block thus gets a slot of its own, under heavy load groups grow.
  *   PLAIN launches every request alone (one block per request).  Outputs:
  *   latency_s[r] = observed completion - arrival; hash_out[r] (optional) an
  *   order-independent 64-bit hash of the bits of request r's Y; stats (6
@@ -510,6 +515,20 @@ int spmv_selftest_wait_timeout(int64_t limit_ns, int64_t* status_out);
  * Errors: SPMV_EINVAL for arguments out of range. */
 int spmv_probe_dfma(int64_t iters, int ctas_per_sm, int lanes, double* out_dev, int64_t out_cap,
                     int64_t* dfma_out, cudaStream_t s);
+
+/* Gather throughput probe (a measurement helper, not part of the paper's
+ * method): the rate at which the GPU serves scattered 8-byte reads, the
+ * bound of a product whose x entries are far apart (each costs its own
+ * cache sector).  Launches SM count x ctas_per_sm (1..8) CTAs of 256 threads
+ * on stream s; thread g of the T launched sums table_dev[idx_dev[k]] over
+ * k = g, g + T, g + 2T, ... < count, four gathers in flight, and writes the
+ * sum to out_dev[g].  table_dev: doubles (8-byte aligned); idx_dev: count
+ * int32 positions into it (4-byte aligned), each must lie inside the table
+ * (the caller's precondition, not checked); out_dev: at least out_cap >=
+ * T doubles.  Time it with events on s; asynchronous, no allocation.
+ * Errors: SPMV_EINVAL for arguments out of range. */
+int spmv_probe_gather(const double* table_dev, const int32_t* idx_dev, int64_t count, int ctas_per_sm,
+                      double* out_dev, int64_t out_cap, cudaStream_t s);
 
 /* Test hook of the merge-path kernel's give-up path (the path a bounded wait
  * that runs out takes), for the plan-free entry points spmv_csr_merge and

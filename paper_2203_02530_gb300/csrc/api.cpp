@@ -1135,6 +1135,27 @@ int spmv_probe_dfma(int64_t iters, int ctas_per_sm, int lanes, double* out_dev, 
     return SPMV_OK;
 }
 
+int spmv_probe_gather(const double* table_dev, const int32_t* idx_dev, int64_t count, int ctas_per_sm,
+                      double* out_dev, int64_t out_cap, cudaStream_t s) {
+    API_TRY
+    need(table_dev != nullptr && idx_dev != nullptr && out_dev != nullptr, SPMV_EINVAL, "NULL pointer");
+    if (count < 0) fail(SPMV_EINVAL, "count = %lld", (long long)count);
+    if (ctas_per_sm < 1 || ctas_per_sm > 8) fail(SPMV_EINVAL, "ctas_per_sm = %d not in [1, 8]", ctas_per_sm);
+    if ((reinterpret_cast<uintptr_t>(out_dev) | reinterpret_cast<uintptr_t>(table_dev)) & 7 ||
+        reinterpret_cast<uintptr_t>(idx_dev) & 3)
+        fail(SPMV_EINVAL, "misaligned pointer");
+    int dev = 0, sms = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int grid = sms * ctas_per_sm;
+    if (out_cap < (int64_t)grid * spmvk::probe_threads())
+        fail(SPMV_EINVAL, "out_cap %lld below the %lld threads of the launch", (long long)out_cap,
+             (long long)grid * spmvk::probe_threads());
+    check_cuda(spmvk::launch_gather_probe(table_dev, idx_dev, count, grid, out_dev, s), "gather probe");
+    API_CATCH
+    return SPMV_OK;
+}
+
 int spmv_selftest_merge_abort(int64_t tile) {
     API_TRY
     if (tile < -1 || tile >= (int64_t(1) << 30)) fail(SPMV_EINVAL, "tile %lld not in [-1, 2^30)", (long long)tile);

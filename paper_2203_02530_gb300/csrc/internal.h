@@ -120,6 +120,8 @@ int warp_tile_cap(int param);
 cudaError_t selftest_wait_timeout(uint64_t limit_ns, int* status_host);
 int probe_threads();
 cudaError_t launch_dfma_probe(int64_t iters, int grid, int lanes, double* out, int64_t* dfma, cudaStream_t s);
+cudaError_t launch_gather_probe(const double* table, const int32_t* idx, int64_t count, int grid, double* out,
+                                cudaStream_t s);
 cudaError_t launch_pairs(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
                          int lanes, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(const CsrArgs& a, const MergeTile* tiles, int tile_begin,

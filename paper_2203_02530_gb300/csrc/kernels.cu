@@ -831,4 +831,37 @@ cudaError_t launch_dfma_probe(int64_t iters, int grid, int lanes, double* out, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// Gather throughput probe: thread g of T sums table[idx[k]] over k = g,
+// g + T, g + 2T, ... (four gathers in flight), the access pattern of a
+// product's x gathers with the column stream read coalesced; each thread
+// stores its sum.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kProbeThreads) gather_probe_kernel(const double* __restrict__ table,
+                                                                     const int32_t* __restrict__ idx,
+                                                                     int64_t count, double* out) {
+    const int64_t T = (int64_t)gridDim.x * kProbeThreads;
+    const int64_t g = (int64_t)blockIdx.x * kProbeThreads + threadIdx.x;
+    double sum = 0.0;
+    int64_t k = g;
+    for (; k + 3 * T < count; k += 4 * T) {
+        const int32_t i0 = __ldg(idx + k), i1 = __ldg(idx + k + T), i2 = __ldg(idx + k + 2 * T),
+                      i3 = __ldg(idx + k + 3 * T);
+        const double v0 = __ldg(table + i0), v1 = __ldg(table + i1), v2 = __ldg(table + i2),
+                     v3 = __ldg(table + i3);
+        sum += v0;
+        sum += v1;
+        sum += v2;
+        sum += v3;
+    }
+    for (; k < count; k += T) sum += __ldg(table + __ldg(idx + k));
+    out[g] = sum;
+}
+
+cudaError_t launch_gather_probe(const double* table, const int32_t* idx, int64_t count, int grid, double* out,
+                                cudaStream_t s) {
+    gather_probe_kernel<<<grid, kProbeThreads, 0, s>>>(table, idx, count, out);
+    return cudaGetLastError();
+}
+
 }  // namespace spmvk

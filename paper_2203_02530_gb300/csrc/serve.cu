@@ -885,8 +885,23 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
     for (int m = 0; m < M; ++m) grouped = grouped && sv->mats->mats[m].lanes == kBatchSliced;
     std::vector<Inflight> slot(sv->n_streams);
     std::vector<std::deque<int64_t>> pending(M);
+    std::vector<int64_t> pend_width(M, 0);   // total width queued per matrix
+    // the matrix whose oldest queued request came first (arrival, then
+    // request index): queues are served oldest first in both modes
+    auto oldest = [&]() {
+        int best = -1;
+        for (int k = 0; k < M; ++k) {
+            if (pending[k].empty()) continue;
+            if (best < 0) {
+                best = k;
+                continue;
+            }
+            const int64_t a = pending[k].front(), b = pending[best].front();
+            if (arrival_s[a] < arrival_s[b] || (arrival_s[a] == arrival_s[b] && a < b)) best = k;
+        }
+        return best;
+    };
     int64_t next = 0, done = 0, blocks = 0, waits_mem = 0, max_inflight = 0, admitted_while_busy = 0;
-    int rr = 0;
     const auto t0 = std::chrono::steady_clock::now();
     auto now_s = [&]() {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -907,6 +922,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
         for (auto& sl : slot) busy_now += sl.busy;
         while (next < n_req && arrival_s[next] <= now) {
             pending[matrix[next]].push_back(next);
+            pend_width[matrix[next]] += width[next];
             if (busy_now) ++admitted_while_busy;
             ++next;
             ++queued;
@@ -926,26 +942,32 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
             sl.reqs.clear();
             sl.allocs.clear();
         }
-        // launches: one block (or one group of blocks) per free slot,
-        // matrices taken round robin
+        // launches: one block (or one group of blocks) per free slot, the
+        // oldest queue first.  Grouping spreads the blocks the queues would
+        // form over the free slots (ceil(blocks / free slots) per group, at
+        // most group_max): under light load every block gets a slot of its
+        // own (no request waits for another's block), under heavy load the
+        // groups grow and the launches fall
         if (queued > 0) {
+            int per_group = 1;
+            if (grouped) {
+                int free_slots = 0;
+                for (auto& sl : slot) free_slots += !sl.busy;
+                int64_t pend_blocks = 0;
+                for (int k = 0; k < M; ++k) pend_blocks += (pend_width[k] + kMaxW - 1) / kMaxW;
+                if (free_slots > 0)
+                    per_group = (int)std::min<int64_t>(sv->group_max,
+                                                       std::max<int64_t>(1, (pend_blocks + free_slots - 1) / free_slots));
+            }
             for (int i = 0; i < sv->n_streams && queued > 0; ++i) {
                 if (slot[i].busy) continue;
-                if (grouped) {
+                if (grouped && per_group > 1) {
                     GroupBlock* hg = sv->h_group[i];
                     int nb = 0, units = 0, longs = 0, max_elems = 0;
                     bool out_of_memory = false;
-                    while (nb < sv->group_max && queued > 0 && !out_of_memory) {
-                        int m = -1;
-                        for (int k = 0; k < M; ++k) {
-                            const int c = (rr + k) % M;
-                            if (!pending[c].empty()) {
-                                m = c;
-                                break;
-                            }
-                        }
+                    while (nb < per_group && queued > 0 && !out_of_memory) {
+                        const int m = oldest();
                         if (m < 0) break;
-                        rr = (m + 1) % M;
                         const BatchMat& Mm = sv->mats->mats[m];
                         auto& q = pending[m];
                         int take = 0, wsum = 0;
@@ -977,6 +999,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                         longs += Mm.n_long;
                         max_elems = std::max(max_elems, Mm.n * wsum);
                         queued -= take;
+                        pend_width[m] -= wsum;
                         slot[i].allocs.emplace_back(off, bytes);
                         ++blocks;
                     }
@@ -1011,16 +1034,8 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                     if (out_of_memory) break;
                     continue;
                 }
-                int m = -1;
-                for (int k = 0; k < M; ++k) {
-                    const int c = (rr + k) % M;
-                    if (!pending[c].empty()) {
-                        m = c;
-                        break;
-                    }
-                }
+                const int m = oldest();
                 if (m < 0) break;
-                rr = (m + 1) % M;
                 const int n = sv->mats->mats[m].n;
                 // the oldest requests of matrix m whose widths sum to <= 8
                 auto& q = pending[m];
@@ -1049,6 +1064,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                 }
                 b.width = wsum;
                 queued -= (int64_t)reqs.size();
+                pend_width[m] -= wsum;
                 double* X = reinterpret_cast<double*>(sv->pool.ptr(off));
                 double* Y = X + (size_t)n * b.width;
                 spmvk::check_cuda(launch_block(sv, m, b, X, Y, hash_out ? sv->d_hash : nullptr,

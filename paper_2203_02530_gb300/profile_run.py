@@ -47,6 +47,7 @@ def run_batch(args):
     total = b.offsets()[-1]
     x_d = torch.from_numpy(W.uniform_x(total, seed=6)).cuda()
     y_d = torch.zeros(total, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()   # made on the current stream, used on s
     s = torch.cuda.Stream()
     for _ in range(args.launches):
         spmv.spmv_batch_run(b.h, x_d, y_d, s)
@@ -105,6 +106,7 @@ def main(argv=None):
     part.set_op_variant(kind, *args.variant)
     x_d = torch.from_numpy(x).cuda()
     y_d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()   # made on the current stream, used on another
     s = torch.cuda.Stream()
     spmv.spmv_pack(part.h, -1, x_d, s)
     spmv.spmv_halo_copy(part.h, -1, s)

@@ -99,6 +99,7 @@ def _load():
         "spmv_selftest_wait_timeout": [i64, P64],
         "spmv_selftest_merge_abort": [i64],
         "spmv_probe_dfma": [i64, i32, i32, vp, i64, P64, vp],
+        "spmv_probe_gather": [vp, vp, i64, i32, vp, i64, vp],
         "spmv_part_check": [vp, P64],
         "spmv_selftest_check": [P64],
         "spmv_last_error": [],
@@ -280,6 +281,12 @@ def spmv_probe_dfma(iters, ctas_per_sm, lanes, out_dev, out_cap, stream):
     _check(lib.spmv_probe_dfma(int(iters), int(ctas_per_sm), int(lanes), _ptr(out_dev), int(out_cap),
                                ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+def spmv_probe_gather(table_dev, idx_dev, count, ctas_per_sm, out_dev, out_cap, stream):
+    """Launch the gather throughput probe (count gathers)."""
+    _check(lib.spmv_probe_gather(_ptr(table_dev), _ptr(idx_dev), int(count), int(ctas_per_sm), _ptr(out_dev),
+                                 int(out_cap), _stream(stream)))
 
 
 def spmv_selftest_merge_abort(tile):

@@ -18,6 +18,20 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
 
 
+def synced(t):
+    """`t` once the current stream's work on it is done: tensors made by
+    PyTorch kernels come from its current stream, while the library runs on
+    streams that do not wait for it."""
+    torch_cuda().cuda.synchronize()
+    return t
+
+
+def refill(t, value=float("nan")):
+    """Fill a device tensor and wait for the fill (see synced)."""
+    t.fill_(value)
+    return synced(t)
+
+
 def assert_fp64_close(got, want, scale, what=""):
     """|got - want| <= 1e-12 * sum_j |a_ij x_j| per element (plus 1e-300).
 

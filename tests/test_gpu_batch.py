@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2203_02530_gb300 import workloads as W
-from tests.gpu_util import assert_fp64_close, dev, torch_cuda
+from tests.gpu_util import assert_fp64_close, dev, refill, synced, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -46,8 +46,8 @@ def test_batch_matches_oracle_and_separate_launches(lanes):
         want, scale = _oracle(mats, x, offs)
         s = torch.cuda.Stream()
         x_d = dev(x)
-        y1 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
-        y2 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
+        y1 = synced(torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda"))
+        y2 = synced(torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda"))
         spmv.spmv_batch_run(b.h, x_d, y1, s)
         spmv.spmv_batch_run_separate(b.h, -1, x_d, y2, s)
         s.synchronize()
@@ -164,15 +164,15 @@ def test_full_size_batch_mix_256_sliced():
         del mats
         s, s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
         x_d = dev(x)
-        y1 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
-        y2 = torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda")
+        y1 = synced(torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda"))
+        y2 = synced(torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda"))
         spmv.spmv_batch_run(b.h, x_d, y1, s)
         spmv.spmv_batch_run_separate(b.h, -1, x_d, y2, s)
         s.synchronize()
         a1 = y1.cpu().numpy()
         assert np.array_equal(a1, y2.cpu().numpy()), "batched and separate launches differ"
         assert_fp64_close(a1, want, scale, "batch mix 256 sliced")
-        y1.fill_(float("nan"))
+        refill(y1)
         spmv.spmv_batch_run(b.h, x_d, y1, s)
         s.synchronize()
         assert np.array_equal(y1.cpu().numpy(), a1)

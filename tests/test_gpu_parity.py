@@ -12,7 +12,7 @@ import pytest
 import oracle
 from oracle import schedules as OS
 from paper_2203_02530_gb300 import workloads as W
-from tests.gpu_util import assert_fp64_close, dev, reference, torch_cuda
+from tests.gpu_util import assert_fp64_close, dev, reference, refill, synced, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -193,7 +193,7 @@ def test_product_parity_every_variant(name, variant):
     want, scale = reference(n, rp, ci, va, x)
     s = torch.cuda.Stream()
     x_d = dev(x)
-    y_d = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda")
+    y_d = synced(torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda"))
     with make_part(n, rp, ci, va, P) as part:
         set_variant(part, variant)
         run_default(part, x_d, y_d, s)
@@ -232,7 +232,7 @@ def test_sliced_layout_matches_thread_per_row_bit_for_bit(name):
     x_d = dev(x)
     out = []
     for v in (("warp", 0), ("sell", 4), ("sell", 9), ("sell", 104), ("sell", 2008), ("sell", 2104)):
-        y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        y_d = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
         with make_part(n, rp, ci, va, P) as part:
             set_variant(part, v)
             run_default(part, x_d, y_d, s)
@@ -258,7 +258,7 @@ def test_sell16_local_matches_sell_bit_for_bit(name):
         for v in (spmv.VARIANT_SELL, spmv.VARIANT_SELL16):
             part.set_op_variant(spmv.OP_LOCAL, v, 9)
             assert part.query(spmv.Q_LOCAL_VARIANT) == 100 * v + 9
-            y_d = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda")
+            y_d = synced(torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device="cuda"))
             run_default(part, x_d, y_d, s)
             s.synchronize()
             out.append(y_d.cpu().numpy()[:n])
@@ -327,7 +327,7 @@ def test_sliced_layout_edge_cases(lens_kind, gran, param):
     want, scale = reference(n, rp, ci, va, x)
     s = torch.cuda.Stream()
     x_d = dev(x)
-    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    y_d = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
     P = 3
     with make_part(n, rp, ci, va, P, gran) as part:
         set_variant(part, ("sell", param))
@@ -344,7 +344,7 @@ def test_sliced_layout_edge_cases(lens_kind, gran, param):
         s.synchronize()
         y1 = y_d.cpu().numpy().copy()
         assert_fp64_close(y1, want, scale, "sliced %s gran %d" % (lens_kind, gran))
-        y_d.fill_(float("nan"))
+        refill(y_d)
         run_default(part, x_d, y_d, s)
         s.synchronize()
         assert np.array_equal(y_d.cpu().numpy(), y1)
@@ -368,7 +368,7 @@ def test_local_and_remote_variants_chosen_separately(name):
             part.set_op_variant(spmv.OP_REMOTE, *rv)
             assert part.query(spmv.Q_LOCAL_VARIANT) == 100 * lv[0] + lv[1]
             assert part.query(spmv.Q_REMOTE_VARIANT) == 100 * rv[0] + rv[1]
-            y_d.fill_(float("nan"))
+            refill(y_d)
             run_default(part, x_d, y_d, s)
             s.synchronize()
             assert_fp64_close(y_d.cpu().numpy(), want, scale, "%s %s %s" % (name, lv, rv))
@@ -399,14 +399,14 @@ def test_every_coarse_schedule_gives_identical_y(name):
         assert len(scheds) == 24
         first = None
         for order, smap in scheds:
-            y_d.fill_(float("nan"))
+            refill(y_d)
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
             assert (part.query(spmv.Q_LAST_RECORDS), part.query(spmv.Q_LAST_WAITS)) == \
                 _sync_expect(edges, smap)
             g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
             torch.cuda.synchronize()
             ye = y_d.cpu().numpy().copy()
-            y_d.fill_(float("nan"))
+            refill(y_d)
             torch.cuda.synchronize()
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
@@ -470,12 +470,12 @@ def test_per_segment_granularity(name, variant):
         first = None
         for trial in range(6):
             order, smap = _random_schedule(dag, 3, rng)
-            y_d.fill_(float("nan"))
+            refill(y_d)
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
             torch.cuda.synchronize()
             ye = y_d.cpu().numpy()[:n].copy()
             g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
-            y_d.fill_(float("nan"))
+            refill(y_d)
             torch.cuda.synchronize()
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
             torch.cuda.synchronize()
@@ -515,7 +515,7 @@ def test_per_partition_schedules_give_identical_y(name, variant):
         first = None
         for it in range(24):
             order, smap = _random_schedule(dag, 4, rng)
-            y_d.fill_(float("nan"))
+            refill(y_d)
             if it % 2:
                 g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
                 part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
@@ -539,7 +539,7 @@ def test_invalid_schedules_are_rejected_before_launch():
     n, rp, ci, va, P, x = case("lap64")
     streams = [torch.cuda.Stream() for _ in range(2)]
     x_d = dev(x)
-    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    y_d = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
     with make_part(n, rp, ci, va, P) as part:
         bad = [([2, 0, 1, 3], [0, 0, 0, 0]),    # copy before pack
                ([0, 2, 3, 1], [0, 0, 0, 0]),    # remote before local
@@ -572,7 +572,7 @@ def test_standalone_merge_product(name):
     ci_d = dev(ci) if ci.size else torch.empty(0, dtype=torch.int32, device="cuda")
     va_d = dev(va) if va.size else torch.empty(0, dtype=torch.float64, device="cuda")
     x_d = dev(x) if n else torch.empty(0, dtype=torch.float64, device="cuda")
-    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    y_d = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
     spmv.spmv_csr_merge(n, int(rp[-1]), rp_d, ci_d, va_d, x_d, y_d, s)
     s.synchronize()
     assert_fp64_close(y_d.cpu().numpy(), want, scale, name)
@@ -588,7 +588,7 @@ def test_standalone_merge_rejects_misaligned():
     torch = torch_cuda()
     n, rp, ci, va, P, x = case("lap64")
     rp_d = dev(rp.astype(np.int32))
-    big = torch.zeros(ci.size + 1, dtype=torch.int32, device="cuda")
+    big = synced(torch.zeros(ci.size + 1, dtype=torch.int32, device="cuda"))
     with pytest.raises(spmv.SpmvError) as e:
         spmv.spmv_csr_merge(n, int(rp[-1]), rp_d, big[1:], dev(va), dev(x),
                             torch.empty(n, dtype=torch.float64, device="cuda"), None)
@@ -661,7 +661,7 @@ def test_full_size_27pt_150_all_schedules():
         first = None
         for order, smap in E.enumerate_schedules(E.Dag(4, part.dag()), 2):
             g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
-            y_d.fill_(float("nan"))
+            refill(y_d)
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
             torch.cuda.synchronize()
             y = y_d.cpu().numpy()
@@ -688,7 +688,7 @@ def test_full_size_powerlaw_4M_per_partition():
     with make_part(n, rp, ci, va, 8, spmv.PER_PARTITION) as part:
         for variant in (("merge", 0), ("tile", 2)):
             set_variant(part, variant)
-            y_d.fill_(float("nan"))
+            refill(y_d)
             order = [4 * p + k for k in (0, 1, 2, 3) for p in range(8)]
             part.run(order, [0] * 32, [s], x_d, y_d, spmv.RUN_EAGER)
             s.synchronize()
@@ -722,7 +722,7 @@ def test_full_size_powerlaw_4M_sliced_schedules():
             order, smap = _random_schedule(dag, 4, rng)
             g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
             for _ in range(2):
-                y_d.fill_(float("nan"))
+                refill(y_d)
                 part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
                 torch.cuda.synchronize()
                 y = y_d.cpu().numpy()
@@ -760,7 +760,7 @@ def test_full_size_27pt_150_benchmark_variants():
             part.set_op_variant(spmv.OP_REMOTE, rv, rpar)
             order, smap = [0, 2, 1, 3], [0, 1, 0, 0]   # pack, copy, remote on 0; local on 1
             g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
-            y_d.fill_(float("nan"))
+            refill(y_d)
             part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
             torch.cuda.synchronize()
             y = y_d.cpu().numpy()
@@ -814,7 +814,7 @@ def test_merge_give_up_path_writes_nothing_outside_y(entry):
     want, scale = reference(n, rp, ci, va, x)
     tiles = (n + int(rp[-1]) + 2047) // 2048
     assert tiles > 40
-    guard = torch.full((n0,), 7.0, dtype=torch.float64, device="cuda")   # y is guard[:n]
+    guard = synced(torch.full((n0,), 7.0, dtype=torch.float64, device="cuda"))   # y is guard[:n]
     args = (n, int(rp[-1]), dev(rp.astype(np.int32)), dev(ci), dev(va), dev(x), guard)
     spmv.spmv_selftest_merge_abort(10)
     try:
@@ -842,7 +842,7 @@ def test_fp64_probe_does_the_work_it_counts():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     k = 1000
     for lanes in (32, 1):
-        out = torch.zeros(sms * 2 * 256, dtype=torch.float64, device="cuda")
+        out = synced(torch.zeros(sms * 2 * 256, dtype=torch.float64, device="cuda"))
         dfma = spmv.spmv_probe_dfma(k, 2, lanes, out, out.numel(), None)
         torch.cuda.synchronize()
         assert dfma == sms * 2 * 8 * lanes * 8 * k
@@ -856,6 +856,26 @@ def test_fp64_probe_does_the_work_it_counts():
     with pytest.raises(spmv.SpmvError) as e:
         spmv.spmv_probe_dfma(10, 2, 32, out, 10, None)
     assert e.value.code == spmv.EINVAL
+
+
+def test_gather_probe_sums_what_it_gathers():
+    """Thread g of the gather probe sums table[idx[k]] for k = g mod T: the
+    stored sums equal numpy's over the same positions (up to rounding)."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    T = sms * 2 * 256
+    rng = np.random.default_rng(21)
+    table = rng.uniform(-1, 1, 1 << 20)
+    count = 9 * T + 12345   # a ragged tail after the four-in-flight rounds
+    idx = rng.integers(0, table.size, count).astype(np.int32)
+    out = synced(torch.zeros(T, dtype=torch.float64, device="cuda"))
+    spmv.spmv_probe_gather(dev(table), dev(idx), count, 2, out, T, None)
+    torch.cuda.synchronize()
+    vals = np.zeros(10 * T)
+    vals[:count] = table[idx]
+    want = vals.reshape(10, T).sum(axis=0)
+    assert np.allclose(out.cpu().numpy(), want, rtol=0, atol=1e-12)
 
 
 def test_merge_abort_hook_rejects_bad_tiles():
@@ -873,7 +893,7 @@ n, rp, ci, va = W.powerlaw(3000, seed=3, cap=500)
 x = W.uniform_x(n, seed=99)
 s = [torch.cuda.Stream() for _ in range(2)]
 x_d = torch.from_numpy(x).cuda()
-y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+y_d = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
 with spmv.Part(n, rp, ci, va, 3, spmv.PER_PARTITION) as part:
     part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, 2008)
     part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_MERGE, 0)
@@ -905,7 +925,7 @@ def test_programmatic_launch_off_and_on_give_the_same_y(tmp_path, no_pdl):
     want, scale = reference(n, rp, ci, va, x)
     s = [torch.cuda.Stream() for _ in range(2)]
     x_d = dev(x)
-    y_d = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    y_d = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
     with make_part(n, rp, ci, va, 3, spmv.PER_PARTITION) as part:
         part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, 2008)
         part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_MERGE, 0)

@@ -23,7 +23,7 @@ import pytest
 
 import oracle
 from paper_2203_02530_gb300 import workloads as W
-from tests.gpu_util import assert_fp64_close, dev, torch_cuda
+from tests.gpu_util import assert_fp64_close, dev, synced, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,7 @@ _USED_MEM_HIGH = 8   # cudaMemPoolAttrUsedMemHigh
 
 def _device_csr(torch, n, rp, ci, va, x):
     return (dev(rp.astype(np.int32)), dev(ci), dev(va), dev(x),
-            torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
+            synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")))
 
 
 def _cudart():
@@ -78,7 +78,7 @@ def test_no_alloc_matches_allocating_entry_point_on_two_calls():
         x = W.uniform_x(n, seed=15)
         scale = oracle.csr_absdot(n, rp, ci, va, x)
         rp_d, ci_d, va_d, x_d, y_ref = _device_csr(torch, n, rp, ci, va, x)
-        y_new = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        y_new = synced(torch.full((n,), float("nan"), dtype=torch.float64, device="cuda"))
         nnz = int(rp[-1])
         spmv.spmv_csr_merge(n, nnz, rp_d, ci_d, va_d, x_d, y_ref, s)
         spmv.spmv_csr_merge_noalloc(n, nnz, rp_d, ci_d, va_d, x_d, y_new, s)
