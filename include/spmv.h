@@ -260,8 +260,18 @@ int spmv_remote(spmv_part* part, int part_idx, double* y_dev, cudaStream_t s);
  *          x_dev / y_dev must equal the captured ones (else SPMV_EINVAL).
  * A graph keeps only dependencies, so two orders that differ only in the
  * relative order of ops on different streams give the same graph.
+ * SPMV_RUN_RELAXED (or-ed into CAPTURE; SPMV_EINVAL with EAGER; ignored by
+ *   REPLAY) lets an op with no DAG predecessor (a pack or a local product)
+ *   overlap the kernel before it on its stream: it does not wait for that
+ *   kernel, which releases it as its CTAs start (programmatic dependent
+ *   launch without the wait), so it fills that kernel's tail.  Every other
+ *   op still waits for the kernels it depends on, and every DAG edge, also
+ *   between two ops of one stream, becomes an event.  An extension, not the
+ *   paper's stream semantics (where the kernels of a stream run one after
+ *   another, the default here).  Ops of one product touch common data only
+ *   along DAG edges, so y is the same, bit for bit.
  */
-enum { SPMV_RUN_EAGER = 0, SPMV_RUN_CAPTURE = 1, SPMV_RUN_REPLAY = 2 };
+enum { SPMV_RUN_EAGER = 0, SPMV_RUN_CAPTURE = 1, SPMV_RUN_REPLAY = 2, SPMV_RUN_RELAXED = 4 };
 int spmv_schedule_run(spmv_part* part, const int32_t* op_order,
                       const int32_t* stream_of_op, int n_ops,
                       cudaStream_t* streams, int n_streams,

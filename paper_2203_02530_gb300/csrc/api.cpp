@@ -2,6 +2,7 @@
 // the four operations of Fig. 3c, and the schedule runner of Sec. III-B with
 // Table III synchronisation, eager or captured as a CUDA graph.
 #include "part.h"
+#include "pdl.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -107,6 +108,7 @@ spmvk::CsrArgs local_args(spmv_part* pt, const double* x, double* y) {
     a.nnz_total = (int)pt->nnz_l;
     a.guarded = 0;
     a.err = pt->err;
+    a.pdl = pt->cur_pdl;
     return a;
 }
 
@@ -123,19 +125,21 @@ spmvk::CsrArgs remote_args(spmv_part* pt, double* y) {
     a.nnz_total = (int)pt->nnz_r;
     a.guarded = 0;
     a.err = pt->err;
+    a.pdl = pt->cur_pdl;
     return a;
 }
 
 // Each op returns the number of kernels it launched.
 int op_pack(spmv_part* pt, int q, const double* x, cudaStream_t s) {
     if (q < 0) {
-        check_cuda(spmvk::launch_gather(x, pt->send_idx, nullptr, pt->sendbuf, pt->n_send, pt->num_sms, s),
+        check_cuda(spmvk::launch_gather(x, pt->send_idx, nullptr, pt->sendbuf, pt->n_send, pt->num_sms, s,
+                                        pt->cur_pdl),
                    "pack");
         return pt->n_send > 0;
     }
     const int64_t c = pt->pack_off[q + 1] - pt->pack_off[q];
     check_cuda(spmvk::launch_gather(x, pt->send_idx, pt->pack_pos + pt->pack_off[q], pt->sendbuf, c,
-                                    pt->num_sms, s),
+                                    pt->num_sms, s, pt->cur_pdl),
                "pack");
     return c > 0;
 }
@@ -143,7 +147,7 @@ int op_pack(spmv_part* pt, int q, const double* x, cudaStream_t s) {
 int op_copy(spmv_part* pt, int p, cudaStream_t s) {
     const int64_t a = p < 0 ? 0 : pt->halo_off[p];
     const int64_t b = p < 0 ? pt->n_send : pt->halo_off[p + 1];
-    check_cuda(spmvk::launch_copy(pt->sendbuf + a, pt->recvbuf + a, b - a, pt->num_sms, s), "halo copy");
+    check_cuda(spmvk::launch_copy(pt->sendbuf + a, pt->recvbuf + a, b - a, pt->num_sms, s, pt->cur_pdl), "halo copy");
     return b > a;
 }
 
@@ -216,14 +220,16 @@ int op_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
 
 // PACK of one halo segment: its send slots [a, b) <- x
 int op_pack_segment(spmv_part* pt, const spmv_part::Seg& g, const double* x, cudaStream_t s) {
-    check_cuda(spmvk::launch_gather(x, pt->send_idx + g.a, nullptr, pt->sendbuf + g.a, g.b - g.a, pt->num_sms, s),
+    check_cuda(spmvk::launch_gather(x, pt->send_idx + g.a, nullptr, pt->sendbuf + g.a, g.b - g.a, pt->num_sms, s,
+                                    pt->cur_pdl),
                "pack segment");
     return 1;
 }
 
 // COPY of one halo segment: recvbuf[a, b) <- sendbuf[a, b)
 int op_copy_segment(spmv_part* pt, const spmv_part::Seg& g, cudaStream_t s) {
-    check_cuda(spmvk::launch_copy(pt->sendbuf + g.a, pt->recvbuf + g.a, g.b - g.a, pt->num_sms, s), "copy segment");
+    check_cuda(spmvk::launch_copy(pt->sendbuf + g.a, pt->recvbuf + g.a, g.b - g.a, pt->num_sms, s, pt->cur_pdl),
+               "copy segment");
     return 1;
 }
 
@@ -278,8 +284,30 @@ void ensure_events(spmv_part* pt, int n_streams) {
 }
 
 // Issue one implementation (order + stream map) with Table III events.
+// Relaxed mode (SPMV_RUN_RELAXED, captured graphs only): an op with no DAG
+// predecessor (a pack or a local product) skips the programmatic wait for
+// the kernel before it on its stream (kPdlNoWait), and that kernel releases
+// it as its CTAs start (kPdlEarly), so the two overlap.  Every other op waits
+// as in the default mode (griddepcontrol.wait: all of its kernel's
+// prerequisite nodes complete), and every DAG edge, also between two ops of
+// one stream, is an event recorded after its source and waited for before
+// its target, so an op's predecessors are always among its prerequisites
+// even when a kernel between them on the stream did not wait.
 void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops, cudaStream_t* streams,
-           int n_streams, const double* x, double* y) {
+           int n_streams, const double* x, double* y, bool relaxed) {
+    std::vector<int> pdl_flags(n_ops, 0);
+    if (relaxed) {
+        std::vector<int> last(n_streams, -1);
+        for (int i = 0; i < n_ops; ++i) {
+            const int v = order[i];
+            const bool free_op = pt->preds[v].empty();
+            if (free_op) {
+                pdl_flags[v] |= spmvk::kPdlNoWait;
+                if (last[stream_of[v]] >= 0) pdl_flags[last[stream_of[v]]] |= spmvk::kPdlEarly;
+            }
+            last[stream_of[v]] = v;
+        }
+    }
     cudaStream_t origin = streams[0];
     std::vector<char> used(n_streams, 0);
     for (int v = 0; v < n_ops; ++v) used[stream_of[v]] = 1;
@@ -287,21 +315,31 @@ void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_
     check_cuda(cudaEventRecord(pt->fork_ev, origin), "fork record");
     for (int s = 1; s < n_streams; ++s)
         if (used[s]) check_cuda(cudaStreamWaitEvent(streams[s], pt->fork_ev, 0), "fork wait");
-    // which ops feed a successor bound to another stream
+    // which ops feed a successor bound to another stream (any successor in
+    // relaxed mode)
     std::vector<char> cross(n_ops, 0);
     for (auto& e : pt->edges)
-        if (stream_of[e.first] != stream_of[e.second]) cross[e.first] = 1;
+        if (relaxed || stream_of[e.first] != stream_of[e.second]) cross[e.first] = 1;
     int64_t records = 0, waits = 0, launches = 0;
     for (int i = 0; i < n_ops; ++i) {
         const int v = order[i];
         cudaStream_t sv = streams[stream_of[v]];
         for (int u : pt->preds[v]) {
-            if (stream_of[u] != stream_of[v]) {   // Table III: BoundGPU_i -> BoundGPU_j
+            if (relaxed || stream_of[u] != stream_of[v]) {   // Table III: BoundGPU_i -> BoundGPU_j
                 check_cuda(cudaStreamWaitEvent(sv, pt->op_ev[u], 0), "stream wait");
                 ++waits;
-            }                                     // same stream: nothing
+            }                                                // same stream: nothing
         }
-        launches += run_op(pt, v, x, y, sv);
+        {
+            pt->cur_pdl = pdl_flags[v];
+            try {
+                launches += run_op(pt, v, x, y, sv);
+            } catch (...) {
+                pt->cur_pdl = 0;
+                throw;
+            }
+            pt->cur_pdl = 0;
+        }
         if (cross[v]) {
             check_cuda(cudaEventRecord(pt->op_ev[v], sv), "event record");
             ++records;
@@ -713,6 +751,8 @@ int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream
     API_TRY
     check_part(pt);
     need(streams != nullptr, SPMV_EINVAL, "streams is NULL");
+    const bool relaxed = (flags & SPMV_RUN_RELAXED) != 0;
+    flags &= ~SPMV_RUN_RELAXED;
     if (flags == SPMV_RUN_REPLAY) {
         need(handle != nullptr, SPMV_EINVAL, "graph handle is NULL");
         auto it = pt->graphs.find(*handle);
@@ -722,17 +762,18 @@ int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream
         return SPMV_OK;
     }
     if (flags != SPMV_RUN_EAGER && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "unknown flags %d", flags);
+    if (relaxed && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "SPMV_RUN_RELAXED applies to SPMV_RUN_CAPTURE only");
     validate_schedule(pt, order, stream_of, n_ops, n_streams);
     need((x != nullptr && y != nullptr) || pt->n == 0, SPMV_EINVAL, "x_dev or y_dev is NULL");
     ensure_events(pt, n_streams);
     if (flags == SPMV_RUN_EAGER) {
-        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y);
+        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y, relaxed);
         return SPMV_OK;
     }
     need(handle != nullptr, SPMV_EINVAL, "graph handle is NULL");
     check_cuda(cudaStreamBeginCapture(streams[0], cudaStreamCaptureModeThreadLocal), "begin capture");
     try {
-        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y);
+        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y, relaxed);
     } catch (...) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(streams[0], &g);

@@ -245,11 +245,74 @@ __device__ __forceinline__ void batch_rows_staged(const BatchArgs& a, const Batc
     }
 }
 
+// One lane's slots j .. j + K - 1 of one slice (K <= the slots left in
+// it): K value and K column loads, then K gathers, then K FMAs in slot
+// order; slots past the lane's row length are discarded by a select.
+template <int K>
+__device__ __forceinline__ void slice_round(const double* vp, const int32_t* cp, const double* x, int j, int len,
+                                            double& sum, uint64_t pol) {
+    int32_t c[K];
+    double v[K], xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        c[u] = ld_stream(cp + 32 * (j + u));
+        v[u] = ld_stream(vp + 32 * (j + u));
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) xv[u] = ldg_keep(x + c[u], pol);
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const double t = fma(v[u], xv[u], sum);
+        sum = j + u < len ? t : sum;
+    }
+}
+
+// The same round over two slices at once (2K gathers in flight per lane).
+template <int K>
+__device__ __forceinline__ void slice_pair_round(const double* vp0, const int32_t* cp0, const double* vp1,
+                                                 const int32_t* cp1, const double* x, int j, int len0, int len1,
+                                                 double& sum0, double& sum1, uint64_t pol) {
+    int32_t c0[K], c1[K];
+    double v0[K], v1[K], x0[K], x1[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        c0[u] = ld_stream(cp0 + 32 * (j + u));
+        v0[u] = ld_stream(vp0 + 32 * (j + u));
+        c1[u] = ld_stream(cp1 + 32 * (j + u));
+        v1[u] = ld_stream(vp1 + 32 * (j + u));
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        x0[u] = ldg_keep(x + c0[u], pol);
+        x1[u] = ldg_keep(x + c1[u], pol);
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const double t0 = fma(v0[u], x0[u], sum0);
+        sum0 = j + u < len0 ? t0 : sum0;
+        const double t1 = fma(v1[u], x1[u], sum1);
+        sum1 = j + u < len1 ? t1 : sum1;
+    }
+}
+
+// The r (< 4) slots left of one slice as one round of r.
+__device__ __forceinline__ void slice_tail(int r, const double* vp, const int32_t* cp, const double* x, int j,
+                                           int len, double& sum, uint64_t pol) {
+    switch (r) {
+        case 1: slice_round<1>(vp, cp, x, j, len, sum, pol); break;
+        case 2: slice_round<2>(vp, cp, x, j, len, sum, pol); break;
+        case 3: slice_round<3>(vp, cp, x, j, len, sum, pol); break;
+        default: break;
+    }
+}
+
 // Slices [s0, s1) of a matrix's sliced layout, two at a time: one lane per
 // row of each, one FMA per stored entry in storage order (padded slots
-// discarded by a select).  Each round issues U slots of both slices' values
-// and columns, then their 2U gathers, so a warp keeps 2U entries per lane in
-// flight even when rows are short.
+// discarded by a select).  Rounds of 4 slots of both slices while both have
+// 4 left (8 gathers in flight per lane), then each slice's last slots as one
+// round of exactly that many (both slices in one round when their counts
+// match, the usual case since slices of a sorted matrix have similar
+// lengths): no slot is loaded twice and no gather repeated.
 __device__ __forceinline__ void batch_slices(const BatchArgs& a, const BatchMat& m, int s0, int s1, uint64_t pol) {
     constexpr int U = 4;
     const int lane = threadIdx.x & 31;
@@ -271,36 +334,24 @@ __device__ __forceinline__ void batch_slices(const BatchArgs& a, const BatchMat&
         const int32_t* cp0 = m.s_col + (int64_t)d0.off + lane;
         const double* vp1 = m.s_val + (int64_t)d1.off + lane;
         const int32_t* cp1 = m.s_col + (int64_t)d1.off + lane;
-        const int lmax = d0.len > d1.len ? d0.len : d1.len;
+        const int lmin = d0.len < d1.len ? d0.len : d1.len;
         double sum0 = 0.0, sum1 = 0.0;
-        for (int j0 = 0; j0 < lmax; j0 += U) {
-            int32_t c0[U], c1[U];
-            double v0[U], v1[U], x0[U], x1[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int ja = j0 + u < d0.len ? j0 + u : d0.len - 1;   // clamped: in this slice
-                const int jb = j0 + u < d1.len ? j0 + u : d1.len - 1;
-                c0[u] = ja >= 0 ? ld_stream(cp0 + 32 * ja) : 0;
-                v0[u] = ja >= 0 ? ld_stream(vp0 + 32 * ja) : 0.0;
-                c1[u] = jb >= 0 ? ld_stream(cp1 + 32 * jb) : 0;
-                v1[u] = jb >= 0 ? ld_stream(vp1 + 32 * jb) : 0.0;
+        int j = 0;
+        for (; j + U <= lmin; j += U) slice_pair_round<U>(vp0, cp0, vp1, cp1, x, j, len0, len1, sum0, sum1, pol);
+        const int r0 = d0.len - j, r1 = d1.len - j;   // warp-uniform
+        if (r0 == r1 && r0 > 0) {   // both below U here
+            switch (r0) {
+                case 1: slice_pair_round<1>(vp0, cp0, vp1, cp1, x, j, len0, len1, sum0, sum1, pol); break;
+                case 2: slice_pair_round<2>(vp0, cp0, vp1, cp1, x, j, len0, len1, sum0, sum1, pol); break;
+                default: slice_pair_round<3>(vp0, cp0, vp1, cp1, x, j, len0, len1, sum0, sum1, pol); break;
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                x0[u] = ldg_keep(x + c0[u], pol);
-                x1[u] = ldg_keep(x + c1[u], pol);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (j0 + u < d0.len) {   // uniform over the warp
-                    const double t = fma(v0[u], x0[u], sum0);
-                    sum0 = j0 + u < len0 ? t : sum0;
-                }
-                if (j0 + u < d1.len) {
-                    const double t = fma(v1[u], x1[u], sum1);
-                    sum1 = j0 + u < len1 ? t : sum1;
-                }
-            }
+        } else {
+            int k = j;
+            for (; k + U <= d0.len; k += U) slice_round<U>(vp0, cp0, x, k, len0, sum0, pol);
+            slice_tail(d0.len - k, vp0, cp0, x, k, len0, sum0, pol);
+            k = j;
+            for (; k + U <= d1.len; k += U) slice_round<U>(vp1, cp1, x, k, len1, sum1, pol);
+            slice_tail(d1.len - k, vp1, cp1, x, k, len1, sum1, pol);
         }
         if (lane < d0.rows) y[m.s_perm ? __ldg(m.s_perm + d0.pos0 + lane) : d0.pos0 + lane] = sum0;
         if (lane < d1.rows) y[m.s_perm ? __ldg(m.s_perm + d1.pos0 + lane) : d1.pos0 + lane] = sum1;
@@ -412,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_range_kernel(BatchArgs a, i
         batch_item(a, it, pol, s_val[w], s_col[w]);
 }
 
-__global__ void __launch_bounds__(kThreads, 5) batch_sliced_range_kernel(BatchArgs a, int first, int last) {
+__global__ void __launch_bounds__(kThreads, 4) batch_sliced_range_kernel(BatchArgs a, int first, int last) {
     const uint64_t pol = policy_evict_last();
     const int nw = (int)gridDim.x * (kThreads / 32);
     for (int it = first + (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); it < last; it += nw)

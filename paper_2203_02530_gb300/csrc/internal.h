@@ -103,13 +103,15 @@ struct CsrArgs {
     int abort_tile;         // test hook of the merge-path kernel: k > 0 makes
                             // tiles k-1 and later take the path of a wait that
                             // ran out (after their copies landed); 0 = never
+    int pdl;                // programmatic-launch flags of the launch
+                            // (kPdlNoWait, kPdlEarly; 0 = wait, no early release)
 };
 
 // Launchers (kernels.cu).  All return cudaGetLastError() after the launch.
 cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* pos,
-                          double* dst, int64_t count, int num_sms, cudaStream_t s);
+                          double* dst, int64_t count, int num_sms, cudaStream_t s, int pdl = 0);
 cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_sms,
-                        cudaStream_t s);
+                        cudaStream_t s, int pdl = 0);
 cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin,
                         int tile_end, const TileGeom& g, int num_sms, cudaStream_t s);
 cudaError_t launch_vector(const CsrArgs& a, const Tile* tiles, int tile_begin, int tile_end,
@@ -157,6 +159,8 @@ cudaError_t launch_check_sell(const SellSlice* slices, int n_slices, const uint8
 inline bool sell_param_balanced(int param) { return param >= 2000; }
 // CTAs of a sliced launch of `units` work units.
 int sell_grid(int param, int units, int num_sms);
+// Entries per lane per step of sliced param `param` (0 if unknown).
+int sell_param_entries(int param);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);
 TileGeom default_tile_geom();

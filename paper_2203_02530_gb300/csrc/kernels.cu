@@ -122,8 +122,8 @@ constexpr int kPackIlp = 4;
 __global__ void __launch_bounds__(256) gather_kernel(const double* __restrict__ x,
                                                      const int32_t* __restrict__ idx,
                                                      const int32_t* __restrict__ pos,
-                                                     double* __restrict__ dst, int64_t count) {
-    pdl_wait();      // the previous kernel of this stream is done
+                                                     double* __restrict__ dst, int64_t count, int pdl) {
+    pdl_begin(pdl);  // the previous kernel of this stream is done (unless independent)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += kPackIlp * stride) {
         int64_t k[kPackIlp];
@@ -145,12 +145,12 @@ __global__ void __launch_bounds__(256) gather_kernel(const double* __restrict__ 
 }
 
 cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* pos,
-                          double* dst, int64_t count, int num_sms, cudaStream_t s) {
+                          double* dst, int64_t count, int num_sms, cudaStream_t s, int pdl) {
     if (count <= 0) return cudaSuccess;
     int64_t blocks = (count + 256 * kPackIlp - 1) / (256 * kPackIlp);
     const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
-    return launch_pdl(gather_kernel, dim3((unsigned)blocks), dim3(256), 0, s, x, idx, pos, dst, count);
+    return launch_pdl(gather_kernel, dim3((unsigned)blocks), dim3(256), 0, s, x, idx, pos, dst, count, pdl);
 }
 
 // ------------------------------------------------------------------------
@@ -158,8 +158,8 @@ cudaError_t launch_gather(const double* x, const int32_t* idx, const int32_t* po
 // kPackIlp loads in flight per thread before their stores.
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ src,
-                                                   double* __restrict__ dst, int64_t count) {
-    pdl_wait();      // the previous kernel of this stream is done
+                                                   double* __restrict__ dst, int64_t count, int pdl) {
+    pdl_begin(pdl);  // the previous kernel of this stream is done (unless independent)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
     if (vec) {
@@ -183,13 +183,13 @@ __global__ void __launch_bounds__(256) copy_kernel(const double* __restrict__ sr
 }
 
 cudaError_t launch_copy(const double* src, double* dst, int64_t count, int num_sms,
-                        cudaStream_t s) {
+                        cudaStream_t s, int pdl) {
     if (count <= 0) return cudaSuccess;
     int64_t blocks = (count / 2 + 256 * kPackIlp - 1) / (256 * kPackIlp);
     if (blocks < 1) blocks = 1;
     const int64_t cap = (int64_t)num_sms * 4;
     if (blocks > cap) blocks = cap;
-    return launch_pdl(copy_kernel, dim3((unsigned)blocks), dim3(256), 0, s, src, dst, count);
+    return launch_pdl(copy_kernel, dim3((unsigned)blocks), dim3(256), 0, s, src, dst, count, pdl);
 }
 
 // ------------------------------------------------------------------------
@@ -218,7 +218,7 @@ struct TileLayout {
 template <int NT, int CAP, int ST, int CH, int LANES>
 __global__ void __launch_bounds__(NT, 1) csr_tile_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                       int tile_begin, int tile_end) {
-    pdl_wait();      // the previous kernel of this stream is done
+    pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
     static_assert(LANES == 1 || LANES == 2 || LANES == 4, "lanes per row");
     using L = TileLayout<NT / LANES, CAP>;
     const uint64_t pol_stream = policy_evict_first();
@@ -451,7 +451,7 @@ cudaError_t launch_tile(const CsrArgs& a, const Tile* tiles, int tile_begin, int
 template <int V>
 __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                          int tile_begin, int tile_end) {
-    pdl_wait();      // the previous kernel of this stream is done
+    pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
     constexpr int GROUPS = 256 / V;
     const uint64_t pol_keep = policy_evict_last();
     const int lane = threadIdx.x % V;
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(CsrArgs a, const Tile* 
 template <int WARPS, int CAP, int ST, int CH>
 __global__ void __launch_bounds__(WARPS * 32, 1) csr_warp_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                                 int tile_begin, int tile_end) {
-    pdl_wait();      // the previous kernel of this stream is done
+    pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
     using L = TileLayout<32, CAP>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[WARPS][ST];
@@ -676,7 +676,7 @@ cudaError_t launch_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int
 template <int V, int U, int MINB>
 __global__ void __launch_bounds__(256, MINB) csr_pair_kernel(CsrArgs a, const Tile* __restrict__ tiles,
                                                           int tile_begin, int tile_end) {
-    pdl_wait();      // the previous kernel of this stream is done
+    pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
     constexpr int GROUPS = 256 / V;
     const uint64_t pol_keep = policy_evict_last();
     const int lane = threadIdx.x % V;
@@ -799,22 +799,34 @@ cudaError_t selftest_wait_timeout(uint64_t limit_ns, int* status_host) {
 // FP64 FMA throughput probe: the first `lanes` lanes of every warp run 8
 // independent chains of `iters` fused multiply-adds each (enough chains to
 // cover the pipe's latency), then store their sum, so no chain is dead code.
-// The multiplier and addend keep every value near 1 (no overflow, no
+// Each chain accumulates through the addend, a = fma(m, c, a), as a product
+// accumulates sum = fma(value, x, sum), with every operand a register of its
+// own (m and c pass through an opaque move, so they are not folded into
+// constant operands).  m c = 1e-6 keeps every value near 1 (no overflow, no
 // subnormals).
 // ------------------------------------------------------------------------
 constexpr int kProbeThreads = 256;
 constexpr int kProbeChains = 8;
 
+__device__ __forceinline__ double opaque(double v) {
+    double r;
+    asm volatile("mov.b64 %0, %1;" : "=d"(r) : "d"(v));
+    return r;
+}
+
 __global__ void __launch_bounds__(kProbeThreads) dfma_probe_kernel(int64_t iters, int lanes, double* out) {
     const int64_t gid = (int64_t)blockIdx.x * kProbeThreads + threadIdx.x;
-    double a[kProbeChains];
+    double a[kProbeChains], m[kProbeChains], c[kProbeChains];
 #pragma unroll
-    for (int u = 0; u < kProbeChains; ++u) a[u] = 1.0 + 1e-3 * u + 1e-9 * (double)(gid & 1023);
+    for (int u = 0; u < kProbeChains; ++u) {
+        a[u] = 1.0 + 1e-3 * u + 1e-9 * (double)(gid & 1023);
+        m[u] = opaque(1e-3);
+        c[u] = opaque(1e-3);
+    }
     if ((int)(threadIdx.x & 31) < lanes) {
-        const double m = 0.9999999999, c = 1e-10;
         for (int64_t i = 0; i < iters; ++i) {
 #pragma unroll
-            for (int u = 0; u < kProbeChains; ++u) a[u] = fma(a[u], m, c);
+            for (int u = 0; u < kProbeChains; ++u) a[u] = fma(m[u], c[u], a[u]);
         }
     }
     double sum = 0.0;

@@ -116,7 +116,9 @@ template <bool GUARD>
 __global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const MergeTile* __restrict__ tiles,
                                                          int tile_begin, int tile_end,
                                                          Carry* __restrict__ carries) {
-    pdl_wait();      // the previous kernel of this stream is done
+    // the previous kernel of this stream is done (unless independent); the
+    // next kernel is this operation's fixup, which needs the carries
+    pdl_begin(a.pdl & kPdlNoWait);
     using L = MergeLayout;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[MERGE_ST];
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(MERGE_NT, 3) merge_kernel(CsrArgs a, const Mer
 // carrying the same row sums the run in tile order and adds it once.
 __global__ void __launch_bounds__(256) merge_fixup_kernel(CsrArgs a, const Carry* __restrict__ carries,
                                                           int tile_begin, int tile_end) {
-    pdl_wait();      // the previous kernel of this stream is done
+    pdl_begin(a.pdl & kPdlEarly);   // the carries of the merge kernel are complete
     const int t = tile_begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (t >= tile_end) return;
     const Carry c = carries[t];

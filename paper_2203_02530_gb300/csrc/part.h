@@ -159,6 +159,7 @@ struct spmv_part {
     std::map<int64_t, spmvk::GraphRec> graphs;
     int64_t next_graph = 1;
     int64_t last_records = 0, last_waits = 0, last_launches = 0;
+    int cur_pdl = 0;                  // programmatic-launch flags of the op being issued
 
     std::vector<spmvk::DevArray> allocs;   // everything to free
     size_t device_bytes = 0;

@@ -501,6 +501,22 @@ void build_sell(spmv_part* pt) {
 // neighbouring slices of the round-robin split together.  A unit's cost is
 // its entries per lane (a slice's longest row; a piece's entries over 32,
 // rounded up) plus 3 for its descriptor, row and store.
+// Estimated time of one work unit of a sliced launch with param `param`,
+// in units of one dependent load-then-gather round: a unit's fixed loads
+// (descriptor, lengths, row map) and store, its rounds (U slots per lane for
+// a slice, whose remainder is one more round; 8 or 4 entries per lane for a
+// long-row piece), and a small per-entry term for the issue of its loads and
+// FMAs.  Long pieces and slices are costed alike, per lane.
+constexpr double SELL_COST_FIXED = 2.0, SELL_COST_ROUND = 2.0, SELL_COST_ENTRY = 0.25;
+
+double sell_unit_cost(int param, bool long_piece, int64_t len) {
+    const int U = sell_param_entries(param);
+    const int64_t per_lane = long_piece ? (len + 31) / 32 : len;
+    const int step = long_piece ? (U >= 8 ? 8 : 4) : U;
+    const int64_t rounds = (per_lane + step - 1) / step;
+    return SELL_COST_FIXED + SELL_COST_ROUND * (double)rounds + SELL_COST_ENTRY * (double)per_lane;
+}
+
 void build_sell_split(spmv_part* pt, int part_idx, int param) {
     spmv_part::SellPart& sp = pt->sell[part_idx];
     const int P = pt->P;
@@ -514,9 +530,9 @@ void build_sell_split(spmv_part* pt, int part_idx, int param) {
         if (sp.cta_split.count(key)) continue;
         std::vector<double> prefix((size_t)units + 1, 0.0);
         for (int u = 0; u < units; ++u) {
-            const int64_t c = u < le - lb ? 3 + (sp.h_long_len[(size_t)(lb + u)] + 31) / 32
-                                          : 3 + sp.h_slice_len[(size_t)(sb + u - (le - lb))];
-            prefix[(size_t)u + 1] = prefix[(size_t)u] + (double)c;
+            const bool lng = u < le - lb;
+            const int64_t len = lng ? sp.h_long_len[(size_t)(lb + u)] : sp.h_slice_len[(size_t)(sb + u - (le - lb))];
+            prefix[(size_t)u + 1] = prefix[(size_t)u] + sell_unit_cost(param, lng, len);
         }
         std::vector<int32_t> off((size_t)grid + 1);
         const double total = prefix[(size_t)units];

@@ -94,6 +94,45 @@ __device__ __forceinline__ void sell_round(const CT* cp, const double* vp, const
     }
 }
 
+// The r < U remaining slots of a slice lane as one round of r.
+template <int U, typename CT>
+__device__ __forceinline__ void sell_tail(int r, const CT* cp, const double* vp, const double* xb, int j, int len,
+                                          double& sum, uint64_t pol_stream, uint64_t pol_keep) {
+    switch (r) {
+        case 1: sell_round<1>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 2: if (U > 2) sell_round<2>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 3: if (U > 3) sell_round<3>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 4: if (U > 4) sell_round<4>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 5: if (U > 5) sell_round<5>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 6: if (U > 6) sell_round<6>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 7: if (U > 7) sell_round<7>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        case 8: if (U > 8) sell_round<8>(cp, vp, xb, j, len, sum, pol_stream, pol_keep); break;
+        default: break;
+    }
+}
+
+// Entries [k, ke) of a long row taken by one lane in steps of 32 (k = the
+// lane's first), R at a time: R value and R column loads, then R gathers,
+// then R FMAs in entry order; in the last round the entries at or past ke
+// are neither loaded nor added.
+template <int R>
+__device__ __forceinline__ void long_round(const CsrArgs& a, const double* xb, int k, int ke, double& part,
+                                           uint64_t pol_stream, uint64_t pol_keep) {
+    double v[R], xv[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const bool m = k + 32 * u < ke;
+        v[u] = m ? ld_stream(a.val + k + 32 * u, pol_stream) : 0.0;
+        const int c = m ? ld_stream(a.col + k + 32 * u, pol_stream) : 0;
+        xv[u] = m ? ld_keep(xb + c, pol_keep) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const double t = fma(v[u], xv[u], part);
+        part = k + 32 * u < ke ? t : part;
+    }
+}
+
 }  // namespace
 
 // One warp per work unit, grid-stride: units [0, n_long) are the launch's
@@ -111,7 +150,7 @@ __device__ __forceinline__ void sell_round(const CT* cp, const double* vp, const
 // half the index bytes where every |column - row| fits in 16 bits.
 template <int U, int MINB, typename CT>
 __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs sa) {
-    pdl_wait();      // the previous kernel of this stream is done
+    pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
     constexpr bool kDelta = sizeof(CT) == 2;
     const uint64_t pol_stream = sell_policy_evict_first();
     const uint64_t pol_keep = sell_policy_evict_last();
@@ -131,28 +170,11 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
             const int kb = L.k0, ke = L.k1;
             const double* xb = a.x + L.xoff;
             double part = 0.0;
-            int k = kb + lane;
-            for (; k + 96 < ke; k += 128) {
-                double v[4], xv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    v[u] = ld_stream(a.val + k + 32 * u, pol_stream);
-                    xv[u] = ld_keep(xb + ld_stream(a.col + k + 32 * u, pol_stream), pol_keep);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) part = fma(v[u], xv[u], part);
-            }
-            if (k + 32 < ke) {   // at most 3 entries of this lane left: two, then one
-                const double v0 = ld_stream(a.val + k, pol_stream), v1 = ld_stream(a.val + k + 32, pol_stream);
-                const int c0 = ld_stream(a.col + k, pol_stream), c1 = ld_stream(a.col + k + 32, pol_stream);
-                const double x0 = ld_keep(xb + c0, pol_keep), x1 = ld_keep(xb + c1, pol_keep);
-                part = fma(v0, x0, part);
-                part = fma(v1, x1, part);
-                k += 64;
-            }
-            if (k < ke)
-                part = fma(ld_stream(a.val + k, pol_stream), ld_keep(xb + ld_stream(a.col + k, pol_stream), pol_keep),
-                           part);
+            // the lane's entries kb + lane, + 32, ... in rounds of LR (at
+            // most 16 per lane: a piece holds at most 512 entries); the last
+            // round is predicated per entry
+            constexpr int LR = U >= 8 ? 8 : 4;
+            for (int k = kb + lane; k < ke; k += 32 * LR) long_round<LR>(a, xb, k, ke, part, pol_stream, pol_keep);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
             if (lane == 0) {
@@ -192,16 +214,11 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
         double sum = 0.0;
         int j = 0;
         for (; j + U <= d.len; j += U) sell_round<U>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
-        // the last d.len mod U slots in rounds of 4, 2 and 1 (each round one
-        // load-then-gather latency), not one slot at a time: short slices,
-        // the common case on skewed rows, keep several gathers in flight
-        if (U > 4)
-            for (; j + 4 <= d.len; j += 4) sell_round<4>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
-        if (U > 2 && j + 2 <= d.len) {   // at most 3 slots left here
-            sell_round<2>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
-            j += 2;
-        }
-        for (; j < d.len; ++j) sell_round<1>(cp, vp, xb, j, len, sum, pol_stream, pol_keep);
+        // the last d.len mod U slots in one round of exactly that many (the
+        // count is the same for the whole warp): one load-then-gather
+        // latency, so the short slices of skewed rows (3 entries, say) keep
+        // all their gathers in flight at once
+        sell_tail<U>(d.len - j, cp, vp, xb, j, len, sum, pol_stream, pol_keep);
         if (store) sell_store(a, row, sum);
     }
 }
@@ -285,6 +302,15 @@ cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const doubl
 bool sell_param_supported(int param) {
     const int base = param >= 2000 ? param - 2000 : param;
     return base == 4 || base == 8 || base == 9 || (base >= 104 && base <= 107);
+}
+
+int sell_param_entries(int param) {
+    switch (param % 1000) {
+        case 4: case 104: return 4;
+        case 8: case 105: case 106: return 8;
+        case 9: case 107: return 9;
+        default: return 0;
+    }
 }
 
 int sell_grid(int param, int units, int num_sms) {

@@ -89,6 +89,8 @@ def main(argv=None):
     ap.add_argument("--variant", type=int, nargs=2, default=[1, 2], metavar=("VARIANT", "PARAM"))
     ap.add_argument("--op", choices=["local", "remote"], default="local")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--rank", type=int, default=-1,
+                    help="launch the operation of this rank only (-1: one launch over all ranks)")
     ap.add_argument("--cache-dir", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build"),
                     help="where the generated power-law matrix is cached (default: the package's "
                          "ignored build folder)")
@@ -112,14 +114,14 @@ def main(argv=None):
     spmv.spmv_halo_copy(part.h, -1, s)
     for _ in range(args.launches):
         if kind == spmv.OP_LOCAL:
-            spmv.spmv_local(part.h, -1, x_d, y_d, s)
+            spmv.spmv_local(part.h, args.rank, x_d, y_d, s)
         else:
-            spmv.spmv_remote(part.h, -1, y_d, s)
+            spmv.spmv_remote(part.h, args.rank, y_d, s)
     s.synchronize()
     err = part.query(spmv.Q_ERROR)
     part.close()
-    print("launched %d x %s (variant %d/%d); error word %d" % (args.launches, args.op,
-                                                               args.variant[0], args.variant[1], err))
+    print("launched %d x %s of rank %d (variant %d/%d); error word %d" % (
+        args.launches, args.op, args.rank, args.variant[0], args.variant[1], err))
     return 0 if err == 0 else 1
 
 

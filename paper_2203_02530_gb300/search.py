@@ -46,16 +46,18 @@ class Recorder:
 
 
 def graph_evaluator(part, streams, x_dev, y_dev, recorder=None, measurements=1,
-                    t_measure=benchmark.T_MEASURE):
+                    t_measure=benchmark.T_MEASURE, relaxed=False):
     """evaluate(order, smap) -> seconds per sample (min over `measurements`
-    measurements of graph replays)."""
+    measurements of graph replays); `relaxed` captures each program with
+    SPMV_RUN_RELAXED (DAG-only ordering)."""
+    flags = spmv.RUN_CAPTURE | (spmv.RUN_RELAXED if relaxed else 0)
 
     def evaluate(order, smap):
         if recorder is not None:
             t = recorder.get(order, smap)
             if t is not None:
                 return t
-        g = part.run(order, smap, streams, x_dev, y_dev, spmv.RUN_CAPTURE)
+        g = part.run(order, smap, streams, x_dev, y_dev, flags)
         try:
             sample = lambda: part.run(order, smap, streams, x_dev, y_dev, spmv.RUN_REPLAY, g)
             sample()

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "spmv.h")
 OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
 COARSE, PER_PARTITION, PER_SEGMENT = 0, 1, 2
-RUN_EAGER, RUN_CAPTURE, RUN_REPLAY = 0, 1, 2
+RUN_EAGER, RUN_CAPTURE, RUN_REPLAY, RUN_RELAXED = 0, 1, 2, 4
 VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP, VARIANT_SELL, VARIANT_SELL16 = (
     0, 1, 2, 3, 4, 5, 6)
 SERVE_BATCHED, SERVE_PLAIN = 0, 1
