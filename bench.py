@@ -410,6 +410,12 @@ def run_ours(args, world, rank, local, fp64=None):
     tuned = autotune.tune(part, x_d, y_d, streams[0], sig=sig, use_cache=not args.retune)
     variant, vparam = tuned["local"]
     tune_times = tuned["times"]
+    # with both products on the sliced layout the CSR copy is a second copy
+    # of the matrix that no product reads: release it
+    plan_bytes = {"tuned": part.query(spmv.Q_DEVICE_BYTES)}
+    if variant in (spmv.VARIANT_SELL, spmv.VARIANT_SELL16) and tuned["remote"][0] == spmv.VARIANT_SELL:
+        part.release_csr()
+    plan_bytes["timed"] = part.query(spmv.Q_DEVICE_BYTES)
 
     # the design space: every schedule (coarse DAG), MCTS samples (per-rank
     # DAG) or the single default order
@@ -572,7 +578,8 @@ def run_ours(args, world, rank, local, fp64=None):
                    "l2": "inputs larger than L2" if 12 * int(rp[-1]) > 129e6
                          else "L2-resident (replay latency)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "alg_bytes_per_step": alg, "plan_device_bytes": dev_bytes},
+                   "alg_bytes_per_step": alg, "plan_device_bytes": dev_bytes,
+                   "plan_device_bytes_before_csr_release": plan_bytes["tuned"]},
         "percent_hbm": round(100.0 * value / world / peak, 2),
         "roofline": dict({"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                           "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -874,6 +881,21 @@ def run_serving(args, world, rank, local, fp64=None):
                      "launches": spmv.spmv_serve_launches(sv.h),
                      "peak_pool_mb": round(st["peak_pool_bytes"] / 1e6, 1), "hash": hs}
     same = bool(np.array_equal(out["served"].pop("hash"), out["plain"].pop("hash")))
+    # the same request mix arriving faster (near the plain form's saturation),
+    # where continuous batching has queues to merge
+    high = {}
+    if args.serve_rate_high > 0:
+        arr_h = W.poisson_arrivals(args.serve_rate_high, args.serve_seconds / 2, seed=9)
+        ch = min(arr_h.size, count)
+        for name, mode in (("served", spmv.SERVE_BATCHED), ("plain", spmv.SERVE_PLAIN)):
+            lat, _, st = sv.run(mat[:ch], wid[:ch], sd[:ch], arr_h[:ch], mode, want_hash=False)
+            el = st["elapsed_ns"] * 1e-9
+            high[name] = {"p50_us": round(float(np.percentile(lat, 50)) * 1e6, 2),
+                          "p99_us": round(float(np.percentile(lat, 99)) * 1e6, 2),
+                          "throughput_req_s": round(ch / el, 1), "blocks": st["blocks"],
+                          "launches": spmv.spmv_serve_launches(sv.h)}
+        high["rate_req_s"] = args.serve_rate_high
+        high["requests"] = int(ch)
     # saturation: every request present at t = 0 (the most either form can do)
     nsat = min(count, args.serve_saturation)
     sat = {}
@@ -923,7 +945,7 @@ def run_serving(args, world, rank, local, fp64=None):
                                    args.serve_layout),
                    "value": "saturation throughput of the served form (all requests present at t=0; a "
                             "step is one request), per-request algorithmic bytes"},
-        "open_loop": out, "saturation": sat,
+        "open_loop": out, "open_loop_high": high, "saturation": sat,
         "served_vs_plain_saturation": round(sat["served"]["gbs"] / sat["plain"]["gbs"], 3),
         "results_identical_served_vs_plain": same,
         "latency_us": {"p50": out["served"]["p50_us"], "p99": out["served"]["p99_us"],
@@ -1073,6 +1095,8 @@ def main(argv=None):
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-streams", type=int, default=32)
+    ap.add_argument("--serve-rate-high", type=float, default=40000.0,
+                    help="a second open-loop arrival rate, near the plain form's saturation (0: none)")
     ap.add_argument("--serve-saturation", type=int, default=20000)
     ap.add_argument("--serve-layout", choices=["sliced", "buckets"], default="sliced")
     args = ap.parse_args(argv)

@@ -162,7 +162,9 @@ enum {
 };
 /* Element count of array `what` (for rank part_idx where per rank), or < 0. */
 int64_t spmv_part_export_len(const spmv_part* part, int what, int part_idx);
-/* Copy array `what` to host_dst (capacity cap elements); synchronises. */
+/* Copy array `what` to host_dst (capacity cap elements); synchronises.  The
+ * matrix arrays of a plan whose CSR copy was released are exported after
+ * rebuilding it (spmv_part_release_csr). */
 int spmv_part_export_plan(const spmv_part* part, int what, int part_idx,
                           void* host_dst, int64_t cap);
 
@@ -225,6 +227,24 @@ enum {
 int spmv_part_set_variant(spmv_part* part, int variant, int param);
 /* Sets the variant of one product: op_kind SPMV_OP_LOCAL or SPMV_OP_REMOTE. */
 int spmv_part_set_op_variant(spmv_part* part, int op_kind, int variant, int param);
+
+/*
+ * Release the plan's CSR copy of the matrix once both products use the
+ * sliced layout (LOCAL SPMV_VARIANT_SELL or SELL16, REMOTE SELL): that
+ * layout is a second copy of every entry, so the plan otherwise holds the
+ * matrix twice.  The entries of rows longer than 64 (which the sliced
+ * products read from the CSR) move to compact arrays of their own; then the
+ * CSR columns and values of A_L and A_R are freed, and A_L's 32-bit slot
+ * columns too while its product uses the 16-bit deltas.  Row pointers stay.
+ * Products give the same y, bit for bit.  Whatever needs the CSR again
+ * (selecting a non-sliced variant, or the 32-bit LOCAL one after SELL16;
+ * spmv_part_export_plan of SPMV_X_L_COL / L_VAL / R_COL / R_VAL;
+ * spmv_part_check) first rebuilds it on the device from the sliced layout
+ * and keeps it.  SPMV_Q_DEVICE_BYTES reports the memory held.  Synchronises.
+ * Errors: SPMV_EINVAL when a product does not use the sliced layout or while
+ * captured graphs exist; a no-op if already released.
+ */
+int spmv_part_release_csr(spmv_part* part);
 
 /*
  * The four operations (Fig. 3c).  `part_idx` = -1 runs the op for every
@@ -441,12 +461,12 @@ int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, doubl
  *   the oldest requests of one matrix into one block of total width <= 8
  *   whenever a slot and pool memory are free; requests arriving while blocks
  *   run join at the next turn of the loop.  When every matrix is in the
- *   sliced layout, BATCHED goes further: the blocks the queues would form
- *   are spread over the free slots, ceil(blocks / free slots) per slot (at
- *   most the group size, spmv_serve_set_group_max), and a slot given more
- *   than one block runs them, across matrices, as one group with one launch
- *   per kernel kind (X generation, slices, long rows); under light load every
- *   block thus gets a slot of its own, under heavy load groups grow.
+ *   sliced layout, BATCHED goes further: a free slot takes ceil(blocks /
+ *   slots) of the blocks the queues would form (at most the group size,
+ *   spmv_serve_set_group_max) and runs more than one, across matrices, as one
+ *   group with one launch per kernel kind (X generation, slices, long rows);
+ *   while no more blocks wait than there are slots every block thus gets a
+ *   slot of its own, and groups grow only with a longer queue.
  *   PLAIN launches every request alone (one block per request).  Outputs:
  *   latency_s[r] = observed completion - arrival; hash_out[r] (optional) an
  *   order-independent 64-bit hash of the bits of request r's Y; stats (6

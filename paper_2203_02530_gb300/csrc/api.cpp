@@ -190,7 +190,12 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
                 if (!sa.cta_off) fail(SPMV_EINVAL, "balanced sliced ranges not prepared");
             }
         }
-        check_cuda(spmvk::launch_sell(a, sa, param, var == SPMV_VARIANT_SELL16, pt->num_sms, s), "sliced product");
+        spmvk::CsrArgs al = a;   // long rows: from the CSR, or its compact copy once the CSR is released
+        if (sp.long_col) {
+            al.col = sp.long_col;
+            al.val = sp.long_val;
+        }
+        check_cuda(spmvk::launch_sell(al, sa, param, var == SPMV_VARIANT_SELL16, pt->num_sms, s), "sliced product");
         return (sa.slice_end > sa.slice_begin || sa.long_end > sa.long_begin) ? 1 : 0;
     }
     const spmvk::Tile* tiles = remote ? pt->rtiles : pt->ltiles;
@@ -516,6 +521,8 @@ int spmv_part_export_plan(const spmv_part* pt, int what, int p, void* dst, int64
     if (len > 0 && !dst) fail(SPMV_EINVAL, "host_dst is NULL");
     if (len == 0) return SPMV_OK;
     check_cuda(cudaDeviceSynchronize(), "synchronize");
+    if (what == SPMV_X_L_COL || what == SPMV_X_L_VAL || what == SPMV_X_R_COL || what == SPMV_X_R_VAL)
+        spmvk::restore_csr(const_cast<spmv_part*>(pt));   // the matrix is unchanged; its CSR copy is rebuilt
     int64_t* d64 = static_cast<int64_t*>(dst);
     int32_t* d32 = static_cast<int32_t*>(dst);
     double* df = static_cast<double*>(dst);
@@ -635,6 +642,11 @@ int spmv_part_dag(const spmv_part* pt, int32_t* edges, int64_t cap_pairs, int64_
 // Validates (variant, param) and prepares the tables it needs.
 static void prepare_variant(spmv_part* pt, int variant, int param, int op_kind) {
     if (!pt->graphs.empty()) fail(SPMV_EINVAL, "destroy the captured graphs before changing the variant");
+    // every variant but the sliced ones reads the CSR; the 32-bit sliced
+    // LOCAL product reads the 32-bit slot columns
+    if (pt->csr_released && (variant != SPMV_VARIANT_SELL16 || op_kind != SPMV_OP_LOCAL) &&
+        (variant != SPMV_VARIANT_SELL || (op_kind != SPMV_OP_REMOTE && !pt->sell[0].col)))
+        spmvk::restore_csr(pt);
     if (variant == SPMV_VARIANT_TILE) {
         static const spmvk::TileGeom geoms[] = {{256, 3456, 2, 16, 2},
                                                 {512, 6912, 2, 16, 2},
@@ -1027,6 +1039,7 @@ int spmv_part_check(spmv_part* pt, int64_t* bad_out) {
     API_TRY
     check_part(pt);
     need(bad_out != nullptr, SPMV_EINVAL, "bad_out is NULL");
+    spmvk::restore_csr(pt);   // the checks read the CSR
     const int P = pt->P;
     // host tables of group offsets and ranges, one device copy
     std::vector<int64_t> tab;
@@ -1193,6 +1206,15 @@ int spmv_probe_gather(const double* table_dev, const int32_t* idx_dev, int64_t c
         fail(SPMV_EINVAL, "out_cap %lld below the %lld threads of the launch", (long long)out_cap,
              (long long)grid * spmvk::probe_threads());
     check_cuda(spmvk::launch_gather_probe(table_dev, idx_dev, count, grid, out_dev, s), "gather probe");
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_part_release_csr(spmv_part* pt) {
+    API_TRY
+    check_part(pt);
+    if (!pt->graphs.empty()) fail(SPMV_EINVAL, "captured graphs exist (they hold the current arrays)");
+    spmvk::release_csr(pt);
     API_CATCH
     return SPMV_OK;
 }

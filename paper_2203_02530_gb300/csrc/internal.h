@@ -142,6 +142,13 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& s, int param, bool del
 cudaError_t launch_sell_delta(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
                               const int32_t* scol, int16_t* scol16, int* bad, int num_sms, cudaStream_t s);
 bool sell_param_supported(int param);
+cudaError_t launch_segment_copy(const int32_t* tab, int n_seg, const double* sv, const int32_t* sc, double* dv,
+                                int32_t* dc, int num_sms, cudaStream_t s);
+cudaError_t launch_sell_unfill(const int32_t* ptr, const SellSlice* slices, int n_slices, const uint8_t* len,
+                               const int32_t* perm, const double* sval, const int32_t* scol, const int16_t* scol16,
+                               int32_t* col, double* val, int num_sms, cudaStream_t s);
+cudaError_t launch_sell_col32(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
+                              const int16_t* scol16, int32_t* scol, int num_sms, cudaStream_t s);
 
 // Index checks (check.cu): count into *bad the indices outside their ranges;
 // read-only, no index is used as an address.
@@ -159,8 +166,6 @@ cudaError_t launch_check_sell(const SellSlice* slices, int n_slices, const uint8
 inline bool sell_param_balanced(int param) { return param >= 2000; }
 // CTAs of a sliced launch of `units` work units.
 int sell_grid(int param, int units, int num_sms);
-// Entries per lane per step of sliced param `param` (0 if unknown).
-int sell_param_entries(int param);
 int tile_ctas_per_sm(const TileGeom& g);
 bool tile_geom_supported(const TileGeom& g);
 TileGeom default_tile_geom();

@@ -127,12 +127,18 @@ struct spmv_part {
         // and grid: key site << 32 | grid
         std::map<int64_t, int32_t*> cta_split;
         int delta_state = 0;              // 0 not checked, 1 built, -1 some delta needs > 16 bits
+        // with the CSR released: the long rows' entries, piece after piece
+        // (the pieces' k0/k1 then index these), and each piece's CSR start
+        double* long_val = nullptr;
+        int32_t* long_col = nullptr;
+        std::vector<int32_t> h_long_csr_k0;
         int64_t entries = 0;              // padded slots
         std::vector<int64_t> slice_off;   // P+1
         std::vector<int64_t> long_off;    // P+1
         std::vector<char> sorted;         // per rank
     } sell[2];
     bool sell_built = false;
+    bool csr_released = false;        // l_col/l_val/r_col/r_val freed (spmv_part_release_csr)
     int64_t sell_entries = 0;         // padded entries, local + remote
 
     // product variant of the LOCAL [0] and REMOTE [1] operations
@@ -175,6 +181,8 @@ void build_warp_tiles(spmv_part* pt, int cap);
 void build_sell(spmv_part* pt);
 bool build_sell_delta16(spmv_part* pt);
 void build_sell_split(spmv_part* pt, int part_idx, int param);
+void release_csr(spmv_part* pt);
+void restore_csr(spmv_part* pt);
 const int32_t* sell_split(const spmv_part* pt, int part_idx, int site, int grid);
 void* dev_alloc(spmv_part* pt, size_t bytes);
 void free_plan(spmv_part* pt);

@@ -501,20 +501,15 @@ void build_sell(spmv_part* pt) {
 // neighbouring slices of the round-robin split together.  A unit's cost is
 // its entries per lane (a slice's longest row; a piece's entries over 32,
 // rounded up) plus 3 for its descriptor, row and store.
-// Estimated time of one work unit of a sliced launch with param `param`,
-// in units of one dependent load-then-gather round: a unit's fixed loads
-// (descriptor, lengths, row map) and store, its rounds (U slots per lane for
-// a slice, whose remainder is one more round; 8 or 4 entries per lane for a
-// long-row piece), and a small per-entry term for the issue of its loads and
-// FMAs.  Long pieces and slices are costed alike, per lane.
-constexpr double SELL_COST_FIXED = 2.0, SELL_COST_ROUND = 2.0, SELL_COST_ENTRY = 0.25;
-
-double sell_unit_cost(int param, bool long_piece, int64_t len) {
-    const int U = sell_param_entries(param);
+// Estimated time of one work unit of a sliced launch: a fixed part (the
+// unit's descriptor, lengths and row-map loads and its stores) plus one per
+// entry of a lane (slots of a slice lane; a long-row piece's entries over
+// 32 lanes).  Measured against costs by dependent rounds (2 + 2 rounds +
+// entries / 4, and 1 + rounds) on the power-law matrix's per-rank launches,
+// this one balanced best.
+double sell_unit_cost(bool long_piece, int64_t len) {
     const int64_t per_lane = long_piece ? (len + 31) / 32 : len;
-    const int step = long_piece ? (U >= 8 ? 8 : 4) : U;
-    const int64_t rounds = (per_lane + step - 1) / step;
-    return SELL_COST_FIXED + SELL_COST_ROUND * (double)rounds + SELL_COST_ENTRY * (double)per_lane;
+    return 3.0 + (double)per_lane;
 }
 
 void build_sell_split(spmv_part* pt, int part_idx, int param) {
@@ -532,7 +527,7 @@ void build_sell_split(spmv_part* pt, int part_idx, int param) {
         for (int u = 0; u < units; ++u) {
             const bool lng = u < le - lb;
             const int64_t len = lng ? sp.h_long_len[(size_t)(lb + u)] : sp.h_slice_len[(size_t)(sb + u - (le - lb))];
-            prefix[(size_t)u + 1] = prefix[(size_t)u] + sell_unit_cost(param, lng, len);
+            prefix[(size_t)u + 1] = prefix[(size_t)u] + sell_unit_cost(lng, len);
         }
         std::vector<int32_t> off((size_t)grid + 1);
         const double total = prefix[(size_t)units];
@@ -551,6 +546,116 @@ const int32_t* sell_split(const spmv_part* pt, int part_idx, int site, int grid)
     const spmv_part::SellPart& sp = pt->sell[part_idx];
     auto it = sp.cta_split.find(((int64_t)site << 32) | grid);
     return it == sp.cta_split.end() ? nullptr : it->second;
+}
+
+// Release of the CSR copy once both products use the sliced layout: each
+// layout's long rows (which the sliced kernel reads from the CSR) move to
+// compact arrays of their own, piece after piece, and the pieces are
+// re-pointed at them; then the CSR columns and values of A_L and A_R are
+// freed, and the 32-bit slot columns of A_L too when its product uses the
+// 16-bit deltas.  Row pointers stay.  restore_csr undoes all of it on the
+// device: slots back into their rows, long rows back, pieces re-pointed.
+void release_csr(spmv_part* pt) {
+    if (pt->csr_released) return;
+    const bool sliced0 = pt->variant[0] == SPMV_VARIANT_SELL || pt->variant[0] == SPMV_VARIANT_SELL16;
+    const bool sliced1 = pt->variant[1] == SPMV_VARIANT_SELL;
+    if (!pt->sell_built || !sliced0 || !sliced1)
+        fail(SPMV_EINVAL, "both products must use the sliced layout before the CSR copy is released");
+    check_cuda(cudaDeviceSynchronize(), "synchronize");
+    const int P = pt->P;
+    for (int i = 0; i < 2; ++i) {
+        spmv_part::SellPart& sp = pt->sell[i];
+        const int nl = (int)sp.long_off[P];
+        std::vector<SellLong> L = download(sp.longs, (size_t)nl);
+        std::vector<int32_t> tab((size_t)3 * nl);
+        sp.h_long_csr_k0.assign((size_t)nl, 0);
+        int64_t c = 0;
+        for (int j = 0; j < nl; ++j) {
+            const int32_t len = L[(size_t)j].k1 - L[(size_t)j].k0;
+            tab[(size_t)3 * j] = L[(size_t)j].k0;
+            tab[(size_t)3 * j + 1] = (int32_t)c;
+            tab[(size_t)3 * j + 2] = len;
+            sp.h_long_csr_k0[(size_t)j] = L[(size_t)j].k0;
+            L[(size_t)j].k0 = (int32_t)c;
+            L[(size_t)j].k1 = (int32_t)(c + len);
+            c += len;
+        }
+        if (nl > 0) {
+            sp.long_val = static_cast<double*>(dev_alloc(pt, (size_t)c * 8));
+            sp.long_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)c * 4));
+            int32_t* d_tab = upload(pt, tab);
+            check_cuda(launch_segment_copy(d_tab, nl, i ? pt->r_val : pt->l_val, i ? pt->r_col : pt->l_col,
+                                           sp.long_val, sp.long_col, pt->num_sms, 0),
+                       "long rows out of the CSR");
+            check_cuda(cudaMemcpy(sp.longs, L.data(), (size_t)nl * sizeof(SellLong), cudaMemcpyHostToDevice),
+                       "long-row pieces");
+            check_cuda(cudaDeviceSynchronize(), "long rows out of the CSR");
+            free_one(pt, d_tab);
+        }
+    }
+    free_one(pt, pt->l_col);
+    free_one(pt, pt->l_val);
+    free_one(pt, pt->r_col);
+    free_one(pt, pt->r_val);
+    pt->l_col = pt->r_col = nullptr;
+    pt->l_val = pt->r_val = nullptr;
+    if (pt->variant[0] == SPMV_VARIANT_SELL16 && pt->sell[0].col16) {
+        free_one(pt, pt->sell[0].col);
+        pt->sell[0].col = nullptr;
+    }
+    pt->csr_released = true;
+}
+
+void restore_csr(spmv_part* pt) {
+    if (!pt->csr_released) return;
+    check_cuda(cudaDeviceSynchronize(), "synchronize");
+    const int P = pt->P;
+    pt->l_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)pt->nnz_l * 4));
+    pt->l_val = static_cast<double*>(dev_alloc(pt, (size_t)pt->nnz_l * 8));
+    pt->r_col = static_cast<int32_t*>(dev_alloc(pt, (size_t)pt->nnz_r * 4));
+    pt->r_val = static_cast<double*>(dev_alloc(pt, (size_t)pt->nnz_r * 8));
+    for (int i = 0; i < 2; ++i) {
+        spmv_part::SellPart& sp = pt->sell[i];
+        int32_t* col = i ? pt->r_col : pt->l_col;
+        double* val = i ? pt->r_val : pt->l_val;
+        check_cuda(launch_sell_unfill(i ? pt->rr_ptr : pt->l_ptr, sp.slices, (int)sp.slice_off[P], sp.len, sp.perm,
+                                      sp.val, sp.col, sp.col16, col, val, pt->num_sms, 0),
+                   "slots back into the CSR");
+        const int nl = (int)sp.long_off[P];
+        if (nl > 0) {
+            std::vector<SellLong> L = download(sp.longs, (size_t)nl);
+            std::vector<int32_t> tab((size_t)3 * nl);
+            for (int j = 0; j < nl; ++j) {
+                const int32_t len = L[(size_t)j].k1 - L[(size_t)j].k0;
+                tab[(size_t)3 * j] = L[(size_t)j].k0;
+                tab[(size_t)3 * j + 1] = sp.h_long_csr_k0[(size_t)j];
+                tab[(size_t)3 * j + 2] = len;
+                L[(size_t)j].k0 = sp.h_long_csr_k0[(size_t)j];
+                L[(size_t)j].k1 = L[(size_t)j].k0 + len;
+            }
+            int32_t* d_tab = upload(pt, tab);
+            check_cuda(launch_segment_copy(d_tab, nl, sp.long_val, sp.long_col, val, col, pt->num_sms, 0),
+                       "long rows back into the CSR");
+            check_cuda(cudaMemcpy(sp.longs, L.data(), (size_t)nl * sizeof(SellLong), cudaMemcpyHostToDevice),
+                       "long-row pieces");
+            check_cuda(cudaDeviceSynchronize(), "long rows back into the CSR");
+            free_one(pt, d_tab);
+            free_one(pt, sp.long_val);
+            free_one(pt, sp.long_col);
+            sp.long_val = nullptr;
+            sp.long_col = nullptr;
+        }
+        sp.h_long_csr_k0.clear();
+    }
+    spmv_part::SellPart& s0 = pt->sell[0];
+    if (!s0.col) {
+        s0.col = static_cast<int32_t*>(dev_alloc(pt, (size_t)s0.entries * 4));
+        check_cuda(launch_sell_col32(s0.slices, (int)s0.slice_off[P], s0.len, s0.perm, s0.col16, s0.col, pt->num_sms,
+                                     0),
+                   "32-bit slot columns");
+    }
+    check_cuda(cudaDeviceSynchronize(), "CSR restored");
+    pt->csr_released = false;
 }
 
 // 16-bit column deltas of the LOCAL sliced layout (built on first use);

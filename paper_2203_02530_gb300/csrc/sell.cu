@@ -170,11 +170,36 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
             const int kb = L.k0, ke = L.k1;
             const double* xb = a.x + L.xoff;
             double part = 0.0;
-            // the lane's entries kb + lane, + 32, ... in rounds of LR (at
-            // most 16 per lane: a piece holds at most 512 entries); the last
-            // round is predicated per entry
-            constexpr int LR = U >= 8 ? 8 : 4;
-            for (int k = kb + lane; k < ke; k += 32 * LR) long_round<LR>(a, xb, k, ke, part, pol_stream, pol_keep);
+            if (U >= 8) {
+                // the lane's entries kb + lane, + 32, ... in rounds of 8 (at
+                // most 16 per lane: a piece holds at most 512 entries); the
+                // last round is predicated per entry
+                for (int k = kb + lane; k < ke; k += 256) long_round<8>(a, xb, k, ke, part, pol_stream, pol_keep);
+            } else {
+                // fewer registers: rounds of 4, then the lane's last 2 and 1
+                int k = kb + lane;
+                for (; k + 96 < ke; k += 128) {
+                    double v[4], xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v[u] = ld_stream(a.val + k + 32 * u, pol_stream);
+                        xv[u] = ld_keep(xb + ld_stream(a.col + k + 32 * u, pol_stream), pol_keep);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) part = fma(v[u], xv[u], part);
+                }
+                if (k + 32 < ke) {
+                    const double v0 = ld_stream(a.val + k, pol_stream), v1 = ld_stream(a.val + k + 32, pol_stream);
+                    const int c0 = ld_stream(a.col + k, pol_stream), c1 = ld_stream(a.col + k + 32, pol_stream);
+                    const double x0 = ld_keep(xb + c0, pol_keep), x1 = ld_keep(xb + c1, pol_keep);
+                    part = fma(v0, x0, part);
+                    part = fma(v1, x1, part);
+                    k += 64;
+                }
+                if (k < ke)
+                    part = fma(ld_stream(a.val + k, pol_stream),
+                               ld_keep(xb + ld_stream(a.col + k, pol_stream), pol_keep), part);
+            }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
             if (lane == 0) {
@@ -299,18 +324,108 @@ cudaError_t launch_sell_fill(const int32_t* ptr, const int32_t* col, const doubl
     return cudaGetLastError();
 }
 
+// Moves of index ranges: segment s (one warp) copies len values and columns
+// from position src of (sv, sc) to position dst of (dv, dc); tab holds
+// (src, dst, len) per segment.  Used to move long rows between the CSR and
+// the compact long-row arrays of a plan whose CSR is released.
+__global__ void __launch_bounds__(256) segment_copy_kernel(const int32_t* __restrict__ tab, int n_seg,
+                                                           const double* __restrict__ sv,
+                                                           const int32_t* __restrict__ sc, double* __restrict__ dv,
+                                                           int32_t* __restrict__ dc) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * 8;
+    for (int g = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); g < n_seg; g += nwarps) {
+        const int src = __ldg(tab + 3 * g), dst = __ldg(tab + 3 * g + 1), len = __ldg(tab + 3 * g + 2);
+        for (int i = lane; i < len; i += 32) {
+            dv[dst + i] = sv[src + i];
+            dc[dst + i] = sc[src + i];
+        }
+    }
+}
+
+// The inverse of sell_fill_kernel: the live slots of every slice back into
+// their CSR rows (ptr of the CSR the layout was filled from).  Columns come
+// from the 32-bit slots, or, when scol is null, from the 16-bit deltas
+// (column = row + delta - xoff, the inverse of sell_delta_kernel).
+__global__ void __launch_bounds__(256) sell_unfill_kernel(const int32_t* __restrict__ ptr,
+                                                          const SellSlice* __restrict__ slices, int n_slices,
+                                                          const uint8_t* __restrict__ lens,
+                                                          const int32_t* __restrict__ perm,
+                                                          const double* __restrict__ sval,
+                                                          const int32_t* __restrict__ scol,
+                                                          const int16_t* __restrict__ scol16,
+                                                          int32_t* __restrict__ col, double* __restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * 8;
+    for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < n_slices; si += nwarps) {
+        const SellSlice d = slices[si];
+        const int pos = d.p0 + lane;
+        const bool live = lane < d.rows && lens[pos] != kSellLenLong;
+        const int row = live ? (perm ? perm[pos] : pos) : 0;
+        const int kb = live ? ptr[row] : 0;
+        const int len = live ? lens[pos] : 0;
+        for (int j = 0; j < len; ++j) {
+            const int64_t o = (int64_t)d.off + 32 * j + lane;
+            val[kb + j] = sval[o];
+            col[kb + j] = scol ? scol[o] : row + (int)scol16[o] - d.xoff;
+        }
+    }
+}
+
+// 32-bit slot columns of a layout from its 16-bit deltas (padding 0, as
+// sell_fill_kernel writes it).
+__global__ void __launch_bounds__(256) sell_col32_kernel(const SellSlice* __restrict__ slices, int n_slices,
+                                                         const uint8_t* __restrict__ lens,
+                                                         const int32_t* __restrict__ perm,
+                                                         const int16_t* __restrict__ scol16,
+                                                         int32_t* __restrict__ scol) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * 8;
+    for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < n_slices; si += nwarps) {
+        const SellSlice d = slices[si];
+        const int pos = d.p0 + lane;
+        const bool live = lane < d.rows && lens[pos] != kSellLenLong;
+        const int row = live ? (perm ? perm[pos] : pos) : 0;
+        const int len = live ? lens[pos] : 0;
+        for (int j = 0; j < d.len; ++j) {
+            const int64_t o = (int64_t)d.off + 32 * j + lane;
+            scol[o] = j < len ? row + (int)scol16[o] - d.xoff : 0;
+        }
+    }
+}
+
+static int warp_grid(int items, int num_sms) {
+    int grid = (items + 7) / 8;
+    if (grid > num_sms * 8) grid = num_sms * 8;
+    return grid;
+}
+
+cudaError_t launch_segment_copy(const int32_t* tab, int n_seg, const double* sv, const int32_t* sc, double* dv,
+                                int32_t* dc, int num_sms, cudaStream_t s) {
+    if (n_seg <= 0) return cudaSuccess;
+    segment_copy_kernel<<<warp_grid(n_seg, num_sms), 256, 0, s>>>(tab, n_seg, sv, sc, dv, dc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_unfill(const int32_t* ptr, const SellSlice* slices, int n_slices, const uint8_t* len,
+                               const int32_t* perm, const double* sval, const int32_t* scol, const int16_t* scol16,
+                               int32_t* col, double* val, int num_sms, cudaStream_t s) {
+    if (n_slices <= 0) return cudaSuccess;
+    sell_unfill_kernel<<<warp_grid(n_slices, num_sms), 256, 0, s>>>(ptr, slices, n_slices, len, perm, sval, scol,
+                                                                    scol16, col, val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_col32(const SellSlice* slices, int n_slices, const uint8_t* len, const int32_t* perm,
+                              const int16_t* scol16, int32_t* scol, int num_sms, cudaStream_t s) {
+    if (n_slices <= 0) return cudaSuccess;
+    sell_col32_kernel<<<warp_grid(n_slices, num_sms), 256, 0, s>>>(slices, n_slices, len, perm, scol16, scol);
+    return cudaGetLastError();
+}
+
 bool sell_param_supported(int param) {
     const int base = param >= 2000 ? param - 2000 : param;
     return base == 4 || base == 8 || base == 9 || (base >= 104 && base <= 107);
-}
-
-int sell_param_entries(int param) {
-    switch (param % 1000) {
-        case 4: case 104: return 4;
-        case 8: case 105: case 106: return 8;
-        case 9: case 107: return 9;
-        default: return 0;
-    }
 }
 
 int sell_grid(int param, int units, int num_sms) {

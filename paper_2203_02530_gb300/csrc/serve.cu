@@ -944,20 +944,18 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
         }
         // launches: one block (or one group of blocks) per free slot, the
         // oldest queue first.  Grouping spreads the blocks the queues would
-        // form over the free slots (ceil(blocks / free slots) per group, at
-        // most group_max): under light load every block gets a slot of its
-        // own (no request waits for another's block), under heavy load the
-        // groups grow and the launches fall
+        // form over all the slots (ceil(blocks / slots) per group, at most
+        // group_max): while no more blocks wait than there are slots, every
+        // block gets a slot of its own (no request waits for another's
+        // block); only a longer queue makes groups, which grow with it, so
+        // that the launches fall when the GPU is the bottleneck
         if (queued > 0) {
             int per_group = 1;
             if (grouped) {
-                int free_slots = 0;
-                for (auto& sl : slot) free_slots += !sl.busy;
                 int64_t pend_blocks = 0;
                 for (int k = 0; k < M; ++k) pend_blocks += (pend_width[k] + kMaxW - 1) / kMaxW;
-                if (free_slots > 0)
-                    per_group = (int)std::min<int64_t>(sv->group_max,
-                                                       std::max<int64_t>(1, (pend_blocks + free_slots - 1) / free_slots));
+                per_group = (int)std::min<int64_t>(
+                    sv->group_max, std::max<int64_t>(1, (pend_blocks + sv->n_streams - 1) / sv->n_streams));
             }
             for (int i = 0; i < sv->n_streams && queued > 0; ++i) {
                 if (slot[i].busy) continue;

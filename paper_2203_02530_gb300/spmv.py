@@ -70,6 +70,7 @@ def _load():
         "spmv_part_op_info": [vp, i32, vp, vp, vp],
         "spmv_part_set_variant": [vp, i32, i32],
         "spmv_part_set_op_variant": [vp, i32, i32, i32],
+        "spmv_part_release_csr": [vp],
         "spmv_pack": [vp, i32, vp, vp],
         "spmv_local": [vp, i32, vp, vp, vp],
         "spmv_halo_copy": [vp, i32, vp],
@@ -192,6 +193,11 @@ def spmv_part_set_variant(h, variant, param=0):
 
 def spmv_part_set_op_variant(h, op_kind, variant, param=0):
     _check(lib.spmv_part_set_op_variant(h, int(op_kind), int(variant), int(param)))
+
+
+def spmv_part_release_csr(h):
+    """Free the plan's CSR copy once both products use the sliced layout."""
+    _check(lib.spmv_part_release_csr(h))
 
 
 def spmv_pack(h, part_idx, x_dev, stream):
@@ -358,6 +364,9 @@ class Part:
 
     def set_op_variant(self, op_kind, variant, param=0):
         spmv_part_set_op_variant(self.h, op_kind, variant, param)
+
+    def release_csr(self):
+        spmv_part_release_csr(self.h)
 
     def run(self, order, stream_of_op, streams, x, y, flags=RUN_EAGER, graph=0):
         return spmv_schedule_run(self.h, order, stream_of_op, streams, x, y, flags, graph)

@@ -582,6 +582,75 @@ def test_relaxed_mode_gives_identical_y(name, gran, variant):
         assert part.query(spmv.Q_ERROR) == 0
 
 
+@pytest.mark.parametrize("name,gran", [("lap64", 0), ("st27_20", 1), ("st27_ragged", 0), ("powerlaw", 1),
+                                       ("powerlaw", 0), ("rand_dup", 1)])
+def test_release_csr_keeps_y_and_restores(name, gran):
+    """spmv_part_release_csr frees the CSR copy once both products are
+    sliced (the long rows move to compact arrays): less device memory, y
+    bit-identical eager and captured; exporting the matrix arrays rebuilds
+    the CSR bit for bit; the index check passes; a CSR variant afterwards
+    still gives the oracle's y; and the call is refused while a product is
+    not sliced or while graphs exist."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    s = torch.cuda.Stream()
+    x_d = dev(x)
+    y_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    mats = (spmv.X_L_COL, spmv.X_L_VAL, spmv.X_R_COL, spmv.X_R_VAL)
+    with make_part(n, rp, ci, va, P, gran) as part:
+        order = [op for k in (0, 1, 2, 3) for op in range(part.n_ops)
+                 if spmv.spmv_part_op_info(part.h, op)[0] == k]
+        smap = [0] * part.n_ops
+
+        def product(flags=spmv.RUN_EAGER):
+            refill(y_d)
+            if flags == spmv.RUN_EAGER:
+                part.run(order, smap, [s], x_d, y_d)
+            else:
+                g = part.run(order, smap, [s], x_d, y_d, flags)
+                part.run(order, smap, [s], x_d, y_d, spmv.RUN_REPLAY, g)
+                s.synchronize()
+                spmv.spmv_graph_destroy(part.h, g)
+            torch.cuda.synchronize()
+            return y_d.cpu().numpy().copy()
+
+        part.set_op_variant(spmv.OP_REMOTE, spmv.VARIANT_SELL, 8)
+        with pytest.raises(spmv.SpmvError) as e:   # LOCAL not sliced yet
+            part.release_csr()
+        assert e.value.code == spmv.EINVAL
+        try:
+            part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL16, 9)
+        except spmv.SpmvError:
+            part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_SELL, 9)
+        y0 = product()
+        assert_fp64_close(y0, want, scale, name)
+        before = {(w, p): part.export(w, p) for w in mats for p in range(P)}
+        bytes0 = part.query(spmv.Q_DEVICE_BYTES)
+        part.release_csr()
+        bytes1 = part.query(spmv.Q_DEVICE_BYTES)
+        # 12 bytes per entry freed, less the compact copy of the long rows
+        assert bytes0 - bytes1 >= 4 * part.query(spmv.Q_NNZ)
+        for flags in (spmv.RUN_EAGER, spmv.RUN_CAPTURE, spmv.RUN_CAPTURE | spmv.RUN_RELAXED):
+            assert np.array_equal(product(flags).view(np.uint64), y0.view(np.uint64)), flags
+        after = {(w, p): part.export(w, p) for w in mats for p in range(P)}   # rebuilds the CSR
+        for k in before:
+            assert before[k].dtype == after[k].dtype and np.array_equal(
+                before[k].view(np.uint8), after[k].view(np.uint8)), k
+        assert part.query(spmv.Q_DEVICE_BYTES) >= bytes0 - 1024
+        assert spmv.spmv_part_check(part.h) == 0
+        assert np.array_equal(product().view(np.uint64), y0.view(np.uint64))
+        part.release_csr()
+        g = part.run(order, smap, [s], x_d, y_d, spmv.RUN_CAPTURE)
+        with pytest.raises(spmv.SpmvError) as e:   # graphs hold the arrays
+            part.release_csr()
+        spmv.spmv_graph_destroy(part.h, g)
+        part.set_op_variant(spmv.OP_LOCAL, spmv.VARIANT_VECTOR, 4)   # needs the CSR: rebuilt
+        assert_fp64_close(product(), want, scale, name + " after restore")
+        assert part.query(spmv.Q_ERROR) == 0
+
+
 def test_invalid_schedules_are_rejected_before_launch():
     from paper_2203_02530_gb300 import spmv
     torch = torch_cuda()
