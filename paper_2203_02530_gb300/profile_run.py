@@ -90,7 +90,8 @@ def main(argv=None):
     ap.add_argument("--op", choices=["local", "remote"], default="local")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--rank", type=int, default=-1,
-                    help="launch the operation of this rank only (-1: one launch over all ranks)")
+                    help="launch the operation of this rank only (-1: one launch over all ranks; -2: one "
+                         "launch per rank, rank after rank, as a per-rank schedule runs them)")
     ap.add_argument("--cache-dir", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build"),
                     help="where the generated power-law matrix is cached (default: the package's "
                          "ignored build folder)")
@@ -112,11 +113,13 @@ def main(argv=None):
     s = torch.cuda.Stream()
     spmv.spmv_pack(part.h, -1, x_d, s)
     spmv.spmv_halo_copy(part.h, -1, s)
+    ranks = list(range(P)) if args.rank == -2 else [args.rank]
     for _ in range(args.launches):
-        if kind == spmv.OP_LOCAL:
-            spmv.spmv_local(part.h, args.rank, x_d, y_d, s)
-        else:
-            spmv.spmv_remote(part.h, args.rank, y_d, s)
+        for r in ranks:
+            if kind == spmv.OP_LOCAL:
+                spmv.spmv_local(part.h, r, x_d, y_d, s)
+            else:
+                spmv.spmv_remote(part.h, r, y_d, s)
     s.synchronize()
     err = part.query(spmv.Q_ERROR)
     part.close()
