@@ -545,6 +545,29 @@ def run_ours(args, world, rank, local, fp64=None):
     for _ in range(k_e2e):
         spmv.spmv_apply_host_pipelined(part.h, xh, yh, cs, streams[0])
     t_e2e = max_over_ranks(dist, (time.perf_counter() - t0) / k_e2e, dev)
+    # where the end-to-end time goes: the host link alone, each direction and
+    # both at once (x in on one stream while y goes out on another)
+    xb_d = torch.empty(n, dtype=torch.float64, device=dev)
+    yb_d = torch.empty(n, dtype=torch.float64, device=dev)
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def link(which):
+        if which in ("in", "both"):
+            with torch.cuda.stream(s_in):
+                xb_d.copy_(xh, non_blocking=True)
+        if which in ("out", "both"):
+            with torch.cuda.stream(s_out):
+                yh.copy_(yb_d, non_blocking=True)
+        s_in.synchronize()
+        s_out.synchronize()
+
+    link_us = {}
+    for which in ("in", "out", "both"):
+        link(which)
+        t0 = time.perf_counter()
+        for _ in range(20):
+            link(which)
+        link_us[which] = round((time.perf_counter() - t0) / 20 * 1e6, 1)
     err = part.query(spmv.Q_ERROR)
     dev_bytes = part.query(spmv.Q_DEVICE_BYTES)
 
@@ -612,7 +635,12 @@ def run_ours(args, world, rank, local, fp64=None):
                 "paths": {"spmv_apply_host_pipelined": {"value": round(alg / t_e2e / 1e9, 2),
                                                         "ms_per_step": round(t_e2e * 1e3, 4)},
                           "spmv_apply_host": {"value": round(alg / t_e2e_graph / 1e9, 2),
-                                              "ms_per_step": round(t_e2e_graph * 1e3, 4)}}},
+                                              "ms_per_step": round(t_e2e_graph * 1e3, 4)}},
+                "breakdown_us": {"x_in_alone": link_us["in"], "y_out_alone": link_us["out"],
+                                 "in_and_out_together": link_us["both"],
+                                 "device_step": round(elapsed / args.steps * 1e6, 1),
+                                 "note": "host-timed pinned copies of x (in) and y (out), %d bytes each; the "
+                                         "pipelined path overlaps both with the products" % (8 * n)}},
         "cpu_baseline": cpu,
         "clocks": clocks, "remeasured": remeasured,
         "gpu_launches": launches_per_step * args.steps,
