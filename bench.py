@@ -722,6 +722,9 @@ def run_batched(args, world, rank, local):
     mrl = [(int(m[1][-1]) / m[0]) if m[0] else 0.0 for m in mats]
     tune_log = []
     lanes = autotune.tune_batch(b, x_d, y_b, s, mean_row_lengths=mrl, log=tune_log)
+    batch_bytes_tuned = b.query(spmv.BQ_DEVICE_BYTES)
+    if all(l == spmv.BATCH_SLICED for l in lanes):   # no product reads the CSR copy any more
+        spmv.spmv_batch_release_csr(b.h)
     alg = b.query(spmv.BQ_ALG_BYTES)
     batched = lambda: spmv.spmv_batch_run(b.h, x_d, y_b, s)
     separate = lambda: spmv.spmv_batch_run_separate(b.h, -1, x_d, y_s, s)
@@ -829,7 +832,8 @@ def run_batched(args, world, rank, local):
                                "5-point / 7-point / Zipf-row (mean ~10) matrices, one persistent launch",
                    "matrices": len(mats), "total_rows": total, "nnz": nnz,
                    "lanes_histogram": {str(v): lanes.count(v) for v in sorted(set(lanes))},
-                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg, "batch_device_bytes": dev_bytes},
+                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg, "batch_device_bytes": dev_bytes,
+                   "batch_device_bytes_before_csr_release": batch_bytes_tuned},
         "percent_hbm": round(100.0 * value / world / peak, 2),
         "plain": {"form": "each matrix through the library's single-matrix product (P=1 plan, LOCAL "
                           "variant tuned per matrix), 256 launches captured in one CUDA graph",
@@ -876,6 +880,8 @@ def run_serving(args, world, rank, local, fp64=None):
     b = spmv.Batch(mats)
     if args.serve_layout == "sliced":
         spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        spmv.spmv_batch_release_csr(b.h)   # the sliced products read only the long rows of the CSR
+    resident = b.query(spmv.BQ_DEVICE_BYTES)
     sv = spmv.Server(b, n_streams=args.serve_streams, budget_bytes=40 << 30)
     rate = args.serve_rate
     arr = W.poisson_arrivals(rate, args.serve_seconds, seed=7)
@@ -972,7 +978,8 @@ def run_serving(args, world, rank, local, fp64=None):
                                    rate, args.serve_seconds, count, total / 1e9, args.serve_streams,
                                    args.serve_layout),
                    "value": "saturation throughput of the served form (all requests present at t=0; a "
-                            "step is one request), per-request algorithmic bytes"},
+                            "step is one request), per-request algorithmic bytes",
+                   "resident_device_bytes": resident},
         "open_loop": out, "open_loop_high": high, "saturation": sat,
         "served_vs_plain_saturation": round(sat["served"]["gbs"] / sat["plain"]["gbs"], 3),
         "results_identical_served_vs_plain": same,

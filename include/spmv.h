@@ -437,6 +437,16 @@ int spmv_batch_run(spmv_batch* batch, const double* x_dev, double* y_dev, cudaSt
  * arrived.  Uses batch-owned device vectors (allocated on first use). */
 int spmv_batch_run_host(spmv_batch* batch, const double* x_host, double* y_host, int chunks,
                         cudaStream_t s_in, cudaStream_t s_compute, cudaStream_t s_out);
+/* Release the batch's CSR copy once every matrix uses the sliced layout
+ * (SPMV_BATCH_SLICED), which is a second copy of every entry: only the rows
+ * longer than 64 entries (which the sliced products, batched and served,
+ * read from the CSR) stay, in compact arrays.  Results are unchanged, bit for
+ * bit.  Setting any matrix to a non-sliced layout afterwards first rebuilds the
+ * full CSR on the device (from the sliced layout and the kept long rows).  A
+ * server created while the CSR is released serves the sliced layout only.
+ * Synchronises.  SPMV_EINVAL while a matrix is not sliced; a no-op if already
+ * released.  SPMV_BQ_DEVICE_BYTES reports the memory held. */
+int spmv_batch_release_csr(spmv_batch* batch);
 /* The same products as one launch per matrix (only matrix m if m >= 0). */
 int spmv_batch_run_separate(spmv_batch* batch, int m, const double* x_dev, double* y_dev,
                             cudaStream_t s);

@@ -423,6 +423,47 @@ __global__ void __launch_bounds__(256) batch_slice_fill_kernel(const int32_t* __
     }
 }
 
+// The inverse of batch_slice_fill_kernel: the live slots of every slice of
+// one matrix back into its CSR rows (ptr: the matrix's full row pointers).
+__global__ void __launch_bounds__(256) batch_slice_unfill_kernel(const int32_t* __restrict__ ptr, BatchMat m,
+                                                                 const double* __restrict__ s_val,
+                                                                 const int32_t* __restrict__ s_col,
+                                                                 int32_t* __restrict__ col, double* __restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)gridDim.x * 8;
+    for (int si = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); si < m.n_slices; si += nw) {
+        const BSlice d = m.s_slices[si];
+        const int pos = d.pos0 + lane;
+        const bool live = lane < d.rows;
+        const int row = live ? (m.s_perm ? m.s_perm[pos] : pos) : 0;
+        const int kb = live ? ptr[row] : 0;
+        const int len = live ? (int)m.s_len[pos] : 0;
+        for (int j = 0; j < len; ++j) {
+            const int64_t o = (int64_t)d.off + 32 * j + lane;
+            val[kb + j] = s_val[o];
+            col[kb + j] = s_col[o];
+        }
+    }
+}
+
+// Moves of entry ranges between two CSR arrays: segment s (one warp) copies
+// tab[3s + 2] entries from position tab[3s] of (sv, sc) to tab[3s + 1] of
+// (dv, dc) (64-bit positions).
+__global__ void __launch_bounds__(256) batch_segment_copy_kernel(const int64_t* __restrict__ tab, int64_t n_seg,
+                                                                 const double* __restrict__ sv,
+                                                                 const int32_t* __restrict__ sc,
+                                                                 double* __restrict__ dv, int32_t* __restrict__ dc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t g = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); g < n_seg; g += nw) {
+        const int64_t src = tab[3 * g], dst = tab[3 * g + 1], len = tab[3 * g + 2];
+        for (int64_t i = lane; i < len; i += 32) {
+            dv[dst + i] = sv[src + i];
+            dc[dst + i] = sc[src + i];
+        }
+    }
+}
+
 // Persistent: every warp claims whole items (order[0 .. n_items)) with an
 // atomic ticket until none is left (no block-wide barrier: warps never wait
 // for each other).  One kernel for the CSR modes (shared-memory slices for
@@ -659,6 +700,126 @@ void build_sliced(spmv_batch* b, int m) {
     b->sliced_built[m] = 1;
 }
 
+template <class T>
+std::vector<T> bdownload(const T* d, size_t count) {
+    std::vector<T> h(count);
+    if (count) spmvk::check_cuda(cudaMemcpy(h.data(), d, count * sizeof(T), cudaMemcpyDeviceToHost), "download");
+    return h;
+}
+
+void run_segment_copy(spmv_batch* b, const std::vector<int64_t>& tab, const double* sv, const int32_t* sc, double* dv,
+                      int32_t* dc) {
+    const int64_t n_seg = (int64_t)tab.size() / 3;
+    if (n_seg == 0) return;
+    int64_t* d_tab = static_cast<int64_t*>(balloc(b, tab.size() * sizeof(int64_t)));
+    spmvk::check_cuda(cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "segments");
+    const int64_t grid = std::min<int64_t>((n_seg + 7) / 8, (int64_t)b->num_sms * 8);
+    batch_segment_copy_kernel<<<(unsigned)grid, 256>>>(d_tab, n_seg, sv, sc, dv, dc);
+    spmvk::check_cuda(cudaGetLastError(), "segment copy");
+    spmvk::check_cuda(cudaDeviceSynchronize(), "segment copy");
+    brelease(b, d_tab, tab.size() * sizeof(int64_t));
+}
+
+// Release of the CSR copy of a batch whose matrices all use the sliced
+// layout: only the rows longer than kLongRow (which the sliced products read
+// from the CSR) stay, in compact arrays whose row pointers give every other
+// row zero length, so every reader of a long row finds it where it looks.
+void batch_release_csr(spmv_batch* b) {
+    if (b->csr_released) return;
+    for (int m = 0; m < b->count; ++m)
+        if (b->mats[m].lanes != kSliced || !b->sliced_built[m])
+            spmvk::fail(SPMV_EINVAL, "matrix %d does not use the sliced layout: the CSR copy is still read", m);
+    spmvk::check_cuda(cudaDeviceSynchronize(), "synchronize");
+    const size_t ptr_total = (size_t)(b->mats.back().ptr_off + b->n.back() + 1);
+    b->h_full_ptr = bdownload(b->ptr, ptr_total);
+    b->full_ent_off.resize(b->count);
+    std::vector<int32_t> cptr(ptr_total, 0);
+    std::vector<long long> ent_off(b->count);
+    std::vector<int64_t> tab;
+    long long ent = 0;
+    for (int m = 0; m < b->count; ++m) {
+        const BatchMat& M = b->mats[m];
+        b->full_ent_off[m] = M.ent_off;
+        const int32_t* fp = b->h_full_ptr.data() + M.ptr_off;
+        int32_t* cp = cptr.data() + M.ptr_off;
+        for (int i = 0; i < M.n; ++i) {
+            const int32_t len = fp[i + 1] - fp[i];
+            const bool keep = len > kLongRow;
+            cp[i + 1] = cp[i] + (keep ? len : 0);
+            if (keep) {
+                tab.push_back(M.ent_off + fp[i]);
+                tab.push_back(ent + cp[i]);
+                tab.push_back(len);
+            }
+        }
+        ent_off[m] = ent;
+        ent += ((long long)cp[M.n] + 3) & ~3LL;
+    }
+    b->full_entries = b->full_ent_off.back() + ((b->nnz.back() + 3) & ~int64_t(3));
+    int32_t* nptr = static_cast<int32_t*>(balloc(b, ptr_total * 4));
+    int32_t* ncol = static_cast<int32_t*>(balloc(b, (size_t)std::max<long long>(ent, 4) * 4));
+    double* nval = static_cast<double*>(balloc(b, (size_t)std::max<long long>(ent, 4) * 8));
+    spmvk::check_cuda(cudaMemcpy(nptr, cptr.data(), ptr_total * 4, cudaMemcpyHostToDevice), "row pointers");
+    run_segment_copy(b, tab, b->val, b->col, nval, ncol);
+    brelease(b, b->ptr, ptr_total * 4);
+    brelease(b, b->col, (size_t)b->full_entries * 4);
+    brelease(b, b->val, (size_t)b->full_entries * 8);
+    b->ptr = nptr;
+    b->col = ncol;
+    b->val = nval;
+    for (int m = 0; m < b->count; ++m) b->mats[m].ent_off = ent_off[m];
+    spmvk::check_cuda(cudaMemcpy(b->d_mats, b->mats.data(), b->mats.size() * sizeof(BatchMat), cudaMemcpyHostToDevice),
+                      "matrix table");
+    b->csr_released = true;
+}
+
+// The rebuild: full arrays again, the slices' slots back into their rows and
+// the long rows copied back from the compact arrays.
+void batch_restore_csr(spmv_batch* b) {
+    if (!b->csr_released) return;
+    spmvk::check_cuda(cudaDeviceSynchronize(), "synchronize");
+    const size_t ptr_total = b->h_full_ptr.size();
+    const std::vector<int32_t> cptr = bdownload(b->ptr, ptr_total);
+    int32_t* fptr = static_cast<int32_t*>(balloc(b, ptr_total * 4));
+    int32_t* fcol = static_cast<int32_t*>(balloc(b, (size_t)b->full_entries * 4));
+    double* fval = static_cast<double*>(balloc(b, (size_t)b->full_entries * 8));
+    spmvk::check_cuda(cudaMemcpy(fptr, b->h_full_ptr.data(), ptr_total * 4, cudaMemcpyHostToDevice), "row pointers");
+    std::vector<int64_t> tab;
+    for (int m = 0; m < b->count; ++m) {
+        const BatchMat& M = b->mats[m];
+        if (M.n_slices > 0) {
+            int grid = (M.n_slices + 7) / 8;
+            if (grid > b->num_sms * 8) grid = b->num_sms * 8;
+            batch_slice_unfill_kernel<<<grid, 256>>>(fptr + M.ptr_off, M, M.s_val, M.s_col, fcol + b->full_ent_off[m],
+                                                     fval + b->full_ent_off[m]);
+            spmvk::check_cuda(cudaGetLastError(), "slots back into the CSR");
+        }
+        const int32_t* fp = b->h_full_ptr.data() + M.ptr_off;
+        const int32_t* cp = cptr.data() + M.ptr_off;
+        for (int i = 0; i < M.n; ++i)
+            if (cp[i + 1] > cp[i]) {
+                tab.push_back(M.ent_off + cp[i]);
+                tab.push_back(b->full_ent_off[m] + fp[i]);
+                tab.push_back(cp[i + 1] - cp[i]);
+            }
+    }
+    spmvk::check_cuda(cudaDeviceSynchronize(), "slots back into the CSR");
+    run_segment_copy(b, tab, b->val, b->col, fval, fcol);
+    const long long ent = b->mats.back().ent_off + (((long long)cptr[(size_t)(b->mats.back().ptr_off + b->n.back())] + 3) & ~3LL);
+    brelease(b, b->ptr, ptr_total * 4);
+    brelease(b, b->col, (size_t)std::max<long long>(ent, 4) * 4);
+    brelease(b, b->val, (size_t)std::max<long long>(ent, 4) * 8);
+    b->ptr = fptr;
+    b->col = fcol;
+    b->val = fval;
+    for (int m = 0; m < b->count; ++m) b->mats[m].ent_off = b->full_ent_off[m];
+    spmvk::check_cuda(cudaMemcpy(b->d_mats, b->mats.data(), b->mats.size() * sizeof(BatchMat), cudaMemcpyHostToDevice),
+                      "matrix table");
+    b->h_full_ptr.clear();
+    b->full_ent_off.clear();
+    b->csr_released = false;
+}
+
 BatchArgs args_of(spmv_batch* b, const double* x, double* y) {
     BatchArgs a{};
     a.ptr = b->ptr;
@@ -799,6 +960,7 @@ int spmv_batch_set_lanes(spmv_batch* b, int m, int lanes) {
         lanes != kSliced)
         spmvk::fail(SPMV_EINVAL, "lanes %d not in {0,1,2,4,8,16,32,64}", lanes);
     spmvk::check_cuda(cudaDeviceSynchronize(), "synchronize");   // no launch may read the tables
+    if (lanes != kSliced) batch_restore_csr(b);                    // the CSR modes read every row
     const int lo = m < 0 ? 0 : m, hi = m < 0 ? b->count : m + 1;
     bool changed = false;
     for (int i = lo; i < hi; ++i) {
@@ -957,6 +1119,14 @@ int spmv_batch_run_host(spmv_batch* b, const double* x_host, double* y_host, int
                               "copy y out");
     }
     spmvk::check_cuda(cudaStreamSynchronize(s_out), "synchronize");
+    BATCH_CATCH
+    return SPMV_OK;
+}
+
+int spmv_batch_release_csr(spmv_batch* b) {
+    BATCH_TRY
+    if (!b) spmvk::fail(SPMV_EINVAL, "batch is NULL");
+    batch_release_csr(b);
     BATCH_CATCH
     return SPMV_OK;
 }

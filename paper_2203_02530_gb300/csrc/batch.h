@@ -72,4 +72,11 @@ struct spmv_batch {
     int n_items = 0;
     size_t device_bytes = 0;
     std::vector<void*> allocs;
+    // CSR released (spmv_batch_release_csr): ptr/col/val then hold only the
+    // long rows (shorter rows have zero length); the full row pointers and
+    // entry offsets are kept on the host for the rebuild
+    bool csr_released = false;
+    std::vector<int32_t> h_full_ptr;
+    std::vector<long long> full_ent_off;
+    long long full_entries = 0;
 };

@@ -89,6 +89,7 @@ def _load():
         "spmv_batch_query": [vp, i32, i32, P64],
         "spmv_batch_run": [vp, vp, vp, vp],
         "spmv_batch_run_separate": [vp, i32, vp, vp, vp],
+        "spmv_batch_release_csr": [vp],
         "spmv_batch_run_host": [vp, vp, vp, i32, vp, vp, vp],
         "spmv_serve_create": [vp, i32, i64, ctypes.POINTER(vp)],
         "spmv_serve_destroy": [vp],
@@ -414,6 +415,11 @@ def spmv_batch_run(h, x_dev, y_dev, stream):
 def spmv_batch_run_host(h, x_host, y_host, chunks, s_in, s_compute, s_out):
     _check(lib.spmv_batch_run_host(h, _ptr(x_host), _ptr(y_host), int(chunks), _stream(s_in),
                                    _stream(s_compute), _stream(s_out)))
+
+
+def spmv_batch_release_csr(h):
+    """Keep only the long rows of the batch's CSR once every matrix is sliced."""
+    _check(lib.spmv_batch_release_csr(h))
 
 
 def spmv_batch_run_separate(h, m, x_dev, y_dev, stream):

@@ -180,3 +180,71 @@ def test_full_size_batch_mix_256_sliced():
         yh = torch.full((offs[-1],), float("nan"), dtype=torch.float64).pin_memory()
         spmv.spmv_batch_run_host(b.h, xh, yh, 16, s_in, s, s_out)
         assert np.array_equal(yh.numpy(), a1)
+
+
+def test_batch_release_csr_keeps_y_and_restores():
+    """spmv_batch_release_csr keeps only the rows longer than 64 of the CSR
+    once every matrix is sliced: less device memory; the batched, per-matrix
+    and host-buffer products and a served request give the same results bit
+    for bit; a CSR layout afterwards rebuilds the full CSR (results within the
+    oracle's bound); back in the sliced layout the results match again; and
+    the release is refused while a matrix is not sliced."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = _mix()
+    with spmv.Batch(mats) as b:
+        offs = b.offsets()
+        spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        spmv.spmv_batch_set_lanes(b.h, 0, 2)
+        with pytest.raises(spmv.SpmvError) as e:
+            spmv.spmv_batch_release_csr(b.h)
+        assert e.value.code == spmv.EINVAL
+        spmv.spmv_batch_set_lanes(b.h, 0, spmv.BATCH_SLICED)
+        x = W.uniform_x(offs[-1], seed=19)
+        want, scale = _oracle(mats, x, offs)
+        s, s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        x_d = dev(x)
+        y = synced(torch.full((offs[-1],), float("nan"), dtype=torch.float64, device="cuda"))
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty(offs[-1], dtype=torch.float64).pin_memory()
+        sv = spmv.Server(b, n_streams=2, budget_bytes=1 << 30)
+        big = max(range(b.count), key=lambda m: mats[m][0])
+        n_big = mats[big][0]
+        yq = synced(torch.zeros(n_big * 3, dtype=torch.float64, device="cuda"))
+        xq = synced(torch.zeros(n_big * 3, dtype=torch.float64, device="cuda"))
+
+        def results():
+            out = []
+            refill(y)
+            spmv.spmv_batch_run(b.h, x_d, y, s)
+            s.synchronize()
+            out.append(y.cpu().numpy().copy())
+            refill(y)
+            spmv.spmv_batch_run_separate(b.h, -1, x_d, y, s)
+            s.synchronize()
+            out.append(y.cpu().numpy().copy())
+            yh.fill_(float("nan"))
+            spmv.spmv_batch_run_host(b.h, xh, yh, 3, s_in, s, s_out)
+            out.append(yh.numpy().copy())
+            spmv.spmv_serve_single(sv.h, big, 3, 12345, yq, xq, s)
+            s.synchronize()
+            out.append(yq.cpu().numpy().copy())
+            return out
+
+        before = results()
+        assert_fp64_close(before[0], want, scale, "sliced batch")
+        bytes0 = b.query(spmv.BQ_DEVICE_BYTES)
+        spmv.spmv_batch_release_csr(b.h)
+        assert b.query(spmv.BQ_DEVICE_BYTES) < bytes0
+        for a, c in zip(before, results()):
+            assert np.array_equal(a.view(np.uint64), c.view(np.uint64))
+        spmv.spmv_batch_set_lanes(b.h, -1, 2)      # a CSR layout: the full CSR is rebuilt
+        refill(y)
+        spmv.spmv_batch_run(b.h, x_d, y, s)
+        s.synchronize()
+        assert_fp64_close(y.cpu().numpy(), want, scale, "CSR layout after the rebuild")
+        spmv.spmv_batch_set_lanes(b.h, -1, spmv.BATCH_SLICED)
+        assert np.array_equal(results()[0].view(np.uint64), before[0].view(np.uint64))
+        spmv.spmv_batch_release_csr(b.h)
+        assert np.array_equal(results()[0].view(np.uint64), before[0].view(np.uint64))
+        sv.close()
