@@ -56,6 +56,7 @@ struct spmv_batch {
     std::vector<int> order;              // claim order of the persistent launch
     std::vector<char> sliced_built;      // per matrix
     int* d_order = nullptr;
+    int* d_order_full = nullptr;         // claim order of a whole-batch launch (sliced items interleaved)
     size_t items_cap = 0;                // capacity of d_items / d_order (items)
     long long total_rows = 0, total_nnz = 0;
     int32_t* ptr = nullptr;
