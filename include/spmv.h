@@ -527,7 +527,8 @@ int spmv_serve_single(spmv_server* server, int matrix, int width, uint64_t seed,
  * naming a row of q, the per-rank pack positions inside the send buffer,
  * row pointers ascending from 0 to the entry count, and, once built, every
  * live slot of the sliced layouts (and of the 16-bit deltas) inside x or the
- * receive buffer, with each long-row piece inside its row.  No index is used
+ * receive buffer, with each long-row piece inside its row, and the y row the
+ * remote layout stores for each of rank p's positions inside p's rows.  No index is used
  * to address memory, so a damaged plan is reported, not dereferenced.  0 for
  * every plan this library builds.  Synchronises. */
 int spmv_part_check(spmv_part* part, int64_t* bad_out);

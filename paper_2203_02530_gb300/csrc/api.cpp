@@ -178,6 +178,7 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         const spmv_part::SellPart& sp = pt->sell[remote ? 1 : 0];
         spmvk::SellArgs sa{sp.slices, sp.longs, sp.val,  sp.col,         sp.col16,     sp.len, sp.perm,
                            0,         0,        0,       0,       sp.long_part, sp.long_cnt, nullptr};
+        sa.ypos = sp.ypos;
         sa.slice_begin = (int)(p < 0 ? 0 : sp.slice_off[p]);
         sa.slice_end = (int)(p < 0 ? sp.slice_off[pt->P] : sp.slice_off[p + 1]);
         sa.long_begin = (int)(p < 0 ? 0 : sp.long_off[p]);
@@ -1110,6 +1111,10 @@ int spmv_part_check(spmv_part* pt, int64_t* bad_out) {
                     r = spmvk::launch_check_sell(sp.slices, (int)sp.slice_off[P], sp.len, sp.perm, nullptr,
                                                  sp.col16, sp.entries, npos, 0, xhi, sp.longs, 0, cptr, d_bad,
                                                  sms, 0);
+                // the composed y rows of rank p's remote positions are p's rows
+                if (r == cudaSuccess && sp.ypos)
+                    r = spmvk::launch_check_list(sp.ypos, pt->n_rr, d_tab + t_rr, P, d_tab + t_blo, d_tab + t_bhi,
+                                                 d_bad, sms, 0);
             }
         }
         unsigned long long h = 0;

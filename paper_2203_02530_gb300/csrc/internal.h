@@ -85,6 +85,8 @@ struct SellArgs {
     int* long_cnt;           // per cut row: pieces done (zero between launches)
     const int32_t* cta_off;  // nullptr: units round-robin over the warps; else
                              // CTA b takes units [cta_off[b], cta_off[b + 1])
+    const int32_t* ypos;     // per position: its y row (row order and row map
+                             // composed; sorted remote layouts), or nullptr
 };
 
 // Operands of one CSR product launch.

@@ -118,6 +118,7 @@ struct spmv_part {
         int32_t* col = nullptr;
         uint8_t* len = nullptr;
         int32_t* perm = nullptr;          // nullptr: every rank in natural order
+        int32_t* ypos = nullptr;          // REMOTE, sorted: y row of each position (perm, then the row map)
         int16_t* col16 = nullptr;         // column - row deltas (LOCAL only), once built
         double* long_part = nullptr;      // partial sums of cut long rows
         int* long_cnt = nullptr;          // pieces done per cut long row

@@ -488,6 +488,17 @@ void build_sell(spmv_part* pt) {
     for (int p = 0; p < P; ++p) lxo[p] = (int32_t)pt->bounds[p];
     pt->sell[0].entries = build_sell_part(pt, pt->sell[0], l_ptr, pt->bounds, lxo, pt->l_ptr, pt->l_col, pt->l_val);
     pt->sell[1].entries = build_sell_part(pt, pt->sell[1], rr_ptr, pt->rr_off, rxo, pt->rr_ptr, pt->r_col, pt->r_val);
+    // the remote product's y row of each position in one table, so that a
+    // sorted slice's store reads one coalesced index instead of its row and
+    // then the scattered row map
+    spmv_part::SellPart& sr = pt->sell[1];
+    if (sr.perm) {
+        const std::vector<int32_t> rr_row = download(pt->rr_row, (size_t)pt->n_rr);
+        const std::vector<int32_t> perm = download(sr.perm, (size_t)pt->n_rr);
+        std::vector<int32_t> ypos((size_t)pt->n_rr);
+        for (size_t q = 0; q < ypos.size(); ++q) ypos[q] = rr_row[(size_t)perm[q]];
+        sr.ypos = upload(pt, ypos);
+    }
     check_cuda(cudaDeviceSynchronize(), "sliced layout");
     pt->sell_entries = pt->sell[0].entries + pt->sell[1].entries;
     pt->sell_built = true;

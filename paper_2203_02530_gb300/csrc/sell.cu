@@ -148,7 +148,8 @@ __device__ __forceinline__ void long_round(const CsrArgs& a, const double* xb, i
 // CT = int32_t: slot columns are the CSR's (x index = xoff + column);
 // CT = int16_t: slot columns are deltas to the row (x index = row + delta),
 // half the index bytes where every |column - row| fits in 16 bits.
-template <int U, int MINB, typename CT>
+// YP: the layout has a y row per position (sa.ypos; sorted remote layouts).
+template <int U, int MINB, typename CT, bool YP = false>
 __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs sa) {
     pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
     constexpr bool kDelta = sizeof(CT) == 2;
@@ -234,7 +235,13 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
         const CT* cp = (kDelta ? reinterpret_cast<const CT*>(sa.col16) : reinterpret_cast<const CT*>(sa.col)) +
                        (int64_t)d.off + lane;
         int row = lane < d.rows ? pos : d.p0;   // lanes past the slice's rows gather x[p0] (padding)
-        if (sa.perm && lane < d.rows) row = __ldg(sa.perm + pos);
+        // with YP, `row` is the y row itself (row order and row map
+        // composed), loaded here so that its latency hides behind the rounds
+        if (YP) {
+            if (lane < d.rows) row = __ldg(sa.ypos + pos);
+        } else if (sa.perm && lane < d.rows) {
+            row = __ldg(sa.perm + pos);
+        }
         const double* xb = kDelta ? a.x + row : a.x + d.xoff;
         double sum = 0.0;
         int j = 0;
@@ -244,7 +251,10 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
         // latency, so the short slices of skewed rows (3 entries, say) keep
         // all their gathers in flight at once
         sell_tail<U>(d.len - j, cp, vp, xb, j, len, sum, pol_stream, pol_keep);
-        if (store) sell_store(a, row, sum);
+        if (store) {
+            if (YP) a.y[row] = a.accumulate ? a.y[row] + sum : sum;
+            else sell_store(a, row, sum);
+        }
     }
 }
 
@@ -453,9 +463,10 @@ cudaError_t launch_sell(const CsrArgs& a, const SellArgs& sa, int param, bool de
     const int grid = sell_grid(param, units, num_sms);
     if (grid <= 0) return cudaErrorInvalidValue;
     if (sell_param_balanced(param) != (sa.cta_off != nullptr)) return cudaErrorInvalidValue;
-#define SELL_LAUNCH(u, b)                                                                   \
-    e = delta16 ? launch_pdl(csr_sell_kernel<u, b, int16_t>, dim3(grid), dim3(256), 0, st, a, sa) \
-                : launch_pdl(csr_sell_kernel<u, b, int32_t>, dim3(grid), dim3(256), 0, st, a, sa)
+#define SELL_LAUNCH(u, b)                                                                        \
+    e = delta16 ? launch_pdl(csr_sell_kernel<u, b, int16_t>, dim3(grid), dim3(256), 0, st, a, sa)      \
+        : sa.ypos ? launch_pdl(csr_sell_kernel<u, b, int32_t, true>, dim3(grid), dim3(256), 0, st, a, sa) \
+                  : launch_pdl(csr_sell_kernel<u, b, int32_t>, dim3(grid), dim3(256), 0, st, a, sa)
     cudaError_t e = cudaSuccess;
     switch (param % 1000) {
         case 4: SELL_LAUNCH(4, 8); break;
