@@ -705,6 +705,8 @@ void build_sliced(spmv_batch* b, int m) {
     M.s_perm = s_perm;
     M.s_slices = s_sl;
     M.n_long = n_long;
+    M.n_vlong = 0;   // long rows come longest first
+    while (M.n_vlong < n_long && L(M.n_vlong) > 2048) ++M.n_vlong;
     M.n_slices = (int)sl.size();
     if (!sl.empty()) {
         int grid = ((int)sl.size() + 7) / 8;
@@ -925,6 +927,7 @@ int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr
         b->n[m] = n[m];
         b->nnz[m] = z;
         b->mats[m] = BatchMat{ptr_total, ent_total, rows_total, (int)n[m], 2};
+        b->mats[m].n_vlong = 0;
         ptr_total += n[m] + 1;
         ent_total += (z + 3) & ~int64_t(3);   // keep every matrix 16-byte aligned
         rows_total += n[m];

@@ -33,6 +33,9 @@ struct BatchMat {
     const BSlice* s_slices;
     int n_long;
     int n_slices;
+    int n_vlong;   // of the long rows, the first n_vlong are longer than 2048
+                   // entries (served by a whole CTA each)
+    int pad;
 };
 
 // Work item: kind 0 = rows [a, b) in CSR form; kind 1 = positions [a, b)

@@ -365,6 +365,86 @@ __device__ __forceinline__ void long_unit(const int32_t* __restrict__ ptr, const
     }
 }
 
+// A long row of more than 2048 entries by the whole CTA: thread t takes
+// entries t, t+256, ... in order (four in flight), W accumulators each, a
+// fixed xor-butterfly in each warp, then the eight warps' sums added in warp
+// order through shared memory; thread 0 stores the row.  All threads of the
+// CTA call it for the same row.
+template <int W>
+__device__ __forceinline__ void long_cta_unit(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                              const double* __restrict__ val, const BatchMat& m, int pos,
+                                              const double* __restrict__ X, double* __restrict__ Y,
+                                              const BlockReq* req, int n_req, unsigned long long* hashes,
+                                              unsigned long long (&h)[kMaxW]) {
+    __shared__ double s_part[kThreads / 32][kMaxW];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int row = m.s_perm ? __ldg(m.s_perm + pos) : pos;
+    const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+    double acc[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] = 0.0;
+    int k = kb + t;
+    for (; k + 3 * kThreads < ke; k += 4 * kThreads) {   // four entries per thread in flight
+        double a[4], xv[4][W];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = __ldg(val + k + kThreads * u);
+            load_row<W>(X + (int64_t)__ldg(col + k + kThreads * u) * W, xv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] = fma(a[u], xv[u][c], acc[c]);
+    }
+    for (; k < ke; k += kThreads) {
+        const double a = __ldg(val + k);
+        double xv[W];
+        load_row<W>(X + (int64_t)__ldg(col + k) * W, xv);
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(a, xv[c], acc[c]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) s_part[warp][c] = acc[c];
+    }
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = s_part[0][c];
+        for (int w = 1; w < kThreads / 32; ++w)
+#pragma unroll
+            for (int c = 0; c < W; ++c) acc[c] += s_part[w][c];
+#pragma unroll
+        for (int c = 0; c < W; ++c) Y[(int64_t)row * W + c] = acc[c];
+        if (hashes) hash_row<W>(req, n_req, row, acc, h);
+    }
+    __syncthreads();   // s_part is reused by the CTA's next unit
+}
+
+// Long-row work units of a matrix, one per CTA: each of its n_vlong longest
+// rows alone, then the other long rows eight at a time, one per warp.
+__host__ __device__ __forceinline__ int long_units(const BatchMat& m) {
+    return m.n_vlong + (m.n_long - m.n_vlong + kThreads / 32 - 1) / (kThreads / 32);
+}
+
+// Long-row unit u of a matrix by the calling CTA (all its threads).
+template <int W>
+__device__ __forceinline__ void long_units_run(const int32_t* ptr, const int32_t* col, const double* val,
+                                               const BatchMat& m, int u, const double* X, double* Y,
+                                               const BlockReq* req, int n_req, unsigned long long* hashes,
+                                               unsigned long long (&h)[kMaxW]) {
+    if (u < m.n_vlong) {
+        long_cta_unit<W>(ptr, col, val, m, u, X, Y, req, n_req, hashes, h);
+    } else {
+        const int pos = m.n_vlong + (u - m.n_vlong) * (kThreads / 32) + (int)(threadIdx.x >> 5);
+        if (pos < m.n_long) long_unit<W>(ptr, col, val, m, pos, X, Y, req, n_req, hashes, h);
+    }
+}
+
 // One block over the sliced layout: one warp per slice (grid-stride).
 // Registers capped so that 4 CTAs (widths 1-3) or 3 CTAs (widths 4-8) fit an
 // SM without spills; uncapped, width 4 took 128 registers (2 CTAs).
@@ -381,7 +461,8 @@ __global__ void __launch_bounds__(kThreads, (W <= 3 ? 4 : 3)) spmm_sliced_kernel
     if (hashes) flush_hash(b.req, b.n_req, h, hashes);
 }
 
-// One block's long rows (positions [0, n_long)), one per warp.
+// One block's long rows (positions [0, n_long)): its long-row units, one per
+// CTA (grid-stride).
 template <int W>
 __global__ void __launch_bounds__(kThreads) spmm_long_kernel(const int32_t* __restrict__ ptr,
                                                              const int32_t* __restrict__ col,
@@ -391,9 +472,9 @@ __global__ void __launch_bounds__(kThreads) spmm_long_kernel(const int32_t* __re
     unsigned long long h[kMaxW];
 #pragma unroll
     for (int r = 0; r < kMaxW; ++r) h[r] = 0;
-    const int nw = (int)gridDim.x * (kThreads / 32);
-    for (int pos = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); pos < m.n_long; pos += nw)
-        long_unit<W>(ptr, col, val, m, pos, X, Y, b.req, b.n_req, hashes, h);
+    const int units = long_units(m);
+    for (int u = (int)blockIdx.x; u < units; u += (int)gridDim.x)
+        long_units_run<W>(ptr, col, val, m, u, X, Y, b.req, b.n_req, hashes, h);
     if (hashes) flush_hash(b.req, b.n_req, h, hashes);
 }
 
@@ -435,8 +516,10 @@ __global__ void __launch_bounds__(kThreads) spmm_group_kernel(const BatchMat* __
     unsigned long long h[kMaxW];
 #pragma unroll
     for (int r = 0; r < kMaxW; ++r) h[r] = 0;
-    const int nw = (int)gridDim.x * (kThreads / 32);
-    for (int u = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5); u < units; u += nw) {
+    // slice units one per warp; long-row units one per CTA (long_units)
+    const int nw = LONG ? (int)gridDim.x : (int)gridDim.x * (kThreads / 32);
+    const int u0 = LONG ? (int)blockIdx.x : (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5);
+    for (int u = u0; u < units; u += nw) {
         int lo = 0, hi = nb - 1;   // the last block whose first unit is <= u
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -453,14 +536,14 @@ __global__ void __launch_bounds__(kThreads) spmm_group_kernel(const BatchMat* __
             const int32_t* mc = col + m.ent_off;
             const double* mv = val + m.ent_off;
             switch (b.width) {
-                case 1: long_unit<1>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                case 2: long_unit<2>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                case 3: long_unit<3>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                case 4: long_unit<4>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                case 5: long_unit<5>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                case 6: long_unit<6>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                case 7: long_unit<7>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
-                default: long_unit<8>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 1: long_units_run<1>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 2: long_units_run<2>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 3: long_units_run<3>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 4: long_units_run<4>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 5: long_units_run<5>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 6: long_units_run<6>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                case 7: long_units_run<7>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
+                default: long_units_run<8>(mp, mc, mv, m, k, X, Y, b.req, b.n_req, hashes, h); break;
             }
         } else {
             switch (b.width) {
@@ -501,7 +584,7 @@ cudaError_t launch_sliced(const BlockDesc& b, const int32_t* ptr, const int32_t*
         if (e != cudaSuccess) return e;
     }
     if (M.n_long > 0) {
-        const int grid = std::min((M.n_long + WPB - 1) / WPB, num_sms * 8);
+        const int grid = std::min(long_units(M), num_sms * 8);
 #define SPMM_LG(w) spmm_long_kernel<w><<<grid, kThreads, 0, s>>>(ptr, col, val, M, X, Y, b, hashes)
         switch (b.width) {
             case 1: SPMM_LG(1); break;
@@ -994,7 +1077,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                         gb.unit0 = units;
                         gb.long0 = longs;
                         units += Mm.n_slices;
-                        longs += Mm.n_long;
+                        longs += long_units(Mm);
                         max_elems = std::max(max_elems, Mm.n * wsum);
                         queued -= take;
                         pend_width[m] -= wsum;
@@ -1021,7 +1104,7 @@ int spmv_serve_run(spmv_server* sv, int64_t n_req, const int32_t* matrix, const 
                         ++sv->launches;
                     }
                     if (longs > 0) {
-                        const int gl = std::min((longs + 7) / 8, sv->num_sms * 8);
+                        const int gl = std::min(longs, sv->num_sms * 8);   // one CTA per long-row unit
                         spmm_group_kernel<true><<<gl, kThreads, 0, st>>>(bt->d_mats, bt->ptr, bt->col, bt->val, pool,
                                                                         sv->d_group[i], nb, longs, hs);
                         ++sv->launches;
