@@ -428,20 +428,23 @@ def run_ours(args, world, rank, local, fp64=None):
     t_search = time.perf_counter()
     # the design space searched in each ordering mode: "strict" runs the
     # kernels of a stream one after another (the paper's semantics),
-    # "relaxed" orders them by the DAG alone (SPMV_RUN_RELAXED)
+    # "relaxed" orders them by the DAG alone (SPMV_RUN_RELAXED), "defer" lets
+    # remote products sum their rows before waiting for the kernel before
+    # them (SPMV_RUN_DEFER)
     by_mode = {}
     for run_mode in args.run_modes.split(","):
-        relaxed = run_mode == "relaxed"
-        rec_m = rec if (rec is not None and not relaxed) else None
+        strict = run_mode == "strict"
+        rec_m = rec if (rec is not None and strict) else None
         # the minimum of a few 0.01 s measurements per program, so that a host
         # hiccup during one measurement does not masquerade as a slow program
         evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec_m, measurements=3
-                                          if mode == "exhaustive" else 2, relaxed=relaxed)
+                                          if mode == "exhaustive" else 2, relaxed=run_mode == "relaxed",
+                                          defer=run_mode == "defer")
         if mode == "exhaustive":
             sched = search.exhaustive(part, streams, evaluate)
         elif mode == "mcts":
             sched, _ = search.mcts(part, streams, evaluate, args.mcts_iters, seed=0)
-            if args.random_baseline and not relaxed:
+            if args.random_baseline and strict:
                 cmp = {"samples": args.random_baseline}
                 mt = [r[2] for r in sched[:args.random_baseline]]
                 cmp["mcts"] = {"best_us": round(min(mt) * 1e6, 2), "worst_us": round(max(mt) * 1e6, 2)}
@@ -458,18 +461,20 @@ def run_ours(args, world, rank, local, fp64=None):
         by_mode[run_mode] = sorted(sched, key=lambda r: r[2])
     run_mode = min(by_mode, key=lambda m: by_mode[m][0][2])
     sched = by_mode[run_mode]
-    relaxed_flag = spmv.RUN_RELAXED if run_mode == "relaxed" else 0
+    mode_flag = {"strict": 0, "relaxed": spmv.RUN_RELAXED, "defer": spmv.RUN_DEFER}[run_mode]
     order, smap, t_best = sched[0]
-    # the variants were tuned on launches timed one after another; a per-rank
-    # program overlaps its kernels, so its best program is re-timed with the
-    # three fastest LOCAL x three fastest REMOTE variants of the tuning and the
-    # fastest pair kept
+    # the variants were tuned on launches timed one after another; a program
+    # overlaps its kernels (a per-rank program its ranks', a deferred remote
+    # product the local product's tail), so the best program is re-timed with
+    # the three fastest LOCAL x three fastest REMOTE variants of the tuning and
+    # the fastest pair kept
     in_context = None
-    if gran != spmv.COARSE and len(sched[0][0]) > 4:
+    if len(sched[0][0]) > 1:
         def top(op):
             c = sorted(((t, v, p) for (o, v, p), t in tune_times.items() if o == op))
             return [(v, p) for _, v, p in c[:3]]
-        ev_ctx = search.graph_evaluator(part, streams, x_d, y_d, measurements=3, relaxed=bool(relaxed_flag))
+        ev_ctx = search.graph_evaluator(part, streams, x_d, y_d, measurements=3, relaxed=run_mode == "relaxed",
+                                        defer=run_mode == "defer")
         in_context = {}
         best = (t_best, tuple(tuned["local"]), tuple(tuned["remote"]))
         for lv in top(spmv.OP_LOCAL):
@@ -490,7 +495,7 @@ def run_ours(args, world, rank, local, fp64=None):
         t_best = best[0]
     t_search = time.perf_counter() - t_search
     spread = sched[-1][2] / sched[0][2]
-    g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE | relaxed_flag)
+    g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE | mode_flag)
     step = lambda: part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
     part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)   # counts the launches of a step
     launches_per_step = part.query(spmv.Q_LAST_LAUNCHES)
@@ -554,7 +559,7 @@ def run_ours(args, world, rank, local, fp64=None):
 
     # end to end through the C ABI with host buffers
     xi, yi = spmv.spmv_part_io_buffers(part.h)
-    ge = part.run(order, smap, streams, xi, yi, spmv.RUN_CAPTURE | relaxed_flag)
+    ge = part.run(order, smap, streams, xi, yi, spmv.RUN_CAPTURE | mode_flag)
     xh = torch.from_numpy(x).pin_memory()
     yh = torch.empty(n, dtype=torch.float64).pin_memory()
     for _ in range(3):
@@ -1149,9 +1154,10 @@ def main(argv=None):
     ap.add_argument("--sub-cpu-seconds", type=float, default=6.0)
     ap.add_argument("--sub-measurements", type=int, default=50)
     ap.add_argument("--mcts-iters", type=int, default=2000)
-    ap.add_argument("--run-modes", default="strict,relaxed",
+    ap.add_argument("--run-modes", default="strict,relaxed,defer",
                     help="orderings searched: strict (the kernels of a stream run in order, the paper's "
-                         "semantics) and/or relaxed (DAG-only ordering, SPMV_RUN_RELAXED); the faster is timed")
+                         "semantics), relaxed (DAG-only ordering, SPMV_RUN_RELAXED) and/or defer (remote "
+                         "products sum their rows before waiting, SPMV_RUN_DEFER); the fastest is timed")
     ap.add_argument("--random-baseline", type=int, default=0,
                     help="also measure this many random programs (uniform over programs, and by "
                          "random decisions) as the search baseline")

@@ -138,8 +138,10 @@ enum {
     SPMV_Q_LAST_LAUNCHES = 19,    /* kernels launched by the last issue */
     SPMV_Q_REMOTE_VARIANT = 20,   /* 100 * variant + param of the REMOTE product
                                      (SPMV_Q_LOCAL_VARIANT: of the LOCAL one) */
-    SPMV_Q_SELL_ENTRIES = 21      /* padded entries of the sliced layout, local
+    SPMV_Q_SELL_ENTRIES = 21,     /* padded entries of the sliced layout, local
                                      plus remote (0 until SELL is first set) */
+    SPMV_Q_LAST_DEFERRED = 22     /* remote products the last spmv_schedule_run
+                                     issued with a deferred wait (SPMV_RUN_DEFER) */
 };
 int spmv_part_query(const spmv_part* part, int what, int part_idx, int64_t* out);
 
@@ -290,8 +292,20 @@ int spmv_remote(spmv_part* part, int part_idx, double* y_dev, cudaStream_t s);
  *   paper's stream semantics (where the kernels of a stream run one after
  *   another, the default here).  Ops of one product touch common data only
  *   along DAG edges, so y is the same, bit for bit.
+ * SPMV_RUN_DEFER (or-ed into CAPTURE; SPMV_EINVAL with EAGER or with
+ *   SPMV_RUN_RELAXED; ignored by REPLAY) keeps the stream semantics above
+ *   but lets a remote product in the sliced layout (SPMV_VARIANT_SELL)
+ *   start while the kernel before it on its stream runs, when that kernel
+ *   writes none of the product's inputs but y (any op that is not the
+ *   product's DAG predecessor, or its local product): the product reads
+ *   A_R and the halo and sums its rows first, and waits for that kernel
+ *   only before it adds the sums into y, so the remote product overlaps
+ *   the tail of, say, the local product of its rank.  The kernel before it
+ *   releases it as its CTAs start.  The product's edges from other streams
+ *   stay full dependencies in the graph (checked after capture).  An
+ *   extension of the paper's stream semantics; y is the same, bit for bit.
  */
-enum { SPMV_RUN_EAGER = 0, SPMV_RUN_CAPTURE = 1, SPMV_RUN_REPLAY = 2, SPMV_RUN_RELAXED = 4 };
+enum { SPMV_RUN_EAGER = 0, SPMV_RUN_CAPTURE = 1, SPMV_RUN_REPLAY = 2, SPMV_RUN_RELAXED = 4, SPMV_RUN_DEFER = 8 };
 int spmv_schedule_run(spmv_part* part, const int32_t* op_order,
                       const int32_t* stream_of_op, int n_ops,
                       cudaStream_t* streams, int n_streams,

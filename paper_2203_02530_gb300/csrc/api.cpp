@@ -132,12 +132,14 @@ spmvk::CsrArgs remote_args(spmv_part* pt, double* y) {
 // Each op returns the number of kernels it launched.
 int op_pack(spmv_part* pt, int q, const double* x, cudaStream_t s) {
     if (q < 0) {
+        if (pt->dry_run) return pt->n_send > 0;
         check_cuda(spmvk::launch_gather(x, pt->send_idx, nullptr, pt->sendbuf, pt->n_send, pt->num_sms, s,
                                         pt->cur_pdl),
                    "pack");
         return pt->n_send > 0;
     }
     const int64_t c = pt->pack_off[q + 1] - pt->pack_off[q];
+    if (pt->dry_run) return c > 0;
     check_cuda(spmvk::launch_gather(x, pt->send_idx, pt->pack_pos + pt->pack_off[q], pt->sendbuf, c,
                                     pt->num_sms, s, pt->cur_pdl),
                "pack");
@@ -147,6 +149,7 @@ int op_pack(spmv_part* pt, int q, const double* x, cudaStream_t s) {
 int op_copy(spmv_part* pt, int p, cudaStream_t s) {
     const int64_t a = p < 0 ? 0 : pt->halo_off[p];
     const int64_t b = p < 0 ? pt->n_send : pt->halo_off[p + 1];
+    if (pt->dry_run) return b > a;
     check_cuda(spmvk::launch_copy(pt->sendbuf + a, pt->recvbuf + a, b - a, pt->num_sms, s, pt->cur_pdl), "halo copy");
     return b > a;
 }
@@ -161,6 +164,7 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         const std::vector<int64_t>& mo = remote ? pt->rmtile_off : pt->lmtile_off;
         const int mb = (int)(p < 0 ? 0 : mo[p]);
         const int me = (int)(p < 0 ? mo[pt->P] : mo[p + 1]);
+        if (pt->dry_run) return me > mb ? 2 : 0;
         check_cuda(spmvk::launch_merge(a, remote ? pt->rmtiles : pt->lmtiles, mb, me,
                                        remote ? pt->rcarry : pt->lcarry, pt->num_sms, s),
                    "merge product");
@@ -170,6 +174,7 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         const std::vector<int64_t>& wo = remote ? pt->rwtile_off : pt->lwtile_off;
         const int wb = (int)(p < 0 ? 0 : wo[p]);
         const int we = (int)(p < 0 ? wo[pt->P] : wo[p + 1]);
+        if (pt->dry_run) return we > wb;
         check_cuda(spmvk::launch_warp(a, remote ? pt->rwtiles : pt->lwtiles, wb, we, param, pt->num_sms, s),
                    "warp product");
         return we > wb;
@@ -183,6 +188,7 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         sa.slice_end = (int)(p < 0 ? sp.slice_off[pt->P] : sp.slice_off[p + 1]);
         sa.long_begin = (int)(p < 0 ? 0 : sp.long_off[p]);
         sa.long_end = (int)(p < 0 ? sp.long_off[pt->P] : sp.long_off[p + 1]);
+        if (pt->dry_run) return (sa.slice_end > sa.slice_begin || sa.long_end > sa.long_begin) ? 1 : 0;
         if (spmvk::sell_param_balanced(param)) {
             const int units = (sa.slice_end - sa.slice_begin) + (sa.long_end - sa.long_begin);
             const int grid = spmvk::sell_grid(param, units, pt->num_sms);
@@ -205,12 +211,14 @@ int launch_product(spmv_part* pt, const spmvk::CsrArgs& a, bool remote, int p, c
         const int bb = (int)(p < 0 ? 0 : bo[p]);
         const int be = (int)(p < 0 ? bo[pt->P] : bo[p + 1]);
         const spmvk::Tile* blocks = remote ? pt->rblocks : pt->lblocks;
+        if (pt->dry_run) return be > bb;
         if (var == SPMV_VARIANT_VECTOR)
             check_cuda(spmvk::launch_vector(a, blocks, bb, be, param, pt->num_sms, s), "vector product");
         else
             check_cuda(spmvk::launch_pairs(a, blocks, bb, be, param, pt->num_sms, s), "pair product");
         return be > bb;
     } else {
+        if (pt->dry_run) return te > tb;
         check_cuda(spmvk::launch_tile(a, tiles, tb, te, pt->geom, pt->num_sms, s), "tile product");
     }
     return te > tb;
@@ -226,17 +234,19 @@ int op_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
 
 // PACK of one halo segment: its send slots [a, b) <- x
 int op_pack_segment(spmv_part* pt, const spmv_part::Seg& g, const double* x, cudaStream_t s) {
+    if (pt->dry_run) return g.b > g.a;
     check_cuda(spmvk::launch_gather(x, pt->send_idx + g.a, nullptr, pt->sendbuf + g.a, g.b - g.a, pt->num_sms, s,
                                     pt->cur_pdl),
                "pack segment");
-    return 1;
+    return g.b > g.a;
 }
 
 // COPY of one halo segment: recvbuf[a, b) <- sendbuf[a, b)
 int op_copy_segment(spmv_part* pt, const spmv_part::Seg& g, cudaStream_t s) {
+    if (pt->dry_run) return g.b > g.a;
     check_cuda(spmvk::launch_copy(pt->sendbuf + g.a, pt->recvbuf + g.a, g.b - g.a, pt->num_sms, s, pt->cur_pdl),
                "copy segment");
-    return 1;
+    return g.b > g.a;
 }
 
 int run_op(spmv_part* pt, int op, const double* x, double* y, cudaStream_t s) {
@@ -299,9 +309,59 @@ void ensure_events(spmv_part* pt, int n_streams) {
 // one stream, is an event recorded after its source and waited for before
 // its target, so an op's predecessors are always among its prerequisites
 // even when a kernel between them on the stream did not wait.
+// Deferred mode (SPMV_RUN_DEFER, stream semantics otherwise): a remote
+// product in the sliced layout whose kernel follows, on its stream, a kernel
+// that writes none of its inputs but y (any op that is not its DAG
+// predecessor, or its local product) reads A_R and the halo and sums its
+// rows before waiting for that kernel, and waits only before its first
+// access to y (kPdlDefer); that kernel releases it as its CTAs start, after
+// its own wait (kPdlEarly).  Every kernel before that one on the stream is
+// then complete, and the remote product's other predecessors are on other
+// streams, behind events whose graph edges are made full dependencies after
+// capture (fix_deferred_edges).
+int op_kind(const spmv_part* pt, int op) {
+    if (pt->gran == SPMV_COARSE) return op;
+    if (pt->gran == SPMV_PER_PARTITION) return op % 4;
+    if (op < 2 * pt->P) return op % 2 == 0 ? SPMV_OP_LOCAL : SPMV_OP_REMOTE;
+    return (op - 2 * pt->P) % 2 == 0 ? SPMV_OP_PACK : SPMV_OP_COPY;
+}
+
+void defer_flags(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops, int n_streams,
+                 const double* x, double* y, cudaStream_t s, std::vector<int>& pdl_flags) {
+    const int rv = pt->variant[1];
+    if (rv != SPMV_VARIANT_SELL && rv != SPMV_VARIANT_SELL16) return;
+    // kernels each op launches (an op with nothing to do launches none, and
+    // the kernel before it on the stream is then the one that releases)
+    std::vector<int> kernels(n_ops, 0);
+    pt->dry_run = true;
+    try {
+        for (int v = 0; v < n_ops; ++v) kernels[v] = run_op(pt, v, x, y, s);
+    } catch (...) {
+        pt->dry_run = false;
+        throw;
+    }
+    pt->dry_run = false;
+    std::vector<int> last(n_streams, -1);   // last op of each stream that launched a kernel
+    for (int i = 0; i < n_ops; ++i) {
+        const int v = order[i];
+        const int u = last[stream_of[v]];
+        if (kernels[v] > 0 && u >= 0 && op_kind(pt, v) == SPMV_OP_REMOTE) {
+            bool feeds = false;   // u writes an input of v other than y
+            for (int w : pt->preds[v])
+                if (w == u && op_kind(pt, u) != SPMV_OP_LOCAL) feeds = true;
+            if (!feeds) {
+                pdl_flags[v] |= spmvk::kPdlDefer;
+                pdl_flags[u] |= spmvk::kPdlEarly;
+            }
+        }
+        if (kernels[v] > 0) last[stream_of[v]] = v;
+    }
+}
+
 void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops, cudaStream_t* streams,
-           int n_streams, const double* x, double* y, bool relaxed) {
+           int n_streams, const double* x, double* y, bool relaxed, bool defer) {
     std::vector<int> pdl_flags(n_ops, 0);
+    if (defer) defer_flags(pt, order, stream_of, n_ops, n_streams, x, y, streams[0], pdl_flags);
     if (relaxed) {
         std::vector<int> last(n_streams, -1);
         for (int i = 0; i < n_ops; ++i) {
@@ -327,6 +387,12 @@ void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_
     for (auto& e : pt->edges)
         if (relaxed || stream_of[e.first] != stream_of[e.second]) cross[e.first] = 1;
     int64_t records = 0, waits = 0, launches = 0;
+    // while capturing a deferred program: the last kernel node of each stream
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (defer) check_cuda(cudaStreamIsCapturing(origin, &cap), "capture status");
+    const bool track = defer && cap == cudaStreamCaptureStatusActive;
+    std::vector<cudaGraphNode_t> last_node(n_streams, nullptr);
+    pt->deferred_nodes.clear();
     for (int i = 0; i < n_ops; ++i) {
         const int v = order[i];
         cudaStream_t sv = streams[stream_of[v]];
@@ -336,15 +402,27 @@ void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_
                 ++waits;
             }                                                // same stream: nothing
         }
+        int k = 0;
         {
             pt->cur_pdl = pdl_flags[v];
             try {
-                launches += run_op(pt, v, x, y, sv);
+                k = run_op(pt, v, x, y, sv);
             } catch (...) {
                 pt->cur_pdl = 0;
                 throw;
             }
             pt->cur_pdl = 0;
+            launches += k;
+        }
+        if (track && k > 0) {
+            // the stream's capture dependency is now the op's last kernel
+            cudaStreamCaptureStatus st;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            check_cuda(cudaStreamGetCaptureInfo(sv, &st, nullptr, nullptr, &deps, nullptr, &nd), "capture info");
+            if (nd != 1) fail(SPMV_EINVAL, "unexpected capture dependencies (%zu) after an op", nd);
+            if (pdl_flags[v] & spmvk::kPdlDefer) pt->deferred_nodes.push_back({deps[0], last_node[stream_of[v]]});
+            last_node[stream_of[v]] = deps[0];
         }
         if (cross[v]) {
             check_cuda(cudaEventRecord(pt->op_ev[v], sv), "event record");
@@ -360,6 +438,8 @@ void issue(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_
     pt->last_records = records;
     pt->last_waits = waits;
     pt->last_launches = launches;
+    pt->last_deferred = 0;
+    for (int v = 0; v < n_ops; ++v) pt->last_deferred += (pdl_flags[v] & spmvk::kPdlDefer) != 0;
 }
 
 int64_t alg_bytes_local(const spmv_part* pt) {
@@ -471,6 +551,7 @@ int spmv_part_query(const spmv_part* pt, int what, int part_idx, int64_t* out) {
         case SPMV_Q_SELL_ENTRIES: *out = pt->sell_entries; break;
         case SPMV_Q_N_LOCAL_TILES: *out = pt->ltile_off.empty() ? 0 : pt->ltile_off[pt->P]; break;
         case SPMV_Q_LAST_LAUNCHES: *out = pt->last_launches; break;
+        case SPMV_Q_LAST_DEFERRED: *out = pt->last_deferred; break;
         default: fail(SPMV_EINVAL, "unknown query %d", what);
     }
     API_CATCH
@@ -758,6 +839,41 @@ int spmv_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
     return SPMV_OK;
 }
 
+// Stream capture gives every incoming edge of a kernel launched with
+// programmatic stream serialization the programmatic type, the edges of its
+// cross-stream event waits included (a kernel that waits at its start waits
+// for all of them alike).  A deferred remote product reads A_R and the halo
+// before its wait, so only the edge from the kernel before it on its stream
+// may stay programmatic: every other incoming edge of its node becomes a
+// full dependency (completion and memory visibility), and the result is
+// checked before the graph is instantiated.
+bool edge_is_default(const cudaGraphEdgeData& e) { return e.type == 0 && e.from_port == 0 && e.to_port == 0; }
+
+void fix_deferred_edges(const spmv_part* pt, cudaGraph_t g) {
+    const cudaGraphEdgeData full{};
+    for (const auto& dn : pt->deferred_nodes) {
+        const cudaGraphNode_t v = dn.first, u = dn.second;
+        for (int pass = 0; pass < 2; ++pass) {   // rewrite, then check
+            size_t nd = 0;
+            check_cuda(cudaGraphNodeGetDependencies(v, nullptr, nullptr, &nd), "node dependencies");
+            std::vector<cudaGraphNode_t> from(nd);
+            std::vector<cudaGraphEdgeData> ed(nd);
+            if (nd) check_cuda(cudaGraphNodeGetDependencies(v, from.data(), ed.data(), &nd), "node dependencies");
+            int from_u = 0;
+            for (size_t i = 0; i < nd; ++i) {
+                if (from[i] == u) {
+                    ++from_u;
+                } else if (!edge_is_default(ed[i])) {
+                    if (pass == 1) fail(SPMV_EINVAL, "a deferred remote product kept a programmatic edge");
+                    check_cuda(cudaGraphRemoveDependencies(g, &from[i], &v, &ed[i], 1), "remove edge");
+                    check_cuda(cudaGraphAddDependencies(g, &from[i], &v, &full, 1), "add edge");
+                }
+            }
+            if (from_u != 1) fail(SPMV_EINVAL, "a deferred remote product lost the edge from its stream predecessor");
+        }
+    }
+}
+
 int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops,
                       cudaStream_t* streams, int n_streams, const double* x, double* y, int flags,
                       int64_t* handle) {
@@ -765,7 +881,8 @@ int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream
     check_part(pt);
     need(streams != nullptr, SPMV_EINVAL, "streams is NULL");
     const bool relaxed = (flags & SPMV_RUN_RELAXED) != 0;
-    flags &= ~SPMV_RUN_RELAXED;
+    const bool defer = (flags & SPMV_RUN_DEFER) != 0;
+    flags &= ~(SPMV_RUN_RELAXED | SPMV_RUN_DEFER);
     if (flags == SPMV_RUN_REPLAY) {
         need(handle != nullptr, SPMV_EINVAL, "graph handle is NULL");
         auto it = pt->graphs.find(*handle);
@@ -776,17 +893,19 @@ int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream
     }
     if (flags != SPMV_RUN_EAGER && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "unknown flags %d", flags);
     if (relaxed && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "SPMV_RUN_RELAXED applies to SPMV_RUN_CAPTURE only");
+    if (relaxed && defer) fail(SPMV_EINVAL, "SPMV_RUN_RELAXED and SPMV_RUN_DEFER exclude each other");
+    if (defer && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "SPMV_RUN_DEFER applies to SPMV_RUN_CAPTURE only");
     validate_schedule(pt, order, stream_of, n_ops, n_streams);
     need((x != nullptr && y != nullptr) || pt->n == 0, SPMV_EINVAL, "x_dev or y_dev is NULL");
     ensure_events(pt, n_streams);
     if (flags == SPMV_RUN_EAGER) {
-        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y, relaxed);
+        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y, relaxed, defer);
         return SPMV_OK;
     }
     need(handle != nullptr, SPMV_EINVAL, "graph handle is NULL");
     check_cuda(cudaStreamBeginCapture(streams[0], cudaStreamCaptureModeThreadLocal), "begin capture");
     try {
-        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y, relaxed);
+        issue(pt, order, stream_of, n_ops, streams, n_streams, x, y, relaxed, defer);
     } catch (...) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(streams[0], &g);
@@ -796,6 +915,14 @@ int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream
     }
     cudaGraph_t g = nullptr;
     check_cuda(cudaStreamEndCapture(streams[0], &g), "end capture");
+    try {
+        fix_deferred_edges(pt, g);
+    } catch (...) {
+        pt->deferred_nodes.clear();
+        cudaGraphDestroy(g);
+        throw;
+    }
+    pt->deferred_nodes.clear();
     cudaGraphExec_t exec = nullptr;
     cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);

@@ -164,9 +164,13 @@ struct spmv_part {
     std::vector<cudaEvent_t> join_ev; // one per stream slot (grown on demand)
     cudaEvent_t fork_ev = nullptr;
     std::map<int64_t, spmvk::GraphRec> graphs;
+    // captured deferred remote products: (its kernel's node, the node of the
+    // kernel before it on its stream), for the edge check after capture
+    std::vector<std::pair<cudaGraphNode_t, cudaGraphNode_t>> deferred_nodes;
     int64_t next_graph = 1;
-    int64_t last_records = 0, last_waits = 0, last_launches = 0;
+    int64_t last_records = 0, last_waits = 0, last_launches = 0, last_deferred = 0;
     int cur_pdl = 0;                  // programmatic-launch flags of the op being issued
+    bool dry_run = false;             // ops count the kernels they would launch, and launch none
 
     std::vector<spmvk::DevArray> allocs;   // everything to free
     size_t device_bytes = 0;

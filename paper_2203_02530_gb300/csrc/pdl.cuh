@@ -11,7 +11,12 @@
 // wait: the kernel's operation has no DAG predecessor, it needs nothing from
 // any other kernel of the product) and kPdlEarly (the next kernel of the
 // stream is such a kernel, so release it as each CTA starts and let it fill
-// this kernel's tail).
+// this kernel's tail).  The deferred mode passes kPdlDefer to a remote
+// product whose stream predecessor writes none of its inputs but y: it reads
+// A_R and the halo and forms its row sums before the wait, and waits only
+// before its first access to y (and, at the latest, before it exits, so that
+// its completion still implies the predecessor's); the predecessor, which
+// waits for its own predecessor first, releases it as its CTAs start.
 // Launched without the attribute (or with SPMV_NO_PDL=1 in the environment)
 // the wait does nothing.
 #pragma once
@@ -26,12 +31,29 @@ namespace spmvk {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-enum { kPdlNoWait = 1, kPdlEarly = 2 };
+enum { kPdlNoWait = 1, kPdlEarly = 2, kPdlDefer = 4 };
 
-// Start of a kernel of the operation DAG (see above).
+// Start of a kernel of the operation DAG (see above); kPdlDefer is ignored
+// here (the kernel waits), so only kernels written for it can defer.
 __device__ __forceinline__ void pdl_begin(int flags) {
     if (!(flags & kPdlNoWait)) pdl_wait();
     if (flags & kPdlEarly) pdl_trigger();
+}
+
+// Start of a kernel that honours kPdlDefer: it then skips the wait here and
+// calls pdl_settle before touching y.
+__device__ __forceinline__ void pdl_begin_deferrable(int flags) {
+    if (!(flags & (kPdlNoWait | kPdlDefer))) pdl_wait();
+    if (flags & kPdlEarly) pdl_trigger();
+}
+
+// A deferring kernel's wait, once per thread: before the thread's first
+// access to y, and before it exits if it never made one.
+__device__ __forceinline__ void pdl_settle(bool& pending) {
+    if (pending) {
+        pdl_wait();
+        pending = false;
+    }
 }
 
 inline bool pdl_enabled() {

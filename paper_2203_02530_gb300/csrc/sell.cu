@@ -151,7 +151,10 @@ __device__ __forceinline__ void long_round(const CsrArgs& a, const double* xb, i
 // YP: the layout has a y row per position (sa.ypos; sorted remote layouts).
 template <int U, int MINB, typename CT, bool YP = false>
 __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs sa) {
-    pdl_begin(a.pdl);  // the previous kernel of this stream is done (unless independent)
+    // the previous kernel of this stream is done (unless independent, or
+    // the wait is deferred to the first access to y)
+    pdl_begin_deferrable(a.pdl);
+    bool pending = (a.pdl & kPdlDefer) != 0;
     constexpr bool kDelta = sizeof(CT) == 2;
     const uint64_t pol_stream = sell_policy_evict_first();
     const uint64_t pol_keep = sell_policy_evict_last();
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            pdl_settle(pending);
             if (lane == 0) {
                 if (L.nparts == 1) {
                     sell_store(a, L.row, part);
@@ -251,11 +255,13 @@ __global__ void __launch_bounds__(256, MINB) csr_sell_kernel(CsrArgs a, SellArgs
         // latency, so the short slices of skewed rows (3 entries, say) keep
         // all their gathers in flight at once
         sell_tail<U>(d.len - j, cp, vp, xb, j, len, sum, pol_stream, pol_keep);
+        pdl_settle(pending);
         if (store) {
             if (YP) a.y[row] = a.accumulate ? a.y[row] + sum : sum;
             else sell_store(a, row, sum);
         }
     }
+    pdl_settle(pending);
 }
 
 // Fill the sliced arrays from the CSR: one warp per slice, one lane per

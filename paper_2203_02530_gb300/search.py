@@ -46,11 +46,12 @@ class Recorder:
 
 
 def graph_evaluator(part, streams, x_dev, y_dev, recorder=None, measurements=1,
-                    t_measure=benchmark.T_MEASURE, relaxed=False):
+                    t_measure=benchmark.T_MEASURE, relaxed=False, defer=False):
     """evaluate(order, smap) -> seconds per sample (min over `measurements`
     measurements of graph replays); `relaxed` captures each program with
-    SPMV_RUN_RELAXED (DAG-only ordering)."""
-    flags = spmv.RUN_CAPTURE | (spmv.RUN_RELAXED if relaxed else 0)
+    SPMV_RUN_RELAXED (DAG-only ordering), `defer` with SPMV_RUN_DEFER
+    (remote products that sum their rows before waiting)."""
+    flags = spmv.RUN_CAPTURE | (spmv.RUN_RELAXED if relaxed else 0) | (spmv.RUN_DEFER if defer else 0)
 
     def evaluate(order, smap):
         if recorder is not None:

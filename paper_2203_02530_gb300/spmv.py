@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "spmv.h")
 OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
 COARSE, PER_PARTITION, PER_SEGMENT = 0, 1, 2
-RUN_EAGER, RUN_CAPTURE, RUN_REPLAY, RUN_RELAXED = 0, 1, 2, 4
+RUN_EAGER, RUN_CAPTURE, RUN_REPLAY, RUN_RELAXED, RUN_DEFER = 0, 1, 2, 4, 8
 VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP, VARIANT_SELL, VARIANT_SELL16 = (
     0, 1, 2, 3, 4, 5, 6)
 SERVE_BATCHED, SERVE_PLAIN = 0, 1
@@ -28,7 +28,7 @@ BATCH_SLICED = 64
 (Q_N, Q_P, Q_GRANULARITY, Q_NNZ, Q_NNZ_LOCAL, Q_NNZ_REMOTE, Q_N_SEND, Q_N_HALO,
  Q_N_REMOTE_ROWS, Q_N_OPS, Q_N_EDGES, Q_ALG_BYTES, Q_ALG_BYTES_LOCAL,
  Q_DEVICE_BYTES, Q_LAST_RECORDS, Q_LAST_WAITS, Q_ERROR, Q_LOCAL_VARIANT,
- Q_N_LOCAL_TILES, Q_LAST_LAUNCHES, Q_REMOTE_VARIANT, Q_SELL_ENTRIES) = range(22)
+ Q_N_LOCAL_TILES, Q_LAST_LAUNCHES, Q_REMOTE_VARIANT, Q_SELL_ENTRIES, Q_LAST_DEFERRED) = range(23)
 (BQ_COUNT, BQ_TOTAL_ROWS, BQ_TOTAL_NNZ, BQ_ITEMS, BQ_ALG_BYTES, BQ_OFFSET, BQ_N, BQ_NNZ,
  BQ_LANES, BQ_DEVICE_BYTES, BQ_LAUNCHES) = range(11)
 (X_BOUNDS, X_L_PTR, X_L_COL, X_L_VAL, X_R_PTR, X_R_COL, X_R_VAL, X_HALO,

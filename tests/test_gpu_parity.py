@@ -582,6 +582,100 @@ def test_relaxed_mode_gives_identical_y(name, gran, variant):
         assert part.query(spmv.Q_ERROR) == 0
 
 
+def _local_then_remote_program(part):
+    """Packs and copies on stream 1, then each rank's local and remote
+    products in turn on stream 0: every remote product follows its rank's
+    local product on its stream (the case SPMV_RUN_DEFER overlaps)."""
+    from paper_2203_02530_gb300 import spmv
+    info = [spmv.spmv_part_op_info(part.h, v) for v in range(part.n_ops)]
+    order = ([v for v in range(part.n_ops) if info[v][0] == spmv.OP_PACK]
+             + [v for v in range(part.n_ops) if info[v][0] == spmv.OP_COPY])
+    smap = [1] * part.n_ops
+    for d in sorted({i[1] for i in info if i[0] == spmv.OP_LOCAL}):
+        for kind in (spmv.OP_LOCAL, spmv.OP_REMOTE):
+            v = [u for u in range(part.n_ops) if info[u][0] == kind and info[u][1] == d][0]
+            order.append(v)
+            smap[v] = 0
+    return order, smap
+
+
+@pytest.mark.parametrize("name,gran,local,remote", [
+    ("st27_20", 0, ("sell", 107), ("sell", 107)), ("st27_20", 0, ("sell16", 9), ("sell", 8)),
+    ("powerlaw", 1, ("sell", 2009), ("sell", 2104)), ("powerlaw", 1, ("merge", 0), ("sell", 8)),
+    ("powerlaw", 2, ("sell", 104), ("sell", 104)), ("st27_ragged", 1, ("vector", 4), ("sell", 4)),
+    ("rand_dup", 1, ("sell", 8), ("sell", 9)), ("empty_rows", 1, ("sell", 4), ("sell", 4)),
+    ("st27_20", 1, ("sell", 9), ("pairs", 2))])
+def test_defer_mode_gives_identical_y(name, gran, local, remote):
+    """SPMV_RUN_DEFER lets a sliced remote product read A_R and the halo and
+    sum its rows before waiting for the kernel before it on its stream (when
+    that kernel writes none of its inputs but y): random programs on 1 to 4
+    streams and the program that puts each rank's remote product right after
+    its local product, captured and replayed into NaN-filled y, give y
+    bit-identical to the stream-ordered mode and within the oracle's bound;
+    that program defers every non-empty remote product (none when the remote
+    variant is not sliced); the flag is refused for eager issue and with
+    SPMV_RUN_RELAXED."""
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    want, scale = reference(n, rp, ci, va, x)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    x_d = dev(x)
+    y_d = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    code = {"sell": spmv.VARIANT_SELL, "sell16": spmv.VARIANT_SELL16, "merge": spmv.VARIANT_MERGE,
+            "vector": spmv.VARIANT_VECTOR, "pairs": spmv.VARIANT_PAIRS}
+    sliced = remote[0] == "sell"
+    with make_part(n, rp, ci, va, P, gran) as part:
+        part.set_op_variant(spmv.OP_LOCAL, code[local[0]], local[1])
+        part.set_op_variant(spmv.OP_REMOTE, code[remote[0]], remote[1])
+        dag = E.Dag(part.n_ops, part.dag())
+        rng = random.Random(9)
+        first = None
+
+        def check(order, smap, flags, reps):
+            nonlocal first
+            g = part.run(order, smap, streams, x_d, y_d, flags) if flags & spmv.RUN_CAPTURE else None
+            deferred = part.query(spmv.Q_LAST_DEFERRED)
+            for _ in range(reps):
+                refill(y_d)
+                if g is None:
+                    part.run(order, smap, streams, x_d, y_d, flags)
+                else:
+                    part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+                torch.cuda.synchronize()
+                y = y_d.cpu().numpy()[:n].copy()
+                if first is None:
+                    first = y
+                    assert_fp64_close(y, want, scale, name)
+                assert np.array_equal(y.view(np.uint64), first.view(np.uint64)), (order, smap, flags)
+            if g is not None:
+                spmv.spmv_graph_destroy(part.h, g)
+            return deferred
+
+        order, smap = _local_then_remote_program(part)
+        check(order, smap, spmv.RUN_EAGER, 1)
+        deferred = check(order, smap, spmv.RUN_CAPTURE | spmv.RUN_DEFER, 5)
+        remote_ops = sum(1 for v in range(part.n_ops)
+                         if spmv.spmv_part_op_info(part.h, v)[0] == spmv.OP_REMOTE)
+        if not sliced:
+            assert deferred == 0
+        elif name != "empty_rows":
+            assert deferred == remote_ops, (deferred, remote_ops)
+        total = 0
+        for it in range(12):
+            order, smap = _random_schedule(dag, 1 + it % 4, rng)
+            check(order, smap, spmv.RUN_CAPTURE, 1)
+            total += check(order, smap, spmv.RUN_CAPTURE | spmv.RUN_DEFER, 3)
+        if not sliced:
+            assert total == 0
+        for bad in (spmv.RUN_EAGER | spmv.RUN_DEFER, spmv.RUN_CAPTURE | spmv.RUN_RELAXED | spmv.RUN_DEFER):
+            with pytest.raises(spmv.SpmvError) as e:
+                part.run(order, smap, streams, x_d, y_d, bad)
+            assert e.value.code == spmv.EINVAL
+        assert part.query(spmv.Q_ERROR) == 0
+
+
 @pytest.mark.parametrize("name,gran", [("lap64", 0), ("st27_20", 1), ("st27_ragged", 0), ("powerlaw", 1),
                                        ("powerlaw", 0), ("rand_dup", 1)])
 def test_release_csr_keeps_y_and_restores(name, gran):
