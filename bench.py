@@ -438,8 +438,8 @@ def run_ours(args, world, rank, local, fp64=None):
         # the minimum of a few 0.01 s measurements per program, so that a host
         # hiccup during one measurement does not masquerade as a slow program
         evaluate = search.graph_evaluator(part, streams, x_d, y_d, recorder=rec_m, measurements=3
-                                          if mode == "exhaustive" else 2, relaxed=run_mode == "relaxed",
-                                          defer=run_mode == "defer")
+                                          if mode == "exhaustive" else 2, relaxed="relaxed" in run_mode,
+                                          defer="defer" in run_mode)
         if mode == "exhaustive":
             sched = search.exhaustive(part, streams, evaluate)
         elif mode == "mcts":
@@ -461,7 +461,8 @@ def run_ours(args, world, rank, local, fp64=None):
         by_mode[run_mode] = sorted(sched, key=lambda r: r[2])
     run_mode = min(by_mode, key=lambda m: by_mode[m][0][2])
     sched = by_mode[run_mode]
-    mode_flag = {"strict": 0, "relaxed": spmv.RUN_RELAXED, "defer": spmv.RUN_DEFER}[run_mode]
+    mode_flag = {"strict": 0, "relaxed": spmv.RUN_RELAXED, "defer": spmv.RUN_DEFER,
+                 "relaxed+defer": spmv.RUN_RELAXED | spmv.RUN_DEFER}[run_mode]
     order, smap, t_best = sched[0]
     # the variants were tuned on launches timed one after another; a program
     # overlaps its kernels (a per-rank program its ranks', a deferred remote
@@ -473,8 +474,8 @@ def run_ours(args, world, rank, local, fp64=None):
         def top(op):
             c = sorted(((t, v, p) for (o, v, p), t in tune_times.items() if o == op))
             return [(v, p) for _, v, p in c[:3]]
-        ev_ctx = search.graph_evaluator(part, streams, x_d, y_d, measurements=3, relaxed=run_mode == "relaxed",
-                                        defer=run_mode == "defer")
+        ev_ctx = search.graph_evaluator(part, streams, x_d, y_d, measurements=3, relaxed="relaxed" in run_mode,
+                                        defer="defer" in run_mode)
         in_context = {}
         best = (t_best, tuple(tuned["local"]), tuple(tuned["remote"]))
         for lv in top(spmv.OP_LOCAL):
@@ -1154,10 +1155,11 @@ def main(argv=None):
     ap.add_argument("--sub-cpu-seconds", type=float, default=6.0)
     ap.add_argument("--sub-measurements", type=int, default=50)
     ap.add_argument("--mcts-iters", type=int, default=2000)
-    ap.add_argument("--run-modes", default="strict,relaxed,defer",
+    ap.add_argument("--run-modes", default="strict,relaxed,relaxed+defer",
                     help="orderings searched: strict (the kernels of a stream run in order, the paper's "
-                         "semantics), relaxed (DAG-only ordering, SPMV_RUN_RELAXED) and/or defer (remote "
-                         "products sum their rows before waiting, SPMV_RUN_DEFER); the fastest is timed")
+                         "semantics), relaxed (DAG-only ordering, SPMV_RUN_RELAXED), defer (remote "
+                         "products sum their rows before waiting, SPMV_RUN_DEFER) and/or relaxed+defer; "
+                         "the fastest is timed")
     ap.add_argument("--random-baseline", type=int, default=0,
                     help="also measure this many random programs (uniform over programs, and by "
                          "random decisions) as the search baseline")

@@ -292,9 +292,9 @@ int spmv_remote(spmv_part* part, int part_idx, double* y_dev, cudaStream_t s);
  *   paper's stream semantics (where the kernels of a stream run one after
  *   another, the default here).  Ops of one product touch common data only
  *   along DAG edges, so y is the same, bit for bit.
- * SPMV_RUN_DEFER (or-ed into CAPTURE; SPMV_EINVAL with EAGER or with
- *   SPMV_RUN_RELAXED; ignored by REPLAY) keeps the stream semantics above
- *   but lets a remote product in the sliced layout (SPMV_VARIANT_SELL)
+ * SPMV_RUN_DEFER (or-ed into CAPTURE, alone or with SPMV_RUN_RELAXED;
+ *   SPMV_EINVAL with EAGER; ignored by REPLAY) keeps the stream semantics
+ *   above but lets a remote product in the sliced layout (SPMV_VARIANT_SELL)
  *   start while the kernel before it on its stream runs, when that kernel
  *   writes none of the product's inputs but y (any op that is not the
  *   product's DAG predecessor, or its local product): the product reads

@@ -318,7 +318,10 @@ void ensure_events(spmv_part* pt, int n_streams) {
 // its own wait (kPdlEarly).  Every kernel before that one on the stream is
 // then complete, and the remote product's other predecessors are on other
 // streams, behind events whose graph edges are made full dependencies after
-// capture (fix_deferred_edges).
+// capture (fix_deferred_edges).  With the relaxed mode as well, the kernel
+// before it may not have waited (an op without DAG predecessors), but every
+// DAG edge is then an event, so the remote product's predecessors other
+// than that kernel are again behind full edges.
 int op_kind(const spmv_part* pt, int op) {
     if (pt->gran == SPMV_COARSE) return op;
     if (pt->gran == SPMV_PER_PARTITION) return op % 4;
@@ -893,7 +896,6 @@ int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream
     }
     if (flags != SPMV_RUN_EAGER && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "unknown flags %d", flags);
     if (relaxed && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "SPMV_RUN_RELAXED applies to SPMV_RUN_CAPTURE only");
-    if (relaxed && defer) fail(SPMV_EINVAL, "SPMV_RUN_RELAXED and SPMV_RUN_DEFER exclude each other");
     if (defer && flags != SPMV_RUN_CAPTURE) fail(SPMV_EINVAL, "SPMV_RUN_DEFER applies to SPMV_RUN_CAPTURE only");
     validate_schedule(pt, order, stream_of, n_ops, n_streams);
     need((x != nullptr && y != nullptr) || pt->n == 0, SPMV_EINVAL, "x_dev or y_dev is NULL");

@@ -613,8 +613,8 @@ def test_defer_mode_gives_identical_y(name, gran, local, remote):
     its local product, captured and replayed into NaN-filled y, give y
     bit-identical to the stream-ordered mode and within the oracle's bound;
     that program defers every non-empty remote product (none when the remote
-    variant is not sliced); the flag is refused for eager issue and with
-    SPMV_RUN_RELAXED."""
+    variant is not sliced); the same with SPMV_RUN_RELAXED as well; the flag
+    is refused for eager issue."""
     from paper_2203_02530_gb300 import spmv
     from paper_2203_02530_gb300 import schedules as E
     torch = torch_cuda()
@@ -656,6 +656,7 @@ def test_defer_mode_gives_identical_y(name, gran, local, remote):
         order, smap = _local_then_remote_program(part)
         check(order, smap, spmv.RUN_EAGER, 1)
         deferred = check(order, smap, spmv.RUN_CAPTURE | spmv.RUN_DEFER, 5)
+        assert check(order, smap, spmv.RUN_CAPTURE | spmv.RUN_DEFER | spmv.RUN_RELAXED, 5) == deferred
         remote_ops = sum(1 for v in range(part.n_ops)
                          if spmv.spmv_part_op_info(part.h, v)[0] == spmv.OP_REMOTE)
         if not sliced:
@@ -667,9 +668,10 @@ def test_defer_mode_gives_identical_y(name, gran, local, remote):
             order, smap = _random_schedule(dag, 1 + it % 4, rng)
             check(order, smap, spmv.RUN_CAPTURE, 1)
             total += check(order, smap, spmv.RUN_CAPTURE | spmv.RUN_DEFER, 3)
+            check(order, smap, spmv.RUN_CAPTURE | spmv.RUN_DEFER | spmv.RUN_RELAXED, 2)
         if not sliced:
             assert total == 0
-        for bad in (spmv.RUN_EAGER | spmv.RUN_DEFER, spmv.RUN_CAPTURE | spmv.RUN_RELAXED | spmv.RUN_DEFER):
+        for bad in (spmv.RUN_EAGER | spmv.RUN_DEFER, spmv.RUN_EAGER | spmv.RUN_RELAXED | spmv.RUN_DEFER):
             with pytest.raises(spmv.SpmvError) as e:
                 part.run(order, smap, streams, x_d, y_d, bad)
             assert e.value.code == spmv.EINVAL
