@@ -470,6 +470,41 @@ std::vector<T> d2h(const T* d, int64_t count) {
     return h;
 }
 
+// Stream capture gives every incoming edge of a kernel launched with
+// programmatic stream serialization the programmatic type, the edges of its
+// cross-stream event waits included (a kernel that waits at its start waits
+// for all of them alike).  A deferred remote product reads A_R and the halo
+// before its wait, so only the edge from the kernel before it on its stream
+// may stay programmatic: every other incoming edge of its node becomes a
+// full dependency (completion and memory visibility), and the result is
+// checked before the graph is instantiated.
+bool edge_is_default(const cudaGraphEdgeData& e) { return e.type == 0 && e.from_port == 0 && e.to_port == 0; }
+
+void fix_deferred_edges(const spmv_part* pt, cudaGraph_t g) {
+    const cudaGraphEdgeData full{};
+    for (const auto& dn : pt->deferred_nodes) {
+        const cudaGraphNode_t v = dn.first, u = dn.second;
+        for (int pass = 0; pass < 2; ++pass) {   // rewrite, then check
+            size_t nd = 0;
+            check_cuda(cudaGraphNodeGetDependencies(v, nullptr, nullptr, &nd), "node dependencies");
+            std::vector<cudaGraphNode_t> from(nd);
+            std::vector<cudaGraphEdgeData> ed(nd);
+            if (nd) check_cuda(cudaGraphNodeGetDependencies(v, from.data(), ed.data(), &nd), "node dependencies");
+            int from_u = 0;
+            for (size_t i = 0; i < nd; ++i) {
+                if (from[i] == u) {
+                    ++from_u;
+                } else if (!edge_is_default(ed[i])) {
+                    if (pass == 1) fail(SPMV_EINVAL, "a deferred remote product kept a programmatic edge");
+                    check_cuda(cudaGraphRemoveDependencies(g, &from[i], &v, &ed[i], 1), "remove edge");
+                    check_cuda(cudaGraphAddDependencies(g, &from[i], &v, &full, 1), "add edge");
+                }
+            }
+            if (from_u != 1) fail(SPMV_EINVAL, "a deferred remote product lost the edge from its stream predecessor");
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -840,41 +875,6 @@ int spmv_remote(spmv_part* pt, int p, double* y, cudaStream_t s) {
     pt->last_launches = op_remote(pt, p, y, s);
     API_CATCH
     return SPMV_OK;
-}
-
-// Stream capture gives every incoming edge of a kernel launched with
-// programmatic stream serialization the programmatic type, the edges of its
-// cross-stream event waits included (a kernel that waits at its start waits
-// for all of them alike).  A deferred remote product reads A_R and the halo
-// before its wait, so only the edge from the kernel before it on its stream
-// may stay programmatic: every other incoming edge of its node becomes a
-// full dependency (completion and memory visibility), and the result is
-// checked before the graph is instantiated.
-bool edge_is_default(const cudaGraphEdgeData& e) { return e.type == 0 && e.from_port == 0 && e.to_port == 0; }
-
-void fix_deferred_edges(const spmv_part* pt, cudaGraph_t g) {
-    const cudaGraphEdgeData full{};
-    for (const auto& dn : pt->deferred_nodes) {
-        const cudaGraphNode_t v = dn.first, u = dn.second;
-        for (int pass = 0; pass < 2; ++pass) {   // rewrite, then check
-            size_t nd = 0;
-            check_cuda(cudaGraphNodeGetDependencies(v, nullptr, nullptr, &nd), "node dependencies");
-            std::vector<cudaGraphNode_t> from(nd);
-            std::vector<cudaGraphEdgeData> ed(nd);
-            if (nd) check_cuda(cudaGraphNodeGetDependencies(v, from.data(), ed.data(), &nd), "node dependencies");
-            int from_u = 0;
-            for (size_t i = 0; i < nd; ++i) {
-                if (from[i] == u) {
-                    ++from_u;
-                } else if (!edge_is_default(ed[i])) {
-                    if (pass == 1) fail(SPMV_EINVAL, "a deferred remote product kept a programmatic edge");
-                    check_cuda(cudaGraphRemoveDependencies(g, &from[i], &v, &ed[i], 1), "remove edge");
-                    check_cuda(cudaGraphAddDependencies(g, &from[i], &v, &full, 1), "add edge");
-                }
-            }
-            if (from_u != 1) fail(SPMV_EINVAL, "a deferred remote product lost the edge from its stream predecessor");
-        }
-    }
 }
 
 int spmv_schedule_run(spmv_part* pt, const int32_t* order, const int32_t* stream_of, int n_ops,
