@@ -443,7 +443,9 @@ def run_ours(args, world, rank, local, fp64=None):
         if mode == "exhaustive":
             sched = search.exhaustive(part, streams, evaluate)
         elif mode == "mcts":
-            sched, _ = search.mcts(part, streams, evaluate, args.mcts_iters, seed=0)
+            # the sample budget is split over the orderings searched
+            n_modes = len(args.run_modes.split(","))
+            sched, _ = search.mcts(part, streams, evaluate, -(-args.mcts_iters // n_modes), seed=0)
             if args.random_baseline and strict:
                 cmp = {"samples": args.random_baseline}
                 mt = [r[2] for r in sched[:args.random_baseline]]
@@ -1150,11 +1152,13 @@ def main(argv=None):
     ap.add_argument("--subs", default="powerlaw,batched,serving",
                     help="with the default workload on one GPU: the other configs of the metric "
                          "measured after it and reported as sub-objects ('' for none)")
-    ap.add_argument("--sub-mcts-iters", type=int, default=500)
+    ap.add_argument("--sub-mcts-iters", type=int, default=2000,
+                    help="MCTS samples of the power-law sub-object, over all orderings searched")
     ap.add_argument("--sub-serve-seconds", type=float, default=3.0)
     ap.add_argument("--sub-cpu-seconds", type=float, default=6.0)
     ap.add_argument("--sub-measurements", type=int, default=50)
-    ap.add_argument("--mcts-iters", type=int, default=2000)
+    ap.add_argument("--mcts-iters", type=int, default=2000,
+                    help="MCTS samples of an MCTS workload, split over the orderings searched")
     ap.add_argument("--run-modes", default="strict,relaxed,relaxed+defer",
                     help="orderings searched: strict (the kernels of a stream run in order, the paper's "
                          "semantics), relaxed (DAG-only ordering, SPMV_RUN_RELAXED), defer (remote "
