@@ -15,6 +15,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 namespace spmvk {
 
 // ------------------------------------------------------------------------
@@ -368,15 +370,15 @@ static cudaError_t run_tile(const CsrArgs& a, const Tile* tiles, int tb, int te,
                             cudaStream_t s) {
     using L = TileLayout<NT / LANES, CAP>;
     const size_t smem = (size_t)ST * L::BYTES;
-    static unsigned long long configured = 0;   // one bit per device ordinal
+    static std::atomic<unsigned long long> configured{0};   // one bit per device ordinal
     int dev = 0;
     cudaError_t e0 = cudaGetDevice(&dev);
     if (e0 != cudaSuccess) return e0;
-    if (dev >= 64 || !(configured >> dev & 1ull)) {
+    if (dev >= 64 || !(configured.load(std::memory_order_acquire) >> dev & 1ull)) {
         cudaError_t e = cudaFuncSetAttribute(csr_tile_kernel<NT, CAP, ST, CH, LANES>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) configured |= 1ull << dev;
+        if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_acq_rel);
     }
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_tile_kernel<NT, CAP, ST, CH, LANES>,
@@ -621,15 +623,15 @@ template <int WARPS, int CAP, int ST, int CH>
 static cudaError_t run_warp(const CsrArgs& a, const Tile* tiles, int tb, int te, int num_sms, cudaStream_t s) {
     using L = TileLayout<32, CAP>;
     const size_t smem = (size_t)WARPS * ST * L::BYTES;
-    static unsigned long long configured = 0;
+    static std::atomic<unsigned long long> configured{0};   // one bit per device ordinal
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(configured >> dev & 1ull)) {
+    if (dev >= 64 || !(configured.load(std::memory_order_acquire) >> dev & 1ull)) {
         e = cudaFuncSetAttribute(csr_warp_kernel<WARPS, CAP, ST, CH>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) configured |= 1ull << dev;
+        if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_acq_rel);
     }
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csr_warp_kernel<WARPS, CAP, ST, CH>, WARPS * 32, smem);
