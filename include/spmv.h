@@ -342,6 +342,42 @@ int spmv_apply_host(spmv_part* part, int64_t graph_handle, const double* x_host,
  */
 int spmv_apply_host_pipelined(spmv_part* part, const double* x_host, double* y_host,
                               cudaStream_t copy_stream, cudaStream_t compute_stream);
+/*
+ * A stream of independent end-to-end products y_k = A x_k, k = 0 .. count-1,
+ * through host buffers (the host-buffer form of a batch of right-hand sides
+ * that arrive one after another; each product as in
+ * spmv_apply_host_pipelined, §III-A's four operations per product).
+ *   x_k = x_host + k * x_stride, y_k = y_host + k * y_stride (strides in
+ *   doubles, >= 0; x_stride 0 sends the same host vector every time, y_stride
+ *   0 lets every product write the same host vector, the last one's result
+ *   staying; otherwise y_stride >= n).  Host vectors should be pinned.
+ *   Overlap: the products alternate between two plan-owned pairs of device
+ *   vectors, so product k+1's x goes in while product k computes and its y
+ *   goes out: the link carries both directions at once.  Product k+1's
+ *   copies in wait until product k-1's readers of that x are done, its
+ *   products until product k-1's y has gone out, and its exchange until
+ *   product k's REMOTE products have read the receive buffer; nothing else
+ *   is shared.  Each y_k is the same, bit for bit, as
+ *   spmv_apply_host_pipelined's for x_k.
+ *   flags: SPMV_HOST_X_BLOCKS sends x rank block by rank block, each rank's
+ *   LOCAL product starting once its block is in (else x goes in one copy);
+ *   SPMV_HOST_Y_PARTS returns each rank's rows as soon as they are final, as
+ *   spmv_apply_host_pipelined does (else y comes back in one copy after the
+ *   last REMOTE product).  Both set is spmv_apply_host_pipelined's order;
+ *   every copy costs a few microseconds beyond its bytes, so in a stream of
+ *   products, where the next product's transfers already fill the link,
+ *   fewer copies can be faster.  The results do not depend on the flags.
+ *   Streams: as spmv_apply_host_pipelined (the two must differ).  Returns
+ *   after every y_k has arrived.  The second pair of device vectors (16 n
+ *   bytes) is allocated by the first call and kept with the plan.
+ *   Errors: SPMV_EINVAL (count or a stride negative, NULL host buffers,
+ *   equal streams, 0 < y_stride < n with count > 1, unknown flags),
+ *   SPMV_ENOMEM, SPMV_ECUDA.
+ */
+enum { SPMV_HOST_X_BLOCKS = 1, SPMV_HOST_Y_PARTS = 2 };
+int spmv_apply_host_many(spmv_part* part, int64_t count, const double* x_host, int64_t x_stride,
+                         double* y_host, int64_t y_stride, int flags, cudaStream_t copy_stream,
+                         cudaStream_t compute_stream);
 
 /*
  * Plain CSR product y = A x on caller-owned DEVICE arrays with the

@@ -962,19 +962,20 @@ int spmv_part_io_buffers(spmv_part* pt, double** x_out, double** y_out) {
     return SPMV_OK;
 }
 
-int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_host, cudaStream_t copy_stream,
-                              cudaStream_t compute_stream) {
-    API_TRY
-    check_part(pt);
-    need(pt->n == 0 || (x_host && y_host), SPMV_EINVAL, "host buffer is NULL");
-    need(copy_stream != compute_stream, SPMV_EINVAL, "the copy and compute streams must differ");
-    if (pt->n == 0) return SPMV_OK;
+namespace {
+
+// The host path's streams, events and per-rank remote-free runs, made once
+// per plan.  Events: 3P+1 used within one product (x block p arrived; LOCAL
+// p done; REMOTE p done; exchange done), then per device buffer pair s of
+// the streamed path: x_s free (its readers are done), y_s free (its copies
+// out are done).
+void host_path_setup(spmv_part* pt) {
+    const int P = pt->P;
     if (!pt->io_x) {
         pt->io_x = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
         pt->io_y = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
     }
-    const int P = pt->P;
-    while ((int)pt->io_ev.size() < 3 * P + 1) {
+    while ((int)pt->io_ev.size() < 3 * P + 5) {
         cudaEvent_t e;
         check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         pt->io_ev.push_back(e);
@@ -982,7 +983,6 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
     if (!pt->io_out) check_cuda(cudaStreamCreateWithFlags(&pt->io_out, cudaStreamNonBlocking), "stream");
     if (!pt->io_alt) check_cuda(cudaStreamCreateWithFlags(&pt->io_alt, cudaStreamNonBlocking), "stream");
     if (!pt->io_aux) check_cuda(cudaStreamCreateWithFlags(&pt->io_aux, cudaStreamNonBlocking), "stream");
-    cudaStream_t out_stream = pt->io_out;
     if (pt->io_free.empty()) {   // once per plan: the remote-free run of every rank
         std::vector<int32_t> rr((size_t)pt->n_rr);
         if (pt->n_rr)
@@ -1000,59 +1000,158 @@ int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_hos
             pt->io_free.push_back({best_a, best_b});
         }
     }
+}
+
+// One product y_host = A x_host through the device vectors xd / yd,
+// transfers overlapped with the products (the order is described at
+// spmv_apply_host_pipelined).  Nothing waits on the host.  With slot >= 0
+// the product is one of a stream of products on two pairs of device vectors:
+// its copies in wait until the readers of the same pair's previous x are
+// done, its products until the same pair's previous y has gone out, and its
+// exchange until the previous product's REMOTE products have read the
+// receive buffer (the only other buffers products share).
+//   x_blocks: x goes in rank block by rank block (else in one copy, after
+//   which every LOCAL product may start); y_parts: each rank's rows go out as
+//   soon as they are final (else y goes out in one copy after the last
+//   REMOTE product).  A copy costs a few microseconds beyond its bytes, so
+//   fewer, larger copies suit a stream of products, where the next
+//   product's transfers hide the latency that the pieces shorten.
+int64_t host_product(spmv_part* pt, const double* x_host, double* y_host, double* xd, double* yd,
+                     cudaStream_t copy_stream, cudaStream_t compute_stream, int slot, bool x_blocks,
+                     bool y_parts) {
+    const int P = pt->P;
+    cudaStream_t out_stream = pt->io_out;
+    cudaEvent_t* ev = pt->io_ev.data();
+    cudaEvent_t x_free = slot >= 0 ? ev[3 * P + 1 + slot] : nullptr;
+    cudaEvent_t y_free = slot >= 0 ? ev[3 * P + 3 + slot] : nullptr;
     // x block by block on the copy stream; rank p's LOCAL product starts as
     // soon as its block has arrived (it reads no other x).  Every copy in is
-    // issued before any wait, so that streams sharing a hardware queue never
-    // hold a copy behind a wait.
+    // issued before any wait on another stream, so that streams sharing a
+    // hardware queue never hold a copy behind a wait.
     int64_t launches = 0;
-    for (int p = 0; p < P; ++p) {
-        const int64_t r0 = pt->bounds[p], r1 = pt->bounds[p + 1];
-        if (r1 > r0)
-            check_cuda(cudaMemcpyAsync(pt->io_x + r0, x_host + r0, (size_t)(r1 - r0) * sizeof(double),
-                                       cudaMemcpyHostToDevice, copy_stream),
-                       "copy x in");
-        check_cuda(cudaEventRecord(pt->io_ev[p], copy_stream), "event");
+    if (x_free) check_cuda(cudaStreamWaitEvent(copy_stream, x_free, 0), "wait");
+    if (x_blocks) {
+        for (int p = 0; p < P; ++p) {
+            const int64_t r0 = pt->bounds[p], r1 = pt->bounds[p + 1];
+            if (r1 > r0)
+                check_cuda(cudaMemcpyAsync(xd + r0, x_host + r0, (size_t)(r1 - r0) * sizeof(double),
+                                           cudaMemcpyHostToDevice, copy_stream),
+                           "copy x in");
+            check_cuda(cudaEventRecord(ev[p], copy_stream), "event");
+        }
+    } else {
+        check_cuda(cudaMemcpyAsync(xd, x_host, (size_t)pt->n * sizeof(double), cudaMemcpyHostToDevice,
+                                   copy_stream),
+                   "copy x in");
+        check_cuda(cudaEventRecord(ev[P - 1], copy_stream), "event");
     }
+    auto x_arrived = [&](int p) { return ev[x_blocks ? p : P - 1]; };
     // y goes out on a stream of its own, so that it overlaps the copies in.
     // Each copy out is issued right after the product that finishes its rows,
     // so that it is queued before the host is through issuing the rest.
     auto copy_out = [&](int64_t a, int64_t b) {
-        if (b > a)
-            check_cuda(cudaMemcpyAsync(y_host + a, pt->io_y + a, (size_t)(b - a) * sizeof(double),
+        if (b > a && y_parts)
+            check_cuda(cudaMemcpyAsync(y_host + a, yd + a, (size_t)(b - a) * sizeof(double),
                                        cudaMemcpyDeviceToHost, out_stream),
                        "copy y out");
     };
+    if (y_free) {
+        check_cuda(cudaStreamWaitEvent(compute_stream, y_free, 0), "wait");
+        check_cuda(cudaStreamWaitEvent(pt->io_alt, y_free, 0), "wait");
+    }
     // The LOCAL products (and later the REMOTE products) alternate between
     // compute_stream and a second stream, so that one rank's launch fills the
     // SMs the previous one leaves idle at its tail.  A rank's remote-free run
     // is final after its LOCAL product.
     for (int p = 0; p < P; ++p) {
         cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
-        check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[p], 0), "wait");
-        launches += op_local(pt, p, pt->io_x, pt->io_y, cs);
-        check_cuda(cudaEventRecord(pt->io_ev[P + p], cs), "event");
-        check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[P + p], 0), "wait");
-        copy_out(pt->io_free[p].first, pt->io_free[p].second);
+        check_cuda(cudaStreamWaitEvent(cs, x_arrived(p), 0), "wait");
+        launches += op_local(pt, p, xd, yd, cs);
+        check_cuda(cudaEventRecord(ev[P + p], cs), "event");
+        if (y_parts) {
+            check_cuda(cudaStreamWaitEvent(out_stream, ev[P + p], 0), "wait");
+            copy_out(pt->io_free[p].first, pt->io_free[p].second);
+        }
     }
     // pack and exchange need all of x: on a third stream as soon as the last
-    // block has arrived, beside the LOCAL products
-    check_cuda(cudaStreamWaitEvent(pt->io_aux, pt->io_ev[P - 1], 0), "wait");
-    launches += op_pack(pt, -1, pt->io_x, pt->io_aux);
+    // block has arrived, beside the LOCAL products.  In a stream of products
+    // the exchange first waits for the previous product's REMOTE products
+    // (the events still hold their last records).
+    check_cuda(cudaStreamWaitEvent(pt->io_aux, ev[P - 1], 0), "wait");
+    launches += op_pack(pt, -1, xd, pt->io_aux);
+    if (slot >= 0)
+        for (int p = 0; p < P; ++p) check_cuda(cudaStreamWaitEvent(pt->io_aux, ev[2 * P + p], 0), "wait");
     launches += op_copy(pt, -1, pt->io_aux);
-    check_cuda(cudaEventRecord(pt->io_ev[3 * P], pt->io_aux), "event");
+    check_cuda(cudaEventRecord(ev[3 * P], pt->io_aux), "event");
+    if (x_free) {   // x_s is free once the pack and every LOCAL product are done
+        for (int p = 0; p < P; ++p) check_cuda(cudaStreamWaitEvent(pt->io_aux, ev[P + p], 0), "wait");
+        check_cuda(cudaEventRecord(x_free, pt->io_aux), "event");
+    }
     // the remote products rank by rank, each after its own LOCAL product (on
     // the same stream) and the exchange; a rank's other rows go out after its
     // REMOTE product, while the later ranks' products run
     for (int p = 0; p < P; ++p) {
         cudaStream_t cs = (p & 1) ? pt->io_alt : compute_stream;
-        check_cuda(cudaStreamWaitEvent(cs, pt->io_ev[3 * P], 0), "wait");
-        launches += op_remote(pt, p, pt->io_y, cs);
-        check_cuda(cudaEventRecord(pt->io_ev[2 * P + p], cs), "event");
-        check_cuda(cudaStreamWaitEvent(out_stream, pt->io_ev[2 * P + p], 0), "wait");
+        check_cuda(cudaStreamWaitEvent(cs, ev[3 * P], 0), "wait");
+        launches += op_remote(pt, p, yd, cs);
+        check_cuda(cudaEventRecord(ev[2 * P + p], cs), "event");
+        check_cuda(cudaStreamWaitEvent(out_stream, ev[2 * P + p], 0), "wait");
         copy_out(pt->bounds[p], pt->io_free[p].first);
         copy_out(pt->io_free[p].second, pt->bounds[p + 1]);
     }
-    check_cuda(cudaStreamSynchronize(out_stream), "synchronize");   // after every REMOTE, so after all work
+    if (!y_parts)   // every rank's REMOTE product (after its LOCAL one) is done
+        check_cuda(cudaMemcpyAsync(y_host, yd, (size_t)pt->n * sizeof(double), cudaMemcpyDeviceToHost,
+                                   out_stream),
+                   "copy y out");
+    if (y_free) check_cuda(cudaEventRecord(y_free, out_stream), "event");
+    return launches;
+}
+
+}  // namespace
+
+int spmv_apply_host_pipelined(spmv_part* pt, const double* x_host, double* y_host, cudaStream_t copy_stream,
+                              cudaStream_t compute_stream) {
+    API_TRY
+    check_part(pt);
+    need(pt->n == 0 || (x_host && y_host), SPMV_EINVAL, "host buffer is NULL");
+    need(copy_stream != compute_stream, SPMV_EINVAL, "the copy and compute streams must differ");
+    if (pt->n == 0) return SPMV_OK;
+    host_path_setup(pt);
+    const int64_t launches =
+        host_product(pt, x_host, y_host, pt->io_x, pt->io_y, copy_stream, compute_stream, -1, true, true);
+    check_cuda(cudaStreamSynchronize(pt->io_out), "synchronize");   // after every REMOTE, so after all work
+    check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
+    pt->last_launches = launches;
+    API_CATCH
+    return SPMV_OK;
+}
+
+int spmv_apply_host_many(spmv_part* pt, int64_t count, const double* x_host, int64_t x_stride, double* y_host,
+                         int64_t y_stride, int flags, cudaStream_t copy_stream, cudaStream_t compute_stream) {
+    API_TRY
+    check_part(pt);
+    if (flags & ~(SPMV_HOST_X_BLOCKS | SPMV_HOST_Y_PARTS)) fail(SPMV_EINVAL, "unknown flags %d", flags);
+    if (count < 0) fail(SPMV_EINVAL, "count = %lld < 0", (long long)count);
+    need(x_stride >= 0 && y_stride >= 0, SPMV_EINVAL, "negative stride");
+    need(pt->n == 0 || count == 0 || (x_host && y_host), SPMV_EINVAL, "host buffer is NULL");
+    need(copy_stream != compute_stream, SPMV_EINVAL, "the copy and compute streams must differ");
+    if (count >= 2 && y_stride != 0 && y_stride < pt->n)
+        fail(SPMV_EINVAL, "y_stride %lld overlaps the results of consecutive products", (long long)y_stride);
+    if (pt->n == 0 || count == 0) return SPMV_OK;
+    host_path_setup(pt);
+    if (!pt->io_x2) {
+        pt->io_x2 = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
+        pt->io_y2 = static_cast<double*>(spmvk::dev_alloc(pt, (size_t)pt->n * sizeof(double)));
+    }
+    int64_t launches = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        const int slot = (int)(k & 1);
+        launches += host_product(pt, x_host + k * x_stride, y_host + k * y_stride, slot ? pt->io_x2 : pt->io_x,
+                                 slot ? pt->io_y2 : pt->io_y, copy_stream, compute_stream, slot,
+                                 (flags & SPMV_HOST_X_BLOCKS) != 0, (flags & SPMV_HOST_Y_PARTS) != 0);
+    }
+    check_cuda(cudaStreamSynchronize(pt->io_out), "synchronize");   // after every REMOTE, so after all work
+    check_cuda(cudaStreamSynchronize(pt->io_aux), "synchronize");
     check_cuda(cudaStreamSynchronize(copy_stream), "synchronize");
     pt->last_launches = launches;
     API_CATCH

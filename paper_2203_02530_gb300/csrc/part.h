@@ -75,7 +75,10 @@ struct spmv_part {
     int* err = nullptr;               // device error word
     double* io_x = nullptr;           // plan-owned x / y for the host-buffer path
     double* io_y = nullptr;
-    std::vector<cudaEvent_t> io_ev;   // 3P+1: x block p arrived; LOCAL p done; REMOTE p done; exchange done
+    double* io_x2 = nullptr;          // the second x / y pair of the streamed host path
+    double* io_y2 = nullptr;
+    std::vector<cudaEvent_t> io_ev;   // 3P+1: x block p arrived; LOCAL p done; REMOTE p done; exchange done;
+                                      // then x free and y free per pair of the streamed host path
     cudaStream_t io_out = nullptr;    // the host path's copies of y out
     cudaStream_t io_alt = nullptr;    // the host path's second stream for LOCAL / REMOTE products
     cudaStream_t io_aux = nullptr;    // the host path's stream for pack and exchange

@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESCHED, EBOUNDS, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 OP_PACK, OP_LOCAL, OP_COPY, OP_REMOTE = 0, 1, 2, 3
 COARSE, PER_PARTITION, PER_SEGMENT = 0, 1, 2
 RUN_EAGER, RUN_CAPTURE, RUN_REPLAY, RUN_RELAXED, RUN_DEFER = 0, 1, 2, 4, 8
+HOST_X_BLOCKS, HOST_Y_PARTS = 1, 2
 VARIANT_TILE, VARIANT_VECTOR, VARIANT_MERGE, VARIANT_PAIRS, VARIANT_WARP, VARIANT_SELL, VARIANT_SELL16 = (
     0, 1, 2, 3, 4, 5, 6)
 SERVE_BATCHED, SERVE_PLAIN = 0, 1
@@ -80,6 +81,7 @@ def _load():
         "spmv_part_io_buffers": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
         "spmv_apply_host": [vp, i64, vp, vp, vp],
         "spmv_apply_host_pipelined": [vp, vp, vp, vp, vp],
+        "spmv_apply_host_many": [vp, i64, vp, i64, vp, i64, i32, vp, vp],
         "spmv_csr_merge": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_merge_noalloc": [i64, i64, vp, vp, vp, vp, vp, vp],
         "spmv_csr_error": [P64],
@@ -249,6 +251,14 @@ def spmv_apply_host(h, graph_handle, x_host, y_host, stream):
 def spmv_apply_host_pipelined(h, x_host, y_host, copy_stream, compute_stream):
     _check(lib.spmv_apply_host_pipelined(h, _ptr(x_host), _ptr(y_host), _stream(copy_stream),
                                          _stream(compute_stream)))
+
+
+def spmv_apply_host_many(h, count, x_host, x_stride, y_host, y_stride, flags, copy_stream, compute_stream):
+    """count independent products through host buffers, consecutive ones
+    overlapped (strides in doubles; 0 reuses the same host vector; flags
+    HOST_X_BLOCKS / HOST_Y_PARTS choose the copies' granularity)."""
+    _check(lib.spmv_apply_host_many(h, int(count), _ptr(x_host), int(x_stride), _ptr(y_host),
+                                    int(y_stride), int(flags), _stream(copy_stream), _stream(compute_stream)))
 
 
 def spmv_csr_merge(n, nnz, row_ptr_dev, col_idx_dev, vals_dev, x_dev, y_dev, stream):

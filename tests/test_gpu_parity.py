@@ -854,6 +854,53 @@ def test_apply_host_pipelined_matches_graph_path(name, variant):
             spmv.spmv_apply_host_pipelined(part.h, xh, y2, s, s)
 
 
+@pytest.mark.parametrize("name,variant", [("st27_ragged", ("sell", 9)), ("powerlaw", ("sell", 4)),
+                                          ("tiny_P_gt_n", ("vector", 2)), ("empty_rows", ("tile", 0))])
+def test_apply_host_many_matches_single_products(name, variant):
+    """A stream of independent products through host buffers, consecutive
+    ones overlapped on two pairs of device vectors: every y_k equals the
+    single pipelined product of x_k bit for bit, whether the host vectors
+    are distinct or shared, and over two calls in a row."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    n, rp, ci, va, P, x = case(name)
+    count = 5
+    rng = np.random.default_rng(11)
+    xs = np.stack([x] + [rng.uniform(-1, 1, n) for _ in range(count - 1)])
+    s, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with make_part(n, rp, ci, va, P) as part:
+        set_variant(part, variant)
+        m = max(n, 1)
+        xh = torch.zeros((count, m), dtype=torch.float64).pin_memory()
+        xh[:, :n] = torch.from_numpy(xs)
+        want = []
+        y1 = torch.empty(m, dtype=torch.float64).pin_memory()
+        for k in range(count):
+            spmv.spmv_apply_host_pipelined(part.h, xh[k], y1, s, s2)
+            want.append(y1.numpy()[:n].copy())
+        ref0, scale0 = reference(n, rp, ci, va, x)
+        assert_fp64_close(want[0], ref0, scale0, "pipelined host path")
+        for flags in [0, spmv.HOST_X_BLOCKS, spmv.HOST_Y_PARTS, spmv.HOST_X_BLOCKS | spmv.HOST_Y_PARTS, 0]:
+            yh = torch.full((count, m), float("nan"), dtype=torch.float64).pin_memory()
+            spmv.spmv_apply_host_many(part.h, count, xh, m, yh, m, flags, s, s2)
+            for k in range(count):
+                assert np.array_equal(yh[k].numpy()[:n].view(np.uint64), want[k].view(np.uint64)), (flags, k)
+        # shared host vectors: the same x every time, every y into one vector
+        ys = torch.full((m,), float("nan"), dtype=torch.float64).pin_memory()
+        spmv.spmv_apply_host_many(part.h, count, xh[2], 0, ys, 0, 0, s, s2)
+        assert np.array_equal(ys.numpy()[:n].view(np.uint64), want[2].view(np.uint64))
+        spmv.spmv_apply_host_many(part.h, 0, None, 0, None, 0, 0, s, s2)
+        for bad in [dict(count=-1), dict(x_stride=-1), dict(copy=s2), dict(flags=4)]:
+            with pytest.raises(spmv.SpmvError) as e:
+                spmv.spmv_apply_host_many(part.h, bad.get("count", 2), xh, bad.get("x_stride", m), yh, m,
+                                          bad.get("flags", 0), bad.get("copy", s), s2)
+            assert e.value.code == spmv.EINVAL
+        if n > 1:
+            with pytest.raises(spmv.SpmvError) as e:
+                spmv.spmv_apply_host_many(part.h, 2, xh, m, yh, 1, 0, s, s2)
+            assert e.value.code == spmv.EINVAL
+
+
 # ------------------------------------------------------------------ full sizes
 def test_full_size_27pt_150_all_schedules():
     """The 3-D 27-point stencil on 150^3 (n = 3 375 000, 89 915 392 entries),
