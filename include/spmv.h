@@ -487,6 +487,22 @@ int spmv_batch_run(spmv_batch* batch, const double* x_dev, double* y_dev, cudaSt
  * arrived.  Uses batch-owned device vectors (allocated on first use). */
 int spmv_batch_run_host(spmv_batch* batch, const double* x_host, double* y_host, int chunks,
                         cudaStream_t s_in, cudaStream_t s_compute, cudaStream_t s_out);
+/* A stream of independent batched products through host buffers: product
+ * k reads x_host + k * x_stride and writes y_host + k * y_stride (strides in
+ * doubles over the batch's concatenated rows, >= 0; 0 reuses one host
+ * vector, the last product's y staying; otherwise y_stride >= the total
+ * rows), each in `chunks` chunks as spmv_batch_run_host.  Consecutive
+ * products alternate between two batch-owned pairs of device vectors, so
+ * product k+1's x goes in while product k computes and its y comes back;
+ * product k+1's copies in wait for the products that read that pair's x
+ * (product k-1), its products for that pair's y to have gone out.  Each y_k
+ * is bit for bit spmv_batch_run_host's.  Returns after every y_k arrived.
+ * Errors: SPMV_EINVAL (negative count or stride, NULL host buffers, chunks
+ * outside [1, 64], equal streams, overlapping y strides), SPMV_ENOMEM,
+ * SPMV_ECUDA. */
+int spmv_batch_run_host_many(spmv_batch* batch, int64_t count, const double* x_host, int64_t x_stride,
+                             double* y_host, int64_t y_stride, int chunks, cudaStream_t s_in,
+                             cudaStream_t s_compute, cudaStream_t s_out);
 /* Release the batch's CSR copy once every matrix uses the sliced layout
  * (SPMV_BATCH_SLICED), which is a second copy of every entry: only the rows
  * longer than 64 entries (which the sliced products, batched and served,

@@ -889,6 +889,102 @@ BatchArgs args_of(spmv_batch* b, const double* x, double* y) {
         return bfail(SPMV_EINVAL, "unexpected exception");                      \
     }
 
+namespace {
+
+// The host-buffer path's device vectors and events, made on first use:
+// 2 events per chunk (x arrived, y computed), then x free and y free for each
+// pair of device vectors of the streamed path.
+void batch_host_setup(spmv_batch* b) {
+    if (!b->io_x) {
+        b->io_x = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
+        b->io_y = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
+        b->io_tickets = static_cast<int*>(balloc(b, 4 * 64 * sizeof(int)));
+    }
+    while ((int)b->io_ev.size() < 2 * 64 + 4) {
+        cudaEvent_t e;
+        spmvk::check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        b->io_ev.push_back(e);
+    }
+}
+
+// One batched product through host buffers and the device vectors xd / yd,
+// nothing waited for on the host.  With slot >= 0 it is one of a stream of
+// products on two pairs of device vectors: its copies in wait until the
+// products that read the same pair's previous x are done, and its products
+// until the same pair's previous y has gone out (all products run on
+// s_compute, so the chunk tickets are reset after the previous product).
+void batch_host_product(spmv_batch* b, const double* x_host, double* y_host, double* xd, double* yd, int chunks,
+                        cudaStream_t s_in, cudaStream_t s_compute, cudaStream_t s_out, int slot) {
+    cudaEvent_t x_free = slot >= 0 ? b->io_ev[2 * 64 + slot] : nullptr;
+    cudaEvent_t y_free = slot >= 0 ? b->io_ev[2 * 64 + 2 + slot] : nullptr;
+    // chunks of whole matrices with about equal rows: x of chunk c goes in
+    // on s_in, its products run on s_compute once it has arrived, and its y
+    // goes back on s_out while later chunks are still moving or computing.
+    // Issued phase by phase (all copies in, all products, all copies out) so
+    // that streams sharing a hardware queue never hold a copy behind a wait.
+    const BatchArgs a = args_of(b, xd, yd);
+    struct Chunk {
+        int m0, m1;
+        long long r0, r1;
+    };
+    std::vector<Chunk> ch;
+    for (int c = 0, m0 = 0; c < chunks && m0 < b->count; ++c) {
+        const long long target = b->total_rows * (long long)(c + 1) / chunks;
+        int m1 = m0 + 1;
+        while (m1 < b->count && b->mats[m1 - 1].row_off + b->n[m1 - 1] < target) ++m1;
+        if (c == chunks - 1) m1 = b->count;
+        ch.push_back(Chunk{m0, m1, b->mats[m0].row_off, b->mats[m1 - 1].row_off + b->n[m1 - 1]});
+        m0 = m1;
+    }
+    if (x_free) spmvk::check_cuda(cudaStreamWaitEvent(s_in, x_free, 0), "wait");
+    for (size_t c = 0; c < ch.size(); ++c) {
+        if (ch[c].r1 > ch[c].r0)
+            spmvk::check_cuda(cudaMemcpyAsync(xd + ch[c].r0, x_host + ch[c].r0,
+                                              (size_t)(ch[c].r1 - ch[c].r0) * sizeof(double),
+                                              cudaMemcpyHostToDevice, s_in),
+                              "copy x in");
+        spmvk::check_cuda(cudaEventRecord(b->io_ev[2 * c], s_in), "event");
+    }
+    // each chunk's items are a contiguous run of the claim order (per
+    // layout), run by the persistent kernels with a ticket of their own
+    if (y_free) spmvk::check_cuda(cudaStreamWaitEvent(s_compute, y_free, 0), "wait");
+    spmvk::check_cuda(cudaMemsetAsync(b->io_tickets, 0, (size_t)4 * ch.size() * sizeof(int), s_compute),
+                      "chunk tickets");
+    const int cp1 = b->count + 1;
+    for (size_t c = 0; c < ch.size(); ++c) {
+        spmvk::check_cuda(cudaStreamWaitEvent(s_compute, b->io_ev[2 * c], 0), "wait");
+        for (int part = 0; part < 2; ++part) {
+            const int o0 = b->order_off[part * cp1 + ch[c].m0], o1 = b->order_off[part * cp1 + ch[c].m1];
+            if (o1 <= o0) continue;
+            BatchArgs pa = a;
+            pa.order = b->d_order + o0;
+            pa.n_items = o1 - o0;
+            pa.ticket = b->io_tickets + 4 * c + 2 * part;
+            int grid = b->num_sms * std::max(1, part == 0 ? b->occupancy_sliced : b->occupancy);
+            const int need = (o1 - o0 + kThreads / 32 - 1) / (kThreads / 32);
+            if (grid > need) grid = need;
+            if (part == 0)
+                batch_sliced_persistent_kernel<<<grid, kThreads, 0, s_compute>>>(pa);
+            else
+                batch_persistent_kernel<<<grid, kThreads, 0, s_compute>>>(pa);
+            spmvk::check_cuda(cudaGetLastError(), "chunk launch");
+        }
+        spmvk::check_cuda(cudaEventRecord(b->io_ev[2 * c + 1], s_compute), "event");
+    }
+    if (x_free) spmvk::check_cuda(cudaEventRecord(x_free, s_compute), "event");
+    for (size_t c = 0; c < ch.size(); ++c) {
+        spmvk::check_cuda(cudaStreamWaitEvent(s_out, b->io_ev[2 * c + 1], 0), "wait");
+        if (ch[c].r1 > ch[c].r0)
+            spmvk::check_cuda(cudaMemcpyAsync(y_host + ch[c].r0, yd + ch[c].r0,
+                                              (size_t)(ch[c].r1 - ch[c].r0) * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s_out),
+                              "copy y out");
+    }
+    if (y_free) spmvk::check_cuda(cudaEventRecord(y_free, s_out), "event");
+}
+
+}  // namespace
+
 extern "C" {
 
 int spmv_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr,
@@ -1089,77 +1185,39 @@ int spmv_batch_run_host(spmv_batch* b, const double* x_host, double* y_host, int
     if (chunks < 1 || chunks > 64) spmvk::fail(SPMV_EINVAL, "chunks = %d not in [1, 64]", chunks);
     if (s_in == s_compute || s_out == s_compute || s_in == s_out) spmvk::fail(SPMV_EINVAL, "the streams must differ");
     if (b->total_rows == 0) return SPMV_OK;
-    if (!b->io_x) {
-        b->io_x = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
-        b->io_y = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
-        b->io_tickets = static_cast<int*>(balloc(b, 4 * 64 * sizeof(int)));
+    batch_host_setup(b);
+    batch_host_product(b, x_host, y_host, b->io_x, b->io_y, chunks, s_in, s_compute, s_out, -1);
+    spmvk::check_cuda(cudaStreamSynchronize(s_out), "synchronize");
+    BATCH_CATCH
+    return SPMV_OK;
+}
+
+int spmv_batch_run_host_many(spmv_batch* b, int64_t count, const double* x_host, int64_t x_stride, double* y_host,
+                             int64_t y_stride, int chunks, cudaStream_t s_in, cudaStream_t s_compute,
+                             cudaStream_t s_out) {
+    BATCH_TRY
+    if (!b) spmvk::fail(SPMV_EINVAL, "batch is NULL");
+    if (count < 0) spmvk::fail(SPMV_EINVAL, "count = %lld < 0", (long long)count);
+    if (x_stride < 0 || y_stride < 0) spmvk::fail(SPMV_EINVAL, "negative stride");
+    if (b->total_rows > 0 && count > 0 && (!x_host || !y_host)) spmvk::fail(SPMV_EINVAL, "host buffer is NULL");
+    if (chunks < 1 || chunks > 64) spmvk::fail(SPMV_EINVAL, "chunks = %d not in [1, 64]", chunks);
+    if (s_in == s_compute || s_out == s_compute || s_in == s_out) spmvk::fail(SPMV_EINVAL, "the streams must differ");
+    if (count >= 2 && y_stride != 0 && y_stride < b->total_rows)
+        spmvk::fail(SPMV_EINVAL, "y_stride %lld overlaps the results of consecutive products", (long long)y_stride);
+    if (b->total_rows == 0 || count == 0) return SPMV_OK;
+    batch_host_setup(b);
+    if (!b->io_x2) {
+        b->io_x2 = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
+        b->io_y2 = static_cast<double*>(balloc(b, (size_t)b->total_rows * sizeof(double)));
     }
-    while ((int)b->io_ev.size() < 2 * chunks) {
-        cudaEvent_t e;
-        spmvk::check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
-        b->io_ev.push_back(e);
-    }
-    // chunks of whole matrices with about equal rows: x of chunk c goes in
-    // on s_in, its products run on s_compute once it has arrived, and its y
-    // goes back on s_out while later chunks are still moving or computing.
-    // Issued phase by phase (all copies in, all products, all copies out) so
-    // that streams sharing a hardware queue never hold a copy behind a wait.
-    const BatchArgs a = args_of(b, b->io_x, b->io_y);
-    struct Chunk {
-        int m0, m1;
-        long long r0, r1;
-    };
-    std::vector<Chunk> ch;
-    for (int c = 0, m0 = 0; c < chunks && m0 < b->count; ++c) {
-        const long long target = b->total_rows * (long long)(c + 1) / chunks;
-        int m1 = m0 + 1;
-        while (m1 < b->count && b->mats[m1 - 1].row_off + b->n[m1 - 1] < target) ++m1;
-        if (c == chunks - 1) m1 = b->count;
-        ch.push_back(Chunk{m0, m1, b->mats[m0].row_off, b->mats[m1 - 1].row_off + b->n[m1 - 1]});
-        m0 = m1;
-    }
-    for (size_t c = 0; c < ch.size(); ++c) {
-        if (ch[c].r1 > ch[c].r0)
-            spmvk::check_cuda(cudaMemcpyAsync(b->io_x + ch[c].r0, x_host + ch[c].r0,
-                                              (size_t)(ch[c].r1 - ch[c].r0) * sizeof(double),
-                                              cudaMemcpyHostToDevice, s_in),
-                              "copy x in");
-        spmvk::check_cuda(cudaEventRecord(b->io_ev[2 * c], s_in), "event");
-    }
-    // each chunk's items are a contiguous run of the claim order (per
-    // layout), run by the persistent kernels with a ticket of their own
-    spmvk::check_cuda(cudaMemsetAsync(b->io_tickets, 0, (size_t)4 * ch.size() * sizeof(int), s_compute),
-                      "chunk tickets");
-    const int cp1 = b->count + 1;
-    for (size_t c = 0; c < ch.size(); ++c) {
-        spmvk::check_cuda(cudaStreamWaitEvent(s_compute, b->io_ev[2 * c], 0), "wait");
-        for (int part = 0; part < 2; ++part) {
-            const int o0 = b->order_off[part * cp1 + ch[c].m0], o1 = b->order_off[part * cp1 + ch[c].m1];
-            if (o1 <= o0) continue;
-            BatchArgs pa = a;
-            pa.order = b->d_order + o0;
-            pa.n_items = o1 - o0;
-            pa.ticket = b->io_tickets + 4 * c + 2 * part;
-            int grid = b->num_sms * std::max(1, part == 0 ? b->occupancy_sliced : b->occupancy);
-            const int need = (o1 - o0 + kThreads / 32 - 1) / (kThreads / 32);
-            if (grid > need) grid = need;
-            if (part == 0)
-                batch_sliced_persistent_kernel<<<grid, kThreads, 0, s_compute>>>(pa);
-            else
-                batch_persistent_kernel<<<grid, kThreads, 0, s_compute>>>(pa);
-            spmvk::check_cuda(cudaGetLastError(), "chunk launch");
-        }
-        spmvk::check_cuda(cudaEventRecord(b->io_ev[2 * c + 1], s_compute), "event");
-    }
-    for (size_t c = 0; c < ch.size(); ++c) {
-        spmvk::check_cuda(cudaStreamWaitEvent(s_out, b->io_ev[2 * c + 1], 0), "wait");
-        if (ch[c].r1 > ch[c].r0)
-            spmvk::check_cuda(cudaMemcpyAsync(y_host + ch[c].r0, b->io_y + ch[c].r0,
-                                              (size_t)(ch[c].r1 - ch[c].r0) * sizeof(double),
-                                              cudaMemcpyDeviceToHost, s_out),
-                              "copy y out");
+    for (int64_t k = 0; k < count; ++k) {
+        const int slot = (int)(k & 1);
+        batch_host_product(b, x_host + k * x_stride, y_host + k * y_stride, slot ? b->io_x2 : b->io_x,
+                           slot ? b->io_y2 : b->io_y, chunks, s_in, s_compute, s_out, slot);
     }
     spmvk::check_cuda(cudaStreamSynchronize(s_out), "synchronize");
+    spmvk::check_cuda(cudaStreamSynchronize(s_compute), "synchronize");
+    spmvk::check_cuda(cudaStreamSynchronize(s_in), "synchronize");
     BATCH_CATCH
     return SPMV_OK;
 }

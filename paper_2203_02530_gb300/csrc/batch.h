@@ -70,7 +70,9 @@ struct spmv_batch {
     int* ticket = nullptr;
     double* io_x = nullptr;              // device vectors of the host-buffer path (built on first use)
     double* io_y = nullptr;
-    std::vector<cudaEvent_t> io_ev;      // per chunk: x arrived, y computed
+    double* io_x2 = nullptr;             // the second pair of the streamed host-buffer path
+    double* io_y2 = nullptr;
+    std::vector<cudaEvent_t> io_ev;      // per chunk (64): x arrived, y computed; then x free, y free per pair
     int* io_tickets = nullptr;           // per chunk: a ticket per layout (4 ints)
     std::vector<int> order_off;          // 2 x (count+1): start of matrix m's items in each part of `order`
     int n_items = 0;

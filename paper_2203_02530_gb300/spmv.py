@@ -93,6 +93,7 @@ def _load():
         "spmv_batch_run_separate": [vp, i32, vp, vp, vp],
         "spmv_batch_release_csr": [vp],
         "spmv_batch_run_host": [vp, vp, vp, i32, vp, vp, vp],
+        "spmv_batch_run_host_many": [vp, i64, vp, i64, vp, i64, i32, vp, vp, vp],
         "spmv_serve_create": [vp, i32, i64, ctypes.POINTER(vp)],
         "spmv_serve_destroy": [vp],
         "spmv_serve_run": [vp, i64, vp, vp, vp, vp, i32, vp, vp, vp],
@@ -425,6 +426,13 @@ def spmv_batch_run(h, x_dev, y_dev, stream):
 def spmv_batch_run_host(h, x_host, y_host, chunks, s_in, s_compute, s_out):
     _check(lib.spmv_batch_run_host(h, _ptr(x_host), _ptr(y_host), int(chunks), _stream(s_in),
                                    _stream(s_compute), _stream(s_out)))
+
+
+def spmv_batch_run_host_many(h, count, x_host, x_stride, y_host, y_stride, chunks, s_in, s_compute, s_out):
+    """count independent batched products through host buffers, consecutive
+    ones overlapped (strides in doubles; 0 reuses the same host vector)."""
+    _check(lib.spmv_batch_run_host_many(h, int(count), _ptr(x_host), int(x_stride), _ptr(y_host), int(y_stride),
+                                        int(chunks), _stream(s_in), _stream(s_compute), _stream(s_out)))
 
 
 def spmv_batch_release_csr(h):

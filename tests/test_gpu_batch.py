@@ -148,6 +148,44 @@ def test_batch_run_host_matches_device_run(chunks):
             spmv.spmv_batch_run_host(b.h, xh, yh, 0, s_in, s_c, s_out)
 
 
+@pytest.mark.parametrize("chunks", [1, 5])
+def test_batch_run_host_many_matches_single_runs(chunks):
+    """A stream of batched products through host buffers, consecutive ones
+    overlapped on two pairs of device vectors: each y_k equals the chunked
+    host-buffer run of x_k bit for bit, with distinct and with shared host
+    vectors, in both layouts."""
+    from paper_2203_02530_gb300 import spmv
+    torch = torch_cuda()
+    mats = _mix()
+    count = 4
+    with spmv.Batch(mats) as b:
+        tot = b.offsets()[-1]
+        rng = np.random.default_rng(17)
+        xh = torch.from_numpy(rng.uniform(-1, 1, (count, tot))).pin_memory()
+        s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        y1 = torch.empty(tot, dtype=torch.float64).pin_memory()
+        for lanes in (2, spmv.BATCH_SLICED):
+            spmv.spmv_batch_set_lanes(b.h, -1, lanes)
+            want = []
+            for k in range(count):
+                spmv.spmv_batch_run_host(b.h, xh[k], y1, chunks, s_in, s_c, s_out)
+                want.append(y1.numpy().copy())
+            for _ in range(2):
+                yh = torch.full((count, tot), float("nan"), dtype=torch.float64).pin_memory()
+                spmv.spmv_batch_run_host_many(b.h, count, xh, tot, yh, tot, chunks, s_in, s_c, s_out)
+                for k in range(count):
+                    assert np.array_equal(yh[k].numpy().view(np.uint64), want[k].view(np.uint64)), (lanes, k)
+            ys = torch.full((tot,), float("nan"), dtype=torch.float64).pin_memory()
+            spmv.spmv_batch_run_host_many(b.h, count, xh[1], 0, ys, 0, chunks, s_in, s_c, s_out)
+            assert np.array_equal(ys.numpy().view(np.uint64), want[1].view(np.uint64))
+        spmv.spmv_batch_run_host_many(b.h, 0, None, 0, None, 0, chunks, s_in, s_c, s_out)
+        for args in [(-1, tot, tot, chunks, s_in), (2, tot, 1, chunks, s_in), (2, tot, tot, 0, s_in),
+                     (2, tot, tot, chunks, s_c)]:
+            with pytest.raises(spmv.SpmvError) as e:
+                spmv.spmv_batch_run_host_many(b.h, args[0], xh, args[1], yh, args[2], args[3], args[4], s_c, s_out)
+            assert e.value.code == spmv.EINVAL
+
+
 def test_full_size_batch_mix_256_sliced():
     """The benchmark's batch (256 matrices, n log-uniform in [1e3, 1e6],
     5-point / 7-point / Zipf rows, 4.19 GB) in the sliced layout the tuner
