@@ -496,6 +496,11 @@ def run_ours(args, world, rank, local, fp64=None):
         tuned = dict(tuned, local=best[1], remote=best[2])
         variant, vparam = tuned["local"]
         t_best = best[0]
+        # a CSR variant timed here rebuilt the CSR copy: release it again when
+        # both kept products are sliced
+        if variant in (spmv.VARIANT_SELL, spmv.VARIANT_SELL16) and tuned["remote"][0] == spmv.VARIANT_SELL:
+            part.release_csr()
+        plan_bytes["timed"] = part.query(spmv.Q_DEVICE_BYTES)
     t_search = time.perf_counter() - t_search
     spread = sched[-1][2] / sched[0][2]
     g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE | mode_flag)
@@ -626,7 +631,7 @@ def run_ours(args, world, rank, local, fp64=None):
             link(which)
         link_us[which] = round((time.perf_counter() - t0) / 20 * 1e6, 1)
     err = part.query(spmv.Q_ERROR)
-    dev_bytes = part.query(spmv.Q_DEVICE_BYTES)
+    dev_bytes = part.query(spmv.Q_DEVICE_BYTES)   # with the host paths' device vectors
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -659,8 +664,9 @@ def run_ours(args, world, rank, local, fp64=None):
                    "l2": "inputs larger than L2" if 12 * int(rp[-1]) > 129e6
                          else "L2-resident (replay latency)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "alg_bytes_per_step": alg, "plan_device_bytes": dev_bytes,
-                   "plan_device_bytes_before_csr_release": plan_bytes["tuned"]},
+                   "alg_bytes_per_step": alg, "plan_device_bytes": plan_bytes["timed"],
+                   "plan_device_bytes_before_csr_release": plan_bytes["tuned"],
+                   "plan_device_bytes_with_host_vectors": dev_bytes},
         "percent_hbm": round(100.0 * value / world / peak, 2),
         "roofline": dict({"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                           "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -787,6 +793,7 @@ def run_batched(args, world, rank, local):
     batch_bytes_tuned = b.query(spmv.BQ_DEVICE_BYTES)
     if all(l == spmv.BATCH_SLICED for l in lanes):   # no product reads the CSR copy any more
         spmv.spmv_batch_release_csr(b.h)
+    batch_bytes_timed = b.query(spmv.BQ_DEVICE_BYTES)
     alg = b.query(spmv.BQ_ALG_BYTES)
     batched = lambda: spmv.spmv_batch_run(b.h, x_d, y_b, s)
     separate = lambda: spmv.spmv_batch_run_separate(b.h, -1, x_d, y_s, s)
@@ -876,7 +883,7 @@ def run_batched(args, world, rank, local):
                "sample": "plain CSR products of the batch's matrices in order (%.2f passes over all 256), "
                          "single-threaded C oracle, %.1f s (nproc=%d)" % (byts / alg, secs, os.cpu_count() or 0)}
     launches = spmv.spmv_batch_query(b.h, spmv.BQ_LAUNCHES, -1)
-    dev_bytes = b.query(spmv.BQ_DEVICE_BYTES)
+    dev_bytes = b.query(spmv.BQ_DEVICE_BYTES)   # with the host paths' device vectors
     b.close()
     if rank != 0:
         return None
@@ -901,8 +908,9 @@ def run_batched(args, world, rank, local):
                                "5-point / 7-point / Zipf-row (mean ~10) matrices, one persistent launch",
                    "matrices": len(mats), "total_rows": total, "nnz": nnz,
                    "lanes_histogram": {str(v): lanes.count(v) for v in sorted(set(lanes))},
-                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg, "batch_device_bytes": dev_bytes,
-                   "batch_device_bytes_before_csr_release": batch_bytes_tuned},
+                   "l2": "inputs larger than L2", "alg_bytes_per_step": alg, "batch_device_bytes": batch_bytes_timed,
+                   "batch_device_bytes_before_csr_release": batch_bytes_tuned,
+                   "batch_device_bytes_with_host_vectors": dev_bytes},
         "percent_hbm": round(100.0 * value / world / peak, 2),
         "plain": {"form": "each matrix through the library's single-matrix product (P=1 plan, LOCAL "
                           "variant tuned per matrix), 256 launches captured in one CUDA graph",
@@ -1060,6 +1068,13 @@ def run_serving(args, world, rank, local, fp64=None):
                    "resident_device_bytes": resident},
         "open_loop": out, "open_loop_high": high, "saturation": sat,
         "served_vs_plain_saturation": round(sat["served"]["gbs"] / sat["plain"]["gbs"], 3),
+        "served_vs_plain_note": "the served runtime groups requests only when more blocks wait than there are "
+                                "free stream slots; at %d req/s at most %d requests were in flight against %d "
+                                "slots, so it issued every request alone, through the same launches as the plain "
+                                "form, and the two latencies coincide; the forms differ where requests queue: "
+                                "open_loop_high and saturation" % (int(args.serve_rate),
+                                                                  out["served"]["max_inflight"],
+                                                                  args.serve_streams),
         "results_identical_served_vs_plain": same,
         "latency_us": {"p50": out["served"]["p50_us"], "p99": out["served"]["p99_us"],
                        "plain_p50": out["plain"]["p50_us"], "plain_p99": out["plain"]["p99_us"],
