@@ -515,13 +515,16 @@ def run_ours(args, world, rank, local, fp64=None):
     nnz_l = part.query(spmv.Q_NNZ_LOCAL)
 
     def timed_region():
+        # the clock sampler starts (and settles) before the warm-up, so that
+        # the warm-up steps run right before the timed ones and the GPU is not
+        # left idle between them
+        sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+        sampler.start()
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
-        sampler.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -804,13 +807,13 @@ def run_batched(args, world, rank, local):
     separate()
     s.synchronize()
     identical = bool(torch.equal(y_b, y_s))
+    sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
+    sampler.start()   # before the warm-up: the timed launches follow the warm-up ones directly
     for _ in range(args.warmup):
         batched()
     s.synchronize()
     if dist:
         dist.barrier()
-    sampler = ClockSampler(uuid=str(getattr(props, "uuid", "")) or None)
-    sampler.start()
     torch.cuda.nvtx.range_push("timed_region")
     t_b = benchmark.time_loop(batched, s, args.steps, warmup=0)
     torch.cuda.nvtx.range_pop()
