@@ -30,6 +30,58 @@ def test_library_exports_every_declared_function(libpath):
         assert callable(getattr(spmv, n)), n
 
 
+def _header_params():
+    """Parameter type lists of every function include/spmv.h declares."""
+    import re
+    from paper_2203_02530_gb300 import spmv
+    text = re.sub(r"/\*.*?\*/", "", open(spmv.HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(?:int|int64_t|uint64_t|const char\*)\s+(spmv_\w+)\s*\(([^)]*)\)\s*;", text):
+        params = [q.strip() for q in m.group(2).split(",") if q.strip() and q.strip() != "void"]
+        out[m.group(1)] = [re.sub(r"\s*\b\w+$", "", q) if " " in q or "*" in q else q for q in params]
+    return out
+
+
+def test_binding_argtypes_match_the_header(libpath):
+    """Every declared function is bound with as many arguments as the
+    header gives it, each of the matching ctypes kind (64-bit integers,
+    32-bit integers, pointers), so a binding cannot pass an argument in
+    the wrong slot or width."""
+    import ctypes as C
+    from paper_2203_02530_gb300 import spmv
+    decl = _header_params()
+    assert set(decl) == set(spmv.declared_functions())
+    for name, params in decl.items():
+        argtypes = getattr(spmv.lib, name).argtypes or []
+        assert len(argtypes) == len(params), (name, params, argtypes)
+        for ctype, ptype in zip(argtypes, params):
+            if "*" in ptype or ptype.endswith("_t stream") or ptype.startswith("cudaStream_t"):
+                kind = "ptr"
+            elif ptype.startswith(("int64_t", "uint64_t")):
+                kind = "i64"
+            elif ptype.startswith("int"):
+                kind = "i32"
+            else:
+                kind = "other"
+            want = {"ptr": (C.c_void_p,), "i64": (C.c_int64, C.c_uint64), "i32": (C.c_int,)}.get(kind)
+            if want is None:
+                continue
+            ok = ctype in want or (kind == "ptr" and issubclass(ctype, (C._Pointer, C.c_void_p, C.c_char_p)))
+            assert ok, (name, ptype, ctype)
+
+
+def test_host_buffer_streams_reject_bad_arguments_without_a_gpu(libpath):
+    """The streamed host-buffer entry points check their handle before any
+    CUDA call."""
+    from paper_2203_02530_gb300 import spmv
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_apply_host_many(None, 2, None, 0, None, 0, 0, None, None)
+    assert e.value.code == spmv.EINVAL
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_batch_run_host_many(None, 2, None, 0, None, 0, 4, None, None, None)
+    assert e.value.code == spmv.EINVAL
+
+
 def test_last_error_is_empty_string_initially(libpath):
     from paper_2203_02530_gb300 import spmv
     assert isinstance(spmv.spmv_last_error(), str)
