@@ -901,6 +901,44 @@ def test_apply_host_many_matches_single_products(name, variant):
             assert e.value.code == spmv.EINVAL
 
 
+@pytest.mark.parametrize("gran", [0, 1, 2])
+@pytest.mark.parametrize("P", [1, 3])
+def test_empty_matrix_every_path(gran, P):
+    """n = 0: the plan is empty (no rows, entries or halo), and every variant
+    family, a random schedule issued eagerly, captured and replayed, the
+    host-buffer paths and the index check run without error and write
+    nothing (one-element sentinels around them stay as they were)."""
+    from paper_2203_02530_gb300 import spmv
+    from paper_2203_02530_gb300 import schedules as E
+    torch = torch_cuda()
+    rp = np.zeros(1, np.int64)
+    rng = random.Random(5)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    x_d = synced(torch.zeros(1, dtype=torch.float64, device="cuda"))
+    y_d = synced(torch.full((1,), 7.0, dtype=torch.float64, device="cuda"))
+    with make_part(0, rp, np.zeros(0, np.int32), np.zeros(0), P, gran) as part:
+        for q in (spmv.Q_N, spmv.Q_NNZ, spmv.Q_NNZ_LOCAL, spmv.Q_NNZ_REMOTE, spmv.Q_N_SEND):
+            assert part.query(q) == 0
+        dag = E.Dag(part.n_ops, part.dag())
+        for v in (("sell", 9), ("sell", 2104), ("vector", 2), ("pairs", 2), ("merge", 0), ("tile", 0),
+                  ("warp", 0)):
+            set_variant(part, v)
+            order, smap = _random_schedule(dag, 2, rng)
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_EAGER)
+            g = part.run(order, smap, streams, x_d, y_d, spmv.RUN_CAPTURE)
+            part.run(order, smap, streams, x_d, y_d, spmv.RUN_REPLAY, g)
+            torch.cuda.synchronize()
+            spmv.spmv_graph_destroy(part.h, g)
+            assert y_d.item() == 7.0 and x_d.item() == 0.0, v
+        xh = torch.zeros(1, dtype=torch.float64).pin_memory()
+        yh = torch.full((1,), 7.0, dtype=torch.float64).pin_memory()
+        spmv.spmv_apply_host_pipelined(part.h, xh, yh, streams[0], streams[1])
+        spmv.spmv_apply_host_many(part.h, 3, xh, 0, yh, 0, spmv.HOST_X_BLOCKS, streams[0], streams[1])
+        assert yh.item() == 7.0
+        assert part.query(spmv.Q_ERROR) == 0
+        assert spmv.spmv_part_check(part.h) == 0
+
+
 # ------------------------------------------------------------------ full sizes
 def test_full_size_27pt_150_all_schedules():
     """The 3-D 27-point stencil on 150^3 (n = 3 375 000, 89 915 392 entries),
