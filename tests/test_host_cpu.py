@@ -6,6 +6,7 @@ import json
 import os
 import random
 
+import numpy as np
 import pytest
 
 from oracle import schedules as S
@@ -105,6 +106,45 @@ def test_invalid_arguments_fail_without_a_gpu(libpath):
     with pytest.raises(spmv.SpmvError) as e:
         spmv.spmv_selftest_merge_abort(-5)
     assert e.value.code == spmv.EINVAL
+
+
+@pytest.mark.parametrize("case,code", [
+    ("n_negative", "EINVAL"), ("P_zero", "EINVAL"), ("P_over_limit", "EBOUNDS"), ("granularity", "EINVAL"),
+    ("row_ptr_decreasing", "EINVAL"), ("column_out_of_range", "EINVAL"), ("column_negative", "EINVAL"),
+    ("null_columns", "EINVAL"), ("n_over_int32", "EBOUNDS")])
+def test_plan_rejects_malformed_input_without_a_gpu(libpath, case, code):
+    """spmv_part_create checks the CSR and the partition count on the host,
+    before any CUDA call, and returns the documented status."""
+    from paper_2203_02530_gb300 import spmv
+    n, P, gran = 4, 2, spmv.COARSE
+    rp = np.array([0, 1, 2, 3, 4], np.int64)
+    ci = np.array([0, 1, 2, 3], np.int32)
+    va = np.ones(4)
+    if case == "n_negative":
+        n = -1
+    elif case == "P_zero":
+        P = 0
+    elif case == "P_over_limit":
+        P = 1025
+    elif case == "granularity":
+        gran = 7
+    elif case == "row_ptr_decreasing":
+        rp = np.array([0, 2, 1, 3, 4], np.int64)
+    elif case == "column_out_of_range":
+        ci = np.array([0, 1, 4, 3], np.int32)
+    elif case == "column_negative":
+        ci = np.array([0, -1, 2, 3], np.int32)
+    elif case == "n_over_int32":
+        n = 2**31
+    if case == "null_columns":
+        out = ctypes.c_void_p()
+        st = spmv.lib.spmv_part_create(n, rp.ctypes.data_as(ctypes.c_void_p), None,
+                                       va.ctypes.data_as(ctypes.c_void_p), P, gran, ctypes.byref(out))
+        assert st == getattr(spmv, code) and not out.value
+        return
+    with pytest.raises(spmv.SpmvError) as e:
+        spmv.spmv_part_create(n, rp, ci, va, P, gran)
+    assert e.value.code == getattr(spmv, code), spmv.spmv_last_error()
 
 
 @pytest.mark.parametrize("streams", [1, 2, 3, 4])
